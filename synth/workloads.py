@@ -1,0 +1,63 @@
+"""Named workloads (particle count, mesh, box, cosmology, codes, schedule).
+
+pm64   : 64^3 particles, 128^3 mesh, 100 Mpc/h, EdS, P ~ k^-2, x1v2,
+         10 steps uniform in a from 0.02 to 0.1.
+pm256  : 256^3 particles, 512^3 mesh, 300 Mpc/h, flat LCDM (0.3, h 0.7,
+         sigma8 0.8) with BBKS, x1v1, 50 steps from z = 49 to z = 0.
+pm128o : the 128^3-particle / 256^3-mesh version of pm256 with the same seed
+         (the size the oracle runs for the pm256 comparison).
+pm512  : 512^3 particles, 1024^3 mesh, 600 Mpc/h, same LCDM, code widths varied.
+All use a coarse cell of 4 fine cells and two fine cells per particle spacing.
+"""
+from dataclasses import dataclass
+
+import numpy as np
+
+from .ics import einstein_de_sitter, lcdm_bbks, zeldovich
+
+
+@dataclass(frozen=True)
+class Workload:
+    name: str
+    n_part_side: int
+    n_fine: int
+    box: float
+    cosmo_kind: str
+    x_bytes: int
+    v_bytes: int
+    a_init: float
+    a_final: float
+    n_steps: int
+    seed: int
+    ratio: int = 4
+
+    @property
+    def n_particles(self):
+        return self.n_part_side ** 3
+
+    def cosmology(self):
+        return einstein_de_sitter() if self.cosmo_kind == "eds" else lcdm_bbks()
+
+    def omega(self):
+        c = self.cosmology()
+        return c.omega_m, c.omega_l, c.h
+
+
+WORKLOADS = {
+    "pm64": Workload("pm64", 64, 128, 100.0, "eds", 1, 2, 0.02, 0.1, 10, 1712001),
+    "pm256": Workload("pm256", 256, 512, 300.0, "lcdm", 1, 1, 0.02, 1.0, 50, 1712002),
+    "pm128o": Workload("pm128o", 128, 256, 300.0, "lcdm", 1, 1, 0.02, 1.0, 50, 1712002),
+    "pm512": Workload("pm512", 512, 1024, 600.0, "lcdm", 1, 1, 0.02, 1.0, 50, 1712003),
+}
+
+
+def uniform_schedule(a_init, a_final, n_steps):
+    """Scale factors a_0 .. a_n, uniform in a."""
+    return np.linspace(a_init, a_final, n_steps + 1)
+
+
+def make_ics(w, n_part_side=None, n_fine=None, seed=None):
+    """Zel'dovich ICs for workload `w` (optionally at another resolution)."""
+    nps = n_part_side or w.n_part_side
+    nf = n_fine or (w.n_fine if n_part_side is None else 2 * nps)
+    return zeldovich(nps, nf, w.box, w.cosmology(), w.a_init, seed if seed is not None else w.seed, w.ratio)
