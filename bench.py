@@ -1,0 +1,370 @@
+#!/usr/bin/env python
+"""Throughput of CUBE's compressed-store PM step on one GB300 (or N replicas).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Workload (default pm256): 256^3 particles, 512^3 FP32 mesh, 300 Mpc/h flat
+LCDM (Om 0.3, h 0.7, sigma8 0.8, BBKS), 1-byte positions and velocities,
+Zel'dovich ICs at z = 49 from seeded synthetic Gaussian random fields, steps
+uniform in a towards z = 0.  One "step" = one cube_pm_step (deposit, 3-D FFT
+Poisson solve, force gather + kick + drift, two-pass re-sort) of the whole
+store.  Prints one JSON line (rank 0).
+
+Timing: W untimed steps, then exactly K steps between a barrier +
+synchronize on both sides, CUDA events on the library's stream; max over
+ranks.  Inputs exceed L2 (the 512^3 mesh alone is 537 MB), so no L2 flush.
+N > 1 runs independent replicas (one simulation per GPU, seed + rank); the
+path has no collective.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+PHASE_BYTES_DOC = "algorithmic bytes per launch: see DESIGN.md, section Measurement"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="pm256")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+def schedule(w, n):
+    """First n steps of the workload's uniform-in-a schedule; a finer uniform
+    schedule over the same range if n exceeds its step count."""
+    import numpy as np
+    total = max(w.n_steps, n)
+    return np.linspace(w.a_init, w.a_final, total + 1)[: n + 1]
+
+
+def phase_bytes(w, geo):
+    """Algorithmic HBM bytes per launch of each traced kernel (minimum the
+    operation must move; the model is stated in the design doc)."""
+    N = w.n_fine
+    Np = w.n_particles
+    Nm = N ** 3
+    Ncc = (N // w.ratio) ** 3
+    H3 = (geo["brick"] + 2) ** 3
+    nbr = Ncc // geo["brick"] ** 3
+    half = N * N * (N // 2 + 1) * 8          # half-complex mesh bytes
+    s_x, s_v = 3 * w.x_bytes, 3 * w.v_bytes
+    return {
+        "deposit": 4 * Nm + s_x * Np + 4 * Ncc,
+        "fft_x_r2c": 4 * Nm + half,
+        "fft_y_fwd": 2 * half,
+        "fft_z_green": 2 * half,
+        "fft_y_inv": 2 * half,
+        "fft_x_c2r": half + 4 * Nm,
+        "pass_a": (s_x + 2 * s_v) * Np + 4 * Nm + (4 + 12 + 28) * Ncc + 4 * H3 * nbr,
+        "codec": 0,
+        "scan": 12 * Ncc,
+        "starts": (4 + 4 + 24 + 12) * Ncc + 8 * H3 * nbr,
+        "pass_b": 2 * (s_x + s_v + 4) * Np + (4 + 12 + 12) * Ncc + 4 * H3 * nbr,
+    }
+
+
+def step_bytes(w):
+    """Whole-step algorithmic bytes of the method's minimum model:
+    (3s + 3n_nu) N_p + 32 N_coarse + 32 N_mesh, s = 3 n_chi + 3 n_nu."""
+    s = 3 * w.x_bytes + 3 * w.v_bytes
+    return (3 * s + 3 * w.v_bytes) * w.n_particles + 32 * (w.n_fine // w.ratio) ** 3 + 32 * w.n_fine ** 3
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def measured_traffic(kernel, workload):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, if it
+    was taken on the current kernel source; else None."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", f"dram_traffic_{workload}.txt")
+    if not os.path.exists(path):
+        return None
+    src = os.path.join(ROOT, "paper_1712_06121_gb300", "csrc")
+    h = hashlib.sha256()
+    for f in sorted(os.listdir(src)):
+        with open(os.path.join(src, f), "rb") as fh:
+            h.update(fh.read())
+    cur = h.hexdigest()[:16]
+    rec = {}
+    with open(path) as f:
+        for line in f:
+            if line.startswith("#") or "=" not in line:
+                continue
+            k, v = line.strip().split("=", 1)
+            rec[k.strip()] = v.strip()
+    if rec.get("source_sha") != cur:
+        return None
+    v = rec.get(f"{kernel}.bytes_per_launch")
+    return float(v) if v else None
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled during the timed region."""
+    FIELDS = ("timestamp,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.out = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
+                                         stdout=self.out, stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        time.sleep(0.2)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.out.close()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({n for r in rows for n, v in zip(names, r[5:9]) if v.lower() == "active"})
+        load = [s for s in sm if mx and s >= 0.3 * max(mx)] or sm
+        return {"sm_mhz": statistics.median(load) if load else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def cpu_baseline(w, steps=1):
+    """The FP64 oracle on the host cores: one step of the same workload at
+    128^3 particles / 256^3 mesh (same seed and cosmology)."""
+    import numpy as np
+    import synth
+    from oracle import pm
+    nps = min(128, w.n_part_side)
+    ic = synth.make_ics(w, n_part_side=nps, n_fine=2 * nps)
+    om, ol, _ = w.omega()
+    P = pm.Params(n_fine=2 * nps, n_particles=nps ** 3, x_bytes=w.x_bytes, v_bytes=w.v_bytes, box=w.box,
+                  omega_m=om, omega_l=ol)
+    st = pm.encode(P, ic.pos, ic.vel, ic.ids, w.a_init, ic.sigma_1d)
+    sch = np.linspace(w.a_init, w.a_final, w.n_steps + 1)
+    t0 = time.perf_counter()
+    for i in range(steps):
+        st = pm.step(st, float(sch[i]), float(sch[i + 1]))
+    dt = time.perf_counter() - t0
+    return {"value": nps ** 3 * steps / dt, "unit": "particle-steps/s", "cores": 1, "kind": "oracle",
+            "sample": f"{steps} oracle step(s) of {w.name} at {nps}^3 particles / {2 * nps}^3 mesh "
+                      f"(numpy FP64, single-threaded), {dt:.1f} s"}
+
+
+def run_reference(args, w):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import numpy as np
+    import synth
+    from oracle import pm
+    nps = min(128, w.n_part_side)
+    ic = synth.make_ics(w, n_part_side=nps, n_fine=2 * nps)
+    om, ol, _ = w.omega()
+    P = pm.Params(n_fine=2 * nps, n_particles=nps ** 3, x_bytes=w.x_bytes, v_bytes=w.v_bytes, box=w.box,
+                  omega_m=om, omega_l=ol)
+    st = pm.encode(P, ic.pos, ic.vel, ic.ids, w.a_init, ic.sigma_1d)
+    sch = schedule(w, args.warmup + args.steps)
+    for i in range(args.warmup):
+        st = pm.step(st, float(sch[i]), float(sch[i + 1]))
+    t0 = time.perf_counter()
+    for i in range(args.warmup, args.warmup + args.steps):
+        st = pm.step(st, float(sch[i]), float(sch[i + 1]))
+    dt = time.perf_counter() - t0
+    value = nps ** 3 * args.steps / dt
+    sample = (f"oracle steps of {w.name} at {nps}^3 particles / {2 * nps}^3 mesh "
+              f"(numpy FP64, single-threaded)")
+    print(json.dumps({
+        "impl": "reference", "metric": "particle-steps/s", "value": value, "unit": "particle-steps/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": config_of(w),
+        "cpu_baseline": {"value": value, "unit": "particle-steps/s", "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "particle-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def config_of(w):
+    return {"workload": f"{w.name}: {w.n_part_side}^3 particles, {w.n_fine}^3 FP32 mesh, {w.box:g} Mpc/h, "
+                        f"{'EdS' if w.cosmo_kind == 'eds' else 'LCDM BBKS'}, x{w.x_bytes}v{w.v_bytes}, "
+                        f"R={w.ratio}, steps uniform in a from z={1 / w.a_init - 1:g}",
+            "l2": ("inputs larger than L2 (no flush)" if 4 * w.n_fine ** 3 > 129e6
+                   else "L2-resident small workload"), "parallelism": "replicas"}
+
+
+def main():
+    args = parse()
+    import synth
+    w = synth.WORKLOADS[args.workload]
+    if args.impl == "reference":
+        run_reference(args, w)
+        return
+    import numpy as np
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1712_06121_gb300 as cube
+
+    ic = synth.make_ics(w, seed=w.seed + rank)
+    om, ol, _ = w.omega()
+    prm = cube.make_params(w.n_fine, w.n_particles, ratio=w.ratio, x_bytes=w.x_bytes, v_bytes=w.v_bytes,
+                           box=w.box, omega_m=om, omega_l=ol)
+    stream = torch.cuda.Stream()
+    ctx = cube.cube_create(prm, stream)
+    pos_d = torch.from_numpy(ic.pos).cuda()
+    vel_d = torch.from_numpy(ic.vel).cuda()
+    ids_d = torch.from_numpy(ic.ids.view(np.int32)).cuda()
+    torch.cuda.synchronize()
+    cube.cube_encode(ctx, pos_d, vel_d, ids_d, w.a_init, ic.sigma_1d)
+    sch = schedule(w, args.warmup + args.steps)
+    for i in range(args.warmup):
+        cube.cube_pm_step(ctx, sch[i], sch[i + 1])
+    geo = {"brick": cube.cube_state_view(ctx).brick}
+    launches0 = cube.cube_stats_get(ctx).kernel_launches
+    cube.cube_profile(ctx, args.steps)
+    clocks = ClockSampler(local)
+    if rank == 0:
+        clocks.start()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    for i in range(args.warmup, args.warmup + args.steps):
+        cube.cube_pm_step(ctx, sch[i], sch[i + 1])
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clk = clocks.stop() if rank == 0 else None
+    ms = ev0.elapsed_time(ev1)
+    stats = cube.cube_stats_get(ctx)                      # raises on a latched device error
+    launches = stats.kernel_launches - launches0
+    phase_ms, phase_kernels, nst = cube.cube_profile_read(ctx)
+    cube.cube_profile(ctx, 0)
+    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+    if dist:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    value = world * w.n_particles * args.steps / (ms_max / 1e3)
+
+    # end to end through the C ABI with pinned host buffers: H2D of the
+    # particles, encode, one step, decode, D2H, every iteration
+    e2e = None
+    if not args.no_e2e:
+        pos_h = torch.from_numpy(ic.pos).pin_memory()
+        vel_h = torch.from_numpy(ic.vel).pin_memory()
+        ids_h = torch.from_numpy(ic.ids.view(np.int32)).pin_memory()
+        out_p = torch.empty_like(pos_h).pin_memory()
+        out_v = torch.empty_like(vel_h).pin_memory()
+        out_i = torch.empty_like(ids_h).pin_memory()
+        n_e2e = max(3, min(args.steps, 10))
+        for it in range(2):                                 # warm the staging buffers
+            cube.cube_encode(ctx, pos_h, vel_h, ids_h, w.a_init, ic.sigma_1d)
+            cube.cube_pm_step(ctx, sch[0], sch[1])
+            cube.cube_decode(ctx, out_p, out_v, out_i)
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for it in range(n_e2e):
+            cube.cube_encode(ctx, pos_h, vel_h, ids_h, w.a_init, ic.sigma_1d)
+            cube.cube_pm_step(ctx, sch[0], sch[1])
+            cube.cube_decode(ctx, out_p, out_v, out_i)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        te = torch.tensor([dt], dtype=torch.float64, device="cuda")
+        if dist:
+            dist.all_reduce(te, op=dist.ReduceOp.MAX)
+        nbytes = 28 * w.n_particles
+        e2e = {"value": world * w.n_particles * n_e2e / float(te.item()), "unit": "particle-steps/s",
+               "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
+               "what": "per iteration: pinned host pos/vel/ids -> cube_encode -> cube_pm_step -> "
+                       "cube_decode -> pinned host"}
+    cube.cube_destroy(ctx)
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+
+    peak, peak_kind = peaks()
+    pb = phase_bytes(w, geo)
+    top = max((k for k in phase_ms if phase_kernels.get(k)), key=lambda k: phase_ms[k])
+    per_launch_ms = phase_ms[top] / max(1, nst) / max(1, phase_kernels[top])
+    achieved = pb[top] / (per_launch_ms / 1e3) / 1e9
+    traffic = measured_traffic(top, w.name)
+    step_frac = step_bytes(w) / (peak * 1e9) / (ms_max / args.steps / 1e3)
+    line = {
+        "metric": "particle-steps/s", "value": value, "unit": "particle-steps/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded GRF Zel'dovich ICs)", "config": config_of(w),
+        "roofline": {"bound": "hbm", "kernel": top, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind},
+        "step_roofline": {"bytes": step_bytes(w), "frac": step_frac,
+                          "model": "(3s+3n_nu)N_p + 32 N_coarse + 32 N_mesh"},
+        "phases_ms_per_step": {k: v / max(1, nst) for k, v in phase_ms.items()},
+        "gpu_launches": int(launches),
+        "clocks": clk,
+        "e2e": e2e,
+    }
+    if world == 1 and not args.no_cpu:
+        line["cpu_baseline"] = cpu_baseline(w)
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

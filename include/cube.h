@@ -1,0 +1,245 @@
+/*
+ * cube.h -- C ABI of libcube: CUBE's information-optimised particle-mesh step
+ * (Yu, Pen & Wang, "CUBE: An Information-optimized parallel Cosmological
+ * N-body Algorithm") on one NVIDIA GB300 (sm_103a).
+ *
+ * The library keeps a simulation's particles in the paper's compressed,
+ * cell-ordered store (Sections 2.1-2.2; the checkpoint {rho_c, v_c, chi_d,
+ * nu_d, I_P} of Section 2.3.1): per-coarse-cell counts rho_c, a coarse
+ * velocity field v_c, n_chi-byte fixed-point positions relative to the parent
+ * coarse cell (Eqs. chi, x) and n_nu-byte arctan-mapped velocities relative to
+ * v_c (Eqs. nu, v).  One cube_pm_step() is one kick + drift of the whole store
+ * with a particle-mesh force on the fine mesh, followed by the two-pass
+ * re-sort of Fig. update_xp.  Every step of that path runs in the library's
+ * own CUDA kernels.
+ *
+ * Units: lengths in fine mesh cells, time in 1/H0, momentum
+ * p = a^2 dx/dt in fine cells x H0, particle mass = N_f^3 / N_p so that the
+ * mean density is 1 per fine cell.  Positions are periodic in [0, N_f).
+ *
+ * Conventions for every entry point:
+ *  - Returns CUBE_OK or an error code; nothing throws across the ABI.
+ *    cube_last_error() gives a message for the calling thread's last error.
+ *  - Array arguments may be host or device pointers; the library asks the
+ *    CUDA runtime which one it is.  Host arrays are staged through the
+ *    context's stream and the call synchronises before returning; with
+ *    device arrays the call only enqueues work on the context's stream,
+ *    except where noted.
+ *  - The caller owns every array it passes.  The library owns the context
+ *    and all device memory inside it (state, scratch, FFT mesh).
+ *  - Particle arrays are structure-of-arrays: float pos[3][N] means
+ *    pos[0..N) = x, pos[N..2N) = y, pos[2N..3N) = z.
+ *  - Errors detected on the device (a particle moving more than one coarse
+ *    cell in a step, non-finite input, a count overflow) are latched in a
+ *    device flag and returned by the next call that synchronises:
+ *    cube_decode, cube_power_spectrum, cube_stats, cube_state_view,
+ *    cube_density, cube_potential, cube_debug_drifted.
+ *  - One context is one simulation; contexts are independent.  A context
+ *    must not be used by two threads at once.
+ */
+#ifndef CUBE_H
+#define CUBE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct cube_ctx cube_ctx;
+
+typedef enum {
+    CUBE_OK = 0,
+    CUBE_E_ARG = 1,        /* invalid argument or unsupported configuration     */
+    CUBE_E_NOMEM = 2,      /* a device or pinned-host allocation failed          */
+    CUBE_E_CUDA = 3,       /* a CUDA runtime call failed (incl. no device)       */
+    CUBE_E_STATE = 4,      /* call out of order, e.g. a step before cube_encode  */
+    CUBE_E_MIGRATION = 5,  /* a particle moved more than one coarse cell         */
+    CUBE_E_OVERFLOW = 6,   /* non-finite input or a counter overflow             */
+    CUBE_E_TIMEOUT = 7     /* a bounded device-side wait gave up (reserved)      */
+} cube_status;
+
+enum { CUBE_GRAD_FD4 = 0 };
+
+typedef struct {
+    int32_t n_fine;        /* N_f fine cells per side: 2^a or 3 * 2^a, 16..1024 */
+    int32_t ratio;         /* R fine cells per coarse cell (Section 2.3.1): 1, 2,
+                              4 or 8, with N_c = N_f / R >= 3                    */
+    int64_t n_particles;   /* N_p >= 1 (< 2^31)                                 */
+    int32_t x_bytes;       /* n_chi in {1, 2}: position code width (Eq. chi)    */
+    int32_t v_bytes;       /* n_nu in {1, 2}: velocity code width (Eq. nu)      */
+    int32_t id_bytes;      /* 0 (no particle IDs) or 4 (uint32 I_P)             */
+    int32_t gradient;      /* CUBE_GRAD_FD4: 4th-order finite-difference force  */
+    int32_t deconv_power;  /* the Green's function is divided by W_CIC(k)^p,
+                              p in {0, 1, 2}; 2 compensates deposit and gather  */
+    int32_t brick;         /* side, in coarse cells, of the storage-order brick:
+                              cells are grouped in bricks of brick^3, bricks and
+                              cells inside them are x-fastest.  0 = automatic:
+                              the largest of 4, 2, 1 dividing N_c with >= 3
+                              bricks per side and brick * R <= 16              */
+    double box;            /* box side L in Mpc/h (units of k and P(k) only)   */
+    double omega_m;        /* Omega_m: source term of lap Phi = 1.5 Om (rho-1)  */
+    double omega_l;        /* Omega_Lambda: expansion rate E(a)                 */
+} cube_params;
+
+/* Message describing the calling thread's most recent error ("" if none).
+   The pointer stays valid until the thread's next failing call. */
+const char* cube_last_error(void);
+
+/* Create a context for one simulation (Section 2.3.3, "initialize": mesh and
+   FFT tables, force-kernel factors).  `cuda_stream` is a cudaStream_t (NULL =
+   the legacy default stream) on which every later call enqueues its work; the
+   current CUDA device at this call is the context's device.  Allocates all
+   device memory the context needs: about (2 (3 n_chi + 3 n_nu + n_I) + 16) N_p
+   + 4.2 N_f^3 + 96 N_c^3 bytes.
+   Errors: CUBE_E_ARG (params), CUBE_E_NOMEM, CUBE_E_CUDA. */
+cube_status cube_create(const cube_params* params, void* cuda_stream, cube_ctx** out);
+
+/* Release the context and its device memory (Section 2.3.3, "finalize").
+   Synchronises the context's stream first.  NULL is accepted. */
+cube_status cube_destroy(cube_ctx* ctx);
+
+/* Build the compressed store from float particles: the two passes of the
+   initial-condition generator (Fig. fig.ic; Section 2.3.2).
+   pos   [3][N_p] float, fine-cell coordinates (wrapped periodically);
+   vel   [3][N_p] float, momenta p;
+   id    [N_p] uint32 particle IDs, or NULL for 0..N_p-1 (ignored if id_bytes=0);
+   a     scale factor of both positions and momenta;
+   sigma per-dimension velocity-code scale sigma_Delta/sqrt(3) of Eqs. nu, v
+         (Eq. vdelta gives it at the ICs); <= 0 measures it from the particles
+         as sqrt(<(v - v_c)^2>).  Either way it is snapped to 2^(m/16).
+   Cells are floor(pos / R); within a cell particles keep their input order.
+   v_c is the cell mean of vel in 2^-24 fixed point.
+   Errors: CUBE_E_ARG, CUBE_E_OVERFLOW (non-finite input, latched), CUBE_E_CUDA. */
+cube_status cube_encode(cube_ctx* ctx, const float* pos, const float* vel, const uint32_t* id,
+                        double a, double sigma);
+
+/* One particle-mesh step from a_from to a_to (> a_from), KD splitting of the
+   (DKKD)^n integrator of Section 2.3.3: positions at a_n = a_from, momenta at
+   a_{n-1/2} (at a_n before the first step).  In order: CIC density of the
+   store; r2c FFT; times the Green's function -(3/2) Om / k^2 / W(k)^p / N_f^3;
+   c2r FFT -> Phi; per particle: decode (Eqs. x, v), CIC gather of -grad Phi
+   (FD4), kick by int da/(a^2 E) over [a_{n-1/2}, (a_from + a_to)/2], re-encode
+   the kicked velocity against the same v_c (Fig. update_vp); measure
+   <(v - v_c)^2> and scale it by the momentum growth g(a_to)/g(a_from) for the
+   next store's codec scale (Section 2.2, last paragraph); drift by
+   int da/(a^3 E) over [a_from, a_to]; new-cell counts and v_c*; scan;
+   stable scatter by new cell with Eq. chi / Eq. nu codes against v_c*
+   (Fig. update_xp).  Particles of one new cell stay in old storage order.
+   Enqueue-only.  Errors: CUBE_E_STATE (no store, or a_from != the store's a),
+   CUBE_E_ARG (a_to <= a_from), CUBE_E_CUDA.  Migration beyond one coarse
+   cell is latched (CUBE_E_MIGRATION). */
+cube_status cube_pm_step(cube_ctx* ctx, double a_from, double a_to);
+
+/* Decode the store to float particles in storage order (Eqs. x, v).
+   pos [3][N_p] fine-cell coordinates, vel [3][N_p] momenta at the store's
+   momentum epoch (a_{n-1/2} after a step: see cube_stats.a_p), id [N_p] or
+   NULL.  Synchronises.  Errors: CUBE_E_STATE, latched device errors. */
+cube_status cube_decode(cube_ctx* ctx, float* pos, float* vel, uint32_t* id);
+
+/* Auto power spectrum of the store's particles (Section 3.2, Eq. cps):
+   CIC density on the fine mesh, delta = rho / <rho> - 1, r2c FFT,
+   P = L^3 / N_f^6 |delta_k|^2 / W(k)^2 averaged over shells i = 1..n_bins of
+   the integer wave-vector length (i - 1/2 <= |n| < i + 1/2), r2c modes
+   weighted 2 except on the kx = 0 and kx = N_f/2 planes.
+   k, pk, nmodes: [n_bins] doubles (host or device), mean |k| in h/Mpc, P in
+   (Mpc/h)^3, weighted mode count.  Overwrites the FFT mesh (the next step
+   rebuilds it).  Synchronises.  Errors: CUBE_E_ARG, CUBE_E_STATE. */
+cube_status cube_power_spectrum(cube_ctx* ctx, int32_t n_bins, double* k, double* pk, double* nmodes);
+
+/* ---------------------------------------------------------------- inspection */
+
+typedef struct {
+    int32_t n_coarse;        /* N_c                                            */
+    int32_t brick;           /* storage-order brick side in coarse cells       */
+    int32_t x_bytes, v_bytes, id_bytes;
+    int64_t n_particles;
+    const uint32_t* counts;  /* device [N_c^3], storage order (rho_c)          */
+    const uint32_t* offsets; /* device [N_c^3 + 1], exclusive scan of counts   */
+    const float* vc;         /* device [3][N_c^3], storage order (v_c)         */
+    const void* chi;         /* device [3][N_p] int8 or int16 (chi_d)          */
+    const void* nu;          /* device [3][N_p] int8 or int16 (nu_d)           */
+    const uint32_t* id;      /* device [N_p] (I_P) or NULL                     */
+    double sigma;            /* per-dimension codec scale of the store         */
+    double a;                /* epoch of the positions                         */
+    double a_p;              /* epoch of the momenta                           */
+} cube_state;
+
+/* Device pointers to the current store (valid until the next cube_pm_step,
+   cube_encode or cube_destroy).  Synchronises.  Errors: CUBE_E_STATE. */
+cube_status cube_state_view(cube_ctx* ctx, cube_state* out);
+
+typedef struct {
+    double mass;             /* total particle mass (= N_f^3)                   */
+    double momentum[3];      /* sum of p over particles, from the 2^-24 fixed-
+                                point cell sums of the last store build        */
+    double sigma;            /* current codec scale                            */
+    double a, a_p;           /* epochs of positions and momenta                */
+    int64_t steps;           /* cube_pm_step calls since cube_encode           */
+    int32_t max_migration;   /* largest |cell shift| of the last step (<= 1)   */
+    uint32_t error_flags;    /* bit 0 migration, bit 1 non-finite, bit 2 count  */
+    double last_step_ms;     /* device time of the last step's kernels         */
+    int64_t kernel_launches; /* CUDA kernels this context has launched         */
+} cube_stats;
+
+/* Bookkeeping of Section 2.3.3 (particle count, mass, momentum, codec scale,
+   largest migration).  Synchronises.  Returns the latched device error, if
+   any, after filling `out`. */
+cube_status cube_stats_get(cube_ctx* ctx, cube_stats* out);
+
+/* CIC density of the current store on the fine mesh, rho[z][y][x] floats
+   (N_f^3, mean 1).  Overwrites the FFT mesh.  Synchronises.
+   Errors: CUBE_E_STATE. */
+cube_status cube_density(cube_ctx* ctx, float* rho);
+
+/* Potential Phi[z][y][x] of the current store: density, r2c FFT, Green's
+   function with CIC deconvolution, c2r FFT (the mesh part of cube_pm_step).
+   Synchronises.  Errors: CUBE_E_STATE. */
+cube_status cube_potential(cube_ctx* ctx, float* phi);
+
+/* Keep (1) or stop keeping (0) each step's drifted particles before the
+   re-sort, for cube_debug_drifted.  Costs 28 bytes per particle per step. */
+cube_status cube_keep_drifted(cube_ctx* ctx, int32_t enable);
+
+/* Drifted particles of the last step, in the old storage order: the state
+   that Fig. update_xp's second loop encodes.
+   cell_old [3][N_p] int32 old coarse cell, u_new [3][N_p] float offset in
+   coarse-cell units relative to cell_old after the drift, p [3][N_p] float
+   kicked momenta (as re-encoded against the old v_c), and *sigma_next the
+   codec scale the new store was encoded with.  Synchronises.
+   Errors: CUBE_E_STATE (not kept, or no step yet). */
+cube_status cube_debug_drifted(cube_ctx* ctx, int32_t* cell_old, float* u_new, float* p,
+                               double* sigma_next);
+
+/* ---------------------------------------------------------------- tracing */
+
+/* Kernel phases of one cube_pm_step, in launch order:
+   0 setup (clears the new-store counters; no kernel), 1 deposit (CIC density),
+   2 fft_x_r2c, 3 fft_y_fwd, 4 fft_z_green (z forward, Green's function, z
+   inverse), 5 fft_y_inv, 6 fft_x_c2r, 7 pass_a (decode, force gather, kick,
+   drift, new-cell histogram), 8 codec (next codec scale and tables), 9 scan
+   (offsets of the new counts), 10 starts (per-brick starts, new v_c),
+   11 pass_b (stable scatter and encode).  ("timing or statistics taken in
+   the simulation", Section 2.3.3, "finalize".) */
+#define CUBE_PHASES 12
+
+/* Record CUDA events on the context's stream at every phase boundary of the
+   next `max_steps` cube_pm_step calls (0 stops recording).  Resets the trace.
+   The events are recorded between kernels and do not synchronise.
+   Errors: CUBE_E_ARG. */
+cube_status cube_profile(cube_ctx* ctx, int32_t max_steps);
+
+/* Per-phase device time summed over the traced steps: ms[CUBE_PHASES]
+   (required), kernels[CUBE_PHASES] kernels launched per phase per step (or
+   NULL), *nsteps traced steps (or NULL).  Synchronises. */
+cube_status cube_profile_read(cube_ctx* ctx, double* ms, int32_t* kernels, int32_t* nsteps);
+
+/* Name of a phase ("" outside 0..CUBE_PHASES-1).  Static storage. */
+const char* cube_phase_name(int32_t phase);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CUBE_H */

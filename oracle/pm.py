@@ -124,13 +124,15 @@ def measured_sigma(vel32, vc_of_particle):
     return float(np.sqrt(np.mean(d * d)))
 
 
-def encode(P, pos, vel, ids=None, a=0.02, sigma=0.0):
+def encode(P, pos, vel, ids=None, a=0.02, sigma=0.0, snap=True):
     """Float particles -> compressed store (the second pass of Fig. fig.ic).
 
     pos: [3][N] fine-cell coordinates, vel: [3][N] momenta (FP32 values).
     Cell = floor(pos / R) (periodic), chi by Eq. chi, v_c by cell_mean_velocity,
     nu by Eq. nu relative to v_c.  Order: by cell, then by input index.
     sigma <= 0 means: measure it from the particles, as the per-step update does.
+    The scale is snapped to 2^(m/16) unless `snap` is False (a scale that is
+    already snapped elsewhere is then used as given).
     """
     pos = np.asarray(pos, dtype=np.float32)
     vel = np.asarray(vel, dtype=np.float32)
@@ -145,7 +147,8 @@ def encode(P, pos, vel, ids=None, a=0.02, sigma=0.0):
         key = layout.storage_index(cell3[0], cell3[1], cell3[2], nc, P.brick_side)
         vc = cell_mean_velocity(key, vel, nc ** 3)
         sigma = measured_sigma(vel, vc[:, key])
-    sigma = codec.snap_sigma(sigma)
+    if snap:
+        sigma = codec.snap_sigma(sigma)
     return _build(P, cell3, chi3, vel, ids, sigma, a, a)
 
 

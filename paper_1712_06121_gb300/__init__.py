@@ -1,0 +1,195 @@
+"""Python binding of libcube (include/cube.h): CUBE's compressed-store
+particle-mesh step on one GB300.
+
+Argument marshalling only: every entry point has the C name and forwards to
+the shared library; all work runs in the library's CUDA kernels.  Arrays may
+be numpy arrays (host), torch tensors (host or CUDA), or raw integer
+addresses.  Importing fails loudly if libcube.so has not been built.
+"""
+import ctypes
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libcube.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"libcube.so is not built ({LIB_PATH}); run "
+                      "`python -m paper_1712_06121_gb300.build` (needs nvcc)")
+
+_lib = ctypes.CDLL(LIB_PATH)
+
+CUBE_OK, CUBE_E_ARG, CUBE_E_NOMEM, CUBE_E_CUDA, CUBE_E_STATE, CUBE_E_MIGRATION, \
+    CUBE_E_OVERFLOW, CUBE_E_TIMEOUT = range(8)
+STATUS_NAMES = ["CUBE_OK", "CUBE_E_ARG", "CUBE_E_NOMEM", "CUBE_E_CUDA", "CUBE_E_STATE",
+                "CUBE_E_MIGRATION", "CUBE_E_OVERFLOW", "CUBE_E_TIMEOUT"]
+CUBE_GRAD_FD4 = 0
+
+
+class CubeError(RuntimeError):
+    def __init__(self, status, message):
+        self.status = status
+        name = STATUS_NAMES[status] if 0 <= status < len(STATUS_NAMES) else str(status)
+        super().__init__(f"{name}: {message}")
+
+
+class cube_params(ctypes.Structure):
+    _fields_ = [("n_fine", ctypes.c_int32), ("ratio", ctypes.c_int32), ("n_particles", ctypes.c_int64),
+                ("x_bytes", ctypes.c_int32), ("v_bytes", ctypes.c_int32), ("id_bytes", ctypes.c_int32),
+                ("gradient", ctypes.c_int32), ("deconv_power", ctypes.c_int32), ("brick", ctypes.c_int32),
+                ("box", ctypes.c_double), ("omega_m", ctypes.c_double), ("omega_l", ctypes.c_double)]
+
+
+class cube_state(ctypes.Structure):
+    _fields_ = [("n_coarse", ctypes.c_int32), ("brick", ctypes.c_int32), ("x_bytes", ctypes.c_int32),
+                ("v_bytes", ctypes.c_int32), ("id_bytes", ctypes.c_int32), ("n_particles", ctypes.c_int64),
+                ("counts", ctypes.c_void_p), ("offsets", ctypes.c_void_p), ("vc", ctypes.c_void_p),
+                ("chi", ctypes.c_void_p), ("nu", ctypes.c_void_p), ("id", ctypes.c_void_p),
+                ("sigma", ctypes.c_double), ("a", ctypes.c_double), ("a_p", ctypes.c_double)]
+
+
+class cube_stats(ctypes.Structure):
+    _fields_ = [("mass", ctypes.c_double), ("momentum", ctypes.c_double * 3), ("sigma", ctypes.c_double),
+                ("a", ctypes.c_double), ("a_p", ctypes.c_double), ("steps", ctypes.c_int64),
+                ("max_migration", ctypes.c_int32), ("error_flags", ctypes.c_uint32),
+                ("last_step_ms", ctypes.c_double), ("kernel_launches", ctypes.c_int64)]
+
+CUBE_PHASES = 12
+
+
+_P = ctypes.c_void_p
+_sigs = {
+    "cube_last_error": ([], ctypes.c_char_p),
+    "cube_create": ([ctypes.POINTER(cube_params), _P, ctypes.POINTER(_P)], ctypes.c_int),
+    "cube_destroy": ([_P], ctypes.c_int),
+    "cube_encode": ([_P, _P, _P, _P, ctypes.c_double, ctypes.c_double], ctypes.c_int),
+    "cube_pm_step": ([_P, ctypes.c_double, ctypes.c_double], ctypes.c_int),
+    "cube_decode": ([_P, _P, _P, _P], ctypes.c_int),
+    "cube_power_spectrum": ([_P, ctypes.c_int32, _P, _P, _P], ctypes.c_int),
+    "cube_state_view": ([_P, ctypes.POINTER(cube_state)], ctypes.c_int),
+    "cube_stats_get": ([_P, ctypes.POINTER(cube_stats)], ctypes.c_int),
+    "cube_density": ([_P, _P], ctypes.c_int),
+    "cube_potential": ([_P, _P], ctypes.c_int),
+    "cube_keep_drifted": ([_P, ctypes.c_int32], ctypes.c_int),
+    "cube_debug_drifted": ([_P, _P, _P, _P, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
+    "cube_profile": ([_P, ctypes.c_int32], ctypes.c_int),
+    "cube_profile_read": ([_P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int32),
+                           ctypes.POINTER(ctypes.c_int32)], ctypes.c_int),
+    "cube_phase_name": ([ctypes.c_int32], ctypes.c_char_p),
+}
+for _name, (_args, _res) in _sigs.items():
+    _f = getattr(_lib, _name)
+    _f.argtypes = _args
+    _f.restype = _res
+
+
+def _ptr(a):
+    """Address of a numpy array / torch tensor / int (None -> NULL)."""
+    if a is None:
+        return None
+    if isinstance(a, int):
+        return a
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return a.data_ptr()
+    if hasattr(a, "ctypes"):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return a.ctypes.data
+    raise TypeError(f"cannot take the address of {type(a)}")
+
+
+def _check(status):
+    if status != CUBE_OK:
+        raise CubeError(status, cube_last_error())
+
+
+def cube_last_error():
+    return _lib.cube_last_error().decode()
+
+
+def make_params(n_fine, n_particles, ratio=4, x_bytes=1, v_bytes=1, id_bytes=4, deconv_power=2,
+                brick=0, box=100.0, omega_m=1.0, omega_l=0.0, gradient=CUBE_GRAD_FD4):
+    return cube_params(n_fine, ratio, n_particles, x_bytes, v_bytes, id_bytes, gradient, deconv_power,
+                       brick, box, omega_m, omega_l)
+
+
+def cube_create(params, stream=None):
+    """Returns the context handle.  `stream`: torch.cuda.Stream, raw handle or None."""
+    if stream is not None and hasattr(stream, "cuda_stream"):
+        stream = stream.cuda_stream
+    ctx = _P()
+    _check(_lib.cube_create(ctypes.byref(params), stream, ctypes.byref(ctx)))
+    return ctx
+
+
+def cube_destroy(ctx):
+    _check(_lib.cube_destroy(ctx))
+
+
+def cube_encode(ctx, pos, vel, ids=None, a=0.02, sigma=0.0):
+    _check(_lib.cube_encode(ctx, _ptr(pos), _ptr(vel), _ptr(ids), float(a), float(sigma)))
+
+
+def cube_pm_step(ctx, a_from, a_to):
+    _check(_lib.cube_pm_step(ctx, float(a_from), float(a_to)))
+
+
+def cube_decode(ctx, pos, vel, ids=None):
+    _check(_lib.cube_decode(ctx, _ptr(pos), _ptr(vel), _ptr(ids)))
+
+
+def cube_power_spectrum(ctx, n_bins, k, pk, nmodes):
+    _check(_lib.cube_power_spectrum(ctx, int(n_bins), _ptr(k), _ptr(pk), _ptr(nmodes)))
+
+
+def cube_state_view(ctx):
+    st = cube_state()
+    _check(_lib.cube_state_view(ctx, ctypes.byref(st)))
+    return st
+
+
+def cube_stats_get(ctx):
+    st = cube_stats()
+    _check(_lib.cube_stats_get(ctx, ctypes.byref(st)))
+    return st
+
+
+def cube_density(ctx, rho):
+    _check(_lib.cube_density(ctx, _ptr(rho)))
+
+
+def cube_potential(ctx, phi):
+    _check(_lib.cube_potential(ctx, _ptr(phi)))
+
+
+def cube_keep_drifted(ctx, enable=True):
+    _check(_lib.cube_keep_drifted(ctx, 1 if enable else 0))
+
+
+def cube_debug_drifted(ctx, cell_old, u_new, p):
+    s = ctypes.c_double()
+    _check(_lib.cube_debug_drifted(ctx, _ptr(cell_old), _ptr(u_new), _ptr(p), ctypes.byref(s)))
+    return s.value
+
+
+def cube_profile(ctx, max_steps):
+    _check(_lib.cube_profile(ctx, int(max_steps)))
+
+
+def cube_profile_read(ctx):
+    """Returns ({phase name: ms summed over traced steps}, {name: kernels per step}, steps)."""
+    ms = (ctypes.c_double * CUBE_PHASES)()
+    kn = (ctypes.c_int32 * CUBE_PHASES)()
+    ns = ctypes.c_int32()
+    _check(_lib.cube_profile_read(ctx, ms, kn, ctypes.byref(ns)))
+    names = [cube_phase_name(i) for i in range(CUBE_PHASES)]
+    return dict(zip(names, list(ms))), dict(zip(names, list(kn))), ns.value
+
+
+def cube_phase_name(phase):
+    return _lib.cube_phase_name(int(phase)).decode()
+
+
+__all__ = [n for n in _sigs] + ["make_params", "cube_params", "cube_state", "cube_stats", "CubeError",
+                                "LIB_PATH", "CUBE_GRAD_FD4", "CUBE_PHASES"]

@@ -1,0 +1,723 @@
+// libcube C ABI: context, tables, and the order of kernels of each call.
+// See include/cube.h for the contract of every entry point.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "cube.h"
+#include "kernels.h"
+
+using namespace cube;
+
+namespace {
+
+thread_local std::string g_err;
+
+cube_status fail(cube_status s, const std::string& msg) {
+    g_err = msg;
+    return s;
+}
+
+#define CK(call)                                                                          \
+    do {                                                                                  \
+        cudaError_t e_ = (call);                                                          \
+        if (e_ != cudaSuccess)                                                            \
+            return fail(e_ == cudaErrorMemoryAllocation ? CUBE_E_NOMEM : CUBE_E_CUDA,     \
+                        std::string(#call) + ": " + cudaGetErrorString(e_));              \
+    } while (0)
+
+constexpr double PI = 3.141592653589793;
+
+// ---------------------------------------------------------------- host FP64 cosmology
+// Gauss-Legendre nodes/weights on [-1, 1] by Newton iteration on P_n.
+struct Gauss {
+    std::vector<double> x, w;
+    explicit Gauss(int n) : x(n), w(n) {
+        for (int i = 0; i < n; ++i) {
+            double z = std::cos(PI * (i + 0.75) / (n + 0.5)), pp = 0.0;
+            for (int it = 0; it < 100; ++it) {
+                double p1 = 1.0, p2 = 0.0;
+                for (int j = 1; j <= n; ++j) {
+                    double p3 = p2;
+                    p2 = p1;
+                    p1 = ((2.0 * j - 1.0) * z * p2 - (j - 1.0) * p3) / j;
+                }
+                pp = n * (z * p1 - p2) / (z * z - 1.0);
+                double dz = p1 / pp;
+                z -= dz;
+                if (std::fabs(dz) < 1e-16) break;
+            }
+            x[i] = z;
+            w[i] = 2.0 / ((1.0 - z * z) * pp * pp);
+        }
+    }
+};
+
+const Gauss& gauss64() {
+    static Gauss g(64);
+    return g;
+}
+
+template <class Fn>
+double integrate(Fn f, double a0, double a1, int panels = 16) {
+    const Gauss& g = gauss64();
+    double s = 0.0, h = (a1 - a0) / panels;
+    for (int p = 0; p < panels; ++p) {
+        double lo = a0 + p * h, mid = lo + 0.5 * h;
+        for (size_t i = 0; i < g.x.size(); ++i) s += g.w[i] * f(mid + 0.5 * h * g.x[i]);
+    }
+    return s * 0.5 * h;
+}
+
+struct Cosmo {
+    double om, ol;
+    bool eds() const { return om == 1.0 && ol == 0.0; }
+    double E(double a) const { return std::sqrt(om / (a * a * a) + (1.0 - om - ol) / (a * a) + ol); }
+    // int da / (a^2 E): kick factor
+    double kick(double a0, double a1) const {
+        if (a1 == a0) return 0.0;
+        if (eds()) return 2.0 * (std::sqrt(a1) - std::sqrt(a0));
+        return integrate([&](double a) { return 1.0 / (a * a * E(a)); }, a0, a1);
+    }
+    // int da / (a^3 E): drift factor
+    double drift(double a0, double a1) const {
+        if (a1 == a0) return 0.0;
+        if (eds()) return 2.0 * (1.0 / std::sqrt(a0) - 1.0 / std::sqrt(a1));
+        return integrate([&](double a) { return 1.0 / (a * a * a * E(a)); }, a0, a1);
+    }
+    // Heath integral int_0^a dx / (x E(x))^3, with x = t^2 to smooth the origin
+    double heath(double a) const {
+        return integrate([&](double t) {
+            if (t == 0.0) return 0.0;
+            double x = t * t, xe = x * E(x);
+            return 2.0 * t / (xe * xe * xe);
+        }, 0.0, std::sqrt(a));
+    }
+    double D(double a) const { return 2.5 * om * E(a) * heath(a); }   // unnormalised
+    double f(double a) const {
+        double e = E(a), ok = 1.0 - om - ol;
+        return (-1.5 * om / (a * a * a) - ok / (a * a)) / (e * e) + 1.0 / (a * a * e * e * e * heath(a));
+    }
+    // momentum growth g = a^2 E f D (the normalisation of D cancels in ratios)
+    double g(double a) const {
+        if (eds()) return a * std::sqrt(a);
+        return a * a * E(a) * f(a) * D(a);
+    }
+};
+
+bool is_device_ptr(const void* p) {
+    if (!p) return false;
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+bool is_2a3b(int n) {
+    if (n <= 0) return false;
+    while (n % 2 == 0) n /= 2;
+    while (n % 3 == 0) n /= 3;
+    return n == 1;
+}
+
+double sinc(double x) { return x == 0.0 ? 1.0 : std::sin(x) / x; }
+
+}  // namespace
+
+struct cube_ctx {
+    cube_params P{};
+    Geo g{};
+    Cosmo cosmo{};
+    cudaStream_t st = nullptr;
+    int device = 0;
+    // store, double-buffered: the step reads [cur] and writes [1 - cur]
+    unsigned* counts[2] = {nullptr, nullptr};
+    unsigned* offsets[2] = {nullptr, nullptr};
+    float* vc[2] = {nullptr, nullptr};
+    void* chi[2] = {nullptr, nullptr};
+    void* nu[2] = {nullptr, nullptr};
+    unsigned* id[2] = {nullptr, nullptr};
+    int cur = 0;
+    // velocity codec tables, [cur] describes the current store
+    double* tanv = nullptr;
+    double* tanh_ = nullptr;
+    CodecDev codec[2]{};
+    // per-step scratch
+    long long* vsum = nullptr;
+    unsigned* ghost = nullptr;
+    double* part = nullptr;
+    int npart = 0;
+    unsigned* flags = nullptr;
+    int* maxmig = nullptr;
+    unsigned* scan_tmp = nullptr;
+    long long* mom = nullptr;
+    float* mesh = nullptr;
+    FftPlan fft{};
+    // host-pointer staging (lazily allocated)
+    void* stage = nullptr;
+    size_t stage_bytes = 0;
+    // drifted-state export
+    bool keep = false;
+    int* dbg_cell = nullptr;
+    float* dbg_u = nullptr;
+    float* dbg_p = nullptr;
+    bool dbg_valid = false;
+    // host mirror of the state
+    bool encoded = false;
+    double a = 0.0, a_p = 0.0;
+    int64_t steps = 0;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    bool timed = false;
+    int64_t launches = 0;               // kernels launched by this context
+    // per-kernel tracing: CUBE_PHASES + 1 boundary events per traced step
+    int prof_max = 0, prof_steps = 0;
+    std::vector<cudaEvent_t> prof_ev;
+    std::vector<void*> allocs;
+
+    StoreDev store(int k) const { return StoreDev{counts[k], offsets[k], vc[k], chi[k], nu[k], id[k]}; }
+};
+
+namespace {
+
+template <class T>
+cudaError_t dalloc(cube_ctx* c, T** p, size_t bytes) {
+    cudaError_t e = cudaMalloc((void**)p, bytes ? bytes : 16);
+    if (e == cudaSuccess) c->allocs.push_back((void*)*p);
+    return e;
+}
+
+cube_status stage_bytes(cube_ctx* c, size_t bytes, void** out) {
+    if (c->stage_bytes < bytes) {
+        if (c->stage) cudaFree(c->stage);
+        c->stage = nullptr;
+        c->stage_bytes = 0;
+        CK(cudaMalloc(&c->stage, bytes));
+        c->stage_bytes = bytes;
+    }
+    *out = c->stage;
+    return CUBE_OK;
+}
+
+cube_status latched(cube_ctx* c) {
+    unsigned f = 0;
+    CK(cudaMemcpyAsync(&f, c->flags, sizeof(unsigned), cudaMemcpyDeviceToHost, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    if (f & ERR_MIGRATION) return fail(CUBE_E_MIGRATION, "a particle moved more than one coarse cell in a step");
+    if (f & ERR_NONFINITE) return fail(CUBE_E_OVERFLOW, "non-finite particle position or velocity");
+    if (f & ERR_COUNT) return fail(CUBE_E_OVERFLOW, "cell counts inconsistent with the particle total");
+    return CUBE_OK;
+}
+
+cube_status check_params(const cube_params* p, int* brick) {
+    if (!p) return fail(CUBE_E_ARG, "params is NULL");
+    const int N = p->n_fine;
+    if (N < 16 || N > 1024 || !is_2a3b(N) || !fft_size_supported(N))
+        return fail(CUBE_E_ARG, "n_fine must be 2^a or 3 * 2^a in [16, 1024]");
+    const int R = p->ratio;
+    if (!(R == 1 || R == 2 || R == 4 || R == 8) || N % R) return fail(CUBE_E_ARG, "ratio must be 1, 2, 4 or 8 and divide n_fine");
+    const int Nc = N / R;
+    if (Nc < 3) return fail(CUBE_E_ARG, "need at least 3 coarse cells per side");
+    if (p->n_particles < 1 || p->n_particles >= (1LL << 31)) return fail(CUBE_E_ARG, "n_particles out of range");
+    if ((p->x_bytes != 1 && p->x_bytes != 2) || (p->v_bytes != 1 && p->v_bytes != 2))
+        return fail(CUBE_E_ARG, "x_bytes and v_bytes must be 1 or 2");
+    if (p->id_bytes != 0 && p->id_bytes != 4) return fail(CUBE_E_ARG, "id_bytes must be 0 or 4");
+    if (p->gradient != CUBE_GRAD_FD4) return fail(CUBE_E_ARG, "only CUBE_GRAD_FD4 is implemented");
+    if (p->deconv_power < 0 || p->deconv_power > 2) return fail(CUBE_E_ARG, "deconv_power must be 0, 1 or 2");
+    if (!(p->box > 0.0) || !(p->omega_m > 0.0) || !(p->omega_l >= 0.0)) return fail(CUBE_E_ARG, "box, omega_m must be > 0");
+    int B = p->brick;
+    if (B == 0) {
+        const int cand[3] = {4, 2, 1};
+        for (int b : cand)
+            if (Nc % b == 0 && Nc / b >= 3 && b * R <= 16) { B = b; break; }
+        if (B == 0) return fail(CUBE_E_ARG, "no valid brick size");
+    }
+    if (B < 1 || Nc % B || Nc / B < 3 || B * R > 16)
+        return fail(CUBE_E_ARG, "brick must divide N_c with >= 3 bricks per side and brick * ratio <= 16");
+    *brick = B;
+    return CUBE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* cube_last_error(void) { return g_err.c_str(); }
+
+cube_status cube_destroy(cube_ctx* c) {
+    if (!c) return CUBE_OK;
+    cudaStreamSynchronize(c->st);
+    for (void* p : c->allocs) cudaFree(p);
+    if (c->stage) cudaFree(c->stage);
+    if (c->dbg_cell) cudaFree(c->dbg_cell);
+    if (c->dbg_u) cudaFree(c->dbg_u);
+    if (c->dbg_p) cudaFree(c->dbg_p);
+    for (cudaEvent_t e : c->prof_ev) cudaEventDestroy(e);
+    if (c->ev0) cudaEventDestroy(c->ev0);
+    if (c->ev1) cudaEventDestroy(c->ev1);
+    delete c;
+    return CUBE_OK;
+}
+
+cube_status cube_create(const cube_params* params, void* cuda_stream, cube_ctx** out) {
+    if (!out) return fail(CUBE_E_ARG, "out is NULL");
+    *out = nullptr;
+    int B = 0;
+    cube_status s = check_params(params, &B);
+    if (s != CUBE_OK) return s;
+    int ndev = 0;
+    CK(cudaGetDeviceCount(&ndev));
+    cube_ctx* c = new cube_ctx();
+    c->P = *params;
+    c->st = (cudaStream_t)cuda_stream;
+    c->cosmo = Cosmo{params->omega_m, params->omega_l};
+    cudaGetDevice(&c->device);
+    Geo& g = c->g;
+    g.N = params->n_fine;
+    g.R = params->ratio;
+    g.r = g.R == 1 ? 0 : g.R == 2 ? 1 : g.R == 4 ? 2 : 3;
+    g.Nc = g.N / g.R;
+    g.B = B;
+    g.nb = g.Nc / B;
+    g.Bh = B + 2;
+    g.nchi = params->x_bytes;
+    g.nnu = params->v_bytes;
+    g.sbits = 8 * g.nchi + 1 - g.r;
+    g.F = B * g.R;
+    g.S = g.N + 4;
+    g.Ncc = g.Nc * g.Nc * g.Nc;
+    g.nbricks = g.nb * g.nb * g.nb;
+    g.Np = params->n_particles;
+    g.nulim = (1 << (8 * g.nnu - 1)) - 1;
+
+    auto bad = [&](cudaError_t e, const char* what) -> cube_status {
+        cube_destroy(c);
+        return fail(e == cudaErrorMemoryAllocation ? CUBE_E_NOMEM : CUBE_E_CUDA,
+                    std::string(what) + ": " + cudaGetErrorString(e));
+    };
+#define AL(ptr, bytes) do { cudaError_t e_ = dalloc(c, &(ptr), (bytes)); if (e_ != cudaSuccess) return bad(e_, #ptr); } while (0)
+    const size_t Np = (size_t)g.Np, Ncc = (size_t)g.Ncc;
+    const int H3 = g.Bh * g.Bh * g.Bh;
+    for (int k = 0; k < 2; ++k) {
+        AL(c->counts[k], Ncc * 4);
+        AL(c->offsets[k], (Ncc + 1) * 4);
+        AL(c->vc[k], 3 * Ncc * 4);
+        AL(c->chi[k], 3 * Np * g.nchi);
+        AL(c->nu[k], 3 * Np * g.nnu);
+        if (params->id_bytes) AL(c->id[k], Np * 4);
+        AL(c->codec[k].dec, (size_t)(2 * g.nulim + 1) * 4);
+        AL(c->codec[k].thr, (size_t)(g.nulim + 2) * 4);
+        AL(c->codec[k].est, 2 * 4);
+        AL(c->codec[k].sigma, 8);
+    }
+    AL(c->tanv, (size_t)(g.nulim + 1) * 8);
+    AL(c->tanh_, (size_t)(g.nulim + 2) * 8);
+    AL(c->vsum, 3 * Ncc * 8);
+    AL(c->ghost, (size_t)g.nbricks * H3 * 4);
+    c->npart = std::max(g.nbricks, 1024);
+    AL(c->part, (size_t)c->npart * 8);
+    AL(c->flags, 4);
+    AL(c->maxmig, 4);
+    AL(c->scan_tmp, (size_t)scan_tmp_words(g.Ncc + 1) * 4 + 64);
+    AL(c->mom, 3 * 8);
+    AL(c->mesh, (size_t)g.N * g.N * g.S * 4);
+    FftPlan& f = c->fft;
+    f.N = g.N;
+    AL(f.tw, (size_t)g.N * 8);
+    AL(f.k2, (size_t)g.N * 4);
+    AL(f.wdec, (size_t)g.N * 4);
+    AL(f.wpk, (size_t)g.N * 8);
+#undef AL
+    // host tables (FP64 libm), uploaded once
+    {
+        std::vector<float2> tw(g.N);
+        std::vector<float> k2(g.N), wd(g.N);
+        std::vector<double> wpk(g.N);
+        for (int i = 0; i < g.N; ++i) {
+            double ang = 2.0 * PI * i / g.N;
+            tw[i] = make_float2((float)std::cos(ang), (float)(-std::sin(ang)));
+            int fr = i <= g.N / 2 ? i : i - g.N;
+            double kk = 2.0 * PI * fr / g.N;
+            k2[i] = (float)(kk * kk);
+            double sn = sinc(PI * fr / g.N);
+            wd[i] = (float)std::pow(sn, -2.0 * params->deconv_power);
+            wpk[i] = std::pow(sn, -4.0);
+        }
+        const int M = 2 * g.nulim + 1;
+        std::vector<double> tv(g.nulim + 1), th(g.nulim + 2);
+        for (int k = 0; k <= g.nulim; ++k) tv[k] = std::tan(PI * k / M);
+        for (int k = 0; k <= g.nulim + 1; ++k) th[k] = std::tan(PI * (k - 0.5) / M);
+        cudaError_t e = cudaSuccess;
+        if (e == cudaSuccess) e = cudaMemcpy(f.tw, tw.data(), g.N * 8, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(f.k2, k2.data(), g.N * 4, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(f.wdec, wd.data(), g.N * 4, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(f.wpk, wpk.data(), g.N * 8, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(c->tanv, tv.data(), tv.size() * 8, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(c->tanh_, th.data(), th.size() * 8, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemset(c->flags, 0, 4);
+        if (e == cudaSuccess) e = cudaEventCreate(&c->ev0);
+        if (e == cudaSuccess) e = cudaEventCreate(&c->ev1);
+        if (e != cudaSuccess) return bad(e, "table upload");
+    }
+    *out = c;
+    return CUBE_OK;
+}
+
+cube_status cube_encode(cube_ctx* c, const float* pos, const float* vel, const uint32_t* id, double a, double sigma) {
+    if (!c) return fail(CUBE_E_ARG, "ctx is NULL");
+    if (!pos || !vel) return fail(CUBE_E_ARG, "pos and vel are required");
+    if (!(a > 0.0)) return fail(CUBE_E_ARG, "a must be > 0");
+    const Geo& g = c->g;
+    const size_t Np = (size_t)g.Np;
+    const bool hpos = !is_device_ptr(pos), hvel = !is_device_ptr(vel), hid = id && !is_device_ptr(id);
+    // scratch: keys, perm, radix workspace, host staging
+    const int key_bits = std::max(1, (int)std::ceil(std::log2((double)g.Ncc)));
+    size_t words = (size_t)(2 * Np) + (size_t)radix_tmp_words(g.Np);
+    size_t stage_off = words * 4;
+    size_t need = stage_off + (hpos ? 12 * Np : 0) + (hvel ? 12 * Np : 0) + (hid ? 4 * Np : 0);
+    void* scratch = nullptr;
+    cube_status s = stage_bytes(c, need, &scratch);
+    if (s != CUBE_OK) return s;
+    unsigned* keys = (unsigned*)scratch;
+    unsigned* perm = keys + Np;
+    unsigned* rtmp = perm + Np;
+    char* sp = (char*)scratch + stage_off;
+    const float* dpos = pos;
+    const float* dvel = vel;
+    const unsigned* did = id;
+    if (hpos) { CK(cudaMemcpyAsync(sp, pos, 12 * Np, cudaMemcpyHostToDevice, c->st)); dpos = (const float*)sp; sp += 12 * Np; }
+    if (hvel) { CK(cudaMemcpyAsync(sp, vel, 12 * Np, cudaMemcpyHostToDevice, c->st)); dvel = (const float*)sp; sp += 12 * Np; }
+    if (hid) { CK(cudaMemcpyAsync(sp, id, 4 * Np, cudaMemcpyHostToDevice, c->st)); did = (const unsigned*)sp; }
+    const int k = c->cur;
+    CK(cudaMemsetAsync(c->flags, 0, 4, c->st));
+    CK(cudaMemsetAsync(c->counts[k], 0, (size_t)g.Ncc * 4, c->st));
+    CK(cudaMemsetAsync(c->vsum, 0, (size_t)g.Ncc * 24, c->st));
+    launch_encode_keys(g, dpos, dvel, keys, perm, c->counts[k], c->vsum, c->flags, c->st);
+    exclusive_scan(c->counts[k], c->offsets[k], g.Ncc, c->scan_tmp, c->st);
+    launch_vc_finalize(g, c->counts[k], c->vsum, c->vc[k], c->st);
+    if (sigma > 0.0) {
+        launch_sigma_finalize(c->part, 0, 1.0, 1.0, sigma, c->codec[k].sigma, c->st);
+    } else {
+        launch_encode_sigma(g, dvel, keys, c->vc[k], c->part, c->st);
+        launch_sigma_finalize(c->part, encode_sigma_blocks(g), 3.0 * (double)g.Np, 1.0, 0.0, c->codec[k].sigma, c->st);
+    }
+    launch_codec_tables(g.nulim, c->tanv, c->tanh_, c->codec[k], c->st);
+    radix_sort_pairs(keys, perm, g.Np, key_bits, rtmp, c->st);
+    launch_encode_scatter(g, dpos, dvel, did, keys, perm, c->vc[k], c->codec[k], c->store(k), c->st);
+    c->launches += 1 + 4 + 1 + (sigma > 0.0 ? 1 : 2) + 1 + (int64_t)((key_bits + 7) / 8) * 6 + 1;
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(c->st));
+    c->encoded = true;
+    c->a = a;
+    c->a_p = a;
+    c->steps = 0;
+    c->dbg_valid = false;
+    c->timed = false;
+    return CUBE_OK;
+}
+
+// kernels launched per phase of a step (see cube_phase_name)
+const int kPhaseKernels[CUBE_PHASES] = {0, 1, 1, 1, 1, 1, 1, 1, 2, 4, 1, 1};
+const char* kPhaseNames[CUBE_PHASES] = {"setup", "deposit", "fft_x_r2c", "fft_y_fwd", "fft_z_green", "fft_y_inv",
+                                        "fft_x_c2r", "pass_a", "codec", "scan", "starts", "pass_b"};
+
+static void mark(cube_ctx* c, int boundary) {
+    if (c->prof_steps < c->prof_max) cudaEventRecord(c->prof_ev[(size_t)c->prof_steps * (CUBE_PHASES + 1) + boundary], c->st);
+}
+
+static double particle_mass(const Geo& g) { return std::pow((double)g.N, 3) / (double)g.Np; }
+
+static void deposit(cube_ctx* c) {
+    const Geo& g = c->g;
+    launch_deposit(g, c->store(c->cur), c->mesh, particle_mass(g) * std::ldexp(1.0, -3 * g.sbits), c->st);
+    c->launches += 1;
+}
+
+// density -> Phi on the mesh; boundaries 1..6 of the step's trace
+static void mesh_potential(cube_ctx* c) {
+    const Geo& g = c->g;
+    deposit(c);
+    mark(c, 2);
+    fft_x_r2c(c->fft, c->mesh, g.S, c->st);
+    mark(c, 3);
+    fft_y(c->fft, c->mesh, g.S, false, c->st);
+    mark(c, 4);
+    const float g0 = (float)(-1.5 * c->P.omega_m / std::pow((double)g.N, 3));
+    fft_z(c->fft, c->mesh, g.S, g0, true, c->st);
+    mark(c, 5);
+    fft_y(c->fft, c->mesh, g.S, true, c->st);
+    mark(c, 6);
+    fft_x_c2r(c->fft, c->mesh, g.S, c->st);
+    mark(c, 7);
+    c->launches += 5;
+}
+
+cube_status cube_pm_step(cube_ctx* c, double a_from, double a_to) {
+    if (!c) return fail(CUBE_E_ARG, "ctx is NULL");
+    if (!c->encoded) return fail(CUBE_E_STATE, "cube_pm_step before cube_encode");
+    if (std::fabs(a_from - c->a) > 1e-12 * std::max(1.0, std::fabs(a_from)))
+        return fail(CUBE_E_STATE, "a_from differs from the store's epoch");
+    if (!(a_to > a_from)) return fail(CUBE_E_ARG, "a_to must exceed a_from");
+    const Geo& g = c->g;
+    const double a_mid = 0.5 * (a_from + a_to);
+    const float kick = (float)c->cosmo.kick(c->a_p, a_mid);
+    const float dc = (float)(c->cosmo.drift(a_from, a_to) / g.R);
+    const double ratio = c->cosmo.g(a_to) / c->cosmo.g(a_from);
+    const int k = c->cur, kn = 1 - k;
+    if (c->keep) {
+        if (!c->dbg_cell) {
+            CK(cudaMalloc((void**)&c->dbg_cell, 12 * (size_t)g.Np));
+            CK(cudaMalloc((void**)&c->dbg_u, 12 * (size_t)g.Np));
+            CK(cudaMalloc((void**)&c->dbg_p, 12 * (size_t)g.Np));
+        }
+    }
+    CK(cudaEventRecord(c->ev0, c->st));
+    mark(c, 0);
+    CK(cudaMemsetAsync(c->counts[kn], 0, (size_t)g.Ncc * 4, c->st));
+    CK(cudaMemsetAsync(c->vsum, 0, (size_t)g.Ncc * 24, c->st));
+    CK(cudaMemsetAsync(c->maxmig, 0, 4, c->st));
+    mark(c, 1);
+    mesh_potential(c);
+    StepScratch w{c->counts[kn], c->vsum, c->ghost, c->part, c->flags, c->maxmig};
+    DriftDebug dbg{c->keep ? c->dbg_cell : nullptr, c->dbg_u, c->dbg_p};
+    launch_passA(g, c->store(k), c->mesh, c->codec[k], kick, dc, w, dbg, c->st);
+    mark(c, 8);
+    launch_sigma_finalize(c->part, g.nbricks, 3.0 * (double)g.Np, ratio, 0.0, c->codec[kn].sigma, c->st);
+    launch_codec_tables(g.nulim, c->tanv, c->tanh_, c->codec[kn], c->st);
+    mark(c, 9);
+    exclusive_scan(c->counts[kn], c->offsets[kn], g.Ncc, c->scan_tmp, c->st);
+    mark(c, 10);
+    launch_starts(g, w, c->offsets[kn], c->vc[kn], c->st);
+    mark(c, 11);
+    launch_passB(g, c->store(k), c->store(kn), c->codec[k], c->codec[kn], dc, w, c->st);
+    mark(c, 12);
+    CK(cudaEventRecord(c->ev1, c->st));
+    c->launches += 1 + 2 + 4 + 1 + 1;
+    if (c->prof_steps < c->prof_max) c->prof_steps += 1;
+    CK(cudaGetLastError());
+    c->cur = kn;
+    c->a = a_to;
+    c->a_p = a_mid;
+    c->steps += 1;
+    c->dbg_valid = c->keep;
+    c->timed = true;
+    return CUBE_OK;
+}
+
+static cube_status to_user(cube_ctx* c, void* dst, const void* src, size_t bytes, bool host) {
+    CK(cudaMemcpyAsync(dst, src, bytes, host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, c->st));
+    return CUBE_OK;
+}
+
+cube_status cube_decode(cube_ctx* c, float* pos, float* vel, uint32_t* id) {
+    if (!c) return fail(CUBE_E_ARG, "ctx is NULL");
+    if (!c->encoded) return fail(CUBE_E_STATE, "no store: call cube_encode first");
+    if (!pos || !vel) return fail(CUBE_E_ARG, "pos and vel are required");
+    const Geo& g = c->g;
+    const size_t Np = (size_t)g.Np;
+    const bool hpos = !is_device_ptr(pos), hvel = !is_device_ptr(vel), hid = id && !is_device_ptr(id);
+    size_t need = (hpos ? 12 * Np : 0) + (hvel ? 12 * Np : 0) + (hid ? 4 * Np : 0);
+    char* sp = nullptr;
+    if (need) {
+        void* p = nullptr;
+        cube_status s = stage_bytes(c, need, &p);
+        if (s != CUBE_OK) return s;
+        sp = (char*)p;
+    }
+    float* dpos = hpos ? (float*)sp : pos;
+    float* dvel = hvel ? (float*)(sp + (hpos ? 12 * Np : 0)) : vel;
+    unsigned* did = id ? (hid ? (unsigned*)(sp + (hpos ? 12 * Np : 0) + (hvel ? 12 * Np : 0)) : id) : nullptr;
+    launch_decode(g, c->store(c->cur), c->codec[c->cur].dec, dpos, dvel, did, c->st);
+    c->launches += 1;
+    CK(cudaGetLastError());
+    cube_status s;
+    if (hpos && (s = to_user(c, pos, dpos, 12 * Np, true)) != CUBE_OK) return s;
+    if (hvel && (s = to_user(c, vel, dvel, 12 * Np, true)) != CUBE_OK) return s;
+    if (hid && (s = to_user(c, id, did, 4 * Np, true)) != CUBE_OK) return s;
+    return latched(c);
+}
+
+cube_status cube_power_spectrum(cube_ctx* c, int32_t n_bins, double* k, double* pk, double* nmodes) {
+    if (!c) return fail(CUBE_E_ARG, "ctx is NULL");
+    if (!c->encoded) return fail(CUBE_E_STATE, "no store: call cube_encode first");
+    if (n_bins < 1 || n_bins > 2048 || !k || !pk || !nmodes) return fail(CUBE_E_ARG, "n_bins in [1, 2048] and outputs required");
+    const Geo& g = c->g;
+    deposit(c);
+    fft_x_r2c(c->fft, c->mesh, g.S, c->st);
+    fft_y(c->fft, c->mesh, g.S, false, c->st);
+    fft_z(c->fft, c->mesh, g.S, 0.0f, false, c->st);
+    c->launches += 5;
+    const int nb = pk_blocks(g.N);
+    double* part = nullptr;
+    double* outk = nullptr;
+    size_t pbytes = (size_t)nb * 3 * n_bins * 8;
+    CK(cudaMallocAsync((void**)&part, pbytes + 3 * (size_t)n_bins * 8, c->st));
+    outk = part + (size_t)nb * 3 * n_bins;
+    const double L = c->P.box;
+    const double pfac = L * L * L / std::pow((double)g.N, 6);
+    launch_pk_bin(c->fft, c->mesh, g.S, n_bins, pfac, 2.0 * PI / L, part, c->st);
+    launch_pk_reduce(part, nb, n_bins, outk, outk + n_bins, outk + 2 * n_bins, c->st);
+    c->launches += 2;
+    cube_status s = CUBE_OK;
+    const bool hk = !is_device_ptr(k), hp = !is_device_ptr(pk), hn = !is_device_ptr(nmodes);
+    if ((s = to_user(c, k, outk, n_bins * 8, hk)) == CUBE_OK && (s = to_user(c, pk, outk + n_bins, n_bins * 8, hp)) == CUBE_OK)
+        s = to_user(c, nmodes, outk + 2 * n_bins, n_bins * 8, hn);
+    cudaFreeAsync(part, c->st);
+    CK(cudaGetLastError());
+    if (s != CUBE_OK) return s;
+    return latched(c);
+}
+
+cube_status cube_state_view(cube_ctx* c, cube_state* out) {
+    if (!c || !out) return fail(CUBE_E_ARG, "NULL argument");
+    if (!c->encoded) return fail(CUBE_E_STATE, "no store: call cube_encode first");
+    const Geo& g = c->g;
+    const int k = c->cur;
+    out->n_coarse = g.Nc;
+    out->brick = g.B;
+    out->x_bytes = g.nchi;
+    out->v_bytes = g.nnu;
+    out->id_bytes = c->P.id_bytes;
+    out->n_particles = g.Np;
+    out->counts = c->counts[k];
+    out->offsets = c->offsets[k];
+    out->vc = c->vc[k];
+    out->chi = c->chi[k];
+    out->nu = c->nu[k];
+    out->id = c->id[k];
+    CK(cudaMemcpyAsync(&out->sigma, c->codec[k].sigma, 8, cudaMemcpyDeviceToHost, c->st));
+    out->a = c->a;
+    out->a_p = c->a_p;
+    return latched(c);
+}
+
+cube_status cube_stats_get(cube_ctx* c, cube_stats* out) {
+    if (!c || !out) return fail(CUBE_E_ARG, "NULL argument");
+    if (!c->encoded) return fail(CUBE_E_STATE, "no store: call cube_encode first");
+    const Geo& g = c->g;
+    launch_momentum(g, c->vsum, c->mom, c->st);
+    long long m[3] = {0, 0, 0};
+    unsigned f = 0;
+    int mig = 0;
+    CK(cudaMemcpyAsync(m, c->mom, sizeof(m), cudaMemcpyDeviceToHost, c->st));
+    CK(cudaMemcpyAsync(&out->sigma, c->codec[c->cur].sigma, 8, cudaMemcpyDeviceToHost, c->st));
+    CK(cudaMemcpyAsync(&f, c->flags, 4, cudaMemcpyDeviceToHost, c->st));
+    CK(cudaMemcpyAsync(&mig, c->maxmig, 4, cudaMemcpyDeviceToHost, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    out->mass = std::pow((double)g.N, 3);
+    for (int d = 0; d < 3; ++d) out->momentum[d] = (double)m[d] * std::ldexp(1.0, -24);
+    out->a = c->a;
+    out->a_p = c->a_p;
+    out->steps = c->steps;
+    out->max_migration = c->steps ? mig : 0;
+    out->error_flags = f;
+    float ms = 0.0f;
+    if (c->timed) cudaEventElapsedTime(&ms, c->ev0, c->ev1);
+    out->last_step_ms = ms;
+    out->kernel_launches = c->launches;
+    return latched(c);
+}
+
+static cube_status mesh_out(cube_ctx* c, float* dst) {
+    const Geo& g = c->g;
+    const size_t bytes = (size_t)g.N * g.N * g.N * 4;
+    const bool host = !is_device_ptr(dst);
+    float* d = dst;
+    if (host) {
+        void* p = nullptr;
+        cube_status s = stage_bytes(c, bytes, &p);
+        if (s != CUBE_OK) return s;
+        d = (float*)p;
+    }
+    launch_unpad(c->mesh, g.N, g.S, d, c->st);
+    c->launches += 1;
+    if (host) CK(cudaMemcpyAsync(dst, d, bytes, cudaMemcpyDeviceToHost, c->st));
+    CK(cudaGetLastError());
+    return latched(c);
+}
+
+cube_status cube_density(cube_ctx* c, float* rho) {
+    if (!c || !rho) return fail(CUBE_E_ARG, "NULL argument");
+    if (!c->encoded) return fail(CUBE_E_STATE, "no store: call cube_encode first");
+    deposit(c);
+    return mesh_out(c, rho);
+}
+
+cube_status cube_potential(cube_ctx* c, float* phi) {
+    if (!c || !phi) return fail(CUBE_E_ARG, "NULL argument");
+    if (!c->encoded) return fail(CUBE_E_STATE, "no store: call cube_encode first");
+    const int saved = c->prof_max;
+    c->prof_max = 0;                    // not a step: keep it out of the trace
+    mesh_potential(c);
+    c->prof_max = saved;
+    return mesh_out(c, phi);
+}
+
+cube_status cube_keep_drifted(cube_ctx* c, int32_t enable) {
+    if (!c) return fail(CUBE_E_ARG, "ctx is NULL");
+    c->keep = enable != 0;
+    if (!c->keep) {
+        CK(cudaStreamSynchronize(c->st));
+        cudaFree(c->dbg_cell);
+        cudaFree(c->dbg_u);
+        cudaFree(c->dbg_p);
+        c->dbg_cell = nullptr;
+        c->dbg_u = c->dbg_p = nullptr;
+        c->dbg_valid = false;
+    }
+    return CUBE_OK;
+}
+
+cube_status cube_debug_drifted(cube_ctx* c, int32_t* cell_old, float* u_new, float* p, double* sigma_next) {
+    if (!c || !cell_old || !u_new || !p) return fail(CUBE_E_ARG, "NULL argument");
+    if (!c->dbg_valid) return fail(CUBE_E_STATE, "no drifted state kept: enable cube_keep_drifted before the step");
+    const size_t b = 12 * (size_t)c->g.Np;
+    cube_status s;
+    if ((s = to_user(c, cell_old, c->dbg_cell, b, !is_device_ptr(cell_old))) != CUBE_OK) return s;
+    if ((s = to_user(c, u_new, c->dbg_u, b, !is_device_ptr(u_new))) != CUBE_OK) return s;
+    if ((s = to_user(c, p, c->dbg_p, b, !is_device_ptr(p))) != CUBE_OK) return s;
+    if (sigma_next) CK(cudaMemcpyAsync(sigma_next, c->codec[c->cur].sigma, 8, cudaMemcpyDeviceToHost, c->st));
+    return latched(c);
+}
+
+cube_status cube_profile(cube_ctx* c, int32_t max_steps) {
+    if (!c) return fail(CUBE_E_ARG, "ctx is NULL");
+    if (max_steps < 0 || max_steps > 100000) return fail(CUBE_E_ARG, "max_steps out of range");
+    CK(cudaStreamSynchronize(c->st));
+    const size_t need = (size_t)max_steps * (CUBE_PHASES + 1);
+    while (c->prof_ev.size() < need) {
+        cudaEvent_t e;
+        CK(cudaEventCreate(&e));
+        c->prof_ev.push_back(e);
+    }
+    c->prof_max = max_steps;
+    c->prof_steps = 0;
+    return CUBE_OK;
+}
+
+cube_status cube_profile_read(cube_ctx* c, double* ms, int32_t* kernels, int32_t* nsteps) {
+    if (!c || !ms) return fail(CUBE_E_ARG, "NULL argument");
+    CK(cudaStreamSynchronize(c->st));
+    for (int p = 0; p < CUBE_PHASES; ++p) {
+        double t = 0.0;
+        for (int s = 0; s < c->prof_steps; ++s) {
+            float e = 0.0f;
+            const size_t b = (size_t)s * (CUBE_PHASES + 1) + p;
+            CK(cudaEventElapsedTime(&e, c->prof_ev[b], c->prof_ev[b + 1]));
+            t += e;
+        }
+        ms[p] = t;
+        if (kernels) kernels[p] = kPhaseKernels[p];
+    }
+    if (nsteps) *nsteps = c->prof_steps;
+    return CUBE_OK;
+}
+
+const char* cube_phase_name(int32_t phase) {
+    return (phase >= 0 && phase < CUBE_PHASES) ? kPhaseNames[phase] : "";
+}
+
+}  // extern "C"

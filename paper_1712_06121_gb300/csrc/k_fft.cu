@@ -1,0 +1,453 @@
+// 3-D real FFT Poisson solve on the fine mesh and the power-spectrum binning.
+//
+// Mesh layout: real rho / Phi as rows of N floats with row stride S = N + 4
+// (z-major, then y); in place, the r2c result is rows of N/2 + 1 complex
+// (kx = 0..N/2) with complex stride S/2.  Transforms are unnormalised; the
+// 1/N^3 of the inverse is folded into the Green's function.
+//
+// Each kernel transforms one tile of NC = 16 columns of length n in shared
+// memory with a mixed-radix (8, 4, 2, 3) Stockham autosort FFT: every pass
+// reads each element once and writes it once, through registers.
+//   x sweep : 16 rows per CTA, r2c / c2r by the even-odd packing into an
+//             N/2-point complex transform (layout [k][row], XOR-swizzled so
+//             row-wise and column-wise accesses are both conflict-free)
+//   y sweep : 16 consecutive kx columns of one z-slab
+//   z sweep : 16 consecutive kx columns of one ky line; forward, times
+//             -(3/2) Om / k^2 / W(k)^p / N^3, inverse, in one pass.
+#include <cmath>
+
+#include "kernels.h"
+
+namespace cube {
+
+namespace {
+
+constexpr int NC = 16;          // columns per tile
+constexpr int LOG_NC = 4;
+constexpr int FFT_T = 512;      // threads per CTA
+
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
+// multiply by -i (forward) or +i (inverse)
+template <bool INV>
+__device__ __forceinline__ float2 rot90(float2 a) {
+    return INV ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x);
+}
+
+template <bool SWZ>
+__device__ __forceinline__ int sidx(int k, int c) {
+    return SWZ ? (k << LOG_NC) + (c ^ (k & (NC - 1))) : (k << LOG_NC) + c;
+}
+
+template <int RAD, bool INV>
+__device__ __forceinline__ void dft(float2* v) {
+    if (RAD == 2) {
+        float2 a = v[0], b = v[1];
+        v[0] = cadd(a, b);
+        v[1] = csub(a, b);
+    } else if (RAD == 3) {
+        const float h = 0.86602540378443865f;   // sqrt(3)/2
+        float2 t1 = cadd(v[1], v[2]);
+        float2 t2 = make_float2(v[0].x - 0.5f * t1.x, v[0].y - 0.5f * t1.y);
+        float2 d = csub(v[1], v[2]);
+        float2 t3 = make_float2(h * d.x, h * d.y);
+        float2 r = rot90<INV>(t3);               // -+ i * t3
+        v[0] = cadd(v[0], t1);
+        v[1] = cadd(t2, r);
+        v[2] = csub(t2, r);
+    } else if (RAD == 4) {
+        float2 a0 = cadd(v[0], v[2]), a1 = csub(v[0], v[2]);
+        float2 b0 = cadd(v[1], v[3]), b1 = rot90<INV>(csub(v[1], v[3]));
+        v[0] = cadd(a0, b0);
+        v[1] = cadd(a1, b1);
+        v[2] = csub(a0, b0);
+        v[3] = csub(a1, b1);
+    } else {   // 8 = 2 x 4
+        const float r = 0.70710678118654752f;
+        float2 a[4], b[4];
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+            a[m] = cadd(v[m], v[m + 4]);
+            b[m] = csub(v[m], v[m + 4]);
+        }
+        // b[m] *= w8^m,  w8 = e^{-+ 2 pi i / 8}
+        b[1] = INV ? make_float2(r * (b[1].x - b[1].y), r * (b[1].x + b[1].y))
+                   : make_float2(r * (b[1].x + b[1].y), r * (b[1].y - b[1].x));
+        b[2] = rot90<INV>(b[2]);
+        b[3] = INV ? make_float2(-r * (b[3].x + b[3].y), r * (b[3].x - b[3].y))
+                   : make_float2(r * (b[3].y - b[3].x), -r * (b[3].x + b[3].y));
+        dft<4, INV>(a);
+        dft<4, INV>(b);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            v[2 * k] = a[k];
+            v[2 * k + 1] = b[k];
+        }
+    }
+}
+
+// one Stockham pass of radix R over the NC-column tile of length n, span Ns;
+// twiddles come from a table of TWN = n * TWM entries e^{-2 pi i k / TWN}
+template <int n, int Ns, int R, int TWM, bool INV, bool SWZ>
+__device__ __forceinline__ void fft_pass(float2* buf, const float2* tw) {
+    constexpr int nq = n / R;
+    constexpr int nbf = nq * NC;
+    constexpr int KMAX = (nbf + FFT_T - 1) / FFT_T;
+    constexpr int step = TWM * (n / (Ns * R));
+    float2 v[KMAX][R];
+#pragma unroll
+    for (int q = 0; q < KMAX; ++q) {
+        const int b = threadIdx.x + q * FFT_T;
+        if (nbf % FFT_T == 0 || b < nbf) {
+            const int c = b & (NC - 1), j = b >> LOG_NC;
+#pragma unroll
+            for (int m = 0; m < R; ++m) v[q][m] = buf[sidx<SWZ>(j + m * nq, c)];
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < KMAX; ++q) {
+        const int b = threadIdx.x + q * FFT_T;
+        if (nbf % FFT_T == 0 || b < nbf) {
+            const int c = b & (NC - 1), j = b >> LOG_NC;
+            const int k = j % Ns;
+#pragma unroll
+            for (int m = 1; m < R; ++m) {
+                float2 w = tw[k * m * step];
+                if (INV) w.y = -w.y;
+                v[q][m] = cmul(v[q][m], w);
+            }
+            dft<R, INV>(v[q]);
+            const int idxD = (j / Ns) * Ns * R + k;
+#pragma unroll
+            for (int m = 0; m < R; ++m) buf[sidx<SWZ>(idxD + m * Ns, c)] = v[q][m];
+        }
+    }
+    __syncthreads();
+}
+
+// all passes of a length-n transform, radices 8, 4, 2, 3 taken greedily
+template <int n, int Ns, int TWM, bool INV, bool SWZ>
+__device__ __forceinline__ void tile_fft(float2* buf, const float2* tw) {
+    if constexpr (Ns < n) {
+        constexpr int rem = n / Ns;
+        constexpr int R = rem % 8 == 0 ? 8 : rem % 4 == 0 ? 4 : rem % 2 == 0 ? 2 : 3;
+        static_assert(rem % R == 0, "length must be 2^a 3^b");
+        fft_pass<n, Ns, R, TWM, INV, SWZ>(buf, tw);
+        tile_fft<n, Ns * R, TWM, INV, SWZ>(buf, tw);
+    }
+}
+
+__device__ __forceinline__ void load_tw(float2* stw, const float2* tw, int N) {
+    for (int i = threadIdx.x; i < N; i += blockDim.x) stw[i] = tw[i];
+}
+
+// ------------------------------------------------------------ x sweep, r2c
+template <int N>
+__global__ void __launch_bounds__(FFT_T) k_fft_x_r2c(float* mesh, int S, const float2* __restrict__ tw) {
+    extern __shared__ float2 fsm[];
+    constexpr int h = N / 2;
+    float2* stw = fsm;               // [N]
+    float2* buf = fsm + N;           // [h][NC]
+    load_tw(stw, tw, N);
+    const int64_t row0 = (int64_t)blockIdx.x * NC;
+    for (int t = threadIdx.x; t < h * NC; t += FFT_T) {
+        const int k = t % h, c = t / h;
+        const float2* src = reinterpret_cast<const float2*>(mesh + (row0 + c) * S);
+        buf[sidx<true>(k, c)] = src[k];
+    }
+    __syncthreads();
+    tile_fft<h, 1, 2, false, true>(buf, stw);
+    // X[k] = (Z[k] + Z*[h-k])/2 - i W^k (Z[k] - Z*[h-k])/2, k = 0..h
+    for (int t = threadIdx.x; t < (h / 2 + 1) * NC; t += FFT_T) {
+        const int k = t % (h / 2 + 1), c = t / (h / 2 + 1);
+        float2* dst = reinterpret_cast<float2*>(mesh + (row0 + c) * S);
+        const float2 zk = buf[sidx<true>(k % h, c)];
+        const float2 zm = buf[sidx<true>((h - k) % h, c)];
+        {
+            float2 e = make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y));
+            float2 o = make_float2(0.5f * (zk.x - zm.x), 0.5f * (zk.y + zm.y));   // (Z - Z*) / 2
+            float2 wo = cmul(stw[k], o);
+            dst[k] = make_float2(e.x + wo.y, e.y - wo.x);                         // e - i wo
+        }
+        if (k != h - k) {
+            const int km = h - k;
+            float2 e = make_float2(0.5f * (zm.x + zk.x), 0.5f * (zm.y - zk.y));
+            float2 o = make_float2(0.5f * (zm.x - zk.x), 0.5f * (zm.y + zk.y));
+            float2 wo = cmul(stw[km], o);
+            dst[km] = make_float2(e.x + wo.y, e.y - wo.x);
+        }
+    }
+}
+
+// ------------------------------------------------------------ x sweep, c2r
+template <int N>
+__global__ void __launch_bounds__(FFT_T) k_fft_x_c2r(float* mesh, int S, const float2* __restrict__ tw) {
+    extern __shared__ float2 fsm[];
+    constexpr int h = N / 2;
+    float2* stw = fsm;               // [N]
+    float2* buf = fsm + N;           // [h][NC]
+    float2* xh = buf + h * NC;       // [NC]: X[N/2]
+    load_tw(stw, tw, N);
+    const int64_t row0 = (int64_t)blockIdx.x * NC;
+    for (int t = threadIdx.x; t < (h + 1) * NC; t += FFT_T) {
+        const int k = t % (h + 1), c = t / (h + 1);
+        const float2* src = reinterpret_cast<const float2*>(mesh + (row0 + c) * S);
+        const float2 v = src[k];
+        if (k < h) buf[sidx<true>(k, c)] = v;
+        else xh[c] = v;
+    }
+    __syncthreads();
+    // Z[k] = E + i O, E = X[k] + X*[h-k], O = W^-k (X[k] - X*[h-k])
+    for (int t = threadIdx.x; t < (h / 2 + 1) * NC; t += FFT_T) {
+        const int k = t % (h / 2 + 1), c = t / (h / 2 + 1);
+        const int km = h - k;
+        const float2 xk = buf[sidx<true>(k, c)];
+        const float2 xm = km < h ? buf[sidx<true>(km, c)] : xh[c];
+        float2 e = make_float2(xk.x + xm.x, xk.y - xm.y);
+        float2 d = make_float2(xk.x - xm.x, xk.y + xm.y);
+        float2 o = cmul(cconj(stw[k]), d);
+        const float2 zk = make_float2(e.x - o.y, e.y + o.x);
+        buf[sidx<true>(k, c)] = zk;
+        if (km != k && km < h) {
+            float2 e2 = make_float2(xm.x + xk.x, xm.y - xk.y);
+            float2 d2 = make_float2(xm.x - xk.x, xm.y + xk.y);
+            float2 o2 = cmul(cconj(stw[km]), d2);
+            buf[sidx<true>(km, c)] = make_float2(e2.x - o2.y, e2.y + o2.x);
+        }
+    }
+    __syncthreads();
+    tile_fft<h, 1, 2, true, true>(buf, stw);
+    for (int t = threadIdx.x; t < h * NC; t += FFT_T) {
+        const int k = t % h, c = t / h;
+        float2* dst = reinterpret_cast<float2*>(mesh + (row0 + c) * S);
+        dst[k] = buf[sidx<true>(k, c)];
+    }
+}
+
+// ------------------------------------------------------------ y sweep
+template <int N, bool INV>
+__global__ void __launch_bounds__(FFT_T) k_fft_y(float* mesh, int S, const float2* __restrict__ tw) {
+    extern __shared__ float2 fsm[];
+    float2* stw = fsm;
+    float2* buf = fsm + N;
+    load_tw(stw, tw, N);
+    const int Sc = S / 2;
+    constexpr int ncol = N / 2 + 1;
+    const int c0 = blockIdx.x * NC;
+    float2* slab = reinterpret_cast<float2*>(mesh) + (int64_t)blockIdx.y * N * Sc;
+    for (int t = threadIdx.x; t < N * NC; t += FFT_T) {
+        const int c = t & (NC - 1), y = t >> LOG_NC;
+        buf[sidx<false>(y, c)] = (c0 + c < ncol) ? slab[(int64_t)y * Sc + c0 + c] : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+    tile_fft<N, 1, 1, INV, false>(buf, stw);
+    for (int t = threadIdx.x; t < N * NC; t += FFT_T) {
+        const int c = t & (NC - 1), y = t >> LOG_NC;
+        if (c0 + c < ncol) slab[(int64_t)y * Sc + c0 + c] = buf[sidx<false>(y, c)];
+    }
+}
+
+// ------------------------------------------------------------ z sweep (+ Green)
+template <int N, int MODE>   // 0: forward only, 1: forward, Green, inverse
+__global__ void __launch_bounds__(FFT_T) k_fft_z(float* mesh, int S, const float2* __restrict__ tw,
+                                                 const float* __restrict__ k2, const float* __restrict__ wdec, float g0) {
+    extern __shared__ float2 fsm[];
+    float2* stw = fsm;
+    float2* buf = fsm + N;
+    load_tw(stw, tw, N);
+    const int Sc = S / 2;
+    constexpr int ncol = N / 2 + 1;
+    const int c0 = blockIdx.x * NC;
+    const int ky = blockIdx.y;
+    float2* base = reinterpret_cast<float2*>(mesh) + (int64_t)ky * Sc;
+    const int64_t zs = (int64_t)N * Sc;
+    for (int t = threadIdx.x; t < N * NC; t += FFT_T) {
+        const int c = t & (NC - 1), z = t >> LOG_NC;
+        buf[sidx<false>(z, c)] = (c0 + c < ncol) ? base[z * zs + c0 + c] : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+    tile_fft<N, 1, 1, false, false>(buf, stw);
+    if (MODE == 1) {
+        const float ky2 = k2[ky], wy = wdec[ky];
+        for (int t = threadIdx.x; t < N * NC; t += FFT_T) {
+            const int c = t & (NC - 1), z = t >> LOG_NC;
+            const int kx = c0 + c;
+            if (kx < ncol) {
+                const float kk = k2[kx] + ky2 + k2[z];
+                const float gr = (kx == 0 && ky == 0 && z == 0) ? 0.0f : g0 / kk * (wdec[kx] * wy * wdec[z]);
+                const float2 v = buf[sidx<false>(z, c)];
+                buf[sidx<false>(z, c)] = make_float2(v.x * gr, v.y * gr);
+            }
+        }
+        __syncthreads();
+        tile_fft<N, 1, 1, true, false>(buf, stw);
+    }
+    for (int t = threadIdx.x; t < N * NC; t += FFT_T) {
+        const int c = t & (NC - 1), z = t >> LOG_NC;
+        if (c0 + c < ncol) base[z * zs + c0 + c] = buf[sidx<false>(z, c)];
+    }
+}
+
+// ------------------------------------------------------------ power spectrum
+__global__ void k_pk_bin(const float* __restrict__ mesh, int N, int S, int nbins, double pfac, double kfund,
+                         const double* __restrict__ wpk, double* __restrict__ part) {
+    extern __shared__ double pacc[];          // [3 * nbins]: weight, weight*|k|, weight*P
+    for (int i = threadIdx.x; i < 3 * nbins; i += blockDim.x) pacc[i] = 0.0;
+    __syncthreads();
+    const int Sc = S / 2, ncol = N / 2 + 1;
+    const int kz = blockIdx.x;
+    const int fz = kz <= N / 2 ? kz : kz - N;
+    const float2* plane = reinterpret_cast<const float2*>(mesh) + (int64_t)kz * N * Sc;
+    for (int t = threadIdx.x; t < N * ncol; t += blockDim.x) {
+        int kx = t % ncol, ky = t / ncol;
+        int fy = ky <= N / 2 ? ky : ky - N;
+        long long n2 = (long long)kx * kx + (long long)fy * fy + (long long)fz * fz;
+        if (n2 == 0) continue;
+        long long i = (long long)sqrt((double)n2);
+        while (i * i > n2) --i;
+        while ((i + 1) * (i + 1) <= n2) ++i;
+        if (n2 > i * (i + 1)) ++i;
+        if (i < 1 || i > nbins) continue;
+        float2 v = plane[(int64_t)ky * Sc + kx];
+        double p = ((double)v.x * v.x + (double)v.y * v.y) * pfac * wpk[kx] * wpk[ky] * wpk[kz];
+        double wt = (kx == 0 || kx == N / 2) ? 1.0 : 2.0;
+        int b = (int)(i - 1);
+        atomicAdd(&pacc[b], wt);
+        atomicAdd(&pacc[nbins + b], wt * kfund * sqrt((double)n2));
+        atomicAdd(&pacc[2 * nbins + b], wt * p);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < 3 * nbins; i += blockDim.x) part[(int64_t)blockIdx.x * 3 * nbins + i] = pacc[i];
+}
+
+__global__ void k_pk_reduce(const double* __restrict__ part, int nblocks, int nbins, double* k, double* pk, double* nm) {
+    int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nbins) return;
+    double w = 0, ks = 0, ps = 0;
+    for (int j = 0; j < nblocks; ++j) {
+        const double* p = part + (int64_t)j * 3 * nbins;
+        w += p[b];
+        ks += p[nbins + b];
+        ps += p[2 * nbins + b];
+    }
+    nm[b] = w;
+    k[b] = w > 0 ? ks / w : nan("");
+    pk[b] = w > 0 ? ps / w : nan("");
+}
+
+__global__ void k_unpad(const float* __restrict__ mesh, int N, int S, float* __restrict__ out) {
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int64_t tot = (int64_t)N * N * N;
+    if (t >= tot) return;
+    int64_t row = t / N;
+    int x = (int)(t - row * N);
+    out[t] = mesh[row * S + x];
+}
+
+size_t tile_smem(int N, int n) { return (size_t)(N + n * NC + NC) * sizeof(float2); }
+
+template <int N>
+struct Sweeps {
+    static void attrs() {
+        static bool done = false;
+        if (done) return;
+        const int big = (int)tile_smem(N, N), half = (int)tile_smem(N, N / 2);
+        cudaFuncSetAttribute(k_fft_x_r2c<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, half);
+        cudaFuncSetAttribute(k_fft_x_c2r<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, half);
+        cudaFuncSetAttribute(k_fft_y<N, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+        cudaFuncSetAttribute(k_fft_y<N, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+        cudaFuncSetAttribute(k_fft_z<N, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+        cudaFuncSetAttribute(k_fft_z<N, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+        done = true;
+    }
+    static void x_r2c(const FftPlan& p, float* mesh, int S, cudaStream_t st) {
+        attrs();
+        k_fft_x_r2c<N><<<(N * N) / NC, FFT_T, tile_smem(N, N / 2), st>>>(mesh, S, p.tw);
+    }
+    static void y(const FftPlan& p, float* mesh, int S, bool inv, cudaStream_t st) {
+        attrs();
+        dim3 gy((N / 2 + NC) / NC, N);
+        if (inv) k_fft_y<N, true><<<gy, FFT_T, tile_smem(N, N), st>>>(mesh, S, p.tw);
+        else k_fft_y<N, false><<<gy, FFT_T, tile_smem(N, N), st>>>(mesh, S, p.tw);
+    }
+    static void z(const FftPlan& p, float* mesh, int S, float g0, bool green, cudaStream_t st) {
+        attrs();
+        dim3 gz((N / 2 + NC) / NC, N);
+        if (green) k_fft_z<N, 1><<<gz, FFT_T, tile_smem(N, N), st>>>(mesh, S, p.tw, p.k2, p.wdec, g0);
+        else k_fft_z<N, 0><<<gz, FFT_T, tile_smem(N, N), st>>>(mesh, S, p.tw, p.k2, p.wdec, g0);
+    }
+    static void x_c2r(const FftPlan& p, float* mesh, int S, cudaStream_t st) {
+        attrs();
+        k_fft_x_c2r<N><<<(N * N) / NC, FFT_T, tile_smem(N, N / 2), st>>>(mesh, S, p.tw);
+    }
+};
+
+// mesh sizes with compiled sweeps: 2^a and 3 * 2^a from 16 to 1024
+#define CUBE_FFT_SIZES(X) X(16) X(24) X(32) X(48) X(64) X(96) X(128) X(192) X(256) X(384) X(512) X(768) X(1024)
+
+}  // namespace
+
+bool fft_size_supported(int N) {
+    switch (N) {
+#define CASE(n) case n:
+        CUBE_FFT_SIZES(CASE)
+#undef CASE
+        return true;
+        default: return false;
+    }
+}
+
+#define DISPATCH()                                       \
+    switch (p.N) {                                       \
+        CUBE_FFT_SIZES(DCASE)                            \
+        default: break;                                  \
+    }
+
+void fft_x_r2c(const FftPlan& p, float* mesh, int S, cudaStream_t st) {
+#define DCASE(n) case n: Sweeps<n>::x_r2c(p, mesh, S, st); break;
+    DISPATCH()
+#undef DCASE
+}
+
+void fft_y(const FftPlan& p, float* mesh, int S, bool inverse, cudaStream_t st) {
+#define DCASE(n) case n: Sweeps<n>::y(p, mesh, S, inverse, st); break;
+    DISPATCH()
+#undef DCASE
+}
+
+void fft_z(const FftPlan& p, float* mesh, int S, float g0, bool green, cudaStream_t st) {
+#define DCASE(n) case n: Sweeps<n>::z(p, mesh, S, g0, green, st); break;
+    DISPATCH()
+#undef DCASE
+}
+
+void fft_x_c2r(const FftPlan& p, float* mesh, int S, cudaStream_t st) {
+#define DCASE(n) case n: Sweeps<n>::x_c2r(p, mesh, S, st); break;
+    DISPATCH()
+#undef DCASE
+}
+
+int pk_blocks(int N) { return N; }
+
+void launch_pk_bin(const FftPlan& p, const float* mesh, int S, int nbins, double pfac, double kfund, double* part,
+                   cudaStream_t st) {
+    size_t sm = (size_t)3 * nbins * sizeof(double);
+    if (sm > 48 * 1024) cudaFuncSetAttribute(k_pk_bin, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_pk_bin<<<p.N, 512, sm, st>>>(mesh, p.N, S, nbins, pfac, kfund, p.wpk, part);
+}
+
+void launch_pk_reduce(const double* part, int nblocks, int nbins, double* k, double* pk, double* nm, cudaStream_t st) {
+    k_pk_reduce<<<(nbins + 127) / 128, 128, 0, st>>>(part, nblocks, nbins, k, pk, nm);
+}
+
+void launch_unpad(const float* mesh, int N, int S, float* out, cudaStream_t st) {
+    int64_t tot = (int64_t)N * N * N;
+    k_unpad<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(mesh, N, S, out);
+}
+
+}  // namespace cube

@@ -1,0 +1,720 @@
+// Kernels on the compressed, cell-ordered particle store:
+//   encode (Fig. fig.ic, Section 2.3.2), decode (Eqs. x, v), CIC deposit,
+//   pass A (decode, CIC gather of -grad Phi, kick, re-encode, drift, new-cell
+//   histogram; Figs. update_vp and update_xp first loop), starts (scan of the
+//   per-brick histograms), pass B (identical drift, stable scatter by new cell,
+//   Eq. chi / Eq. nu encode against the new v_c; Fig. update_xp second loop).
+//
+// Every per-particle pass runs one CTA per storage brick: the brick's cells
+// are contiguous in the store, so the CTA reads a contiguous particle range
+// and finds each particle's cell by binary search in the brick's offsets.
+#include <algorithm>
+
+#include "kernels.h"
+
+namespace cube {
+
+namespace {
+
+constexpr int T_BRICK = 256;                 // threads of the per-brick kernels
+constexpr int W_BRICK = T_BRICK / 32;
+constexpr double PI_D = 3.141592653589793;   // nearest double to pi
+
+__device__ __forceinline__ int upper_cell(const unsigned* off, int ncell, unsigned i) {
+    // largest c in [0, ncell) with off[c] <= i  (off[ncell] > i)
+    int lo = 0, hi = ncell;
+    while (hi - lo > 1) {
+        int mid = (lo + hi) >> 1;
+        if (off[mid] <= i) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ void brick_coords(const Geo& g, int brick, int* bx, int* by, int* bz) {
+    *bx = brick % g.nb;
+    *by = (brick / g.nb) % g.nb;
+    *bz = brick / (g.nb * g.nb);
+}
+
+__device__ double block_sum_double(double v, double* sh) {
+    // fixed-shape tree: deterministic for a given block size
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if (lane == 0) sh[w] = v;
+    __syncthreads();
+    double s = 0.0;
+    if (threadIdx.x == 0)
+        for (int i = 0; i < nw; ++i) s += sh[i];
+    __syncthreads();
+    return s;
+}
+
+__device__ __forceinline__ double snap_sigma_dev(double x) {
+    // nearest 2^(m/16) in log2 (ties up), floor 2^-30
+    x = fmax(x, 9.313225746154785e-10);
+    double m = floor(16.0 * log2(x) + 0.5);
+    return exp2(m / 16.0);
+}
+
+// ------------------------------------------------------------------ encode
+template <int NX>
+__global__ void k_encode_keys(Geo g, const float* __restrict__ pos, const float* __restrict__ vel,
+                              unsigned* __restrict__ key, unsigned* __restrict__ val, unsigned* counts,
+                              long long* vsum, unsigned* flags) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= g.Np) return;
+    const int nbits = 8 * NX;
+    const long long tot = (long long)g.Nc << nbits;
+    const float scale = ldexpf(1.0f, nbits - g.r);
+    int cell[3];
+    bool bad = false;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        float x = pos[d * g.Np + i];
+        if (!isfinite(x)) { bad = true; x = 0.0f; }
+        long long bf = __float2ll_rd(x * scale);
+        bf %= tot;
+        if (bf < 0) bf += tot;
+        cell[d] = (int)(bf >> nbits);
+    }
+    unsigned k = (unsigned)cell_rank(g, cell[0], cell[1], cell[2]);
+    key[i] = k;
+    val[i] = (unsigned)i;
+    atomicAdd(&counts[k], 1u);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        float v = vel[d * g.Np + i];
+        if (!isfinite(v)) { bad = true; v = 0.0f; }
+        atomicAdd(reinterpret_cast<unsigned long long*>(&vsum[(int64_t)d * g.Ncc + k]),
+                  (unsigned long long)vel_fix(v));
+    }
+    if (bad) atomicOr(flags, ERR_NONFINITE);
+}
+
+__global__ void k_vc_finalize(int ncc, const unsigned* __restrict__ counts, const long long* __restrict__ vsum,
+                              float* __restrict__ vc) {
+    int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= ncc) return;
+    unsigned n = counts[c];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) vc[(int64_t)d * ncc + c] = vel_unfix_mean(vsum[(int64_t)d * ncc + c], n);
+}
+
+__global__ void k_encode_sigma(Geo g, const float* __restrict__ vel, const unsigned* __restrict__ key,
+                               const float* __restrict__ vc, double* __restrict__ part) {
+    __shared__ double sh[32];
+    float acc = 0.0f;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < g.Np; i += (int64_t)gridDim.x * blockDim.x) {
+        unsigned k = key[i];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            float v = vel[d * g.Np + i];
+            if (!isfinite(v)) v = 0.0f;
+            float e = v - vc[(int64_t)d * g.Ncc + k];
+            acc = __fmaf_rn(e, e, acc);
+        }
+    }
+    double s = block_sum_double((double)acc, sh);
+    if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+__global__ void k_sigma_finalize(const double* __restrict__ part, int nparts, double count, double ratio,
+                                 double fixed, double* sigma_out) {
+    __shared__ double sh[32];
+    double s = 0.0;
+    for (int i = threadIdx.x; i < nparts; i += blockDim.x) s += part[i];
+    s = block_sum_double(s, sh);
+    if (threadIdx.x == 0) {
+        double x = fixed > 0.0 ? fixed : sqrt(s / count) * ratio;
+        *sigma_out = snap_sigma_dev(x);
+    }
+}
+
+__global__ void k_codec_tables(int lim, const double* __restrict__ tanv, const double* __restrict__ tanh_,
+                               const double* __restrict__ sigma, float* __restrict__ dec, float* __restrict__ thr,
+                               float* __restrict__ est) {
+    const double sg = *sigma;
+    const double s = sqrt(PI_D / (2.0 * sg * sg));
+    const double gam = sqrt(2.0 * sg * sg / PI_D);
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k <= lim + 1; k += gridDim.x * blockDim.x) {
+        if (k == 0) {
+            dec[lim] = 0.0f;
+            thr[0] = 0.0f;
+            const double m = (double)(2 * lim + 1);
+            est[0] = (float)(m / PI_D * s);
+            est[1] = (float)(m / PI_D);
+        } else if (k <= lim) {
+            float dv = (float)(tanv[k] * gam);
+            dec[lim + k] = dv;
+            dec[lim - k] = -dv;
+            thr[k] = __double2float_ru(tanh_[k] / s);
+        } else {
+            thr[lim + 1] = __int_as_float(0x7f800000);   // +inf
+        }
+    }
+}
+
+template <int NX, int NV>
+__global__ void k_encode_scatter(Geo g, const float* __restrict__ pos, const float* __restrict__ vel,
+                                 const unsigned* __restrict__ id_in, const unsigned* __restrict__ key,
+                                 const unsigned* __restrict__ perm, const float* __restrict__ vc,
+                                 const float* __restrict__ thr, const float* __restrict__ est, StoreDev s) {
+    int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= g.Np) return;
+    const int64_t i = perm[j];
+    const unsigned k = key[j];
+    if (i >= g.Np || k >= (unsigned)g.Ncc) return;      // only if the sort went wrong
+    const int nbits = 8 * NX;
+    const long long tot = (long long)g.Nc << nbits;
+    const float scale = ldexpf(1.0f, nbits - g.r);
+    const float e0 = est[0], e1 = est[1];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        float x = pos[d * g.Np + i];
+        if (!isfinite(x)) x = 0.0f;
+        long long bf = __float2ll_rd(x * scale);
+        bf %= tot;
+        if (bf < 0) bf += tot;
+        int chi = (int)(bf & ((1 << nbits) - 1)) - (1 << (nbits - 1));
+        store_code<NX>(s.chi, d * g.Np + j, chi);
+        float v = vel[d * g.Np + i];
+        if (!isfinite(v)) v = 0.0f;
+        float dd = v - vc[(int64_t)d * g.Ncc + k];
+        int nu = nu_from_thresholds(dd, thr, g.nulim, nu_estimate(dd, e0, e1));
+        store_code<NV>(s.nu, d * g.Np + j, nu);
+    }
+    if (s.id) s.id[j] = id_in ? id_in[i] : (unsigned)i;
+}
+
+// ------------------------------------------------------------------ decode
+template <int NX, int NV>
+__global__ void __launch_bounds__(T_BRICK) k_decode(Geo g, StoreDev s, const float* __restrict__ dec,
+                                                    float* __restrict__ pos, float* __restrict__ vel,
+                                                    unsigned* __restrict__ id) {
+    extern __shared__ unsigned sm_off[];
+    const int nbc = g.B * g.B * g.B;
+    const int L0 = blockIdx.x * nbc;
+    for (int c = threadIdx.x; c <= nbc; c += blockDim.x) sm_off[c] = s.offsets[L0 + c];
+    __syncthreads();
+    int bx, by, bz;
+    brick_coords(g, blockIdx.x, &bx, &by, &bz);
+    const int nbits = 8 * NX, half = 1 << (nbits - 1);
+    const double pscale = ldexp(1.0, g.r - nbits - 1);
+    const unsigned np_ = (unsigned)g.Np;
+    const unsigned q1 = min(sm_off[nbc], np_);
+    for (unsigned i = min(sm_off[0], q1) + threadIdx.x; i < q1; i += blockDim.x) {
+        int lc = upper_cell(sm_off, nbc, i);
+        int l[3] = {lc % g.B, (lc / g.B) % g.B, lc / (g.B * g.B)};
+        int c[3] = {bx * g.B + l[0], by * g.B + l[1], bz * g.B + l[2]};
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            int Q = 2 * (load_code<NX>(s.chi, d * g.Np + i) + half) + 1;
+            long long q = ((long long)c[d] << (nbits + 1)) + Q;
+            pos[d * g.Np + i] = __double2float_rn((double)q * pscale);
+            int nu = load_nu<NV>(s.nu, d * g.Np + i, g.nulim);
+            vel[d * g.Np + i] = s.vc[(int64_t)d * g.Ncc + L0 + lc] + dec[nu + g.nulim];
+        }
+        if (id) id[i] = s.id ? s.id[i] : i;
+    }
+}
+
+// ------------------------------------------------------------------ CIC deposit
+// Owner computes: a CTA produces the density of its brick's fine nodes
+// [o, o + F)^3 from the particles of the brick's cells and of the one-cell
+// layer below it (a particle in fine cell i also feeds node i + 1).  Weights
+// are integers (numerators over 2^s per axis) summed in int64, so the result
+// is exact and independent of the summation order; rho = m * sum * 2^(-3s).
+template <int NX>
+__global__ void __launch_bounds__(T_BRICK) k_deposit(Geo g, StoreDev s, float* __restrict__ mesh, double scale) {
+    extern __shared__ unsigned long long dep_smem[];
+    const int F = g.F, F3 = F * F * F;
+    const int E = g.B + 1, E3 = E * E * E;
+    unsigned long long* acc = dep_smem;                              // [F3]
+    unsigned* cstart = reinterpret_cast<unsigned*>(acc + F3);        // [E3]
+    unsigned* cpref = cstart + E3;                                   // [E3 + 1]
+    int bx, by, bz;
+    brick_coords(g, blockIdx.x, &bx, &by, &bz);
+    const int c0[3] = {bx * g.B, by * g.B, bz * g.B};
+    for (int t = threadIdx.x; t < F3; t += blockDim.x) acc[t] = 0ull;
+    for (int t = threadIdx.x; t < E3; t += blockDim.x) {
+        int lx = t % E - 1, ly = (t / E) % E - 1, lz = t / (E * E) - 1;
+        int L = cell_rank(g, wrapi(c0[0] + lx, g.Nc), wrapi(c0[1] + ly, g.Nc), wrapi(c0[2] + lz, g.Nc));
+        unsigned a = s.offsets[L];
+        cstart[t] = a;
+        cpref[t + 1] = s.offsets[L + 1] - a;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned run = 0;
+        cpref[0] = 0;
+        for (int t = 0; t < E3; ++t) { run += cpref[t + 1]; cpref[t + 1] = run; }
+    }
+    __syncthreads();
+    const int nbits = 8 * NX, half = 1 << (nbits - 1);
+    const int sb = g.sbits, wmask = (1 << sb) - 1, wone = 1 << sb;
+    const unsigned total = cpref[E3];
+    for (unsigned q = threadIdx.x; q < total; q += blockDim.x) {
+        int t = upper_cell(cpref, E3, q);
+        unsigned i = cstart[t] + (q - cpref[t]);
+        if (i >= (unsigned)g.Np) continue;
+        int l[3] = {t % E - 1, (t / E) % E - 1, t / (E * E) - 1};
+        int nd[3], wn[3], wm[3];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            int Q = 2 * (load_code<NX>(s.chi, d * g.Np + i) + half) + 1;
+            nd[d] = g.R * l[d] + (Q >> sb);
+            wn[d] = Q & wmask;
+            wm[d] = wone - wn[d];
+        }
+#pragma unroll
+        for (int dz = 0; dz < 2; ++dz) {
+            int z = nd[2] + dz;
+            if (z < 0 || z >= F) continue;
+#pragma unroll
+            for (int dy = 0; dy < 2; ++dy) {
+                int y = nd[1] + dy;
+                if (y < 0 || y >= F) continue;
+                long long wyz = (long long)(dz ? wn[2] : wm[2]) * (dy ? wn[1] : wm[1]);
+#pragma unroll
+                for (int dx = 0; dx < 2; ++dx) {
+                    int x = nd[0] + dx;
+                    if (x < 0 || x >= F) continue;
+                    long long w = wyz * (dx ? wn[0] : wm[0]);
+                    atomicAdd(&acc[(z * F + y) * F + x], (unsigned long long)w);
+                }
+            }
+        }
+    }
+    __syncthreads();
+    const int ox = c0[0] * g.R, oy = c0[1] * g.R, oz = c0[2] * g.R;
+    for (int t = threadIdx.x; t < F3; t += blockDim.x) {
+        int x = t % F, y = (t / F) % F, z = t / (F * F);
+        double v = (double)(long long)acc[t] * scale;
+        mesh[((int64_t)(oz + z) * g.N + (oy + y)) * g.S + ox + x] = __double2float_rn(v);
+    }
+}
+
+// ------------------------------------------------------------------ pass A
+// One CTA per brick.  Shared memory: Phi tile of (F + 5)^3 fine nodes
+// ([o - 2, o + F + 3) per axis, periodic), brick offsets, the histogram of
+// destination cells over the brick and its one-cell halo (Bh^3 cells) with
+// fixed-point momentum sums, and (1-byte velocities) the codec tables.
+template <int NX, int NV>
+__global__ void __launch_bounds__(T_BRICK) k_passA(Geo g, StoreDev s, const float* __restrict__ phi, CodecDev cur,
+                                                   float kick, float dc, StepScratch w, DriftDebug dbg) {
+    extern __shared__ unsigned char pa_smem[];
+    const int F = g.F, T = F + 5, T3 = T * T * T;
+    const int nbc = g.B * g.B * g.B, Bh = g.Bh, H3 = Bh * Bh * Bh;
+    const int lim = g.nulim;
+    long long* vs = reinterpret_cast<long long*>(pa_smem);                 // [3][H3]
+    float* tile = reinterpret_cast<float*>(vs + 3 * H3);                    // [T3]
+    unsigned* hist = reinterpret_cast<unsigned*>(tile + T3);                // [H3]
+    unsigned* sm_off = hist + H3;                                           // [nbc + 1]
+    float* sdec = reinterpret_cast<float*>(sm_off + nbc + 1);               // NV == 1: [2 lim + 1]
+    float* sthr = sdec + (NV == 1 ? 2 * lim + 1 : 0);                       // NV == 1: [lim + 2]
+    const float* dec = cur.dec;
+    const float* thr = cur.thr;
+    if (NV == 1) {
+        for (int t = threadIdx.x; t < 2 * lim + 1; t += blockDim.x) sdec[t] = cur.dec[t];
+        for (int t = threadIdx.x; t < lim + 2; t += blockDim.x) sthr[t] = cur.thr[t];
+        dec = sdec;
+        thr = sthr;
+    }
+    int bx, by, bz;
+    brick_coords(g, blockIdx.x, &bx, &by, &bz);
+    const int L0 = blockIdx.x * nbc;
+    for (int c = threadIdx.x; c <= nbc; c += blockDim.x) sm_off[c] = s.offsets[L0 + c];
+    for (int t = threadIdx.x; t < H3; t += blockDim.x) {
+        hist[t] = 0u;
+        vs[t] = 0;
+        vs[H3 + t] = 0;
+        vs[2 * H3 + t] = 0;
+    }
+    const int ox = bx * F - 2, oy = by * F - 2, oz = bz * F - 2;
+    for (int t = threadIdx.x; t < T3; t += blockDim.x) {
+        int x = t % T, y = (t / T) % T, z = t / (T * T);
+        int gx = wrapi(ox + x, g.N), gy = wrapi(oy + y, g.N), gz = wrapi(oz + z, g.N);
+        tile[t] = phi[((int64_t)gz * g.N + gy) * g.S + gx];
+    }
+    __syncthreads();
+    const float e0 = cur.est[0], e1 = cur.est[1];
+    const int nbits = 8 * NX, half = 1 << (nbits - 1);
+    const int sb = g.sbits, wmask = (1 << sb) - 1;
+    const float winv = ldexpf(1.0f, -sb);
+    const float inv2q = ldexpf(1.0f, -(nbits + 1));
+    const float two8n = ldexpf(1.0f, nbits);
+    float sacc = 0.0f;
+    int mig = 0;
+    bool migbad = false;
+    const int TT = T * T;
+    const unsigned q1 = min(sm_off[nbc], (unsigned)g.Np);
+    for (unsigned i = min(sm_off[0], q1) + threadIdx.x; i < q1; i += blockDim.x) {
+        int lc = upper_cell(sm_off, nbc, i);
+        int l[3] = {lc % g.B, (lc / g.B) % g.B, lc / (g.B * g.B)};
+        int Q[3], n[3];
+        float wv[3];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            Q[d] = 2 * (load_code<NX>(s.chi, d * g.Np + i) + half) + 1;
+            n[d] = 2 + g.R * l[d] + (Q[d] >> sb);
+            wv[d] = (float)(Q[d] & wmask) * winv;
+        }
+        // CIC gather of the FD4 gradient: per axis, 4 rows of 6 nodes
+        const int base = (n[2] * T + n[1]) * T + n[0];
+        float gx = 0.0f, gy = 0.0f, gz = 0.0f;
+#pragma unroll
+        for (int a = 0; a < 2; ++a) {
+#pragma unroll
+            for (int b = 0; b < 2; ++b) {
+                {   // x rows at (y + a, z + b)
+                    const float* r = tile + base + a * T + b * TT;
+                    float g0 = 8.0f * (r[1] - r[-1]) - (r[2] - r[-2]);
+                    float g1 = 8.0f * (r[2] - r[0]) - (r[3] - r[-1]);
+                    float wyz = (a ? wv[1] : 1.0f - wv[1]) * (b ? wv[2] : 1.0f - wv[2]);
+                    gx += wyz * ((1.0f - wv[0]) * g0 + wv[0] * g1);
+                }
+                {   // y columns at (x + a, z + b)
+                    const float* r = tile + base + a + b * TT;
+                    float g0 = 8.0f * (r[T] - r[-T]) - (r[2 * T] - r[-2 * T]);
+                    float g1 = 8.0f * (r[2 * T] - r[0]) - (r[3 * T] - r[-T]);
+                    float wxz = (a ? wv[0] : 1.0f - wv[0]) * (b ? wv[2] : 1.0f - wv[2]);
+                    gy += wxz * ((1.0f - wv[1]) * g0 + wv[1] * g1);
+                }
+                {   // z columns at (x + a, y + b)
+                    const float* r = tile + base + a + b * T;
+                    float g0 = 8.0f * (r[TT] - r[-TT]) - (r[2 * TT] - r[-2 * TT]);
+                    float g1 = 8.0f * (r[2 * TT] - r[0]) - (r[3 * TT] - r[-TT]);
+                    float wxy = (a ? wv[0] : 1.0f - wv[0]) * (b ? wv[1] : 1.0f - wv[1]);
+                    gz += wxy * ((1.0f - wv[2]) * g0 + wv[2] * g1);
+                }
+            }
+        }
+        const float fsc = -1.0f / 12.0f;
+        const float force[3] = {gx * fsc, gy * fsc, gz * fsc};
+        int e[3];
+        float pv[3], un[3];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            const float vcd = s.vc[(int64_t)d * g.Ncc + L0 + lc];
+            int nu = load_nu<NV>(s.nu, d * g.Np + i, g.nulim);
+            float v = vcd + dec[nu + lim];
+            float p1 = __fmaf_rn(force[d], kick, v);
+            float dd = p1 - vcd;
+            int nu1 = nu_from_thresholds(dd, thr, lim, nu_estimate(dd, e0, e1));
+            store_code<NV>(s.nu, d * g.Np + i, nu1);
+            float p2 = vcd + dec[nu1 + lim];
+            float r2 = p2 - vcd;
+            sacc = __fmaf_rn(r2, r2, sacc);
+            int bin = drift_bin(Q[d], p2, dc, inv2q, two8n, &un[d]);
+            int sh = bin >> nbits;
+            if (sh < -1 || sh > 1) { migbad = true; sh = max(-1, min(1, sh)); }
+            mig = max(mig, abs(sh));
+            e[d] = l[d] + sh + 1;
+            pv[d] = p2;
+        }
+        int ei = e[0] + Bh * (e[1] + Bh * e[2]);
+        atomicAdd(&hist[ei], 1u);
+#pragma unroll
+        for (int d = 0; d < 3; ++d)
+            atomicAdd(reinterpret_cast<unsigned long long*>(&vs[d * H3 + ei]), (unsigned long long)vel_fix(pv[d]));
+        if (dbg.cell_old) {
+            const int cg[3] = {bx * g.B + l[0], by * g.B + l[1], bz * g.B + l[2]};
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                dbg.cell_old[d * g.Np + i] = cg[d];
+                dbg.u_new[d * g.Np + i] = un[d];
+                dbg.p[d * g.Np + i] = pv[d];
+            }
+        }
+    }
+    if (migbad) atomicOr(w.flags, ERR_MIGRATION);
+    __syncthreads();
+    const int cbx = bx * g.B - 1, cby = by * g.B - 1, cbz = bz * g.B - 1;
+    for (int t = threadIdx.x; t < H3; t += blockDim.x) {
+        unsigned h = hist[t];
+        w.ghost[(int64_t)blockIdx.x * H3 + t] = h;
+        if (h) {
+            int ex = t % Bh, ey = (t / Bh) % Bh, ez = t / (Bh * Bh);
+            int L = cell_rank(g, wrapi(cbx + ex, g.Nc), wrapi(cby + ey, g.Nc), wrapi(cbz + ez, g.Nc));
+            atomicAdd(&w.counts_new[L], h);
+#pragma unroll
+            for (int d = 0; d < 3; ++d)
+                atomicAdd(reinterpret_cast<unsigned long long*>(&w.vsum_new[(int64_t)d * g.Ncc + L]),
+                          (unsigned long long)vs[d * H3 + t]);
+        }
+    }
+    __shared__ double red[32];
+    double tot = block_sum_double((double)sacc, red);
+    if (threadIdx.x == 0) w.part[blockIdx.x] = tot;
+    // block max of the migration
+    __shared__ int mmax;
+    if (threadIdx.x == 0) mmax = 0;
+    __syncthreads();
+    if (mig) atomicMax(&mmax, mig);
+    __syncthreads();
+    if (threadIdx.x == 0 && mmax) atomicMax(w.maxmig, mmax);
+}
+
+// ------------------------------------------------------------------ starts
+// For every new cell c: the bricks whose one-cell-halo region holds c, in
+// storage order of the bricks, take consecutive ranges of c's slots starting
+// at offset*[c]: the per-brick histogram entries become per-brick starts.
+// Also v_c* = mean momentum of the cell (fixed point).
+__global__ void k_starts(Geo g, StepScratch w, const unsigned* __restrict__ off_new, float* __restrict__ vc_new) {
+    int L = blockIdx.x * blockDim.x + threadIdx.x;
+    if (L >= g.Ncc) return;
+    const int nbc = g.B * g.B * g.B, Bh = g.Bh, H3 = Bh * Bh * Bh;
+    const int b = L / nbc, lc = L - b * nbc;
+    const int bc[3] = {b % g.nb, (b / g.nb) % g.nb, b / (g.nb * g.nb)};
+    const int l[3] = {lc % g.B, (lc / g.B) % g.B, lc / (g.B * g.B)};
+    int cb[3][3], ce[3][3], nc[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        int k = 0;
+        cb[d][k] = bc[d]; ce[d][k] = l[d] + 1; ++k;
+        if (l[d] == 0) { cb[d][k] = wrapi(bc[d] - 1, g.nb); ce[d][k] = g.B + 1; ++k; }
+        if (l[d] == g.B - 1) { cb[d][k] = wrapi(bc[d] + 1, g.nb); ce[d][k] = 0; ++k; }
+        nc[d] = k;
+    }
+    int bl[27], slot[27], m = 0;
+    for (int z = 0; z < nc[2]; ++z)
+        for (int y = 0; y < nc[1]; ++y)
+            for (int x = 0; x < nc[0]; ++x) {
+                int bi = cb[0][x] + g.nb * (cb[1][y] + g.nb * cb[2][z]);
+                int e = ce[0][x] + Bh * (ce[1][y] + Bh * ce[2][z]);
+                int j = m++;
+                while (j > 0 && bl[j - 1] > bi) { bl[j] = bl[j - 1]; slot[j] = slot[j - 1]; --j; }
+                bl[j] = bi;
+                slot[j] = e;
+            }
+    unsigned run = off_new[L];
+    for (int j = 0; j < m; ++j) {
+        int64_t sidx = (int64_t)bl[j] * H3 + slot[j];
+        unsigned h = w.ghost[sidx];
+        w.ghost[sidx] = run;
+        run += h;
+    }
+    const unsigned cnt = w.counts_new[L];
+    if (run != off_new[L] + cnt) atomicOr(w.flags, ERR_COUNT);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) vc_new[(int64_t)d * g.Ncc + L] = vel_unfix_mean(w.vsum_new[(int64_t)d * g.Ncc + L], cnt);
+}
+
+// ------------------------------------------------------------------ pass B
+template <int NX, int NV>
+__global__ void __launch_bounds__(T_BRICK) k_passB(Geo g, StoreDev so, StoreDev sn, CodecDev cur, CodecDev next,
+                                                   float dc, const unsigned* __restrict__ ghost,
+                                                   const float* __restrict__ vc_new, unsigned* flags) {
+    extern __shared__ unsigned pb_smem[];
+    const int nbc = g.B * g.B * g.B, Bh = g.Bh, H3 = Bh * Bh * Bh;
+    const int lim = g.nulim;
+    unsigned* sm_off = pb_smem;                       // [nbc + 1]
+    unsigned* run = sm_off + nbc + 1;                 // [H3]
+    unsigned* wcnt = run + H3;                        // [W_BRICK * H3]
+    float* sdec = reinterpret_cast<float*>(wcnt + W_BRICK * H3);
+    float* sthr = sdec + (NV == 1 ? 2 * lim + 1 : 0);
+    const float* dec = cur.dec;
+    const float* thr = next.thr;
+    if (NV == 1) {
+        for (int t = threadIdx.x; t < 2 * lim + 1; t += blockDim.x) sdec[t] = cur.dec[t];
+        for (int t = threadIdx.x; t < lim + 2; t += blockDim.x) sthr[t] = next.thr[t];
+        dec = sdec;
+        thr = sthr;
+    }
+    const int L0 = blockIdx.x * nbc;
+    for (int c = threadIdx.x; c <= nbc; c += blockDim.x) sm_off[c] = so.offsets[L0 + c];
+    for (int t = threadIdx.x; t < H3; t += blockDim.x) run[t] = ghost[(int64_t)blockIdx.x * H3 + t];
+    __syncthreads();
+    int bx, by, bz;
+    brick_coords(g, blockIdx.x, &bx, &by, &bz);
+    const int nbits = 8 * NX, half = 1 << (nbits - 1), bmask = (1 << nbits) - 1;
+    const float inv2q = ldexpf(1.0f, -(nbits + 1));
+    const float two8n = ldexpf(1.0f, nbits);
+    const float e0 = next.est[0], e1 = next.est[1];
+    const unsigned p1 = min(sm_off[nbc], (unsigned)g.Np), p0 = min(sm_off[0], p1);
+    for (unsigned base = p0; base < p1; base += blockDim.x) {
+        const unsigned i = base + threadIdx.x;
+        const bool act = i < p1;
+        int ei = 0, chi[3] = {0, 0, 0}, cn[3] = {0, 0, 0};
+        float pv[3] = {0.f, 0.f, 0.f};
+        if (act) {
+            int lc = upper_cell(sm_off, nbc, i);
+            int l[3] = {lc % g.B, (lc / g.B) % g.B, lc / (g.B * g.B)};
+            const int cg[3] = {bx * g.B + l[0], by * g.B + l[1], bz * g.B + l[2]};
+            int e[3];
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                int Q = 2 * (load_code<NX>(so.chi, d * g.Np + i) + half) + 1;
+                int nu = load_nu<NV>(so.nu, d * g.Np + i, g.nulim);
+                float p2 = so.vc[(int64_t)d * g.Ncc + L0 + lc] + dec[nu + lim];
+                float un;
+                int bin = drift_bin(Q, p2, dc, inv2q, two8n, &un);
+                int sh = max(-1, min(1, bin >> nbits));
+                e[d] = l[d] + sh + 1;
+                chi[d] = (bin & bmask) - half;
+                cn[d] = wrapi(cg[d] + sh, g.Nc);
+                pv[d] = p2;
+            }
+            ei = e[0] + Bh * (e[1] + Bh * e[2]);
+        }
+        int pos = stable_round_rank<W_BRICK>(ei, act, run, wcnt, H3);
+        if (act && (pos < 0 || pos >= (int)g.Np)) {
+            atomicOr(flags, ERR_COUNT);
+        } else if (act) {
+            const int Ln = cell_rank(g, cn[0], cn[1], cn[2]);
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                store_code<NX>(sn.chi, d * g.Np + pos, chi[d]);
+                float dd = pv[d] - vc_new[(int64_t)d * g.Ncc + Ln];
+                store_code<NV>(sn.nu, d * g.Np + pos, nu_from_thresholds(dd, thr, lim, nu_estimate(dd, e0, e1)));
+            }
+            if (sn.id) sn.id[pos] = so.id[i];
+        }
+    }
+}
+
+__global__ void k_momentum(int ncc, const long long* __restrict__ vsum, long long* out3) {
+    // exact integer sums of the fixed-point cell momenta
+    for (int d = 0; d < 3; ++d) {
+        long long s = 0;
+        for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < ncc; c += gridDim.x * blockDim.x)
+            s += vsum[(int64_t)d * ncc + c];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+        if ((threadIdx.x & 31) == 0) atomicAdd(reinterpret_cast<unsigned long long*>(&out3[d]), (unsigned long long)s);
+    }
+}
+
+template <int NX, int NV>
+struct Disp {
+    static void passA(const Geo& g, const StoreDev& s, const float* phi, const CodecDev& cur, float kick, float dc,
+                      const StepScratch& w, const DriftDebug& dbg, size_t sm, cudaStream_t st) {
+        k_passA<NX, NV><<<g.nbricks, T_BRICK, sm, st>>>(g, s, phi, cur, kick, dc, w, dbg);
+    }
+    static void passB(const Geo& g, const StoreDev& so, const StoreDev& sn, const CodecDev& cur,
+                      const CodecDev& next, float dc, const unsigned* ghost, const float* vcn, unsigned* flags,
+                      size_t sm, cudaStream_t st) {
+        k_passB<NX, NV><<<g.nbricks, T_BRICK, sm, st>>>(g, so, sn, cur, next, dc, ghost, vcn, flags);
+    }
+};
+
+template <int NX, int NV>
+void set_smem_attrs() {
+    static bool done = false;
+    if (done) return;
+    cudaFuncSetAttribute(k_passA<NX, NV>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_passB<NX, NV>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_deposit<NX>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    done = true;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ launchers
+static inline int nblk(int64_t n, int t) { return (int)((n + t - 1) / t); }
+
+void launch_encode_keys(const Geo& g, const float* pos, const float* vel, unsigned* key, unsigned* val,
+                        unsigned* counts, long long* vsum, unsigned* flags, cudaStream_t st) {
+    if (g.nchi == 1) k_encode_keys<1><<<nblk(g.Np, 256), 256, 0, st>>>(g, pos, vel, key, val, counts, vsum, flags);
+    else k_encode_keys<2><<<nblk(g.Np, 256), 256, 0, st>>>(g, pos, vel, key, val, counts, vsum, flags);
+}
+
+void launch_vc_finalize(const Geo& g, const unsigned* counts, const long long* vsum, float* vc, cudaStream_t st) {
+    k_vc_finalize<<<nblk(g.Ncc, 256), 256, 0, st>>>(g.Ncc, counts, vsum, vc);
+}
+
+int encode_sigma_blocks(const Geo& g) { return (int)std::min<int64_t>(1024, std::max<int64_t>(1, nblk(g.Np, 256))); }
+
+void launch_encode_sigma(const Geo& g, const float* vel, const unsigned* key, const float* vc, double* part,
+                         cudaStream_t st) {
+    k_encode_sigma<<<encode_sigma_blocks(g), 256, 0, st>>>(g, vel, key, vc, part);
+}
+
+void launch_sigma_finalize(const double* part, int nparts, double count, double ratio, double fixed,
+                           double* sigma_out, cudaStream_t st) {
+    k_sigma_finalize<<<1, 256, 0, st>>>(part, nparts, count, ratio, fixed, sigma_out);
+}
+
+void launch_codec_tables(int nulim, const double* tanv, const double* tanh_, const CodecDev& c, cudaStream_t st) {
+    k_codec_tables<<<nblk(nulim + 2, 256), 256, 0, st>>>(nulim, tanv, tanh_, c.sigma, c.dec, c.thr, c.est);
+}
+
+void launch_encode_scatter(const Geo& g, const float* pos, const float* vel, const unsigned* id_in,
+                           const unsigned* key_sorted, const unsigned* perm, const float* vc, const CodecDev& c,
+                           StoreDev s, cudaStream_t st) {
+    int nb = nblk(g.Np, 256);
+    if (g.nchi == 1 && g.nnu == 1) k_encode_scatter<1, 1><<<nb, 256, 0, st>>>(g, pos, vel, id_in, key_sorted, perm, vc, c.thr, c.est, s);
+    else if (g.nchi == 1) k_encode_scatter<1, 2><<<nb, 256, 0, st>>>(g, pos, vel, id_in, key_sorted, perm, vc, c.thr, c.est, s);
+    else if (g.nnu == 1) k_encode_scatter<2, 1><<<nb, 256, 0, st>>>(g, pos, vel, id_in, key_sorted, perm, vc, c.thr, c.est, s);
+    else k_encode_scatter<2, 2><<<nb, 256, 0, st>>>(g, pos, vel, id_in, key_sorted, perm, vc, c.thr, c.est, s);
+}
+
+void launch_decode(const Geo& g, const StoreDev& s, const float* dec, float* pos, float* vel, unsigned* id,
+                   cudaStream_t st) {
+    size_t sm = (size_t)(g.B * g.B * g.B + 1) * sizeof(unsigned);
+    if (g.nchi == 1 && g.nnu == 1) k_decode<1, 1><<<g.nbricks, T_BRICK, sm, st>>>(g, s, dec, pos, vel, id);
+    else if (g.nchi == 1) k_decode<1, 2><<<g.nbricks, T_BRICK, sm, st>>>(g, s, dec, pos, vel, id);
+    else if (g.nnu == 1) k_decode<2, 1><<<g.nbricks, T_BRICK, sm, st>>>(g, s, dec, pos, vel, id);
+    else k_decode<2, 2><<<g.nbricks, T_BRICK, sm, st>>>(g, s, dec, pos, vel, id);
+}
+
+static size_t deposit_smem(const Geo& g) {
+    const int F3 = g.F * g.F * g.F, E = g.B + 1, E3 = E * E * E;
+    return (size_t)F3 * 8 + (size_t)(2 * E3 + 1) * 4;
+}
+
+void launch_deposit(const Geo& g, const StoreDev& s, float* mesh, double scale, cudaStream_t st) {
+    size_t sm = deposit_smem(g);
+    if (g.nchi == 1) {
+        set_smem_attrs<1, 1>(); set_smem_attrs<1, 2>();
+        k_deposit<1><<<g.nbricks, T_BRICK, sm, st>>>(g, s, mesh, scale);
+    } else {
+        set_smem_attrs<2, 1>(); set_smem_attrs<2, 2>();
+        k_deposit<2><<<g.nbricks, T_BRICK, sm, st>>>(g, s, mesh, scale);
+    }
+}
+
+static size_t passA_smem(const Geo& g) {
+    const int T = g.F + 5, H3 = g.Bh * g.Bh * g.Bh, nbc = g.B * g.B * g.B;
+    size_t sm = (size_t)3 * H3 * 8 + (size_t)T * T * T * 4 + (size_t)H3 * 4 + (size_t)(nbc + 1) * 4;
+    if (g.nnu == 1) sm += (size_t)(3 * g.nulim + 3) * 4;
+    return (sm + 15) & ~(size_t)15;
+}
+
+void launch_passA(const Geo& g, const StoreDev& s, const float* phi, const CodecDev& cur, float kick, float dc,
+                  const StepScratch& w, const DriftDebug& dbg, cudaStream_t st) {
+    size_t sm = passA_smem(g);
+    if (g.nchi == 1 && g.nnu == 1) { set_smem_attrs<1, 1>(); Disp<1, 1>::passA(g, s, phi, cur, kick, dc, w, dbg, sm, st); }
+    else if (g.nchi == 1) { set_smem_attrs<1, 2>(); Disp<1, 2>::passA(g, s, phi, cur, kick, dc, w, dbg, sm, st); }
+    else if (g.nnu == 1) { set_smem_attrs<2, 1>(); Disp<2, 1>::passA(g, s, phi, cur, kick, dc, w, dbg, sm, st); }
+    else { set_smem_attrs<2, 2>(); Disp<2, 2>::passA(g, s, phi, cur, kick, dc, w, dbg, sm, st); }
+}
+
+void launch_starts(const Geo& g, const StepScratch& w, const unsigned* off_new, float* vc_new, cudaStream_t st) {
+    k_starts<<<nblk(g.Ncc, 256), 256, 0, st>>>(g, w, off_new, vc_new);
+}
+
+static size_t passB_smem(const Geo& g) {
+    const int H3 = g.Bh * g.Bh * g.Bh, nbc = g.B * g.B * g.B;
+    size_t sm = (size_t)(nbc + 1 + H3 + W_BRICK * H3) * 4;
+    if (g.nnu == 1) sm += (size_t)(3 * g.nulim + 3) * 4;
+    return (sm + 15) & ~(size_t)15;
+}
+
+void launch_passB(const Geo& g, const StoreDev& so, const StoreDev& sn, const CodecDev& cur, const CodecDev& next,
+                  float dc, const StepScratch& w, cudaStream_t st) {
+    size_t sm = passB_smem(g);
+    const float* vcn = sn.vc;
+    if (g.nchi == 1 && g.nnu == 1) { set_smem_attrs<1, 1>(); Disp<1, 1>::passB(g, so, sn, cur, next, dc, w.ghost, vcn, w.flags, sm, st); }
+    else if (g.nchi == 1) { set_smem_attrs<1, 2>(); Disp<1, 2>::passB(g, so, sn, cur, next, dc, w.ghost, vcn, w.flags, sm, st); }
+    else if (g.nnu == 1) { set_smem_attrs<2, 1>(); Disp<2, 1>::passB(g, so, sn, cur, next, dc, w.ghost, vcn, w.flags, sm, st); }
+    else { set_smem_attrs<2, 2>(); Disp<2, 2>::passB(g, so, sn, cur, next, dc, w.ghost, vcn, w.flags, sm, st); }
+}
+
+void launch_momentum(const Geo& g, const long long* vsum, long long* out3, cudaStream_t st) {
+    cudaMemsetAsync(out3, 0, 3 * sizeof(long long), st);
+    k_momentum<<<std::min(1024, nblk(g.Ncc, 256)), 256, 0, st>>>(g.Ncc, vsum, out3);
+}
+
+}  // namespace cube

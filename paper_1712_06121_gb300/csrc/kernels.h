@@ -1,0 +1,123 @@
+// Internal launch interface between libcube's host code and its kernels.
+#pragma once
+
+#include "cube_common.cuh"
+
+namespace cube {
+
+// Stable ranking of one round of blockDim.x items by `digit` in [0, nd):
+// items are ordered by (warp, lane), i.e. by thread index, and equal digits
+// keep that order.  run[nd] holds each digit's next free position and is
+// advanced by the round's counts; wcnt[NWARPS * nd] is scratch.  Every thread
+// of the block must call it (it synchronises).  Returns the item's position,
+// or -1 for inactive threads.
+template <int NWARPS>
+__device__ __forceinline__ int stable_round_rank(int digit, bool active, unsigned* run, unsigned* wcnt, int nd) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int i = threadIdx.x; i < NWARPS * nd; i += blockDim.x) wcnt[i] = 0u;
+    __syncthreads();
+    unsigned act = __ballot_sync(0xffffffffu, active);
+    int lrank = 0;
+    if (active) {
+        unsigned peers = __match_any_sync(act, digit);
+        lrank = __popc(peers & ((1u << lane) - 1u));
+        if (lrank == 0) wcnt[w * nd + digit] = (unsigned)__popc(peers);
+    }
+    __syncthreads();
+    for (int d = threadIdx.x; d < nd; d += blockDim.x) {
+        unsigned s = run[d];
+        for (int ww = 0; ww < NWARPS; ++ww) {
+            unsigned t = wcnt[ww * nd + d];
+            wcnt[ww * nd + d] = s;
+            s += t;
+        }
+        run[d] = s;
+    }
+    __syncthreads();
+    int pos = active ? (int)(wcnt[w * nd + digit] + (unsigned)lrank) : -1;
+    __syncthreads();
+    return pos;
+}
+
+// ------------------------------------------------------------ k_scan.cu
+int scan_tmp_words(int64_t n);
+void exclusive_scan(const unsigned* in, unsigned* out, int64_t n, unsigned* tmp, cudaStream_t st);
+int64_t radix_tmp_words(int64_t n);
+void radix_sort_pairs(unsigned* keys, unsigned* vals, int64_t n, int key_bits, unsigned* tmp, cudaStream_t st);
+
+// ------------------------------------------------------------ k_store.cu
+struct StoreDev {
+    unsigned* counts;   // [Ncc]
+    unsigned* offsets;  // [Ncc + 1]
+    float* vc;          // [3][Ncc]
+    void* chi;          // [3][Np]
+    void* nu;           // [3][Np]
+    unsigned* id;       // [Np] or null
+};
+
+struct CodecDev {
+    float* dec;         // [2 lim + 1]: dec[nu + lim] = tan(pi nu / M) * sqrt(2 sigma^2 / pi)
+    float* thr;         // [lim + 2]: encode thresholds (see nu_from_thresholds)
+    float* est;         // [2]: (M/pi) s and M/pi, for the starting guess
+    double* sigma;      // device scalar
+};
+
+struct DriftDebug {
+    int* cell_old;      // [3][Np] or null
+    float* u_new;       // [3][Np]
+    float* p;           // [3][Np]
+};
+
+struct StepScratch {
+    unsigned* counts_new;   // [Ncc]
+    long long* vsum_new;    // [3][Ncc]
+    unsigned* ghost;        // [nbricks][Bh^3]: histogram, then starts
+    double* part;           // [max(nbricks, blocks)] partial sums
+    unsigned* flags;        // device error flags
+    int* maxmig;            // largest |cell shift| of the step
+};
+
+void launch_encode_keys(const Geo& g, const float* pos, const float* vel, unsigned* key, unsigned* val,
+                        unsigned* counts, long long* vsum, unsigned* flags, cudaStream_t st);
+void launch_vc_finalize(const Geo& g, const unsigned* counts, const long long* vsum, float* vc, cudaStream_t st);
+int encode_sigma_blocks(const Geo& g);
+void launch_encode_sigma(const Geo& g, const float* vel, const unsigned* key_sorted_or_raw, const float* vc,
+                         double* part, cudaStream_t st);
+void launch_sigma_finalize(const double* part, int nparts, double count, double ratio, double fixed,
+                           double* sigma_out, cudaStream_t st);
+void launch_codec_tables(int nulim, const double* tanv, const double* tanh, const CodecDev& c, cudaStream_t st);
+void launch_encode_scatter(const Geo& g, const float* pos, const float* vel, const unsigned* id_in,
+                           const unsigned* key_sorted, const unsigned* perm, const float* vc, const CodecDev& c,
+                           StoreDev s, cudaStream_t st);
+void launch_decode(const Geo& g, const StoreDev& s, const float* dec, float* pos, float* vel, unsigned* id,
+                   cudaStream_t st);
+void launch_deposit(const Geo& g, const StoreDev& s, float* mesh, double scale, cudaStream_t st);
+void launch_passA(const Geo& g, const StoreDev& s, const float* phi, const CodecDev& cur, float kick, float dc,
+                  const StepScratch& w, const DriftDebug& dbg, cudaStream_t st);
+void launch_starts(const Geo& g, const StepScratch& w, const unsigned* off_new, float* vc_new, cudaStream_t st);
+void launch_passB(const Geo& g, const StoreDev& s_old, const StoreDev& s_new, const CodecDev& cur,
+                  const CodecDev& next, float dc, const StepScratch& w, cudaStream_t st);
+void launch_momentum(const Geo& g, const long long* vsum, long long* out3, cudaStream_t st);
+
+// ------------------------------------------------------------ k_fft.cu
+struct FftPlan {
+    int N;              // transform length along every axis
+    float2* tw;         // [N] e^{-2 pi i k / N}
+    float* k2;          // [N] (2 pi f / N)^2, f the signed frequency of index i
+    float* wdec;        // [N] sinc(pi f / N)^(-2 p)  (deconvolution factor per axis)
+    double* wpk;        // [N] sinc(pi f / N)^(-4)    (P(k) window correction per axis)
+};
+
+bool fft_size_supported(int N);                                                    // compiled mesh sizes
+void fft_x_r2c(const FftPlan& p, float* mesh, int S, cudaStream_t st);                 // rows: r2c
+void fft_y(const FftPlan& p, float* mesh, int S, bool inverse, cudaStream_t st);        // y columns
+void fft_z(const FftPlan& p, float* mesh, int S, float g0, bool green, cudaStream_t st); // z (+ Green, inverse)
+void fft_x_c2r(const FftPlan& p, float* mesh, int S, cudaStream_t st);                 // rows: c2r
+int pk_blocks(int N);
+void launch_pk_bin(const FftPlan& p, const float* mesh, int S, int nbins, double pfac, double kfund,
+                   double* part, cudaStream_t st);
+void launch_pk_reduce(const double* part, int nblocks, int nbins, double* k, double* pk, double* nm,
+                      cudaStream_t st);
+void launch_unpad(const float* mesh, int N, int S, float* out, cudaStream_t st);
+
+}  // namespace cube

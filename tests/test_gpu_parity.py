@@ -1,0 +1,378 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle.
+
+Integer work (counts, offsets, order, chi, nu, ids) must be bit-exact when
+both sides start from identical inputs: the same float particles for encode,
+the GPU's exported drifted particles for the re-sort.  The fixed-point cell
+velocities v_c are bit-exact too.  Densities (exact integer CIC weights on
+both sides) within 1e-5 of the mean; the potential (FP32 FFT) within 1e-4 of
+its largest value; the power spectrum within 1e-4 relative.
+"""
+import numpy as np
+import pytest
+
+import synth
+from oracle import layout, mesh, pm
+
+from gpu_util import assert_store_equal, oracle_params, read_store
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def cube():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from conftest import build_lib
+    build_lib()
+    import paper_1712_06121_gb300 as c
+    torch.cuda.set_device(0)
+    return c
+
+
+def _ics(nps, nf, name="pm64", seed=None):
+    w = synth.WORKLOADS[name]
+    return w, synth.make_ics(w, n_part_side=nps, n_fine=nf, seed=seed)
+
+
+def _ctx(cube, nf, n, xb, vb, w, brick=0, deconv=2):
+    om, ol, _ = w.omega()
+    prm = cube.make_params(nf, n, x_bytes=xb, v_bytes=vb, box=w.box, omega_m=om, omega_l=ol, brick=brick,
+                           deconv_power=deconv)
+    return prm, cube.cube_create(prm, torch.cuda.current_stream())
+
+
+CODES = [(1, 1), (1, 2), (2, 1), (2, 2)]
+
+
+# ---------------------------------------------------------------- encode / decode
+@pytest.mark.parametrize("xb,vb", CODES)
+@pytest.mark.parametrize("nps,nf", [(32, 64), (24, 48)])
+def test_encode_matches_oracle(cube, xb, vb, nps, nf):
+    w, ic = _ics(nps, nf)
+    prm, ctx = _ctx(cube, nf, nps ** 3, xb, vb, w)
+    try:
+        cube.cube_encode(ctx, ic.pos, ic.vel, ic.ids, w.a_init, ic.sigma_1d)
+        g = read_store(cube, ctx)
+        P = oracle_params(pm, prm, g["brick"])
+        ref = pm.encode(P, ic.pos, ic.vel, ic.ids, w.a_init, g["sigma"], snap=False)
+        assert g["sigma"] == pytest.approx(pm.codec.snap_sigma(ic.sigma_1d), rel=1e-14)
+        assert_store_equal(g, ref, f"encode x{xb}v{vb}")
+    finally:
+        cube.cube_destroy(ctx)
+
+
+def test_encode_measured_sigma(cube):
+    w, ic = _ics(32, 64)
+    prm, ctx = _ctx(cube, 64, 32 ** 3, 1, 2, w)
+    try:
+        cube.cube_encode(ctx, torch.from_numpy(ic.pos).cuda(), torch.from_numpy(ic.vel).cuda(), None,
+                         w.a_init, 0.0)
+        g = read_store(cube, ctx)
+        ref = pm.encode(oracle_params(pm, prm, g["brick"]), ic.pos, ic.vel, None, w.a_init, 0.0)
+        assert g["sigma"] == pytest.approx(ref.sigma, rel=1e-12)
+        assert np.array_equal(g["ids"], ref.ids)          # NULL ids -> input index
+    finally:
+        cube.cube_destroy(ctx)
+
+
+@pytest.mark.parametrize("xb,vb", CODES)
+def test_decode_matches_oracle(cube, xb, vb):
+    w, ic = _ics(32, 64)
+    n = 32 ** 3
+    prm, ctx = _ctx(cube, 64, n, xb, vb, w)
+    try:
+        cube.cube_encode(ctx, ic.pos, ic.vel, ic.ids, w.a_init, ic.sigma_1d)
+        g = read_store(cube, ctx)
+        ref = pm.encode(oracle_params(pm, prm, g["brick"]), ic.pos, ic.vel, ic.ids, w.a_init, g["sigma"],
+                        snap=False)
+        pos = torch.empty((3, n), dtype=torch.float32, device="cuda")
+        vel = torch.empty((3, n), dtype=torch.float32, device="cuda")
+        ids = torch.empty(n, dtype=torch.int32, device="cuda")
+        cube.cube_decode(ctx, pos, vel, ids)
+        rpos, rvel, rids = pm.decode(ref)
+        assert np.array_equal(pos.cpu().numpy(), rpos.astype(np.float32))
+        assert np.array_equal(ids.cpu().numpy().view(np.uint32), rids)
+        err = np.abs(vel.cpu().numpy() - rvel)
+        assert np.max(err) <= 4e-7 * np.max(np.abs(rvel))
+        # host-pointer path returns the same bytes
+        hp = np.empty((3, n), np.float32)
+        hv = np.empty((3, n), np.float32)
+        cube.cube_decode(ctx, hp, hv, None)
+        assert np.array_equal(hp, pos.cpu().numpy()) and np.array_equal(hv, vel.cpu().numpy())
+    finally:
+        cube.cube_destroy(ctx)
+
+
+def test_section_2_1_worked_example_on_gpu(cube):
+    """Section 2.1's example along x (N_c = 4, 1-byte codes): chi = (-128, 127,
+    0, 60), rho_c = (1, 0, 2, 1) decode to x = (0.001953125, 2.998046875,
+    2.501953125, 3.736328125) coarse cells; y and z sit in bin 0 of cell 0."""
+    x = np.array([0.001953125, 2.998046875, 2.501953125, 3.736328125])
+    n = 4
+    pos = np.zeros((3, n), np.float32)
+    pos[0] = 4 * x                      # fine units, R = 4
+    pos[1] = pos[2] = 4 * 0.001953125
+    vel = np.zeros((3, n), np.float32)
+    prm = cube.make_params(16, n, x_bytes=1, v_bytes=1, box=10.0)
+    ctx = cube.cube_create(prm, torch.cuda.current_stream())
+    try:
+        cube.cube_encode(ctx, pos, vel, None, 0.5, 1.0)
+        g = read_store(cube, ctx)
+        assert g["chi"][0].tolist() == [-128, 127, 0, 60]
+        assert g["chi"][1].tolist() == [-128] * 4
+        row = layout.storage_index(np.arange(4), 0, 0, 4, g["brick"])
+        assert g["counts"][row].tolist() == [1, 0, 2, 1]
+        out = np.empty((3, n), np.float32)
+        cube.cube_decode(ctx, out, np.empty((3, n), np.float32), None)
+        assert np.array_equal(out[0].astype(np.float64) / 4, x)
+    finally:
+        cube.cube_destroy(ctx)
+
+
+# ---------------------------------------------------------------- mesh
+@pytest.mark.parametrize("nps,nf,xb", [(32, 64, 1), (24, 48, 2), (8, 16, 1), (12, 24, 1), (48, 96, 1)])
+def test_density_matches_oracle(cube, nps, nf, xb):
+    w, ic = _ics(nps, nf)
+    prm, ctx = _ctx(cube, nf, nps ** 3, xb, 1, w)
+    try:
+        cube.cube_encode(ctx, ic.pos, ic.vel, ic.ids, w.a_init, ic.sigma_1d)
+        g = read_store(cube, ctx)
+        ref = pm.encode(oracle_params(pm, prm, g["brick"]), ic.pos, ic.vel, ic.ids, w.a_init, g["sigma"],
+                        snap=False)
+        rho = np.empty((nf, nf, nf), np.float32)
+        cube.cube_density(ctx, rho)
+        want = pm.density(ref)
+        assert np.max(np.abs(rho - want)) <= 1e-5
+        assert np.sum(rho, dtype=np.float64) == pytest.approx(nf ** 3, rel=1e-6)
+    finally:
+        cube.cube_destroy(ctx)
+
+
+@pytest.mark.parametrize("nps,nf,deconv", [(8, 16, 2), (12, 24, 2), (16, 32, 0), (24, 48, 2), (32, 64, 1),
+                                           (48, 96, 2), (64, 128, 2), (96, 192, 2)])
+def test_potential_matches_oracle(cube, nps, nf, deconv):
+    w, ic = _ics(nps, nf)
+    prm, ctx = _ctx(cube, nf, nps ** 3, 1, 1, w, deconv=deconv)
+    try:
+        cube.cube_encode(ctx, ic.pos, ic.vel, ic.ids, w.a_init, ic.sigma_1d)
+        rho = np.empty((nf, nf, nf), np.float32)
+        cube.cube_density(ctx, rho)
+        phi = np.empty((nf, nf, nf), np.float32)
+        cube.cube_potential(ctx, phi)
+        want = mesh.potential(rho.astype(np.float64), prm.omega_m, deconv)
+        err = np.max(np.abs(phi - want)) / np.max(np.abs(want))
+        assert err <= 1e-4, err
+    finally:
+        cube.cube_destroy(ctx)
+
+
+@pytest.mark.parametrize("nps,nf", [(32, 64), (48, 96)])
+def test_power_spectrum_matches_oracle(cube, nps, nf):
+    w, ic = _ics(nps, nf)
+    prm, ctx = _ctx(cube, nf, nps ** 3, 1, 2, w)
+    try:
+        cube.cube_encode(ctx, ic.pos, ic.vel, ic.ids, w.a_init, ic.sigma_1d)
+        g = read_store(cube, ctx)
+        ref = pm.encode(oracle_params(pm, prm, g["brick"]), ic.pos, ic.vel, ic.ids, w.a_init, g["sigma"],
+                        snap=False)
+        nb = nf // 2
+        k, p, m = (np.empty(nb) for _ in range(3))
+        cube.cube_power_spectrum(ctx, nb, k, p, m)
+        rk, rp, rm = pm.power_spectrum(ref, nb)
+        assert np.array_equal(m, rm)
+        assert np.allclose(k, rk, rtol=1e-12)
+        assert np.allclose(p, rp, rtol=1e-4)
+    finally:
+        cube.cube_destroy(ctx)
+
+
+# ---------------------------------------------------------------- the step
+def _drifted(cube, ctx, n):
+    cell = np.empty((3, n), np.int32)
+    u = np.empty((3, n), np.float32)
+    p = np.empty((3, n), np.float32)
+    sig = cube.cube_debug_drifted(ctx, cell, u, p)
+    return cell, u, p, sig
+
+
+@pytest.mark.parametrize("xb,vb", CODES)
+@pytest.mark.parametrize("nps,nf,brick", [(32, 64, 0), (32, 64, 2), (24, 48, 0), (16, 32, 1)])
+def test_step_resort_is_bit_exact(cube, xb, vb, nps, nf, brick):
+    """Fig. update_xp: the GPU's re-sorted store equals the oracle's re-encode
+    of the GPU's drifted particles (codes, counts, order, v_c), for 3 steps."""
+    w, ic = _ics(nps, nf)
+    n = nps ** 3
+    prm, ctx = _ctx(cube, nf, n, xb, vb, w, brick=brick)
+    try:
+        cube.cube_encode(ctx, ic.pos, ic.vel, ic.ids, w.a_init, ic.sigma_1d)
+        cube.cube_keep_drifted(ctx, True)
+        sched = synth.uniform_schedule(w.a_init, 0.05, 3)
+        for i in range(3):
+            before = read_store(cube, ctx)
+            cube.cube_pm_step(ctx, sched[i], sched[i + 1])
+            cell, u, p, sig = _drifted(cube, ctx, n)
+            g = read_store(cube, ctx)
+            P = oracle_params(pm, prm, g["brick"])
+            # the drifted cells are the old store's cells in old storage order
+            old = pm.Store(P, before["counts"], before["vc"], before["chi"], before["nu"], before["ids"],
+                           before["sigma"], before["a"], before["a_p"])
+            assert np.array_equal(np.stack(old.cells()), cell)
+            ref = pm.encode_drifted(P, cell, u, p, before["ids"], sig, g["a"], g["a_p"])
+            assert_store_equal(g, ref, f"step {i} x{xb}v{vb}")
+    finally:
+        cube.cube_destroy(ctx)
+
+
+def test_step_matches_oracle_step(cube):
+    """One step from the same store: the GPU's drifted offsets and kicked
+    momenta agree with the oracle's FP64 step (FP32 force differences flip a
+    few velocity codes by one bin at most)."""
+    w, ic = _ics(32, 64)
+    n = 32 ** 3
+    prm, ctx = _ctx(cube, 64, n, 2, 2, w)
+    try:
+        cube.cube_encode(ctx, ic.pos, ic.vel, ic.ids, w.a_init, ic.sigma_1d)
+        g0 = read_store(cube, ctx)
+        P = oracle_params(pm, prm, g0["brick"])
+        st = pm.encode(P, ic.pos, ic.vel, ic.ids, w.a_init, g0["sigma"], snap=False)
+        cube.cube_keep_drifted(ctx, True)
+        cube.cube_pm_step(ctx, w.a_init, w.a_init + 0.008)
+        cell, u, p, sig = _drifted(cube, ctx, n)
+        ref = pm.step(st, w.a_init, w.a_init + 0.008, keep_drifted=True)
+        assert np.array_equal(ref.extra["cell_old"], cell)
+        dp = np.abs(p - ref.extra["p"])
+        bin_v = np.max(np.abs(np.diff(pm.codec.vel_decode_offset(np.arange(-3, 4), g0["sigma"], 2))))
+        assert np.mean(dp > 0) < 0.01 and np.max(dp) <= 1.01 * bin_v
+        assert np.max(np.abs(u - ref.extra["u_new"])) < 1e-5
+        assert sig == pytest.approx(ref.sigma, rel=1e-12)
+    finally:
+        cube.cube_destroy(ctx)
+
+
+def test_full_run_pm64_matches_oracle(cube):
+    """The 64^3 / 128^3 EdS x1v2 workload, 10 steps a = 0.02 -> 0.1: RMS
+    displacement difference (matched by id) <= 1e-3 fine cells and P(k)
+    within 0.5% for k < k_Nyquist / 2."""
+    w = synth.WORKLOADS["pm64"]
+    ic = synth.make_ics(w)
+    n = w.n_particles
+    prm, ctx = _ctx(cube, w.n_fine, n, w.x_bytes, w.v_bytes, w)
+    sched = synth.uniform_schedule(w.a_init, w.a_final, w.n_steps)
+    try:
+        cube.cube_encode(ctx, ic.pos, ic.vel, ic.ids, w.a_init, ic.sigma_1d)
+        for i in range(w.n_steps):
+            cube.cube_pm_step(ctx, sched[i], sched[i + 1])
+        pos = np.empty((3, n), np.float32)
+        vel = np.empty((3, n), np.float32)
+        ids = np.empty(n, np.uint32)
+        cube.cube_decode(ctx, pos, vel, ids)
+        nb = w.n_fine // 2
+        k, pk, nm = (np.empty(nb) for _ in range(3))
+        cube.cube_power_spectrum(ctx, nb, k, pk, nm)
+        g0 = None
+    finally:
+        cube.cube_destroy(ctx)
+    P = pm.Params(n_fine=w.n_fine, n_particles=n, x_bytes=w.x_bytes, v_bytes=w.v_bytes, box=w.box)
+    st = pm.run(pm.encode(P, ic.pos, ic.vel, ic.ids, w.a_init, ic.sigma_1d), sched)
+    rpos, rvel, rids = pm.decode(st)
+    order_g = np.argsort(ids)
+    order_r = np.argsort(rids)
+    d = pos[:, order_g].astype(np.float64) - rpos[:, order_r]
+    d -= w.n_fine * np.round(d / w.n_fine)
+    rms = np.sqrt(np.mean(np.sum(d * d, axis=0)))
+    assert rms <= 1e-3, rms
+    rk, rp, rm = pm.power_spectrum(st, nb)
+    sel = k < 0.5 * np.pi * w.n_fine / w.box
+    assert np.max(np.abs(pk[sel] / rp[sel] - 1)) <= 5e-3
+    del g0
+
+
+# ---------------------------------------------------------------- errors, determinism
+def test_call_order_and_argument_errors(cube):
+    w, ic = _ics(16, 32)
+    prm, ctx = _ctx(cube, 32, 16 ** 3, 1, 1, w)
+    try:
+        with pytest.raises(cube.CubeError) as e:
+            cube.cube_pm_step(ctx, 0.02, 0.03)
+        assert e.value.status == cube.CUBE_E_STATE
+        cube.cube_encode(ctx, ic.pos, ic.vel, ic.ids, 0.02, ic.sigma_1d)
+        with pytest.raises(cube.CubeError) as e:
+            cube.cube_pm_step(ctx, 0.03, 0.04)
+        assert e.value.status == cube.CUBE_E_STATE
+        with pytest.raises(cube.CubeError) as e:
+            cube.cube_pm_step(ctx, 0.02, 0.02)
+        assert e.value.status == cube.CUBE_E_ARG
+        with pytest.raises(cube.CubeError) as e:
+            cube.cube_debug_drifted(ctx, np.empty((3, 4096), np.int32), np.empty((3, 4096), np.float32),
+                                    np.empty((3, 4096), np.float32))
+        assert e.value.status == cube.CUBE_E_STATE
+    finally:
+        cube.cube_destroy(ctx)
+
+
+def test_migration_beyond_one_cell_is_latched(cube):
+    """A step far too long for the mesh moves particles more than one coarse
+    cell: the kernels clamp the move, the flag is latched and the next
+    synchronising call reports CUBE_E_MIGRATION."""
+    n = 16 ** 3
+    g = np.arange(16) * 2 + 0.5
+    z, y, x = np.meshgrid(g, g, g, indexing="ij")
+    pos = np.stack([x.ravel(), y.ravel(), z.ravel()]).astype(np.float32)
+    vel = np.zeros((3, n), np.float32)
+    vel[0] = 50.0                                    # 50 fine cells x H0
+    prm = cube.make_params(32, n, x_bytes=1, v_bytes=2, box=50.0)
+    ctx = cube.cube_create(prm, torch.cuda.current_stream())
+    try:
+        cube.cube_encode(ctx, pos, vel, None, 0.5, 1.0)
+        cube.cube_pm_step(ctx, 0.5, 0.6)
+        with pytest.raises(cube.CubeError) as e:
+            cube.cube_stats_get(ctx)
+        assert e.value.status == cube.CUBE_E_MIGRATION
+    finally:
+        cube.cube_destroy(ctx)
+
+
+def test_nonfinite_input_is_reported(cube):
+    w, ic = _ics(16, 32)
+    pos = ic.pos.copy()
+    pos[1, 7] = np.nan
+    prm, ctx = _ctx(cube, 32, 16 ** 3, 1, 1, w)
+    try:
+        cube.cube_encode(ctx, pos, ic.vel, ic.ids, 0.02, ic.sigma_1d)
+        with pytest.raises(cube.CubeError) as e:
+            cube.cube_stats_get(ctx)
+        assert e.value.status == cube.CUBE_E_OVERFLOW
+    finally:
+        cube.cube_destroy(ctx)
+
+
+def _run_decoded(cube, ic, w, nps, nf, brick, steps=3):
+    n = nps ** 3
+    prm, ctx = _ctx(cube, nf, n, 1, 2, w, brick=brick)
+    try:
+        cube.cube_encode(ctx, ic.pos, ic.vel, ic.ids, w.a_init, ic.sigma_1d)
+        sched = synth.uniform_schedule(w.a_init, 0.05, steps)
+        for i in range(steps):
+            cube.cube_pm_step(ctx, sched[i], sched[i + 1])
+        pos, vel, ids = np.empty((3, n), np.float32), np.empty((3, n), np.float32), np.empty(n, np.uint32)
+        cube.cube_decode(ctx, pos, vel, ids)
+        o = np.argsort(ids)
+        return pos[:, o], vel[:, o], read_store(cube, ctx)
+    finally:
+        cube.cube_destroy(ctx)
+
+
+def test_runs_are_deterministic_and_brick_invariant(cube):
+    """Section 3: different tilings give exactly the same results.  Two runs
+    are bit-identical, and brick sides 1, 2, 4 give the same particles."""
+    w, ic = _ics(32, 64)
+    a = _run_decoded(cube, ic, w, 32, 64, 4)
+    b = _run_decoded(cube, ic, w, 32, 64, 4)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+    for k in ("counts", "chi", "nu", "ids", "vc"):
+        assert np.array_equal(a[2][k], b[2][k])
+    for brick in (1, 2):
+        c = _run_decoded(cube, ic, w, 32, 64, brick)
+        assert np.array_equal(a[0], c[0]) and np.array_equal(a[1], c[1])
