@@ -40,6 +40,8 @@ def parse():
     ap.add_argument("--workload", default="pm256")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--nps", type=int, default=0,
+                    help="particles per side (mesh = 2 x nps) instead of the workload's, for small profiling cases")
     return ap.parse_args()
 
 
@@ -236,8 +238,11 @@ def config_of(w):
 
 def main():
     args = parse()
+    import dataclasses
     import synth
     w = synth.WORKLOADS[args.workload]
+    if args.nps:
+        w = dataclasses.replace(w, name=f"{w.name}@{args.nps}", n_part_side=args.nps, n_fine=2 * args.nps)
     if args.impl == "reference":
         run_reference(args, w)
         return

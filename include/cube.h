@@ -218,8 +218,9 @@ cube_status cube_debug_drifted(cube_ctx* ctx, int32_t* cell_old, float* u_new, f
    0 setup (clears the new-store counters; no kernel), 1 deposit (CIC density),
    2 fft_x_r2c, 3 fft_y_fwd, 4 fft_z_green (z forward, Green's function, z
    inverse), 5 fft_y_inv, 6 fft_x_c2r, 7 pass_a (decode, force gather, kick,
-   drift, new-cell histogram), 8 codec (next codec scale and tables), 9 scan
-   (offsets of the new counts), 10 starts (per-brick starts, new v_c),
+   drift, per-brick histograms of the new cells), 8 codec (next codec scale
+   and tables), 9 scan (of the histograms in cell-major, brick-minor order:
+   per-brick starts), 10 cells (new counts, offsets and v_c),
    11 pass_b (stable scatter and encode).  ("timing or statistics taken in
    the simulation", Section 2.3.3, "finalize".) */
 #define CUBE_PHASES 12

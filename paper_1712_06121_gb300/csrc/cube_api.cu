@@ -149,7 +149,7 @@ struct cube_ctx {
     // per-step scratch
     long long* vsum = nullptr;
     unsigned* ghost = nullptr;
-    double* part = nullptr;
+    float* part = nullptr;
     int npart = 0;
     unsigned* flags = nullptr;
     int* maxmig = nullptr;
@@ -316,12 +316,12 @@ cube_status cube_create(const cube_params* params, void* cuda_stream, cube_ctx**
     AL(c->tanv, (size_t)(g.nulim + 1) * 8);
     AL(c->tanh_, (size_t)(g.nulim + 2) * 8);
     AL(c->vsum, 3 * Ncc * 8);
-    AL(c->ghost, (size_t)g.nbricks * H3 * 4);
+    AL(c->ghost, ((size_t)g.nbricks * H3 + 1) * 4);
     c->npart = std::max(g.nbricks, 1024);
-    AL(c->part, (size_t)c->npart * 8);
+    AL(c->part, (size_t)c->npart * 4);
     AL(c->flags, 4);
     AL(c->maxmig, 4);
-    AL(c->scan_tmp, (size_t)scan_tmp_words(g.Ncc + 1) * 4 + 64);
+    AL(c->scan_tmp, (size_t)scan_tmp_words(std::max<int64_t>(g.Ncc + 1, (int64_t)g.nbricks * H3 + 1)) * 4 + 64);
     AL(c->mom, 3 * 8);
     AL(c->mesh, (size_t)g.N * g.N * g.S * 4);
     FftPlan& f = c->fft;
@@ -422,7 +422,7 @@ cube_status cube_encode(cube_ctx* c, const float* pos, const float* vel, const u
 // kernels launched per phase of a step (see cube_phase_name)
 const int kPhaseKernels[CUBE_PHASES] = {0, 1, 1, 1, 1, 1, 1, 1, 2, 4, 1, 1};
 const char* kPhaseNames[CUBE_PHASES] = {"setup", "deposit", "fft_x_r2c", "fft_y_fwd", "fft_z_green", "fft_y_inv",
-                                        "fft_x_c2r", "pass_a", "codec", "scan", "starts", "pass_b"};
+                                        "fft_x_c2r", "pass_a", "codec", "scan", "cells", "pass_b"};
 
 static void mark(cube_ctx* c, int boundary) {
     if (c->prof_steps < c->prof_max) cudaEventRecord(c->prof_ev[(size_t)c->prof_steps * (CUBE_PHASES + 1) + boundary], c->st);
@@ -476,7 +476,6 @@ cube_status cube_pm_step(cube_ctx* c, double a_from, double a_to) {
     }
     CK(cudaEventRecord(c->ev0, c->st));
     mark(c, 0);
-    CK(cudaMemsetAsync(c->counts[kn], 0, (size_t)g.Ncc * 4, c->st));
     CK(cudaMemsetAsync(c->vsum, 0, (size_t)g.Ncc * 24, c->st));
     CK(cudaMemsetAsync(c->maxmig, 0, 4, c->st));
     mark(c, 1);
@@ -488,9 +487,9 @@ cube_status cube_pm_step(cube_ctx* c, double a_from, double a_to) {
     launch_sigma_finalize(c->part, g.nbricks, 3.0 * (double)g.Np, ratio, 0.0, c->codec[kn].sigma, c->st);
     launch_codec_tables(g.nulim, c->tanv, c->tanh_, c->codec[kn], c->st);
     mark(c, 9);
-    exclusive_scan(c->counts[kn], c->offsets[kn], g.Ncc, c->scan_tmp, c->st);
+    exclusive_scan(c->ghost, c->ghost, (int64_t)g.nbricks * (g.Bh * g.Bh * g.Bh), c->scan_tmp, c->st);
     mark(c, 10);
-    launch_starts(g, w, c->offsets[kn], c->vc[kn], c->st);
+    launch_cells(g, w, c->offsets[kn], c->vc[kn], c->st);
     mark(c, 11);
     launch_passB(g, c->store(k), c->store(kn), c->codec[k], c->codec[kn], dc, w, c->st);
     mark(c, 12);

@@ -85,6 +85,48 @@ __device__ __forceinline__ int load_code(const void* base, int64_t idx) {
     return (int)reinterpret_cast<const int16_t*>(base)[idx];
 }
 
+// ---- flattened (cell-major, brick-minor) order of the per-brick histograms
+// A brick b sees the cells of its one-cell halo region, local index e in
+// [0, Bh^3).  A coarse cell c lies in the regions of n_x n_y n_z bricks
+// (per axis: its home brick, plus the lower neighbour if it is the first
+// cell of the brick, plus the upper one if it is the last).  Ordering the
+// (cell, brick) pairs by cell storage rank, then brick storage rank, gives a
+// permutation of the nbricks * Bh^3 (brick, e) pairs; an exclusive scan in
+// that order yields, for each pair, where brick b's particles moving into
+// cell c start (stable by old index, since bricks are in storage order).
+
+// candidates per axis for a cell at brick-local coordinate l
+__host__ __device__ __forceinline__ int ncand(int l, int B) { return 1 + (l == 0) + (l == B - 1); }
+// number of candidate slots of the cells before local coordinate l on an axis
+__host__ __device__ __forceinline__ int ncand_before(int l) { return l + (l > 0); }
+
+// first flattened slot of the cell with home brick hb (storage rank) and
+// brick-local coordinates l[3]
+__host__ __device__ __forceinline__ int64_t flat_base(const Geo& g, int hb, const int* l) {
+    const int S1 = g.B + 2, S2 = S1 * S1;
+    const int pre = ncand_before(l[2]) * S2 + ncand(l[2], g.B) * (ncand_before(l[1]) * S1 + ncand(l[1], g.B) * ncand_before(l[0]));
+    return (int64_t)hb * (S2 * S1) + pre;
+}
+
+// flattened slot of (brick with coordinates bc[3], halo-region index e[3])
+__host__ __device__ __forceinline__ int64_t flat_slot(const Geo& g, const int* bc, const int* e) {
+    int l[3], hbc[3], rank = 0;
+#pragma unroll
+    for (int d = 2; d >= 0; --d) {
+        const int c = wrapi(bc[d] * g.B - 1 + e[d], g.Nc);
+        l[d] = c % g.B;
+        hbc[d] = c / g.B;
+        // candidate brick coordinates on this axis, ranked by value
+        const int lo = (l[d] == 0) ? wrapi(hbc[d] - 1, g.nb) : -1;
+        const int hi = (l[d] == g.B - 1) ? wrapi(hbc[d] + 1, g.nb) : -1;
+        const int me = bc[d];
+        int r = (hbc[d] < me) + (lo >= 0 && lo < me) + (hi >= 0 && hi < me);
+        rank = rank * ncand(l[d], g.B) + r;
+    }
+    const int hb = hbc[0] + g.nb * (hbc[1] + g.nb * hbc[2]);
+    return flat_base(g, hb, l) + rank;
+}
+
 // velocity code clamped to the table range [-lim, lim] (the encoder never
 // writes anything else; the clamp keeps table reads in bounds regardless)
 template <int NB>
@@ -96,6 +138,46 @@ template <int NB>
 __device__ __forceinline__ void store_code(void* base, int64_t idx, int v) {
     if (NB == 1) reinterpret_cast<int8_t*>(base)[idx] = (int8_t)v;
     else reinterpret_cast<int16_t*>(base)[idx] = (int16_t)v;
+}
+
+// Asynchronous global -> shared copies (cp.async): all copies of a tile are
+// issued before any is waited for, so the tile's load latency is paid once.
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+// Exact sum of a 64-bit integer over the lanes of `peers` (every lane of the
+// group calls it with the same mask): values biased to [0, 2^63), split into
+// three 21-bit chunks summed with 32-bit warp reductions, recombined mod 2^64.
+// Requires |v| < 2^62.
+__device__ __forceinline__ long long group_sum_i64(unsigned peers, long long v) {
+    const unsigned long long u = (unsigned long long)v + (1ull << 62);
+    const unsigned s0 = __reduce_add_sync(peers, (unsigned)(u & 0x1FFFFFull));
+    const unsigned s1 = __reduce_add_sync(peers, (unsigned)((u >> 21) & 0x1FFFFFull));
+    const unsigned s2 = __reduce_add_sync(peers, (unsigned)(u >> 42));
+    const unsigned long long t = (unsigned long long)s0 + ((unsigned long long)s1 << 21) +
+                                 ((unsigned long long)s2 << 42);
+    return (long long)(t - (unsigned long long)__popc(peers) * (1ull << 62));
+}
+
+// 64-bit add into shared memory from 32-bit atomics: the low word's
+// wrap-arounds are carried into the high word, so the final value is the
+// exact sum mod 2^64 whatever the order.  lohi = {low word, high word}.
+__device__ __forceinline__ void smem_add_u64(unsigned* lohi, unsigned long long u) {
+    const unsigned lo = (unsigned)u, hi = (unsigned)(u >> 32);
+    const unsigned old = atomicAdd(&lohi[0], lo);
+    const unsigned up = hi + ((old + lo < old) ? 1u : 0u);
+    if (up) atomicAdd(&lohi[1], up);
 }
 
 // Drift inside the old coarse cell, identical in both re-sort passes:

@@ -142,8 +142,22 @@ __device__ __forceinline__ void tile_fft(float2* buf, const float2* tw) {
     }
 }
 
+// twiddle table into shared memory (asynchronous; waited for with the tile)
 __device__ __forceinline__ void load_tw(float2* stw, const float2* tw, int N) {
-    for (int i = threadIdx.x; i < N; i += blockDim.x) stw[i] = tw[i];
+    for (int i = threadIdx.x; i < N; i += blockDim.x) cp_async8(&stw[i], &tw[i]);
+}
+
+// NC-column tile of rows 0..n-1 (row stride `rs` complex) into buf[row][NC]:
+// 16-byte copies of column pairs; pairs starting at or past `ncol` are zeroed
+// instead of read (the second column of the last pair may be the row's
+// padding slot, which exists in memory and is never written back)
+__device__ __forceinline__ void load_columns(float2* buf, const float2* src, int n, int64_t rs, int c0, int ncol) {
+    for (int q = threadIdx.x; q < n * (NC / 2); q += blockDim.x) {
+        const int r = q / (NC / 2), cp = 2 * (q % (NC / 2));
+        float2* d = &buf[(r << LOG_NC) + cp];
+        if (c0 + cp < ncol) cp_async16(d, src + r * rs + c0 + cp);
+        else d[0] = d[1] = make_float2(0.f, 0.f);
+    }
 }
 
 // ------------------------------------------------------------ x sweep, r2c
@@ -158,8 +172,9 @@ __global__ void __launch_bounds__(FFT_T) k_fft_x_r2c(float* mesh, int S, const f
     for (int t = threadIdx.x; t < h * NC; t += FFT_T) {
         const int k = t % h, c = t / h;
         const float2* src = reinterpret_cast<const float2*>(mesh + (row0 + c) * S);
-        buf[sidx<true>(k, c)] = src[k];
+        cp_async8(&buf[sidx<true>(k, c)], &src[k]);
     }
+    cp_async_wait_all();
     __syncthreads();
     tile_fft<h, 1, 2, false, true>(buf, stw);
     // X[k] = (Z[k] + Z*[h-k])/2 - i W^k (Z[k] - Z*[h-k])/2, k = 0..h
@@ -197,10 +212,9 @@ __global__ void __launch_bounds__(FFT_T) k_fft_x_c2r(float* mesh, int S, const f
     for (int t = threadIdx.x; t < (h + 1) * NC; t += FFT_T) {
         const int k = t % (h + 1), c = t / (h + 1);
         const float2* src = reinterpret_cast<const float2*>(mesh + (row0 + c) * S);
-        const float2 v = src[k];
-        if (k < h) buf[sidx<true>(k, c)] = v;
-        else xh[c] = v;
+        cp_async8(k < h ? &buf[sidx<true>(k, c)] : &xh[c], &src[k]);
     }
+    cp_async_wait_all();
     __syncthreads();
     // Z[k] = E + i O, E = X[k] + X*[h-k], O = W^-k (X[k] - X*[h-k])
     for (int t = threadIdx.x; t < (h / 2 + 1) * NC; t += FFT_T) {
@@ -240,10 +254,8 @@ __global__ void __launch_bounds__(FFT_T) k_fft_y(float* mesh, int S, const float
     constexpr int ncol = N / 2 + 1;
     const int c0 = blockIdx.x * NC;
     float2* slab = reinterpret_cast<float2*>(mesh) + (int64_t)blockIdx.y * N * Sc;
-    for (int t = threadIdx.x; t < N * NC; t += FFT_T) {
-        const int c = t & (NC - 1), y = t >> LOG_NC;
-        buf[sidx<false>(y, c)] = (c0 + c < ncol) ? slab[(int64_t)y * Sc + c0 + c] : make_float2(0.f, 0.f);
-    }
+    load_columns(buf, slab, N, Sc, c0, ncol);
+    cp_async_wait_all();
     __syncthreads();
     tile_fft<N, 1, 1, INV, false>(buf, stw);
     for (int t = threadIdx.x; t < N * NC; t += FFT_T) {
@@ -259,6 +271,8 @@ __global__ void __launch_bounds__(FFT_T) k_fft_z(float* mesh, int S, const float
     extern __shared__ float2 fsm[];
     float2* stw = fsm;
     float2* buf = fsm + N;
+    float* sk2 = reinterpret_cast<float*>(buf + N * NC + NC);     // [N]
+    float* swd = sk2 + N;                                          // [N]
     load_tw(stw, tw, N);
     const int Sc = S / 2;
     constexpr int ncol = N / 2 + 1;
@@ -266,20 +280,23 @@ __global__ void __launch_bounds__(FFT_T) k_fft_z(float* mesh, int S, const float
     const int ky = blockIdx.y;
     float2* base = reinterpret_cast<float2*>(mesh) + (int64_t)ky * Sc;
     const int64_t zs = (int64_t)N * Sc;
-    for (int t = threadIdx.x; t < N * NC; t += FFT_T) {
-        const int c = t & (NC - 1), z = t >> LOG_NC;
-        buf[sidx<false>(z, c)] = (c0 + c < ncol) ? base[z * zs + c0 + c] : make_float2(0.f, 0.f);
-    }
+    load_columns(buf, base, N, zs, c0, ncol);
+    if (MODE == 1)
+        for (int i = threadIdx.x; i < N; i += blockDim.x) {
+            cp_async4(&sk2[i], &k2[i]);
+            cp_async4(&swd[i], &wdec[i]);
+        }
+    cp_async_wait_all();
     __syncthreads();
     tile_fft<N, 1, 1, false, false>(buf, stw);
     if (MODE == 1) {
-        const float ky2 = k2[ky], wy = wdec[ky];
+        const float ky2 = sk2[ky], wy = swd[ky];
         for (int t = threadIdx.x; t < N * NC; t += FFT_T) {
             const int c = t & (NC - 1), z = t >> LOG_NC;
             const int kx = c0 + c;
             if (kx < ncol) {
-                const float kk = k2[kx] + ky2 + k2[z];
-                const float gr = (kx == 0 && ky == 0 && z == 0) ? 0.0f : g0 / kk * (wdec[kx] * wy * wdec[z]);
+                const float kk = sk2[kx] + ky2 + sk2[z];
+                const float gr = (kx == 0 && ky == 0 && z == 0) ? 0.0f : g0 / kk * (swd[kx] * wy * swd[z]);
                 const float2 v = buf[sidx<false>(z, c)];
                 buf[sidx<false>(z, c)] = make_float2(v.x * gr, v.y * gr);
             }
@@ -349,7 +366,8 @@ __global__ void k_unpad(const float* __restrict__ mesh, int N, int S, float* __r
     out[t] = mesh[row * S + x];
 }
 
-size_t tile_smem(int N, int n) { return (size_t)(N + n * NC + NC) * sizeof(float2); }
+// twiddles (N) + tile (n x NC) + one spare column + Green tables (2 x N floats)
+size_t tile_smem(int N, int n) { return (size_t)(N + n * NC + NC) * sizeof(float2) + (size_t)2 * N * sizeof(float); }
 
 template <int N>
 struct Sweeps {

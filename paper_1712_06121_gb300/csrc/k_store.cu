@@ -1,8 +1,9 @@
 // Kernels on the compressed, cell-ordered particle store:
 //   encode (Fig. fig.ic, Section 2.3.2), decode (Eqs. x, v), CIC deposit,
 //   pass A (decode, CIC gather of -grad Phi, kick, re-encode, drift, new-cell
-//   histogram; Figs. update_vp and update_xp first loop), starts (scan of the
-//   per-brick histograms), pass B (identical drift, stable scatter by new cell,
+//   histograms; Figs. update_vp and update_xp first loop), cells (counts,
+//   offsets and v_c of the new store from the scanned histograms), pass B
+//   (identical drift, stable scatter by new cell,
 //   Eq. chi / Eq. nu encode against the new v_c; Fig. update_xp second loop).
 //
 // Every per-particle pass runs one CTA per storage brick: the brick's cells
@@ -102,7 +103,7 @@ __global__ void k_vc_finalize(int ncc, const unsigned* __restrict__ counts, cons
 }
 
 __global__ void k_encode_sigma(Geo g, const float* __restrict__ vel, const unsigned* __restrict__ key,
-                               const float* __restrict__ vc, double* __restrict__ part) {
+                               const float* __restrict__ vc, float* __restrict__ part) {
     __shared__ double sh[32];
     float acc = 0.0f;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < g.Np; i += (int64_t)gridDim.x * blockDim.x) {
@@ -116,15 +117,17 @@ __global__ void k_encode_sigma(Geo g, const float* __restrict__ vel, const unsig
         }
     }
     double s = block_sum_double((double)acc, sh);
-    if (threadIdx.x == 0) part[blockIdx.x] = s;
+    if (threadIdx.x == 0) part[blockIdx.x] = (float)s;
 }
 
-__global__ void k_sigma_finalize(const double* __restrict__ part, int nparts, double count, double ratio,
+__global__ void k_sigma_finalize(const float* __restrict__ part, int nparts, double count, double ratio,
                                  double fixed, double* sigma_out) {
     __shared__ double sh[32];
-    double s = 0.0;
-    for (int i = threadIdx.x; i < nparts; i += blockDim.x) s += part[i];
-    s = block_sum_double(s, sh);
+    // contiguous chunk per thread in FP32, then a fixed tree in FP64
+    const int per = (nparts + blockDim.x - 1) / blockDim.x;
+    float acc = 0.0f;
+    for (int i = threadIdx.x * per, e = min(nparts, i + per); i < e; ++i) acc += part[i];
+    double s = block_sum_double((double)acc, sh);
     if (threadIdx.x == 0) {
         double x = fixed > 0.0 ? fixed : sqrt(s / count) * ratio;
         *sigma_out = snap_sigma_dev(x);
@@ -142,7 +145,7 @@ __global__ void k_codec_tables(int lim, const double* __restrict__ tanv, const d
             dec[lim] = 0.0f;
             thr[0] = 0.0f;
             const double m = (double)(2 * lim + 1);
-            est[0] = (float)(m / PI_D * s);
+            est[0] = (float)s;
             est[1] = (float)(m / PI_D);
         } else if (k <= lim) {
             float dv = (float)(tanv[k] * gam);
@@ -226,7 +229,7 @@ __global__ void __launch_bounds__(T_BRICK) k_decode(Geo g, StoreDev s, const flo
 // are integers (numerators over 2^s per axis) summed in int64, so the result
 // is exact and independent of the summation order; rho = m * sum * 2^(-3s).
 template <int NX>
-__global__ void __launch_bounds__(T_BRICK) k_deposit(Geo g, StoreDev s, float* __restrict__ mesh, double scale) {
+__global__ void __launch_bounds__(T_BRICK) k_deposit(Geo g, StoreDev s, float* __restrict__ mesh, float fscale) {
     extern __shared__ unsigned long long dep_smem[];
     const int F = g.F, F3 = F * F * F;
     const int E = g.B + 1, E3 = E * E * E;
@@ -281,7 +284,7 @@ __global__ void __launch_bounds__(T_BRICK) k_deposit(Geo g, StoreDev s, float* _
                     int x = nd[0] + dx;
                     if (x < 0 || x >= F) continue;
                     long long w = wyz * (dx ? wn[0] : wm[0]);
-                    atomicAdd(&acc[(z * F + y) * F + x], (unsigned long long)w);
+                    smem_add_u64(reinterpret_cast<unsigned*>(&acc[(z * F + y) * F + x]), (unsigned long long)w);
                 }
             }
         }
@@ -290,8 +293,9 @@ __global__ void __launch_bounds__(T_BRICK) k_deposit(Geo g, StoreDev s, float* _
     const int ox = c0[0] * g.R, oy = c0[1] * g.R, oz = c0[2] * g.R;
     for (int t = threadIdx.x; t < F3; t += blockDim.x) {
         int x = t % F, y = (t / F) % F, z = t / (F * F);
-        double v = (double)(long long)acc[t] * scale;
-        mesh[((int64_t)(oz + z) * g.N + (oy + y)) * g.S + ox + x] = __double2float_rn(v);
+        // one rounding when the scale is a power of two (particle mass 2^k)
+        float v = __ll2float_rn((long long)acc[t]) * fscale;
+        mesh[((int64_t)(oz + z) * g.N + (oy + y)) * g.S + ox + x] = v;
     }
 }
 
@@ -332,10 +336,16 @@ __global__ void __launch_bounds__(T_BRICK) k_passA(Geo g, StoreDev s, const floa
         vs[2 * H3 + t] = 0;
     }
     const int ox = bx * F - 2, oy = by * F - 2, oz = bz * F - 2;
-    for (int t = threadIdx.x; t < T3; t += blockDim.x) {
-        int x = t % T, y = (t / T) % T, z = t / (T * T);
-        int gx = wrapi(ox + x, g.N), gy = wrapi(oy + y, g.N), gz = wrapi(oz + z, g.N);
-        tile[t] = phi[((int64_t)gz * g.N + gy) * g.S + gx];
+    {   // one warp per tile row of T nodes
+        const int lane = threadIdx.x & 31;
+        const bool inner = ox >= 0 && ox + T <= g.N;      // row needs no periodic wrap
+        for (int row = threadIdx.x >> 5; row < T * T; row += blockDim.x >> 5) {
+            const int z = row / T, y = row - z * T;
+            const float* src = phi + ((int64_t)wrapi(oz + z, g.N) * g.N + wrapi(oy + y, g.N)) * g.S;
+            for (int x = lane; x < T; x += 32)
+                cp_async4(&tile[row * T + x], src + (inner ? ox + x : wrapi(ox + x, g.N)));
+        }
+        cp_async_wait_all();
     }
     __syncthreads();
     const float e0 = cur.est[0], e1 = cur.est[1];
@@ -413,11 +423,21 @@ __global__ void __launch_bounds__(T_BRICK) k_passA(Geo g, StoreDev s, const floa
             e[d] = l[d] + sh + 1;
             pv[d] = p2;
         }
-        int ei = e[0] + Bh * (e[1] + Bh * e[2]);
-        atomicAdd(&hist[ei], 1u);
+        const int ei = e[0] + Bh * (e[1] + Bh * e[2]);
+        {   // lanes with the same destination cell add once, through their leader
+            const unsigned am = __activemask();
+            const unsigned peers = __match_any_sync(am, ei);
+            const bool lead = (threadIdx.x & 31) == __ffs(peers) - 1;
+            long long sv[3];
 #pragma unroll
-        for (int d = 0; d < 3; ++d)
-            atomicAdd(reinterpret_cast<unsigned long long*>(&vs[d * H3 + ei]), (unsigned long long)vel_fix(pv[d]));
+            for (int d = 0; d < 3; ++d) sv[d] = group_sum_i64(peers, vel_fix(pv[d]));
+            if (lead) {
+                atomicAdd(&hist[ei], (unsigned)__popc(peers));
+#pragma unroll
+                for (int d = 0; d < 3; ++d)
+                    smem_add_u64(reinterpret_cast<unsigned*>(&vs[d * H3 + ei]), (unsigned long long)sv[d]);
+            }
+        }
         if (dbg.cell_old) {
             const int cg[3] = {bx * g.B + l[0], by * g.B + l[1], bz * g.B + l[2]};
 #pragma unroll
@@ -430,14 +450,14 @@ __global__ void __launch_bounds__(T_BRICK) k_passA(Geo g, StoreDev s, const floa
     }
     if (migbad) atomicOr(w.flags, ERR_MIGRATION);
     __syncthreads();
-    const int cbx = bx * g.B - 1, cby = by * g.B - 1, cbz = bz * g.B - 1;
+    const int bc[3] = {bx, by, bz};
     for (int t = threadIdx.x; t < H3; t += blockDim.x) {
-        unsigned h = hist[t];
-        w.ghost[(int64_t)blockIdx.x * H3 + t] = h;
+        const unsigned h = hist[t];
+        const int e[3] = {t % Bh, (t / Bh) % Bh, t / (Bh * Bh)};
+        w.ghost[flat_slot(g, bc, e)] = h;                 // every slot has exactly one writer
         if (h) {
-            int ex = t % Bh, ey = (t / Bh) % Bh, ez = t / (Bh * Bh);
-            int L = cell_rank(g, wrapi(cbx + ex, g.Nc), wrapi(cby + ey, g.Nc), wrapi(cbz + ez, g.Nc));
-            atomicAdd(&w.counts_new[L], h);
+            const int L = cell_rank(g, wrapi(bx * g.B - 1 + e[0], g.Nc), wrapi(by * g.B - 1 + e[1], g.Nc),
+                                    wrapi(bz * g.B - 1 + e[2], g.Nc));
 #pragma unroll
             for (int d = 0; d < 3; ++d)
                 atomicAdd(reinterpret_cast<unsigned long long*>(&w.vsum_new[(int64_t)d * g.Ncc + L]),
@@ -446,7 +466,7 @@ __global__ void __launch_bounds__(T_BRICK) k_passA(Geo g, StoreDev s, const floa
     }
     __shared__ double red[32];
     double tot = block_sum_double((double)sacc, red);
-    if (threadIdx.x == 0) w.part[blockIdx.x] = tot;
+    if (threadIdx.x == 0) w.part[blockIdx.x] = (float)tot;
     // block max of the migration
     __shared__ int mmax;
     if (threadIdx.x == 0) mmax = 0;
@@ -456,47 +476,27 @@ __global__ void __launch_bounds__(T_BRICK) k_passA(Geo g, StoreDev s, const floa
     if (threadIdx.x == 0 && mmax) atomicMax(w.maxmig, mmax);
 }
 
-// ------------------------------------------------------------------ starts
-// For every new cell c: the bricks whose one-cell-halo region holds c, in
-// storage order of the bricks, take consecutive ranges of c's slots starting
-// at offset*[c]: the per-brick histogram entries become per-brick starts.
-// Also v_c* = mean momentum of the cell (fixed point).
-__global__ void k_starts(Geo g, StepScratch w, const unsigned* __restrict__ off_new, float* __restrict__ vc_new) {
-    int L = blockIdx.x * blockDim.x + threadIdx.x;
+// ------------------------------------------------------------------ new cells
+// After the exclusive scan of the flattened histograms, a cell's first slot
+// holds offset*[c] and its slots span counts*[c] particles.  Also
+// v_c* = mean momentum of the cell's new particles (fixed point).
+__global__ void k_cells(Geo g, StepScratch w, unsigned* __restrict__ off_new, float* __restrict__ vc_new) {
+    const int L = blockIdx.x * blockDim.x + threadIdx.x;
     if (L >= g.Ncc) return;
-    const int nbc = g.B * g.B * g.B, Bh = g.Bh, H3 = Bh * Bh * Bh;
-    const int b = L / nbc, lc = L - b * nbc;
-    const int bc[3] = {b % g.nb, (b / g.nb) % g.nb, b / (g.nb * g.nb)};
+    const int nbc = g.B * g.B * g.B;
+    const int hb = L / nbc, lc = L - hb * nbc;
     const int l[3] = {lc % g.B, (lc / g.B) % g.B, lc / (g.B * g.B)};
-    int cb[3][3], ce[3][3], nc[3];
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-        int k = 0;
-        cb[d][k] = bc[d]; ce[d][k] = l[d] + 1; ++k;
-        if (l[d] == 0) { cb[d][k] = wrapi(bc[d] - 1, g.nb); ce[d][k] = g.B + 1; ++k; }
-        if (l[d] == g.B - 1) { cb[d][k] = wrapi(bc[d] + 1, g.nb); ce[d][k] = 0; ++k; }
-        nc[d] = k;
+    const int64_t base = flat_base(g, hb, l);
+    const int n = ncand(l[0], g.B) * ncand(l[1], g.B) * ncand(l[2], g.B);
+    const unsigned off = w.ghost[base];
+    const unsigned cnt = w.ghost[base + n] - off;
+    off_new[L] = off;
+    w.counts_new[L] = cnt;
+    if (L == g.Ncc - 1) {
+        const unsigned total = w.ghost[(int64_t)g.nbricks * (g.Bh * g.Bh * g.Bh)];
+        off_new[g.Ncc] = total;
+        if (total != (unsigned)g.Np) atomicOr(w.flags, ERR_COUNT);
     }
-    int bl[27], slot[27], m = 0;
-    for (int z = 0; z < nc[2]; ++z)
-        for (int y = 0; y < nc[1]; ++y)
-            for (int x = 0; x < nc[0]; ++x) {
-                int bi = cb[0][x] + g.nb * (cb[1][y] + g.nb * cb[2][z]);
-                int e = ce[0][x] + Bh * (ce[1][y] + Bh * ce[2][z]);
-                int j = m++;
-                while (j > 0 && bl[j - 1] > bi) { bl[j] = bl[j - 1]; slot[j] = slot[j - 1]; --j; }
-                bl[j] = bi;
-                slot[j] = e;
-            }
-    unsigned run = off_new[L];
-    for (int j = 0; j < m; ++j) {
-        int64_t sidx = (int64_t)bl[j] * H3 + slot[j];
-        unsigned h = w.ghost[sidx];
-        w.ghost[sidx] = run;
-        run += h;
-    }
-    const unsigned cnt = w.counts_new[L];
-    if (run != off_new[L] + cnt) atomicOr(w.flags, ERR_COUNT);
 #pragma unroll
     for (int d = 0; d < 3; ++d) vc_new[(int64_t)d * g.Ncc + L] = vel_unfix_mean(w.vsum_new[(int64_t)d * g.Ncc + L], cnt);
 }
@@ -524,10 +524,16 @@ __global__ void __launch_bounds__(T_BRICK) k_passB(Geo g, StoreDev so, StoreDev 
     }
     const int L0 = blockIdx.x * nbc;
     for (int c = threadIdx.x; c <= nbc; c += blockDim.x) sm_off[c] = so.offsets[L0 + c];
-    for (int t = threadIdx.x; t < H3; t += blockDim.x) run[t] = ghost[(int64_t)blockIdx.x * H3 + t];
-    __syncthreads();
     int bx, by, bz;
     brick_coords(g, blockIdx.x, &bx, &by, &bz);
+    {
+        const int bc[3] = {bx, by, bz};
+        for (int t = threadIdx.x; t < H3; t += blockDim.x) {
+            const int e[3] = {t % Bh, (t / Bh) % Bh, t / (Bh * Bh)};
+            run[t] = ghost[flat_slot(g, bc, e)];
+        }
+    }
+    __syncthreads();
     const int nbits = 8 * NX, half = 1 << (nbits - 1), bmask = (1 << nbits) - 1;
     const float inv2q = ldexpf(1.0f, -(nbits + 1));
     const float two8n = ldexpf(1.0f, nbits);
@@ -626,14 +632,14 @@ void launch_vc_finalize(const Geo& g, const unsigned* counts, const long long* v
 
 int encode_sigma_blocks(const Geo& g) { return (int)std::min<int64_t>(1024, std::max<int64_t>(1, nblk(g.Np, 256))); }
 
-void launch_encode_sigma(const Geo& g, const float* vel, const unsigned* key, const float* vc, double* part,
+void launch_encode_sigma(const Geo& g, const float* vel, const unsigned* key, const float* vc, float* part,
                          cudaStream_t st) {
     k_encode_sigma<<<encode_sigma_blocks(g), 256, 0, st>>>(g, vel, key, vc, part);
 }
 
-void launch_sigma_finalize(const double* part, int nparts, double count, double ratio, double fixed,
+void launch_sigma_finalize(const float* part, int nparts, double count, double ratio, double fixed,
                            double* sigma_out, cudaStream_t st) {
-    k_sigma_finalize<<<1, 256, 0, st>>>(part, nparts, count, ratio, fixed, sigma_out);
+    k_sigma_finalize<<<1, 1024, 0, st>>>(part, nparts, count, ratio, fixed, sigma_out);
 }
 
 void launch_codec_tables(int nulim, const double* tanv, const double* tanh_, const CodecDev& c, cudaStream_t st) {
@@ -668,10 +674,10 @@ void launch_deposit(const Geo& g, const StoreDev& s, float* mesh, double scale, 
     size_t sm = deposit_smem(g);
     if (g.nchi == 1) {
         set_smem_attrs<1, 1>(); set_smem_attrs<1, 2>();
-        k_deposit<1><<<g.nbricks, T_BRICK, sm, st>>>(g, s, mesh, scale);
+        k_deposit<1><<<g.nbricks, T_BRICK, sm, st>>>(g, s, mesh, (float)scale);
     } else {
         set_smem_attrs<2, 1>(); set_smem_attrs<2, 2>();
-        k_deposit<2><<<g.nbricks, T_BRICK, sm, st>>>(g, s, mesh, scale);
+        k_deposit<2><<<g.nbricks, T_BRICK, sm, st>>>(g, s, mesh, (float)scale);
     }
 }
 
@@ -691,8 +697,8 @@ void launch_passA(const Geo& g, const StoreDev& s, const float* phi, const Codec
     else { set_smem_attrs<2, 2>(); Disp<2, 2>::passA(g, s, phi, cur, kick, dc, w, dbg, sm, st); }
 }
 
-void launch_starts(const Geo& g, const StepScratch& w, const unsigned* off_new, float* vc_new, cudaStream_t st) {
-    k_starts<<<nblk(g.Ncc, 256), 256, 0, st>>>(g, w, off_new, vc_new);
+void launch_cells(const Geo& g, const StepScratch& w, unsigned* off_new, float* vc_new, cudaStream_t st) {
+    k_cells<<<nblk(g.Ncc, 256), 256, 0, st>>>(g, w, off_new, vc_new);
 }
 
 static size_t passB_smem(const Geo& g) {

@@ -71,8 +71,9 @@ struct DriftDebug {
 struct StepScratch {
     unsigned* counts_new;   // [Ncc]
     long long* vsum_new;    // [3][Ncc]
-    unsigned* ghost;        // [nbricks][Bh^3]: histogram, then starts
-    double* part;           // [max(nbricks, blocks)] partial sums
+    unsigned* ghost;        // [nbricks * Bh^3 + 1]: per-brick histograms in flattened
+                            // (cell, brick) order, scanned in place into starts
+    float* part;            // [max(nbricks, blocks)] partial sums
     unsigned* flags;        // device error flags
     int* maxmig;            // largest |cell shift| of the step
 };
@@ -82,8 +83,8 @@ void launch_encode_keys(const Geo& g, const float* pos, const float* vel, unsign
 void launch_vc_finalize(const Geo& g, const unsigned* counts, const long long* vsum, float* vc, cudaStream_t st);
 int encode_sigma_blocks(const Geo& g);
 void launch_encode_sigma(const Geo& g, const float* vel, const unsigned* key_sorted_or_raw, const float* vc,
-                         double* part, cudaStream_t st);
-void launch_sigma_finalize(const double* part, int nparts, double count, double ratio, double fixed,
+                         float* part, cudaStream_t st);
+void launch_sigma_finalize(const float* part, int nparts, double count, double ratio, double fixed,
                            double* sigma_out, cudaStream_t st);
 void launch_codec_tables(int nulim, const double* tanv, const double* tanh, const CodecDev& c, cudaStream_t st);
 void launch_encode_scatter(const Geo& g, const float* pos, const float* vel, const unsigned* id_in,
@@ -94,7 +95,7 @@ void launch_decode(const Geo& g, const StoreDev& s, const float* dec, float* pos
 void launch_deposit(const Geo& g, const StoreDev& s, float* mesh, double scale, cudaStream_t st);
 void launch_passA(const Geo& g, const StoreDev& s, const float* phi, const CodecDev& cur, float kick, float dc,
                   const StepScratch& w, const DriftDebug& dbg, cudaStream_t st);
-void launch_starts(const Geo& g, const StepScratch& w, const unsigned* off_new, float* vc_new, cudaStream_t st);
+void launch_cells(const Geo& g, const StepScratch& w, unsigned* off_new, float* vc_new, cudaStream_t st);
 void launch_passB(const Geo& g, const StoreDev& s_old, const StoreDev& s_new, const CodecDev& cur,
                   const CodecDev& next, float dc, const StepScratch& w, cudaStream_t st);
 void launch_momentum(const Geo& g, const long long* vsum, long long* out3, cudaStream_t st);
