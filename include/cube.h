@@ -75,9 +75,9 @@ typedef struct {
                               p in {0, 1, 2}; 2 compensates deposit and gather  */
     int32_t brick;         /* side, in coarse cells, of the storage-order brick:
                               cells are grouped in bricks of brick^3, bricks and
-                              cells inside them are x-fastest.  0 = automatic:
-                              the largest of 4, 2, 1 dividing N_c with >= 3
-                              bricks per side and brick * R <= 16              */
+                              cells inside them are x-fastest.  1, 2 or 4 with
+                              >= 3 bricks per side and 4 <= brick * R <= 16;
+                              0 = automatic: the largest such value            */
     double box;            /* box side L in Mpc/h (units of k and P(k) only)   */
     double omega_m;        /* Omega_m: source term of lap Phi = 1.5 Om (rho-1)  */
     double omega_l;        /* Omega_Lambda: expansion rate E(a)                 */

@@ -232,11 +232,12 @@ cube_status check_params(const cube_params* p, int* brick) {
     if (B == 0) {
         const int cand[3] = {4, 2, 1};
         for (int b : cand)
-            if (Nc % b == 0 && Nc / b >= 3 && b * R <= 16) { B = b; break; }
+            if (Nc % b == 0 && Nc / b >= 3 && b * R <= 16 && b * R >= 4) { B = b; break; }
         if (B == 0) return fail(CUBE_E_ARG, "no valid brick size");
     }
-    if (B < 1 || Nc % B || Nc / B < 3 || B * R > 16)
-        return fail(CUBE_E_ARG, "brick must divide N_c with >= 3 bricks per side and brick * ratio <= 16");
+    if (!(B == 1 || B == 2 || B == 4) || Nc % B || Nc / B < 3 || B * R > 16 || B * R < 4)
+        return fail(CUBE_E_ARG, "brick must be 1, 2 or 4, divide N_c with >= 3 bricks per side, "
+                                "and 4 <= brick * ratio <= 16");
     *brick = B;
     return CUBE_OK;
 }
@@ -292,6 +293,10 @@ cube_status cube_create(const cube_params* params, void* cuda_stream, cube_ctx**
     g.nbricks = g.nb * g.nb * g.nb;
     g.Np = params->n_particles;
     g.nulim = (1 << (8 * g.nnu - 1)) - 1;
+    g.lB = 0;
+    while ((1 << g.lB) < g.B) ++g.lB;
+    g.lF = 0;
+    while ((1 << g.lF) < g.F) ++g.lF;
 
     auto bad = [&](cudaError_t e, const char* what) -> cube_status {
         cube_destroy(c);

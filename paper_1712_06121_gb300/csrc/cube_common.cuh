@@ -37,19 +37,24 @@ struct Geo {
     int nbricks;  // nb^3
     int64_t Np;
     int nulim;    // 2^(8 nnu - 1) - 1: largest |nu|
+    int lB, lF;   // log2(B), log2(F): brick and fine-tile sides are powers of two
 };
 
 // storage rank of coarse cell (cx, cy, cz), coordinates already in [0, Nc)
+// (brick side B = 2^lB)
 __host__ __device__ __forceinline__ int cell_rank(const Geo& g, int cx, int cy, int cz) {
-    int bx = cx / g.B, by = cy / g.B, bz = cz / g.B;
-    int lx = cx - bx * g.B, ly = cy - by * g.B, lz = cz - bz * g.B;
-    return (bx + g.nb * (by + g.nb * bz)) * (g.B * g.B * g.B) + lx + g.B * (ly + g.B * lz);
+    const int m = g.B - 1;
+    const int bx = cx >> g.lB, by = cy >> g.lB, bz = cz >> g.lB;
+    return ((bx + g.nb * (by + g.nb * bz)) << (3 * g.lB)) + (cx & m) + ((cy & m) << g.lB) + ((cz & m) << (2 * g.lB));
 }
 
 __host__ __device__ __forceinline__ int wrapi(int v, int n) {
     v %= n;
     return v < 0 ? v + n : v;
 }
+
+// periodic wrap of a coordinate known to lie in [-n, 2n)
+__host__ __device__ __forceinline__ int wrap1(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
 
 // 2^-24 fixed point of a velocity (round to nearest even); exact for |v| < 2^39
 __device__ __forceinline__ long long vel_fix(float v) {
@@ -113,12 +118,12 @@ __host__ __device__ __forceinline__ int64_t flat_slot(const Geo& g, const int* b
     int l[3], hbc[3], rank = 0;
 #pragma unroll
     for (int d = 2; d >= 0; --d) {
-        const int c = wrapi(bc[d] * g.B - 1 + e[d], g.Nc);
-        l[d] = c % g.B;
-        hbc[d] = c / g.B;
+        const int c = wrap1((bc[d] << g.lB) - 1 + e[d], g.Nc);
+        l[d] = c & (g.B - 1);
+        hbc[d] = c >> g.lB;
         // candidate brick coordinates on this axis, ranked by value
-        const int lo = (l[d] == 0) ? wrapi(hbc[d] - 1, g.nb) : -1;
-        const int hi = (l[d] == g.B - 1) ? wrapi(hbc[d] + 1, g.nb) : -1;
+        const int lo = (l[d] == 0) ? wrap1(hbc[d] - 1, g.nb) : -1;
+        const int hi = (l[d] == g.B - 1) ? wrap1(hbc[d] + 1, g.nb) : -1;
         const int me = bc[d];
         int r = (hbc[d] < me) + (lo >= 0 && lo < me) + (hi >= 0 && hi < me);
         rank = rank * ncand(l[d], g.B) + r;

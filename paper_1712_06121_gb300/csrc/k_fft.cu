@@ -115,11 +115,13 @@ __device__ __forceinline__ void fft_pass(float2* buf, const float2* tw) {
         if (nbf % FFT_T == 0 || b < nbf) {
             const int c = b & (NC - 1), j = b >> LOG_NC;
             const int k = j % Ns;
+            if (Ns > 1) {                                  // span 1: all twiddles are 1
 #pragma unroll
-            for (int m = 1; m < R; ++m) {
-                float2 w = tw[k * m * step];
-                if (INV) w.y = -w.y;
-                v[q][m] = cmul(v[q][m], w);
+                for (int m = 1; m < R; ++m) {
+                    float2 w = tw[k * m * step];
+                    if (INV) w.y = -w.y;
+                    v[q][m] = cmul(v[q][m], w);
+                }
             }
             dft<R, INV>(v[q]);
             const int idxD = (j / Ns) * Ns * R + k;

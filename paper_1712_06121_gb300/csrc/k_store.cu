@@ -208,7 +208,7 @@ __global__ void __launch_bounds__(T_BRICK) k_decode(Geo g, StoreDev s, const flo
     const unsigned q1 = min(sm_off[nbc], np_);
     for (unsigned i = min(sm_off[0], q1) + threadIdx.x; i < q1; i += blockDim.x) {
         int lc = upper_cell(sm_off, nbc, i);
-        int l[3] = {lc % g.B, (lc / g.B) % g.B, lc / (g.B * g.B)};
+        int l[3] = {lc & (g.B - 1), (lc >> g.lB) & (g.B - 1), lc >> (2 * g.lB)};
         int c[3] = {bx * g.B + l[0], by * g.B + l[1], bz * g.B + l[2]};
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
@@ -231,21 +231,23 @@ __global__ void __launch_bounds__(T_BRICK) k_decode(Geo g, StoreDev s, const flo
 template <int NX>
 __global__ void __launch_bounds__(T_BRICK) k_deposit(Geo g, StoreDev s, float* __restrict__ mesh, float fscale) {
     extern __shared__ unsigned long long dep_smem[];
-    const int F = g.F, F3 = F * F * F;
+    const int F = g.F, lF = g.lF, F3 = 1 << (3 * lF);
     const int E = g.B + 1, E3 = E * E * E;
-    unsigned long long* acc = dep_smem;                              // [F3]
-    unsigned* cstart = reinterpret_cast<unsigned*>(acc + F3);        // [E3]
+    unsigned* acc = reinterpret_cast<unsigned*>(dep_smem);          // [F3] {lo, hi} words
+    unsigned* cstart = acc + 2 * F3;                                 // [E3]
     unsigned* cpref = cstart + E3;                                   // [E3 + 1]
+    int* cpack = reinterpret_cast<int*>(cpref + E3 + 1);             // [E3] packed cell offsets
     int bx, by, bz;
     brick_coords(g, blockIdx.x, &bx, &by, &bz);
     const int c0[3] = {bx * g.B, by * g.B, bz * g.B};
-    for (int t = threadIdx.x; t < F3; t += blockDim.x) acc[t] = 0ull;
+    for (int t = threadIdx.x; t < 2 * F3; t += blockDim.x) acc[t] = 0u;
     for (int t = threadIdx.x; t < E3; t += blockDim.x) {
-        int lx = t % E - 1, ly = (t / E) % E - 1, lz = t / (E * E) - 1;
-        int L = cell_rank(g, wrapi(c0[0] + lx, g.Nc), wrapi(c0[1] + ly, g.Nc), wrapi(c0[2] + lz, g.Nc));
-        unsigned a = s.offsets[L];
+        const int lx = t % E - 1, ly = (t / E) % E - 1, lz = t / (E * E) - 1;
+        const int L = cell_rank(g, wrapi(c0[0] + lx, g.Nc), wrapi(c0[1] + ly, g.Nc), wrapi(c0[2] + lz, g.Nc));
+        const unsigned a = s.offsets[L];
         cstart[t] = a;
         cpref[t + 1] = s.offsets[L + 1] - a;
+        cpack[t] = (lx + 1) | ((ly + 1) << 8) | ((lz + 1) << 16);
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -258,33 +260,43 @@ __global__ void __launch_bounds__(T_BRICK) k_deposit(Geo g, StoreDev s, float* _
     const int sb = g.sbits, wmask = (1 << sb) - 1, wone = 1 << sb;
     const unsigned total = cpref[E3];
     for (unsigned q = threadIdx.x; q < total; q += blockDim.x) {
-        int t = upper_cell(cpref, E3, q);
-        unsigned i = cstart[t] + (q - cpref[t]);
+        const int t = upper_cell(cpref, E3, q);
+        const unsigned i = cstart[t] + (q - cpref[t]);
         if (i >= (unsigned)g.Np) continue;
-        int l[3] = {t % E - 1, (t / E) % E - 1, t / (E * E) - 1};
+        const int pk = cpack[t];
+        const int l[3] = {(pk & 255) - 1, ((pk >> 8) & 255) - 1, (pk >> 16) - 1};
         int nd[3], wn[3], wm[3];
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
-            int Q = 2 * (load_code<NX>(s.chi, d * g.Np + i) + half) + 1;
-            nd[d] = g.R * l[d] + (Q >> sb);
+            const int Q = 2 * (load_code<NX>(s.chi, d * g.Np + i) + half) + 1;
+            nd[d] = l[d] * g.R + (Q >> sb);
             wn[d] = Q & wmask;
             wm[d] = wone - wn[d];
         }
 #pragma unroll
         for (int dz = 0; dz < 2; ++dz) {
-            int z = nd[2] + dz;
+            const int z = nd[2] + dz;
             if (z < 0 || z >= F) continue;
 #pragma unroll
             for (int dy = 0; dy < 2; ++dy) {
-                int y = nd[1] + dy;
+                const int y = nd[1] + dy;
                 if (y < 0 || y >= F) continue;
-                long long wyz = (long long)(dz ? wn[2] : wm[2]) * (dy ? wn[1] : wm[1]);
 #pragma unroll
                 for (int dx = 0; dx < 2; ++dx) {
-                    int x = nd[0] + dx;
+                    const int x = nd[0] + dx;
                     if (x < 0 || x >= F) continue;
-                    long long w = wyz * (dx ? wn[0] : wm[0]);
-                    smem_add_u64(reinterpret_cast<unsigned*>(&acc[(z * F + y) * F + x]), (unsigned long long)w);
+                    unsigned* a = &acc[2 * ((((z << lF) + y) << lF) + x)];
+                    if (NX == 1) {   // weight numerators of 1-byte codes: product < 2^27
+                        const unsigned w = (unsigned)(dz ? wn[2] : wm[2]) * (unsigned)(dy ? wn[1] : wm[1]) *
+                                           (unsigned)(dx ? wn[0] : wm[0]);
+                        const unsigned old = atomicAdd(a, w);
+                        if (old + w < old) atomicAdd(a + 1, 1u);
+                    } else {
+                        const unsigned long long w = (unsigned long long)(dz ? wn[2] : wm[2]) *
+                                                     (unsigned long long)(dy ? wn[1] : wm[1]) *
+                                                     (unsigned long long)(dx ? wn[0] : wm[0]);
+                        smem_add_u64(a, w);
+                    }
                 }
             }
         }
@@ -292,9 +304,10 @@ __global__ void __launch_bounds__(T_BRICK) k_deposit(Geo g, StoreDev s, float* _
     __syncthreads();
     const int ox = c0[0] * g.R, oy = c0[1] * g.R, oz = c0[2] * g.R;
     for (int t = threadIdx.x; t < F3; t += blockDim.x) {
-        int x = t % F, y = (t / F) % F, z = t / (F * F);
-        // one rounding when the scale is a power of two (particle mass 2^k)
-        float v = __ll2float_rn((long long)acc[t]) * fscale;
+        const int x = t & (F - 1), y = (t >> lF) & (F - 1), z = t >> (2 * lF);
+        const unsigned lo = acc[2 * t], hi = acc[2 * t + 1];
+        // exact integer sum; one rounding when the scale is a power of two (mass 2^k)
+        const float v = (hi ? __ull2float_rn(((unsigned long long)hi << 32) | lo) : __uint2float_rn(lo)) * fscale;
         mesh[((int64_t)(oz + z) * g.N + (oy + y)) * g.S + ox + x] = v;
     }
 }
@@ -308,11 +321,13 @@ template <int NX, int NV>
 __global__ void __launch_bounds__(T_BRICK) k_passA(Geo g, StoreDev s, const float* __restrict__ phi, CodecDev cur,
                                                    float kick, float dc, StepScratch w, DriftDebug dbg) {
     extern __shared__ unsigned char pa_smem[];
-    const int F = g.F, T = F + 5, T3 = T * T * T;
+    // Phi tile: T x T rows (y, z: [o - 2, o + F + 3)) of TX = F + 8 nodes
+    // (x: [o - 4, o + F + 4)), row stride TS = F + 12 floats
+    const int F = g.F, T = F + 5, TX = F + 8, TS = F + 12, T3 = T * T * TS;
     const int nbc = g.B * g.B * g.B, Bh = g.Bh, H3 = Bh * Bh * Bh;
     const int lim = g.nulim;
     long long* vs = reinterpret_cast<long long*>(pa_smem);                 // [3][H3]
-    float* tile = reinterpret_cast<float*>(vs + 3 * H3);                    // [T3]
+    float* tile = reinterpret_cast<float*>(pa_smem + ((3 * H3 * 8 + 15) & ~15));   // [T3], 16-byte aligned
     unsigned* hist = reinterpret_cast<unsigned*>(tile + T3);                // [H3]
     unsigned* sm_off = hist + H3;                                           // [nbc + 1]
     float* sdec = reinterpret_cast<float*>(sm_off + nbc + 1);               // NV == 1: [2 lim + 1]
@@ -335,15 +350,16 @@ __global__ void __launch_bounds__(T_BRICK) k_passA(Geo g, StoreDev s, const floa
         vs[H3 + t] = 0;
         vs[2 * H3 + t] = 0;
     }
-    const int ox = bx * F - 2, oy = by * F - 2, oz = bz * F - 2;
-    {   // one warp per tile row of T nodes
-        const int lane = threadIdx.x & 31;
-        const bool inner = ox >= 0 && ox + T <= g.N;      // row needs no periodic wrap
-        for (int row = threadIdx.x >> 5; row < T * T; row += blockDim.x >> 5) {
+    // tile origin (o - 4, o - 2, o - 2): rows of TX = F + 8 nodes start on a
+    // 16-byte boundary, so they load as 4-node chunks, each wrapped on its own
+    const int ox = bx * F - 4, oy = by * F - 2, oz = bz * F - 2;
+    {
+        const int CX = TX >> 2, nrow = T * T;
+        for (int q = threadIdx.x; q < nrow * CX; q += blockDim.x) {
+            const int row = q / CX, cx = q - row * CX;
             const int z = row / T, y = row - z * T;
-            const float* src = phi + ((int64_t)wrapi(oz + z, g.N) * g.N + wrapi(oy + y, g.N)) * g.S;
-            for (int x = lane; x < T; x += 32)
-                cp_async4(&tile[row * T + x], src + (inner ? ox + x : wrapi(ox + x, g.N)));
+            const float* src = phi + ((int64_t)wrap1(oz + z, g.N) * g.N + wrap1(oy + y, g.N)) * g.S;
+            cp_async16(&tile[row * TS + 4 * cx], src + wrap1(ox + 4 * cx, g.N));
         }
         cp_async_wait_all();
     }
@@ -357,28 +373,28 @@ __global__ void __launch_bounds__(T_BRICK) k_passA(Geo g, StoreDev s, const floa
     float sacc = 0.0f;
     int mig = 0;
     bool migbad = false;
-    const int TT = T * T;
+    const int TT = T * TS;   // z stride of the tile
     const unsigned q1 = min(sm_off[nbc], (unsigned)g.Np);
     for (unsigned i = min(sm_off[0], q1) + threadIdx.x; i < q1; i += blockDim.x) {
         int lc = upper_cell(sm_off, nbc, i);
-        int l[3] = {lc % g.B, (lc / g.B) % g.B, lc / (g.B * g.B)};
+        int l[3] = {lc & (g.B - 1), (lc >> g.lB) & (g.B - 1), lc >> (2 * g.lB)};
         int Q[3], n[3];
         float wv[3];
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
             Q[d] = 2 * (load_code<NX>(s.chi, d * g.Np + i) + half) + 1;
-            n[d] = 2 + g.R * l[d] + (Q[d] >> sb);
+            n[d] = (d == 0 ? 4 : 2) + (l[d] << g.r) + (Q[d] >> sb);
             wv[d] = (float)(Q[d] & wmask) * winv;
         }
         // CIC gather of the FD4 gradient: per axis, 4 rows of 6 nodes
-        const int base = (n[2] * T + n[1]) * T + n[0];
+        const int base = (n[2] * T + n[1]) * TS + n[0];
         float gx = 0.0f, gy = 0.0f, gz = 0.0f;
 #pragma unroll
         for (int a = 0; a < 2; ++a) {
 #pragma unroll
             for (int b = 0; b < 2; ++b) {
                 {   // x rows at (y + a, z + b)
-                    const float* r = tile + base + a * T + b * TT;
+                    const float* r = tile + base + a * TS + b * TT;
                     float g0 = 8.0f * (r[1] - r[-1]) - (r[2] - r[-2]);
                     float g1 = 8.0f * (r[2] - r[0]) - (r[3] - r[-1]);
                     float wyz = (a ? wv[1] : 1.0f - wv[1]) * (b ? wv[2] : 1.0f - wv[2]);
@@ -386,13 +402,13 @@ __global__ void __launch_bounds__(T_BRICK) k_passA(Geo g, StoreDev s, const floa
                 }
                 {   // y columns at (x + a, z + b)
                     const float* r = tile + base + a + b * TT;
-                    float g0 = 8.0f * (r[T] - r[-T]) - (r[2 * T] - r[-2 * T]);
-                    float g1 = 8.0f * (r[2 * T] - r[0]) - (r[3 * T] - r[-T]);
+                    float g0 = 8.0f * (r[TS] - r[-TS]) - (r[2 * TS] - r[-2 * TS]);
+                    float g1 = 8.0f * (r[2 * TS] - r[0]) - (r[3 * TS] - r[-TS]);
                     float wxz = (a ? wv[0] : 1.0f - wv[0]) * (b ? wv[2] : 1.0f - wv[2]);
                     gy += wxz * ((1.0f - wv[1]) * g0 + wv[1] * g1);
                 }
                 {   // z columns at (x + a, y + b)
-                    const float* r = tile + base + a + b * T;
+                    const float* r = tile + base + a + b * TS;
                     float g0 = 8.0f * (r[TT] - r[-TT]) - (r[2 * TT] - r[-2 * TT]);
                     float g1 = 8.0f * (r[2 * TT] - r[0]) - (r[3 * TT] - r[-TT]);
                     float wxy = (a ? wv[0] : 1.0f - wv[0]) * (b ? wv[1] : 1.0f - wv[1]);
@@ -456,8 +472,8 @@ __global__ void __launch_bounds__(T_BRICK) k_passA(Geo g, StoreDev s, const floa
         const int e[3] = {t % Bh, (t / Bh) % Bh, t / (Bh * Bh)};
         w.ghost[flat_slot(g, bc, e)] = h;                 // every slot has exactly one writer
         if (h) {
-            const int L = cell_rank(g, wrapi(bx * g.B - 1 + e[0], g.Nc), wrapi(by * g.B - 1 + e[1], g.Nc),
-                                    wrapi(bz * g.B - 1 + e[2], g.Nc));
+            const int L = cell_rank(g, wrap1(bx * g.B - 1 + e[0], g.Nc), wrap1(by * g.B - 1 + e[1], g.Nc),
+                                    wrap1(bz * g.B - 1 + e[2], g.Nc));
 #pragma unroll
             for (int d = 0; d < 3; ++d)
                 atomicAdd(reinterpret_cast<unsigned long long*>(&w.vsum_new[(int64_t)d * g.Ncc + L]),
@@ -502,18 +518,25 @@ __global__ void k_cells(Geo g, StepScratch w, unsigned* __restrict__ off_new, fl
 }
 
 // ------------------------------------------------------------------ pass B
+// One warp per brick (8 bricks per CTA): the brick's particles are taken 32
+// at a time in index order; lanes moving to the same cell get consecutive
+// slots in lane order from the cell's running start (match + popc), so the
+// new order within a cell is the old index order.  No block barriers.
+constexpr int PB_WARPS = 8;
+
 template <int NX, int NV>
-__global__ void __launch_bounds__(T_BRICK) k_passB(Geo g, StoreDev so, StoreDev sn, CodecDev cur, CodecDev next,
-                                                   float dc, const unsigned* __restrict__ ghost,
-                                                   const float* __restrict__ vc_new, unsigned* flags) {
+__global__ void __launch_bounds__(PB_WARPS * 32) k_passB(Geo g, StoreDev so, StoreDev sn, CodecDev cur, CodecDev next,
+                                                        float dc, const unsigned* __restrict__ ghost,
+                                                        const float* __restrict__ vc_new, unsigned* flags) {
     extern __shared__ unsigned pb_smem[];
     const int nbc = g.B * g.B * g.B, Bh = g.Bh, H3 = Bh * Bh * Bh;
     const int lim = g.nulim;
-    unsigned* sm_off = pb_smem;                       // [nbc + 1]
-    unsigned* run = sm_off + nbc + 1;                 // [H3]
-    unsigned* wcnt = run + H3;                        // [W_BRICK * H3]
-    float* sdec = reinterpret_cast<float*>(wcnt + W_BRICK * H3);
-    float* sthr = sdec + (NV == 1 ? 2 * lim + 1 : 0);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    float* sdec = reinterpret_cast<float*>(pb_smem);                       // NV == 1: [2 lim + 1]
+    float* sthr = sdec + (NV == 1 ? 2 * lim + 1 : 0);                       // NV == 1: [lim + 2]
+    unsigned* wbase = reinterpret_cast<unsigned*>(sthr + (NV == 1 ? lim + 2 : 0));
+    unsigned* sm_off = wbase + warp * (nbc + 1 + H3);                       // [nbc + 1] per warp
+    unsigned* run = sm_off + nbc + 1;                                       // [H3] per warp
     const float* dec = cur.dec;
     const float* thr = next.thr;
     if (NV == 1) {
@@ -522,61 +545,68 @@ __global__ void __launch_bounds__(T_BRICK) k_passB(Geo g, StoreDev so, StoreDev 
         dec = sdec;
         thr = sthr;
     }
-    const int L0 = blockIdx.x * nbc;
-    for (int c = threadIdx.x; c <= nbc; c += blockDim.x) sm_off[c] = so.offsets[L0 + c];
-    int bx, by, bz;
-    brick_coords(g, blockIdx.x, &bx, &by, &bz);
-    {
-        const int bc[3] = {bx, by, bz};
-        for (int t = threadIdx.x; t < H3; t += blockDim.x) {
-            const int e[3] = {t % Bh, (t / Bh) % Bh, t / (Bh * Bh)};
-            run[t] = ghost[flat_slot(g, bc, e)];
-        }
-    }
     __syncthreads();
+    const int brick = blockIdx.x * PB_WARPS + warp;
+    if (brick >= g.nbricks) return;
+    const int L0 = brick * nbc;
+    int bx, by, bz;
+    brick_coords(g, brick, &bx, &by, &bz);
+    const int bc[3] = {bx, by, bz};
+    for (int c = lane; c <= nbc; c += 32) sm_off[c] = so.offsets[L0 + c];
+    for (int t = lane; t < H3; t += 32) {
+        const int e[3] = {t % Bh, (t / Bh) % Bh, t / (Bh * Bh)};
+        run[t] = ghost[flat_slot(g, bc, e)];
+    }
+    __syncwarp();
     const int nbits = 8 * NX, half = 1 << (nbits - 1), bmask = (1 << nbits) - 1;
     const float inv2q = ldexpf(1.0f, -(nbits + 1));
     const float two8n = ldexpf(1.0f, nbits);
     const float e0 = next.est[0], e1 = next.est[1];
     const unsigned p1 = min(sm_off[nbc], (unsigned)g.Np), p0 = min(sm_off[0], p1);
-    for (unsigned base = p0; base < p1; base += blockDim.x) {
-        const unsigned i = base + threadIdx.x;
+    for (unsigned base = p0; base < p1; base += 32) {
+        const unsigned i = base + lane;
         const bool act = i < p1;
-        int ei = 0, chi[3] = {0, 0, 0}, cn[3] = {0, 0, 0};
-        float pv[3] = {0.f, 0.f, 0.f};
+        const unsigned am = __ballot_sync(0xffffffffu, act);
         if (act) {
-            int lc = upper_cell(sm_off, nbc, i);
-            int l[3] = {lc % g.B, (lc / g.B) % g.B, lc / (g.B * g.B)};
-            const int cg[3] = {bx * g.B + l[0], by * g.B + l[1], bz * g.B + l[2]};
-            int e[3];
+            const int lc = upper_cell(sm_off, nbc, i);
+            const int l[3] = {lc & (g.B - 1), (lc >> g.lB) & (g.B - 1), lc >> (2 * g.lB)};
+            int e[3], chi[3], cn[3];
+            float pv[3];
 #pragma unroll
             for (int d = 0; d < 3; ++d) {
-                int Q = 2 * (load_code<NX>(so.chi, d * g.Np + i) + half) + 1;
-                int nu = load_nu<NV>(so.nu, d * g.Np + i, g.nulim);
-                float p2 = so.vc[(int64_t)d * g.Ncc + L0 + lc] + dec[nu + lim];
+                const int Q = 2 * (load_code<NX>(so.chi, d * g.Np + i) + half) + 1;
+                const int nu = load_nu<NV>(so.nu, d * g.Np + i, lim);
+                const float p2 = so.vc[(int64_t)d * g.Ncc + L0 + lc] + dec[nu + lim];
                 float un;
-                int bin = drift_bin(Q, p2, dc, inv2q, two8n, &un);
-                int sh = max(-1, min(1, bin >> nbits));
+                const int bin = drift_bin(Q, p2, dc, inv2q, two8n, &un);
+                const int sh = max(-1, min(1, bin >> nbits));
                 e[d] = l[d] + sh + 1;
                 chi[d] = (bin & bmask) - half;
-                cn[d] = wrapi(cg[d] + sh, g.Nc);
+                cn[d] = wrap1(bc[d] * g.B + l[d] + sh, g.Nc);
                 pv[d] = p2;
             }
-            ei = e[0] + Bh * (e[1] + Bh * e[2]);
-        }
-        int pos = stable_round_rank<W_BRICK>(ei, act, run, wcnt, H3);
-        if (act && (pos < 0 || pos >= (int)g.Np)) {
-            atomicOr(flags, ERR_COUNT);
-        } else if (act) {
-            const int Ln = cell_rank(g, cn[0], cn[1], cn[2]);
+            const int ei = e[0] + Bh * (e[1] + Bh * e[2]);
+            const unsigned peers = __match_any_sync(am, ei);
+            const int leader = __ffs(peers) - 1;
+            unsigned start = 0;
+            if (lane == leader) start = run[ei];
+            start = __shfl_sync(peers, start, leader);
+            if (lane == leader) run[ei] = start + (unsigned)__popc(peers);
+            const unsigned pos = start + (unsigned)__popc(peers & ((1u << lane) - 1u));
+            if (pos >= (unsigned)g.Np) {
+                atomicOr(flags, ERR_COUNT);
+            } else {
+                const int Ln = cell_rank(g, cn[0], cn[1], cn[2]);
 #pragma unroll
-            for (int d = 0; d < 3; ++d) {
-                store_code<NX>(sn.chi, d * g.Np + pos, chi[d]);
-                float dd = pv[d] - vc_new[(int64_t)d * g.Ncc + Ln];
-                store_code<NV>(sn.nu, d * g.Np + pos, nu_from_thresholds(dd, thr, lim, nu_estimate(dd, e0, e1)));
+                for (int d = 0; d < 3; ++d) {
+                    store_code<NX>(sn.chi, d * g.Np + pos, chi[d]);
+                    const float dd = pv[d] - vc_new[(int64_t)d * g.Ncc + Ln];
+                    store_code<NV>(sn.nu, d * g.Np + pos, nu_from_thresholds(dd, thr, lim, nu_estimate(dd, e0, e1)));
+                }
+                if (sn.id) sn.id[pos] = so.id[i];
             }
-            if (sn.id) sn.id[pos] = so.id[i];
         }
+        __syncwarp();
     }
 }
 
@@ -601,7 +631,8 @@ struct Disp {
     static void passB(const Geo& g, const StoreDev& so, const StoreDev& sn, const CodecDev& cur,
                       const CodecDev& next, float dc, const unsigned* ghost, const float* vcn, unsigned* flags,
                       size_t sm, cudaStream_t st) {
-        k_passB<NX, NV><<<g.nbricks, T_BRICK, sm, st>>>(g, so, sn, cur, next, dc, ghost, vcn, flags);
+        k_passB<NX, NV><<<(g.nbricks + PB_WARPS - 1) / PB_WARPS, PB_WARPS * 32, sm, st>>>(g, so, sn, cur, next, dc,
+                                                                                       ghost, vcn, flags);
     }
 };
 
@@ -667,7 +698,7 @@ void launch_decode(const Geo& g, const StoreDev& s, const float* dec, float* pos
 
 static size_t deposit_smem(const Geo& g) {
     const int F3 = g.F * g.F * g.F, E = g.B + 1, E3 = E * E * E;
-    return (size_t)F3 * 8 + (size_t)(2 * E3 + 1) * 4;
+    return (size_t)F3 * 8 + (size_t)(3 * E3 + 1) * 4;
 }
 
 void launch_deposit(const Geo& g, const StoreDev& s, float* mesh, double scale, cudaStream_t st) {
@@ -682,8 +713,9 @@ void launch_deposit(const Geo& g, const StoreDev& s, float* mesh, double scale, 
 }
 
 static size_t passA_smem(const Geo& g) {
-    const int T = g.F + 5, H3 = g.Bh * g.Bh * g.Bh, nbc = g.B * g.B * g.B;
-    size_t sm = (size_t)3 * H3 * 8 + (size_t)T * T * T * 4 + (size_t)H3 * 4 + (size_t)(nbc + 1) * 4;
+    const int T = g.F + 5, TS = g.F + 12, H3 = g.Bh * g.Bh * g.Bh, nbc = g.B * g.B * g.B;
+    size_t sm = (((size_t)3 * H3 * 8 + 15) & ~(size_t)15) + (size_t)T * T * TS * 4 + (size_t)H3 * 4 +
+                (size_t)(nbc + 1) * 4;
     if (g.nnu == 1) sm += (size_t)(3 * g.nulim + 3) * 4;
     return (sm + 15) & ~(size_t)15;
 }
@@ -703,7 +735,7 @@ void launch_cells(const Geo& g, const StepScratch& w, unsigned* off_new, float* 
 
 static size_t passB_smem(const Geo& g) {
     const int H3 = g.Bh * g.Bh * g.Bh, nbc = g.B * g.B * g.B;
-    size_t sm = (size_t)(nbc + 1 + H3 + W_BRICK * H3) * 4;
+    size_t sm = (size_t)PB_WARPS * (nbc + 1 + H3) * 4;
     if (g.nnu == 1) sm += (size_t)(3 * g.nulim + 3) * 4;
     return (sm + 15) & ~(size_t)15;
 }
