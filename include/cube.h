@@ -239,6 +239,29 @@ cube_status cube_profile_read(cube_ctx* ctx, double* ms, int32_t* kernels, int32
 /* Name of a phase ("" outside 0..CUBE_PHASES-1).  Static storage. */
 const char* cube_phase_name(int32_t phase);
 
+/* ---------------------------------------------------------------- allocation-free entry point */
+
+/* Exclusive prefix sum of per-cell particle counts into the offsets of the
+   cell-ordered store, without allocating anything.  The paper has no
+   counterpart: it exists for callers that cannot call cudaMalloc -- code
+   running inside a CUDA-graph capture, under a custom or pooled allocator
+   that must own every allocation, or in an embedded runtime with a fixed
+   memory budget.
+   counts  [n_cells] uint32 device array, read-only;
+   offsets [n_cells + 1] uint32 device array, written: offsets[i] = sum of
+           counts[0..i), offsets[n_cells] = total (the caller owns both);
+   cuda_stream: cudaStream_t to enqueue on (NULL = legacy default stream).
+   Scratch: a fixed 256 KiB array in the library's device memory, held by
+   every GPU that loads libcube until the process exits; it limits n_cells to
+   268,435,456 (CUBE_E_ARG beyond).  The first call on a device looks up the
+   array's device address with that device current (make that first call
+   before any stream capture).  All calls share the array, so calls that
+   overlap on the GPU race with each other; each call writes every scratch
+   word it reads, so nothing needs clearing between calls.  Enqueue-only.
+   Errors: CUBE_E_ARG, CUBE_E_CUDA (message via cube_last_error). */
+cube_status cube_counts_to_offsets_noalloc(const uint32_t* counts, int64_t n_cells, uint32_t* offsets,
+                                           void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -75,6 +75,7 @@ _sigs = {
     "cube_profile_read": ([_P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int32),
                            ctypes.POINTER(ctypes.c_int32)], ctypes.c_int),
     "cube_phase_name": ([ctypes.c_int32], ctypes.c_char_p),
+    "cube_counts_to_offsets_noalloc": ([_P, ctypes.c_int64, _P, _P], ctypes.c_int),
 }
 for _name, (_args, _res) in _sigs.items():
     _f = getattr(_lib, _name)
@@ -185,6 +186,13 @@ def cube_profile_read(ctx):
     _check(_lib.cube_profile_read(ctx, ms, kn, ctypes.byref(ns)))
     names = [cube_phase_name(i) for i in range(CUBE_PHASES)]
     return dict(zip(names, list(ms))), dict(zip(names, list(kn))), ns.value
+
+
+def cube_counts_to_offsets_noalloc(counts, n_cells, offsets, stream=None):
+    """Offsets of the cell-ordered store from per-cell counts, allocating nothing."""
+    if stream is not None and hasattr(stream, "cuda_stream"):
+        stream = stream.cuda_stream
+    _check(_lib.cube_counts_to_offsets_noalloc(_ptr(counts), int(n_cells), _ptr(offsets), stream))
 
 
 def cube_phase_name(phase):

@@ -128,6 +128,8 @@ double sinc(double x) { return x == 0.0 ? 1.0 : std::sin(x) / x; }
 
 }  // namespace
 
+void cube::set_last_error(const std::string& msg) { g_err = msg; }
+
 struct cube_ctx {
     cube_params P{};
     Geo g{};

@@ -1,6 +1,8 @@
 // Internal launch interface between libcube's host code and its kernels.
 #pragma once
 
+#include <string>
+
 #include "cube_common.cuh"
 
 namespace cube {
@@ -38,6 +40,9 @@ __device__ __forceinline__ int stable_round_rank(int digit, bool active, unsigne
     __syncthreads();
     return pos;
 }
+
+// ------------------------------------------------------------ cube_api.cu
+void set_last_error(const std::string& msg);     // message for cube_last_error()
 
 // ------------------------------------------------------------ k_scan.cu
 int scan_tmp_words(int64_t n);
