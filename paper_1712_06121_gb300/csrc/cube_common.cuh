@@ -80,8 +80,24 @@ __device__ __forceinline__ int nu_from_thresholds(float d, const float* __restri
     return d < 0.0f ? -k : k;
 }
 
-__device__ __forceinline__ int nu_estimate(float d, float m_over_pi_s, float m_over_pi) {
-    return __float2int_rn(m_over_pi * atanf(fabsf(d) * m_over_pi_s));
+// Starting guess for nu_from_thresholds: (M/pi) atan(|d| s) with the
+// arctangent from the polynomial of Abramowitz & Stegun 4.4.47 (Hastings),
+// |error| <= 1e-5 rad on [0, 1], and atan(x) = pi/2 - atan(1/x) above 1.
+// The error is well under one code for 2-byte codes, so the exact search
+// that follows takes at most a step or two.
+__device__ __forceinline__ int nu_estimate(float d, float s, float m_over_pi) {
+    const float x = fabsf(d) * s;
+    const bool big = x > 1.0f;
+    const float t = big ? __frcp_rn(x) : x;
+    const float t2 = t * t;
+    float p = 0.0208351f;
+    p = __fmaf_rn(p, t2, -0.0851330f);
+    p = __fmaf_rn(p, t2, 0.1801410f);
+    p = __fmaf_rn(p, t2, -0.3302995f);
+    p = __fmaf_rn(p, t2, 0.9998660f);
+    float a = p * t;
+    if (big) a = 1.57079633f - a;
+    return __float2int_rn(m_over_pi * a);
 }
 
 template <int NB>
@@ -160,6 +176,9 @@ __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+// wait until at most one committed group (the most recent) is still in flight
+__device__ __forceinline__ void cp_async_wait_prev() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
 
 // Exact sum of a 64-bit integer over the lanes of `peers` (every lane of the
 // group calls it with the same mask): values biased to [0, 2^63), split into

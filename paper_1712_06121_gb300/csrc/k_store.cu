@@ -258,7 +258,10 @@ __global__ void __launch_bounds__(T_BRICK) k_deposit(Geo g, StoreDev s, float* _
     __syncthreads();
     const int nbits = 8 * NX, half = 1 << (nbits - 1);
     const int sb = g.sbits, wmask = (1 << sb) - 1, wone = 1 << sb;
-    const unsigned total = cpref[E3];
+    const unsigned total = min(cpref[E3], (unsigned)g.Np);   // bounded even for inconsistent offsets
+    // a node's 32-bit sum of 1-byte-code weights (each < 2^(3 s)) cannot wrap
+    // when fewer than 2^(32 - 3 s) particles feed the brick
+    const bool small = 3 * sb < 32 && total < (1u << (32 - 3 * sb));
     for (unsigned q = threadIdx.x; q < total; q += blockDim.x) {
         const int t = upper_cell(cpref, E3, q);
         const unsigned i = cstart[t] + (q - cpref[t]);
@@ -273,24 +276,30 @@ __global__ void __launch_bounds__(T_BRICK) k_deposit(Geo g, StoreDev s, float* _
             wn[d] = Q & wmask;
             wm[d] = wone - wn[d];
         }
+        // all 8 corners inside the brick's nodes: no per-corner range checks
+        const bool inside = nd[0] >= 0 && nd[1] >= 0 && nd[2] >= 0 && nd[0] < F - 1 && nd[1] < F - 1 && nd[2] < F - 1;
 #pragma unroll
         for (int dz = 0; dz < 2; ++dz) {
             const int z = nd[2] + dz;
-            if (z < 0 || z >= F) continue;
+            if (!inside && (z < 0 || z >= F)) continue;
 #pragma unroll
             for (int dy = 0; dy < 2; ++dy) {
                 const int y = nd[1] + dy;
-                if (y < 0 || y >= F) continue;
+                if (!inside && (y < 0 || y >= F)) continue;
 #pragma unroll
                 for (int dx = 0; dx < 2; ++dx) {
                     const int x = nd[0] + dx;
-                    if (x < 0 || x >= F) continue;
+                    if (!inside && (x < 0 || x >= F)) continue;
                     unsigned* a = &acc[2 * ((((z << lF) + y) << lF) + x)];
                     if (NX == 1) {   // weight numerators of 1-byte codes: product < 2^27
                         const unsigned w = (unsigned)(dz ? wn[2] : wm[2]) * (unsigned)(dy ? wn[1] : wm[1]) *
                                            (unsigned)(dx ? wn[0] : wm[0]);
-                        const unsigned old = atomicAdd(a, w);
-                        if (old + w < old) atomicAdd(a + 1, 1u);
+                        if (small) {
+                            atomicAdd(a, w);          // the 32-bit sum cannot wrap: no carry
+                        } else {
+                            const unsigned old = atomicAdd(a, w);
+                            if (old + w < old) atomicAdd(a + 1, 1u);
+                        }
                     } else {
                         const unsigned long long w = (unsigned long long)(dz ? wn[2] : wm[2]) *
                                                      (unsigned long long)(dy ? wn[1] : wm[1]) *
@@ -322,8 +331,8 @@ __global__ void __launch_bounds__(T_BRICK) k_passA(Geo g, StoreDev s, const floa
                                                    float kick, float dc, StepScratch w, DriftDebug dbg) {
     extern __shared__ unsigned char pa_smem[];
     // Phi tile: T x T rows (y, z: [o - 2, o + F + 3)) of TX = F + 8 nodes
-    // (x: [o - 4, o + F + 4)), row stride TS = F + 12 floats
-    const int F = g.F, T = F + 5, TX = F + 8, TS = F + 12, T3 = T * T * TS;
+    // (x: [o - 4, o + F + 4)), row stride TS = TX floats
+    const int F = g.F, T = F + 5, TX = F + 8, TS = TX, T3 = T * T * TS;
     const int nbc = g.B * g.B * g.B, Bh = g.Bh, H3 = Bh * Bh * Bh;
     const int lim = g.nulim;
     long long* vs = reinterpret_cast<long long*>(pa_smem);                 // [3][H3]
@@ -713,7 +722,7 @@ void launch_deposit(const Geo& g, const StoreDev& s, float* mesh, double scale, 
 }
 
 static size_t passA_smem(const Geo& g) {
-    const int T = g.F + 5, TS = g.F + 12, H3 = g.Bh * g.Bh * g.Bh, nbc = g.B * g.B * g.B;
+    const int T = g.F + 5, TS = g.F + 8, H3 = g.Bh * g.Bh * g.Bh, nbc = g.B * g.B * g.B;
     size_t sm = (((size_t)3 * H3 * 8 + 15) & ~(size_t)15) + (size_t)T * T * TS * 4 + (size_t)H3 * 4 +
                 (size_t)(nbc + 1) * 4;
     if (g.nnu == 1) sm += (size_t)(3 * g.nulim + 3) * 4;
