@@ -180,18 +180,16 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 // wait until at most one committed group (the most recent) is still in flight
 __device__ __forceinline__ void cp_async_wait_prev() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
 
-// Exact sum of a 64-bit integer over the lanes of `peers` (every lane of the
-// group calls it with the same mask): values biased to [0, 2^63), split into
-// three 21-bit chunks summed with 32-bit warp reductions, recombined mod 2^64.
-// Requires |v| < 2^62.
-__device__ __forceinline__ long long group_sum_i64(unsigned peers, long long v) {
-    const unsigned long long u = (unsigned long long)v + (1ull << 62);
-    const unsigned s0 = __reduce_add_sync(peers, (unsigned)(u & 0x1FFFFFull));
-    const unsigned s1 = __reduce_add_sync(peers, (unsigned)((u >> 21) & 0x1FFFFFull));
-    const unsigned s2 = __reduce_add_sync(peers, (unsigned)(u >> 42));
-    const unsigned long long t = (unsigned long long)s0 + ((unsigned long long)s1 << 21) +
-                                 ((unsigned long long)s2 << 42);
-    return (long long)(t - (unsigned long long)__popc(peers) * (1ull << 62));
+// Lanes of `active` whose 8-bit value v (0 <= v < 256) equals this lane's:
+// one ballot per bit, intersected.  Every lane of `active` must call it.
+__device__ __forceinline__ unsigned same_value_lanes(unsigned active, int v) {
+    unsigned m = active;
+#pragma unroll
+    for (int b = 0; b < 8; ++b) {
+        const unsigned bb = __ballot_sync(active, (v >> b) & 1);
+        m &= ((v >> b) & 1) ? bb : ~bb;
+    }
+    return m;
 }
 
 // 64-bit add into shared memory from 32-bit atomics: the low word's

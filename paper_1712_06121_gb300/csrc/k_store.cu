@@ -250,10 +250,20 @@ __global__ void __launch_bounds__(T_BRICK) k_deposit(Geo g, StoreDev s, float* _
         cpack[t] = (lx + 1) | ((ly + 1) << 8) | ((lz + 1) << 16);
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-        unsigned run = 0;
-        cpref[0] = 0;
-        for (int t = 0; t < E3; ++t) { run += cpref[t + 1]; cpref[t + 1] = run; }
+    if (threadIdx.x < 32) {   // inclusive scan of the E3 counts by warp 0, 32 at a time
+        const int lane = threadIdx.x;
+        unsigned carry = 0;
+        if (lane == 0) cpref[0] = 0;
+        for (int b = 0; b < E3; b += 32) {
+            unsigned v = (b + lane < E3) ? cpref[b + lane + 1] : 0u;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned u = __shfl_up_sync(0xffffffffu, v, o);
+                if (lane >= o) v += u;
+            }
+            if (b + lane < E3) cpref[b + lane + 1] = carry + v;
+            carry += __shfl_sync(0xffffffffu, v, 31);
+        }
     }
     __syncthreads();
     const int nbits = 8 * NX, half = 1 << (nbits - 1);
@@ -449,20 +459,11 @@ __global__ void __launch_bounds__(T_BRICK) k_passA(Geo g, StoreDev s, const floa
             pv[d] = p2;
         }
         const int ei = e[0] + Bh * (e[1] + Bh * e[2]);
-        {   // lanes with the same destination cell add once, through their leader
-            const unsigned am = __activemask();
-            const unsigned peers = __match_any_sync(am, ei);
-            const bool lead = (threadIdx.x & 31) == __ffs(peers) - 1;
-            long long sv[3];
+        // per-lane shared-memory atomics (measured faster here than warp aggregation)
+        atomicAdd(&hist[ei], 1u);
 #pragma unroll
-            for (int d = 0; d < 3; ++d) sv[d] = group_sum_i64(peers, vel_fix(pv[d]));
-            if (lead) {
-                atomicAdd(&hist[ei], (unsigned)__popc(peers));
-#pragma unroll
-                for (int d = 0; d < 3; ++d)
-                    smem_add_u64(reinterpret_cast<unsigned*>(&vs[d * H3 + ei]), (unsigned long long)sv[d]);
-            }
-        }
+        for (int d = 0; d < 3; ++d)
+            smem_add_u64(reinterpret_cast<unsigned*>(&vs[d * H3 + ei]), (unsigned long long)vel_fix(pv[d]));
         if (dbg.cell_old) {
             const int cg[3] = {bx * g.B + l[0], by * g.B + l[1], bz * g.B + l[2]};
 #pragma unroll

@@ -7,7 +7,8 @@
 
 namespace cube {
 
-// Stable ranking of one round of blockDim.x items by `digit` in [0, nd):
+// Stable ranking of one round of blockDim.x items by `digit` in [0, nd),
+// nd <= 256:
 // items are ordered by (warp, lane), i.e. by thread index, and equal digits
 // keep that order.  run[nd] holds each digit's next free position and is
 // advanced by the round's counts; wcnt[NWARPS * nd] is scratch.  Every thread
@@ -21,7 +22,7 @@ __device__ __forceinline__ int stable_round_rank(int digit, bool active, unsigne
     unsigned act = __ballot_sync(0xffffffffu, active);
     int lrank = 0;
     if (active) {
-        unsigned peers = __match_any_sync(act, digit);
+        unsigned peers = same_value_lanes(act, digit);
         lrank = __popc(peers & ((1u << lane) - 1u));
         if (lrank == 0) wcnt[w * nd + digit] = (unsigned)__popc(peers);
     }
