@@ -221,8 +221,8 @@ cube_status cube_debug_drifted(cube_ctx* ctx, int32_t* cell_old, float* u_new, f
    drift, per-brick histograms of the new cells), 8 codec (next codec scale
    and tables), 9 scan (of the histograms in cell-major, brick-minor order:
    per-brick starts), 10 cells (new counts, offsets and v_c),
-   11 pass_b (stable scatter and encode).  ("timing or statistics taken in
-   the simulation", Section 2.3.3, "finalize".) */
+   11 pass_b (stable scatter and encode).  Section 2.3.3 places such timing
+   statistics in the code's final stage. */
 #define CUBE_PHASES 12
 
 /* Record CUDA events on the context's stream at every phase boundary of the

@@ -151,7 +151,8 @@ def test_density_matches_oracle(cube, nps, nf, xb):
 
 
 @pytest.mark.parametrize("nps,nf,deconv", [(8, 16, 2), (12, 24, 2), (16, 32, 0), (24, 48, 2), (32, 64, 1),
-                                           (48, 96, 2), (64, 128, 2), (96, 192, 2)])
+                                           (48, 96, 2), (64, 128, 2), (96, 192, 2), (128, 256, 2),
+                                           (192, 384, 2)])
 def test_potential_matches_oracle(cube, nps, nf, deconv):
     w, ic = _ics(nps, nf)
     prm, ctx = _ctx(cube, nf, nps ** 3, 1, 1, w, deconv=deconv)
