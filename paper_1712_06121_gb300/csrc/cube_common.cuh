@@ -88,7 +88,9 @@ __device__ __forceinline__ int nu_from_thresholds(float d, const float* __restri
 __device__ __forceinline__ int nu_estimate(float d, float s, float m_over_pi) {
     const float x = fabsf(d) * s;
     const bool big = x > 1.0f;
-    const float t = big ? __frcp_rn(x) : x;
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));    // a guess needs no exact reciprocal
+    const float t = big ? r : x;
     const float t2 = t * t;
     float p = 0.0208351f;
     p = __fmaf_rn(p, t2, -0.0851330f);

@@ -51,6 +51,20 @@ __device__ double block_sum_double(double v, double* sh) {
     return s;
 }
 
+__device__ float block_sum_float(float v, float* sh) {
+    // fixed-shape tree: deterministic for a given block size
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if (lane == 0) sh[w] = v;
+    __syncthreads();
+    float s = 0.0f;
+    if (threadIdx.x == 0)
+        for (int i = 0; i < nw; ++i) s += sh[i];
+    __syncthreads();
+    return s;
+}
+
 __device__ __forceinline__ double snap_sigma_dev(double x) {
     // nearest 2^(m/16) in log2 (ties up), floor 2^-30
     x = fmax(x, 9.313225746154785e-10);
@@ -337,7 +351,7 @@ __global__ void __launch_bounds__(T_BRICK) k_deposit(Geo g, StoreDev s, float* _
 // destination cells over the brick and its one-cell halo (Bh^3 cells) with
 // fixed-point momentum sums, and (1-byte velocities) the codec tables.
 template <int NX, int NV>
-__global__ void __launch_bounds__(T_BRICK) k_passA(Geo g, StoreDev s, const float* __restrict__ phi, CodecDev cur,
+__global__ void __launch_bounds__(T_BRICK, 4) k_passA(Geo g, StoreDev s, const float* __restrict__ phi, CodecDev cur,
                                                    float kick, float dc, StepScratch w, DriftDebug dbg) {
     extern __shared__ unsigned char pa_smem[];
     // Phi tile: T x T rows (y, z: [o - 2, o + F + 3)) of TX = F + 8 nodes
@@ -351,6 +365,7 @@ __global__ void __launch_bounds__(T_BRICK) k_passA(Geo g, StoreDev s, const floa
     unsigned* sm_off = hist + H3;                                           // [nbc + 1]
     float* sdec = reinterpret_cast<float*>(sm_off + nbc + 1);               // NV == 1: [2 lim + 1]
     float* sthr = sdec + (NV == 1 ? 2 * lim + 1 : 0);                       // NV == 1: [lim + 2]
+    float* svc = sthr + (NV == 1 ? lim + 2 : 0);                            // [3][nbc]: v_c of the brick
     const float* dec = cur.dec;
     const float* thr = cur.thr;
     if (NV == 1) {
@@ -362,6 +377,8 @@ __global__ void __launch_bounds__(T_BRICK) k_passA(Geo g, StoreDev s, const floa
     int bx, by, bz;
     brick_coords(g, blockIdx.x, &bx, &by, &bz);
     const int L0 = blockIdx.x * nbc;
+    for (int t = threadIdx.x; t < 3 * nbc; t += blockDim.x)
+        cp_async4(&svc[t], &s.vc[(int64_t)(t >> (3 * g.lB)) * g.Ncc + L0 + (t & (nbc - 1))]);
     for (int c = threadIdx.x; c <= nbc; c += blockDim.x) sm_off[c] = s.offsets[L0 + c];
     for (int t = threadIdx.x; t < H3; t += blockDim.x) {
         hist[t] = 0u;
@@ -373,15 +390,40 @@ __global__ void __launch_bounds__(T_BRICK) k_passA(Geo g, StoreDev s, const floa
     // 16-byte boundary, so they load as 4-node chunks, each wrapped on its own
     const int ox = bx * F - 4, oy = by * F - 2, oz = bz * F - 2;
     {
-        const int CX = TX >> 2, nrow = T * T;
-        for (int q = threadIdx.x; q < nrow * CX; q += blockDim.x) {
-            const int row = q / CX, cx = q - row * CX;
-            const int z = row / T, y = row - z * T;
-            const float* src = phi + ((int64_t)wrap1(oz + z, g.N) * g.N + wrap1(oy + y, g.N)) * g.S;
-            cp_async16(&tile[row * TS + 4 * cx], src + wrap1(ox + 4 * cx, g.N));
+        // thread t < RPI * CX owns chunk column cx of rows t / CX, + RPI, + 2 RPI, ...:
+        // the row's (y, z) advance by constants, with no division in the loop
+        const int CX = TX >> 2, nrow = T * T, RPI = T_BRICK / CX;
+        if (threadIdx.x < RPI * CX) {
+            const int cx = threadIdx.x % CX;
+            int row = threadIdx.x / CX;
+            int z = row / T, y = row - z * T;
+            const int dz = RPI / T, dy = RPI - dz * T;
+            const float* xsrc = phi + wrap1(ox + 4 * cx, g.N);
+            float* dst = tile + 4 * cx;
+            for (; row < nrow; row += RPI) {
+                cp_async16(dst + row * TS, xsrc + ((int64_t)wrap1(oz + z, g.N) * g.N + wrap1(oy + y, g.N)) * g.S);
+                y += dy;
+                z += dz;
+                if (y >= T) {
+                    y -= T;
+                    ++z;
+                }
+            }
         }
-        cp_async_wait_all();
     }
+    // the brick's particle range, and the first round's codes, requested
+    // while the tile is in flight
+    const unsigned q1 = min(s.offsets[L0 + nbc], (unsigned)g.Np);
+    unsigned i = min(s.offsets[L0], q1) + threadIdx.x;
+    int nchi[3] = {0, 0, 0}, nnu[3] = {0, 0, 0};
+    if (i < q1) {
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            nchi[d] = load_code<NX>(s.chi, d * g.Np + i);
+            nnu[d] = load_nu<NV>(s.nu, d * g.Np + i, lim);
+        }
+    }
+    cp_async_wait_all();
     __syncthreads();
     const float e0 = cur.est[0], e1 = cur.est[1];
     const int nbits = 8 * NX, half = 1 << (nbits - 1);
@@ -393,15 +435,23 @@ __global__ void __launch_bounds__(T_BRICK) k_passA(Geo g, StoreDev s, const floa
     int mig = 0;
     bool migbad = false;
     const int TT = T * TS;   // z stride of the tile
-    const unsigned q1 = min(sm_off[nbc], (unsigned)g.Np);
-    for (unsigned i = min(sm_off[0], q1) + threadIdx.x; i < q1; i += blockDim.x) {
+    for (; i < q1; i += blockDim.x) {
+        // this round's codes; the next round's are requested now
+        const int cchi[3] = {nchi[0], nchi[1], nchi[2]}, cnu[3] = {nnu[0], nnu[1], nnu[2]};
+        if (i + blockDim.x < q1) {
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                nchi[d] = load_code<NX>(s.chi, d * g.Np + i + blockDim.x);
+                nnu[d] = load_nu<NV>(s.nu, d * g.Np + i + blockDim.x, lim);
+            }
+        }
         int lc = upper_cell(sm_off, nbc, i);
         int l[3] = {lc & (g.B - 1), (lc >> g.lB) & (g.B - 1), lc >> (2 * g.lB)};
         int Q[3], n[3];
         float wv[3];
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
-            Q[d] = 2 * (load_code<NX>(s.chi, d * g.Np + i) + half) + 1;
+            Q[d] = 2 * (cchi[d] + half) + 1;
             n[d] = (d == 0 ? 4 : 2) + (l[d] << g.r) + (Q[d] >> sb);
             wv[d] = (float)(Q[d] & wmask) * winv;
         }
@@ -441,8 +491,8 @@ __global__ void __launch_bounds__(T_BRICK) k_passA(Geo g, StoreDev s, const floa
         float pv[3], un[3];
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
-            const float vcd = s.vc[(int64_t)d * g.Ncc + L0 + lc];
-            int nu = load_nu<NV>(s.nu, d * g.Np + i, g.nulim);
+            const float vcd = svc[(d << (3 * g.lB)) + lc];
+            const int nu = cnu[d];
             float v = vcd + dec[nu + lim];
             float p1 = __fmaf_rn(force[d], kick, v);
             float dd = p1 - vcd;
@@ -490,9 +540,9 @@ __global__ void __launch_bounds__(T_BRICK) k_passA(Geo g, StoreDev s, const floa
                           (unsigned long long)vs[d * H3 + t]);
         }
     }
-    __shared__ double red[32];
-    double tot = block_sum_double((double)sacc, red);
-    if (threadIdx.x == 0) w.part[blockIdx.x] = (float)tot;
+    __shared__ float red[T_BRICK / 32];
+    const float tot = block_sum_float(sacc, red);
+    if (threadIdx.x == 0) w.part[blockIdx.x] = tot;
     // block max of the migration
     __shared__ int mmax;
     if (threadIdx.x == 0) mmax = 0;
@@ -727,6 +777,7 @@ static size_t passA_smem(const Geo& g) {
     size_t sm = (((size_t)3 * H3 * 8 + 15) & ~(size_t)15) + (size_t)T * T * TS * 4 + (size_t)H3 * 4 +
                 (size_t)(nbc + 1) * 4;
     if (g.nnu == 1) sm += (size_t)(3 * g.nulim + 3) * 4;
+    sm += (size_t)3 * nbc * 4;
     return (sm + 15) & ~(size_t)15;
 }
 
