@@ -144,6 +144,158 @@ __device__ __forceinline__ void tile_fft(float2* buf, const float2* tw) {
     }
 }
 
+// First pass (span 1, no twiddles) of a column tile straight from global
+// memory: column c of element j + m n/R is src[(j + m n/R) rs + c0 + c], zero
+// at or past column ncol.  The caller's cp.async copies (twiddles, tables)
+// are waited for before the closing barrier.
+template <int n, int R, bool INV>
+__device__ __forceinline__ void fft_pass_load(float2* buf, const float2* __restrict__ src, int64_t rs, int c0,
+                                              int ncol) {
+    constexpr int nq = n / R;
+    constexpr int nbf = nq * NC;
+    constexpr int KMAX = (nbf + FFT_T - 1) / FFT_T;
+#pragma unroll 1
+    for (int q = 0; q < KMAX; ++q) {
+        const int b = threadIdx.x + q * FFT_T;
+        if (nbf % FFT_T == 0 || b < nbf) {
+            const int c = b & (NC - 1), j = b >> LOG_NC;
+            const bool ok = c0 + c < ncol;
+            const float2* p = src + (int64_t)j * rs + c0 + c;
+            float2 v[R];
+#pragma unroll
+            for (int m = 0; m < R; ++m) v[m] = ok ? p[(int64_t)m * nq * rs] : make_float2(0.f, 0.f);
+            dft<R, INV>(v);
+#pragma unroll
+            for (int m = 0; m < R; ++m) buf[sidx<false>(j * R + m, c)] = v[m];
+        }
+    }
+    cp_async_wait_all();
+    __syncthreads();
+}
+
+// Last pass of a column tile: results (natural order, element j + m Ns) go
+// straight to dst[(j + m Ns) rs + c0 + c] for columns below ncol, each first
+// passed through post(element, column, value).  Shared memory is only read:
+// the caller synchronises before reusing the tile.
+template <int n, int Ns, int R, int TWM, bool INV, class Post>
+__device__ __forceinline__ void fft_pass_store(const float2* buf, const float2* tw, float2* dst, int64_t rs, int c0,
+                                               int ncol, Post post) {
+    constexpr int nq = n / R;
+    static_assert(nq == Ns, "the last pass has span n / R");
+    constexpr int nbf = nq * NC;
+    constexpr int KMAX = (nbf + FFT_T - 1) / FFT_T;
+    constexpr int step = TWM * (n / (Ns * R));
+#pragma unroll 1
+    for (int q = 0; q < KMAX; ++q) {
+        const int b = threadIdx.x + q * FFT_T;
+        if (nbf % FFT_T == 0 || b < nbf) {
+            const int c = b & (NC - 1), j = b >> LOG_NC;
+            float2 v[R];
+#pragma unroll
+            for (int m = 0; m < R; ++m) v[m] = buf[sidx<false>(j + m * nq, c)];
+            if (Ns > 1) {
+#pragma unroll
+                for (int m = 1; m < R; ++m) {
+                    float2 w = tw[j * m * step];
+                    if (INV) w.y = -w.y;
+                    v[m] = cmul(v[m], w);
+                }
+            }
+            dft<R, INV>(v);
+            if (c0 + c < ncol) {
+                float2* p = dst + (int64_t)j * rs + c0 + c;
+#pragma unroll
+                for (int m = 0; m < R; ++m) p[(int64_t)m * Ns * rs] = post(j + m * Ns, c, v[m]);
+            }
+        }
+    }
+}
+
+struct NoPost {
+    __device__ __forceinline__ float2 operator()(int, int, float2 v) const { return v; }
+};
+
+// passes from span Ns on, the last one through fft_pass_store
+template <int n, int Ns, int TWM, bool INV, class Post>
+__device__ __forceinline__ void tile_fft_to_global(float2* buf, const float2* tw, float2* dst, int64_t rs, int c0,
+                                                   int ncol, Post post) {
+    constexpr int rem = n / Ns;
+    constexpr int R = rem % 8 == 0 ? 8 : rem % 4 == 0 ? 4 : rem % 2 == 0 ? 2 : 3;
+    static_assert(rem % R == 0, "length must be 2^a 3^b");
+    if constexpr (Ns * R == n) {
+        fft_pass_store<n, Ns, R, TWM, INV>(buf, tw, dst, rs, c0, ncol, post);
+    } else {
+        fft_pass<n, Ns, R, TWM, INV, false>(buf, tw);
+        tile_fft_to_global<n, Ns * R, TWM, INV>(buf, tw, dst, rs, c0, ncol, post);
+    }
+}
+
+// passes from span Ns up to (not including) the last, in shared memory
+template <int n, int Ns, int TWM, bool INV>
+__device__ __forceinline__ void tile_fft_but_last(float2* buf, const float2* tw) {
+    constexpr int rem = n / Ns;
+    constexpr int R = rem % 8 == 0 ? 8 : rem % 4 == 0 ? 4 : rem % 2 == 0 ? 2 : 3;
+    if constexpr (Ns * R < n) {
+        fft_pass<n, Ns, R, TWM, INV, false>(buf, tw);
+        tile_fft_but_last<n, Ns * R, TWM, INV>(buf, tw);
+    }
+}
+
+template <int n>
+constexpr int first_radix() {
+    return n % 8 == 0 ? 8 : n % 4 == 0 ? 4 : n % 2 == 0 ? 2 : 3;
+}
+
+template <int n>
+constexpr int last_span() {   // span of the last pass of tile_fft<n, 1, ...>
+    int ns = 1;
+    while (true) {
+        const int rem = n / ns;
+        const int r = rem % 8 == 0 ? 8 : rem % 4 == 0 ? 4 : rem % 2 == 0 ? 2 : 3;
+        if (ns * r == n) return ns;
+        ns *= r;
+    }
+}
+
+// last pass in shared memory, each result passed through post(element, column, value)
+template <int n, int Ns, int R, int TWM, bool INV, class Post>
+__device__ __forceinline__ void fft_pass_post(float2* buf, const float2* tw, Post post) {
+    constexpr int nq = n / R;
+    constexpr int nbf = nq * NC;
+    constexpr int KMAX = (nbf + FFT_T - 1) / FFT_T;
+    constexpr int step = TWM * (n / (Ns * R));
+    float2 v[KMAX][R];
+#pragma unroll
+    for (int q = 0; q < KMAX; ++q) {
+        const int b = threadIdx.x + q * FFT_T;
+        if (nbf % FFT_T == 0 || b < nbf) {
+            const int c = b & (NC - 1), j = b >> LOG_NC;
+#pragma unroll
+            for (int m = 0; m < R; ++m) v[q][m] = buf[sidx<false>(j + m * nq, c)];
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < KMAX; ++q) {
+        const int b = threadIdx.x + q * FFT_T;
+        if (nbf % FFT_T == 0 || b < nbf) {
+            const int c = b & (NC - 1), j = b >> LOG_NC;
+            if (Ns > 1) {
+#pragma unroll
+                for (int m = 1; m < R; ++m) {
+                    float2 w = tw[j * m * step];
+                    if (INV) w.y = -w.y;
+                    v[q][m] = cmul(v[q][m], w);
+                }
+            }
+            dft<R, INV>(v[q]);
+#pragma unroll
+            for (int m = 0; m < R; ++m) buf[sidx<false>(j + m * Ns, c)] = post(j + m * Ns, c, v[q][m]);
+        }
+    }
+    __syncthreads();
+}
+
 // twiddle table into shared memory (asynchronous; waited for with the tile)
 __device__ __forceinline__ void load_tw(float2* stw, const float2* tw, int N) {
     for (int i = threadIdx.x; i < N; i += blockDim.x) cp_async8(&stw[i], &tw[i]);
@@ -246,8 +398,10 @@ __global__ void __launch_bounds__(FFT_T) k_fft_x_c2r(float* mesh, int S, const f
 }
 
 // ------------------------------------------------------------ y sweep
+// The tile's first pass reads global memory and its last pass writes it:
+// shared memory holds only the intermediate passes.
 template <int N, bool INV>
-__global__ void __launch_bounds__(FFT_T) k_fft_y(float* mesh, int S, const float2* __restrict__ tw) {
+__global__ void __launch_bounds__(FFT_T, N <= 512 ? 2 : 1) k_fft_y(float* mesh, int S, const float2* __restrict__ tw) {
     extern __shared__ float2 fsm[];
     float2* stw = fsm;
     float2* buf = fsm + N;
@@ -256,19 +410,28 @@ __global__ void __launch_bounds__(FFT_T) k_fft_y(float* mesh, int S, const float
     constexpr int ncol = N / 2 + 1;
     const int c0 = blockIdx.x * NC;
     float2* slab = reinterpret_cast<float2*>(mesh) + (int64_t)blockIdx.y * N * Sc;
-    load_columns(buf, slab, N, Sc, c0, ncol);
-    cp_async_wait_all();
-    __syncthreads();
-    tile_fft<N, 1, 1, INV, false>(buf, stw);
-    for (int t = threadIdx.x; t < N * NC; t += FFT_T) {
-        const int c = t & (NC - 1), y = t >> LOG_NC;
-        if (c0 + c < ncol) slab[(int64_t)y * Sc + c0 + c] = buf[sidx<false>(y, c)];
-    }
+    fft_pass_load<N, first_radix<N>(), INV>(buf, slab, Sc, c0, ncol);
+    tile_fft_to_global<N, first_radix<N>(), 1, INV>(buf, stw, slab, Sc, c0, ncol, NoPost{});
 }
 
 // ------------------------------------------------------------ z sweep (+ Green)
+// Green's function -(3/2) Om / k^2 / W(k)^p / N^3 of one column (kx, ky), kz = z
+struct GreenPost {
+    const float* sk2;
+    const float* swd;
+    float g0, ky2, wy;
+    int c0, ky, ncol;
+    __device__ __forceinline__ float2 operator()(int z, int c, float2 v) const {
+        const int kx = c0 + c;
+        if (kx >= ncol) return v;
+        const float kk = sk2[kx] + ky2 + sk2[z];
+        const float gr = (kx == 0 && ky == 0 && z == 0) ? 0.0f : g0 / kk * (swd[kx] * wy * swd[z]);
+        return make_float2(v.x * gr, v.y * gr);
+    }
+};
+
 template <int N, int MODE>   // 0: forward only, 1: forward, Green, inverse
-__global__ void __launch_bounds__(FFT_T) k_fft_z(float* mesh, int S, const float2* __restrict__ tw,
+__global__ void __launch_bounds__(FFT_T, N <= 512 ? 2 : 1) k_fft_z(float* mesh, int S, const float2* __restrict__ tw,
                                                  const float* __restrict__ k2, const float* __restrict__ wdec, float g0) {
     extern __shared__ float2 fsm[];
     float2* stw = fsm;
@@ -282,33 +445,20 @@ __global__ void __launch_bounds__(FFT_T) k_fft_z(float* mesh, int S, const float
     const int ky = blockIdx.y;
     float2* base = reinterpret_cast<float2*>(mesh) + (int64_t)ky * Sc;
     const int64_t zs = (int64_t)N * Sc;
-    load_columns(buf, base, N, zs, c0, ncol);
     if (MODE == 1)
         for (int i = threadIdx.x; i < N; i += blockDim.x) {
             cp_async4(&sk2[i], &k2[i]);
             cp_async4(&swd[i], &wdec[i]);
         }
-    cp_async_wait_all();
-    __syncthreads();
-    tile_fft<N, 1, 1, false, false>(buf, stw);
+    fft_pass_load<N, first_radix<N>(), false>(buf, base, zs, c0, ncol);
     if (MODE == 1) {
-        const float ky2 = sk2[ky], wy = swd[ky];
-        for (int t = threadIdx.x; t < N * NC; t += FFT_T) {
-            const int c = t & (NC - 1), z = t >> LOG_NC;
-            const int kx = c0 + c;
-            if (kx < ncol) {
-                const float kk = sk2[kx] + ky2 + sk2[z];
-                const float gr = (kx == 0 && ky == 0 && z == 0) ? 0.0f : g0 / kk * (swd[kx] * wy * swd[z]);
-                const float2 v = buf[sidx<false>(z, c)];
-                buf[sidx<false>(z, c)] = make_float2(v.x * gr, v.y * gr);
-            }
-        }
-        __syncthreads();
-        tile_fft<N, 1, 1, true, false>(buf, stw);
-    }
-    for (int t = threadIdx.x; t < N * NC; t += FFT_T) {
-        const int c = t & (NC - 1), z = t >> LOG_NC;
-        if (c0 + c < ncol) base[z * zs + c0 + c] = buf[sidx<false>(z, c)];
+        tile_fft_but_last<N, first_radix<N>(), 1, false>(buf, stw);
+        constexpr int Ns = last_span<N>();
+        const GreenPost gp{sk2, swd, g0, sk2[ky], swd[ky], c0, ky, ncol};
+        fft_pass_post<N, Ns, N / Ns, 1, false>(buf, stw, gp);
+        tile_fft_to_global<N, 1, 1, true>(buf, stw, base, zs, c0, ncol, NoPost{});
+    } else {
+        tile_fft_to_global<N, first_radix<N>(), 1, false>(buf, stw, base, zs, c0, ncol, NoPost{});
     }
 }
 

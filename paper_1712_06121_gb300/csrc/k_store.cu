@@ -585,7 +585,7 @@ __global__ void k_cells(Geo g, StepScratch w, unsigned* __restrict__ off_new, fl
 constexpr int PB_WARPS = 8;
 
 template <int NX, int NV>
-__global__ void __launch_bounds__(PB_WARPS * 32) k_passB(Geo g, StoreDev so, StoreDev sn, CodecDev cur, CodecDev next,
+__global__ void __launch_bounds__(PB_WARPS * 32, 6) k_passB(Geo g, StoreDev so, StoreDev sn, CodecDev cur, CodecDev next,
                                                         float dc, const unsigned* __restrict__ ghost,
                                                         const float* __restrict__ vc_new, unsigned* flags) {
     extern __shared__ unsigned pb_smem[];
@@ -595,8 +595,10 @@ __global__ void __launch_bounds__(PB_WARPS * 32) k_passB(Geo g, StoreDev so, Sto
     float* sdec = reinterpret_cast<float*>(pb_smem);                       // NV == 1: [2 lim + 1]
     float* sthr = sdec + (NV == 1 ? 2 * lim + 1 : 0);                       // NV == 1: [lim + 2]
     unsigned* wbase = reinterpret_cast<unsigned*>(sthr + (NV == 1 ? lim + 2 : 0));
-    unsigned* sm_off = wbase + warp * (nbc + 1 + H3);                       // [nbc + 1] per warp
+    unsigned* sm_off = wbase + warp * (4 * nbc + 1 + 4 * H3);               // [nbc + 1] per warp
     unsigned* run = sm_off + nbc + 1;                                       // [H3] per warp
+    float* svc = reinterpret_cast<float*>(run + H3);                        // [3][nbc]: v_c of the brick
+    float* svn = svc + 3 * nbc;                                             // [3][H3]: v_c* of the halo region
     const float* dec = cur.dec;
     const float* thr = next.thr;
     if (NV == 1) {
@@ -612,37 +614,63 @@ __global__ void __launch_bounds__(PB_WARPS * 32) k_passB(Geo g, StoreDev so, Sto
     int bx, by, bz;
     brick_coords(g, brick, &bx, &by, &bz);
     const int bc[3] = {bx, by, bz};
+    // the brick's particle range and the first round's codes and ids first,
+    // so their latency overlaps the staging below
+    const unsigned p1 = min(so.offsets[L0 + nbc], (unsigned)g.Np), p0 = min(so.offsets[L0], p1);
+    int nchi[3] = {0, 0, 0}, nnu[3] = {0, 0, 0};
+    unsigned nid = 0;
+    if (p0 + lane < p1) {
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            nchi[d] = load_code<NX>(so.chi, d * g.Np + p0 + lane);
+            nnu[d] = load_nu<NV>(so.nu, d * g.Np + p0 + lane, lim);
+        }
+        if (sn.id) nid = so.id[p0 + lane];
+    }
     for (int c = lane; c <= nbc; c += 32) sm_off[c] = so.offsets[L0 + c];
+    for (int t = lane; t < 3 * nbc; t += 32) svc[t] = so.vc[(int64_t)(t >> (3 * g.lB)) * g.Ncc + L0 + (t & (nbc - 1))];
     for (int t = lane; t < H3; t += 32) {
         const int e[3] = {t % Bh, (t / Bh) % Bh, t / (Bh * Bh)};
         run[t] = ghost[flat_slot(g, bc, e)];
+        const int L = cell_rank(g, wrap1(bx * g.B - 1 + e[0], g.Nc), wrap1(by * g.B - 1 + e[1], g.Nc),
+                                wrap1(bz * g.B - 1 + e[2], g.Nc));
+#pragma unroll
+        for (int d = 0; d < 3; ++d) svn[d * H3 + t] = vc_new[(int64_t)d * g.Ncc + L];
     }
     __syncwarp();
     const int nbits = 8 * NX, half = 1 << (nbits - 1), bmask = (1 << nbits) - 1;
     const float inv2q = ldexpf(1.0f, -(nbits + 1));
     const float two8n = ldexpf(1.0f, nbits);
     const float e0 = next.est[0], e1 = next.est[1];
-    const unsigned p1 = min(sm_off[nbc], (unsigned)g.Np), p0 = min(sm_off[0], p1);
     for (unsigned base = p0; base < p1; base += 32) {
         const unsigned i = base + lane;
         const bool act = i < p1;
         const unsigned am = __ballot_sync(0xffffffffu, act);
+        // this round's codes; the next round's are requested now
+        const int cchi[3] = {nchi[0], nchi[1], nchi[2]}, cnu[3] = {nnu[0], nnu[1], nnu[2]};
+        const unsigned cid = nid;
+        if (i + 32 < p1) {
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                nchi[d] = load_code<NX>(so.chi, d * g.Np + i + 32);
+                nnu[d] = load_nu<NV>(so.nu, d * g.Np + i + 32, lim);
+            }
+            if (sn.id) nid = so.id[i + 32];
+        }
         if (act) {
             const int lc = upper_cell(sm_off, nbc, i);
             const int l[3] = {lc & (g.B - 1), (lc >> g.lB) & (g.B - 1), lc >> (2 * g.lB)};
-            int e[3], chi[3], cn[3];
+            int e[3], chi[3];
             float pv[3];
 #pragma unroll
             for (int d = 0; d < 3; ++d) {
-                const int Q = 2 * (load_code<NX>(so.chi, d * g.Np + i) + half) + 1;
-                const int nu = load_nu<NV>(so.nu, d * g.Np + i, lim);
-                const float p2 = so.vc[(int64_t)d * g.Ncc + L0 + lc] + dec[nu + lim];
+                const int Q = 2 * (cchi[d] + half) + 1;
+                const float p2 = svc[(d << (3 * g.lB)) + lc] + dec[cnu[d] + lim];
                 float un;
                 const int bin = drift_bin(Q, p2, dc, inv2q, two8n, &un);
                 const int sh = max(-1, min(1, bin >> nbits));
                 e[d] = l[d] + sh + 1;
                 chi[d] = (bin & bmask) - half;
-                cn[d] = wrap1(bc[d] * g.B + l[d] + sh, g.Nc);
                 pv[d] = p2;
             }
             const int ei = e[0] + Bh * (e[1] + Bh * e[2]);
@@ -656,14 +684,13 @@ __global__ void __launch_bounds__(PB_WARPS * 32) k_passB(Geo g, StoreDev so, Sto
             if (pos >= (unsigned)g.Np) {
                 atomicOr(flags, ERR_COUNT);
             } else {
-                const int Ln = cell_rank(g, cn[0], cn[1], cn[2]);
 #pragma unroll
                 for (int d = 0; d < 3; ++d) {
                     store_code<NX>(sn.chi, d * g.Np + pos, chi[d]);
-                    const float dd = pv[d] - vc_new[(int64_t)d * g.Ncc + Ln];
+                    const float dd = pv[d] - svn[d * H3 + ei];
                     store_code<NV>(sn.nu, d * g.Np + pos, nu_from_thresholds(dd, thr, lim, nu_estimate(dd, e0, e1)));
                 }
-                if (sn.id) sn.id[pos] = so.id[i];
+                if (sn.id) sn.id[pos] = cid;
             }
         }
         __syncwarp();
@@ -796,7 +823,7 @@ void launch_cells(const Geo& g, const StepScratch& w, unsigned* off_new, float* 
 
 static size_t passB_smem(const Geo& g) {
     const int H3 = g.Bh * g.Bh * g.Bh, nbc = g.B * g.B * g.B;
-    size_t sm = (size_t)PB_WARPS * (nbc + 1 + H3) * 4;
+    size_t sm = (size_t)PB_WARPS * (4 * nbc + 1 + 4 * H3) * 4;
     if (g.nnu == 1) sm += (size_t)(3 * g.nulim + 3) * 4;
     return (sm + 15) & ~(size_t)15;
 }
