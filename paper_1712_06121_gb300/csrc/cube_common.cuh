@@ -61,11 +61,41 @@ __device__ __forceinline__ long long vel_fix(float v) {
     return __float2ll_rn(v * 16777216.0f);
 }
 
-// v_c = mean of the cell's fixed-point velocities, rounded to FP32
+// v_c = mean of the cell's fixed-point velocities s / n, as the FP32 value
+// fl32(fl64(s) / n * 2^-24).  For |s| < 2^53 and n < 2^27 the quotient s / n
+// is either an FP32 rounding midpoint or at least 2^-52 (relative) away from
+// every one -- more than FP64's half ulp -- so the FP64 rounding never moves
+// the FP32 result: it is the correctly rounded fl32(s / n * 2^-24), formed
+// here from a 64-bit integer quotient of 26-27 bits and a sticky bit (the
+// FP64 division is very slow on this part).  Larger inputs divide in FP64.
 __device__ __forceinline__ float vel_unfix_mean(long long s, unsigned n) {
-    if (n == 0) return 0.0f;
-    double m = __ll2double_rn(s) / (double)n;
-    return __double2float_rn(m * (1.0 / 16777216.0));
+    if (n == 0 || s == 0) return 0.0f;
+    const unsigned long long a = s < 0 ? 0ull - (unsigned long long)s : (unsigned long long)s;
+    if (a >= (1ull << 53) || n >= (1u << 27)) {
+        const double m = __ll2double_rn(s) / (double)n;
+        return __double2float_rn(m * (1.0 / 16777216.0));
+    }
+    const int la = 63 - __clzll((long long)a), ln = 31 - __clz((int)n);
+    const int k = 26 - (la - ln);                      // shift giving a quotient in [2^25, 2^27)
+    unsigned long long q;
+    bool sticky;
+    int e;
+    if (k >= 0) {
+        const unsigned long long num = a << k;         // < 2^53
+        q = num / n;
+        sticky = num - q * n != 0;
+        e = -k;
+    } else {
+        q = a / n;
+        sticky = a - q * n != 0;
+        e = 0;
+    }
+    const int t = 64 - __clzll((long long)q) - 24;     // bits below the 24 kept
+    const unsigned long long low = q & ((1ull << t) - 1), half = 1ull << (t - 1);
+    unsigned long long q24 = q >> t;
+    if (low > half || (low == half && (sticky || (q24 & 1)))) ++q24;   // nearest, ties to even
+    const float v = ldexpf((float)q24, e + t - 24);
+    return s < 0 ? -v : v;
 }
 
 // Eq. nu via exact thresholds: thr[k] (k = 1..lim) is the smallest float >=
