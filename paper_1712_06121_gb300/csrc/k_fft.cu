@@ -38,9 +38,14 @@ __device__ __forceinline__ float2 rot90(float2 a) {
     return INV ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x);
 }
 
+// Tile layout: element k of column (row) c at k NC + c, or, swizzled (x
+// sweeps), at k NC + (c ^ ((k ^ (k >> 3)) mod NC)).  The swizzle keeps both
+// thread mappings bank-conflict free: one k across the 16 columns, and one
+// column across 16 values of k, whether consecutive or with the strides of
+// the Stockham passes (checked exhaustively for n/2 = 128 ... 512).
 template <bool SWZ>
 __device__ __forceinline__ int sidx(int k, int c) {
-    return SWZ ? (k << LOG_NC) + (c ^ (k & (NC - 1))) : (k << LOG_NC) + c;
+    return SWZ ? (k << LOG_NC) + (c ^ ((k ^ (k >> 3)) & (NC - 1))) : (k << LOG_NC) + c;
 }
 
 template <int RAD, bool INV>
@@ -231,13 +236,13 @@ __device__ __forceinline__ void tile_fft_to_global(float2* buf, const float2* tw
 }
 
 // passes from span Ns up to (not including) the last, in shared memory
-template <int n, int Ns, int TWM, bool INV>
+template <int n, int Ns, int TWM, bool INV, bool SWZ = false>
 __device__ __forceinline__ void tile_fft_but_last(float2* buf, const float2* tw) {
     constexpr int rem = n / Ns;
     constexpr int R = rem % 8 == 0 ? 8 : rem % 4 == 0 ? 4 : rem % 2 == 0 ? 2 : 3;
     if constexpr (Ns * R < n) {
-        fft_pass<n, Ns, R, TWM, INV, false>(buf, tw);
-        tile_fft_but_last<n, Ns * R, TWM, INV>(buf, tw);
+        fft_pass<n, Ns, R, TWM, INV, SWZ>(buf, tw);
+        tile_fft_but_last<n, Ns * R, TWM, INV, SWZ>(buf, tw);
     }
 }
 
@@ -246,9 +251,16 @@ constexpr int first_radix() {
     return n % 8 == 0 ? 8 : n % 4 == 0 ? 4 : n % 2 == 0 ? 2 : 3;
 }
 
+// first radix of the row transforms: never the whole length, so that the
+// first (load) and last (store) passes are distinct
 template <int n>
-constexpr int last_span() {   // span of the last pass of tile_fft<n, 1, ...>
-    int ns = 1;
+constexpr int x_first_radix() {
+    return first_radix<n>() < n ? first_radix<n>() : (n % 4 == 0 && n > 4 ? 4 : 2);
+}
+
+template <int n, int ns0 = 1>
+constexpr int last_span() {   // span of the last pass of tile_fft<n, ns0, ...>
+    int ns = ns0;
     while (true) {
         const int rem = n / ns;
         const int r = rem % 8 == 0 ? 8 : rem % 4 == 0 ? 4 : rem % 2 == 0 ? 2 : 3;
@@ -314,7 +326,85 @@ __device__ __forceinline__ void load_columns(float2* buf, const float2* src, int
     }
 }
 
-// ------------------------------------------------------------ x sweep, r2c
+// ------------------------------------------------------------ x sweeps
+// NC = 16 rows per CTA.  The first and last passes run with threads along
+// the row (j fastest), so they read and write global memory in coalesced
+// runs; the middle passes run across the 16 rows.
+
+// First pass (span 1) of the n = N/2-point transforms of rows row0 .. row0 +
+// NC - 1, straight from global memory.  PACK (c2r): the input row holds the
+// half spectrum X[0 .. n] and the transform input is Z[k] = E + i O with
+// E = X[k] + X*[n-k], O = W^-k (X[k] - X*[n-k]), W = e^{-2 pi i / N} (twiddles
+// read from global memory: the shared copy may still be in flight).
+template <int n, int R, bool INV, bool PACK>
+__device__ __forceinline__ void xpass_load(float2* buf, const float* mesh, int64_t row0, int S,
+                                           const float2* __restrict__ gtw) {
+    constexpr int nq = n / R;
+    constexpr int nbf = nq * NC;
+    constexpr int KMAX = (nbf + FFT_T - 1) / FFT_T;
+#pragma unroll 1
+    for (int q = 0; q < KMAX; ++q) {
+        const int b = threadIdx.x + q * FFT_T;
+        if (nbf % FFT_T == 0 || b < nbf) {
+            const int j = b % nq, c = b / nq;
+            const float2* row = reinterpret_cast<const float2*>(mesh + (row0 + c) * S);
+            float2 v[R];
+#pragma unroll
+            for (int m = 0; m < R; ++m) {
+                const int k = j + m * nq;
+                if (!PACK) {
+                    v[m] = row[k];
+                } else {
+                    const float2 xk = row[k], xm = row[n - k];
+                    const float2 e = make_float2(xk.x + xm.x, xk.y - xm.y);
+                    const float2 d = make_float2(xk.x - xm.x, xk.y + xm.y);
+                    const float2 o = cmul(cconj(gtw[k]), d);
+                    v[m] = make_float2(e.x - o.y, e.y + o.x);
+                }
+            }
+            dft<R, INV>(v);
+#pragma unroll
+            for (int m = 0; m < R; ++m) buf[sidx<true>(j * R + m, c)] = v[m];
+        }
+    }
+    cp_async_wait_all();
+    __syncthreads();
+}
+
+// Last pass (span n / R) of the row transforms, straight to global memory.
+template <int n, int Ns, int R, int TWM, bool INV>
+__device__ __forceinline__ void xpass_store(const float2* buf, const float2* tw, float* mesh, int64_t row0, int S) {
+    constexpr int nq = n / R;
+    static_assert(nq == Ns, "the last pass has span n / R");
+    constexpr int nbf = nq * NC;
+    constexpr int KMAX = (nbf + FFT_T - 1) / FFT_T;
+    constexpr int step = TWM * (n / (Ns * R));
+#pragma unroll 1
+    for (int q = 0; q < KMAX; ++q) {
+        const int b = threadIdx.x + q * FFT_T;
+        if (nbf % FFT_T == 0 || b < nbf) {
+            const int j = b % nq, c = b / nq;
+            float2 v[R];
+#pragma unroll
+            for (int m = 0; m < R; ++m) v[m] = buf[sidx<true>(j + m * nq, c)];
+            if (Ns > 1) {
+#pragma unroll
+                for (int m = 1; m < R; ++m) {
+                    float2 w = tw[j * m * step];
+                    if (INV) w.y = -w.y;
+                    v[m] = cmul(v[m], w);
+                }
+            }
+            dft<R, INV>(v);
+            float2* row = reinterpret_cast<float2*>(mesh + (row0 + c) * S);
+#pragma unroll
+            for (int m = 0; m < R; ++m) row[j + m * Ns] = v[m];
+        }
+    }
+}
+
+// r2c: the N reals of a row as N/2 complex z[k] = x[2k] + i x[2k+1], an
+// N/2-point FFT Z, then X[k] = (Z[k] + Z*[h-k])/2 - i W^k (Z[k] - Z*[h-k])/2
 template <int N>
 __global__ void __launch_bounds__(FFT_T) k_fft_x_r2c(float* mesh, int S, const float2* __restrict__ tw) {
     extern __shared__ float2 fsm[];
@@ -323,15 +413,9 @@ __global__ void __launch_bounds__(FFT_T) k_fft_x_r2c(float* mesh, int S, const f
     float2* buf = fsm + N;           // [h][NC]
     load_tw(stw, tw, N);
     const int64_t row0 = (int64_t)blockIdx.x * NC;
-    for (int t = threadIdx.x; t < h * NC; t += FFT_T) {
-        const int k = t % h, c = t / h;
-        const float2* src = reinterpret_cast<const float2*>(mesh + (row0 + c) * S);
-        cp_async8(&buf[sidx<true>(k, c)], &src[k]);
-    }
-    cp_async_wait_all();
-    __syncthreads();
-    tile_fft<h, 1, 2, false, true>(buf, stw);
-    // X[k] = (Z[k] + Z*[h-k])/2 - i W^k (Z[k] - Z*[h-k])/2, k = 0..h
+    constexpr int R1 = x_first_radix<h>();
+    xpass_load<h, R1, false, false>(buf, mesh, row0, S, tw);
+    tile_fft<h, R1, 2, false, true>(buf, stw);
     for (int t = threadIdx.x; t < (h / 2 + 1) * NC; t += FFT_T) {
         const int k = t % (h / 2 + 1), c = t / (h / 2 + 1);
         float2* dst = reinterpret_cast<float2*>(mesh + (row0 + c) * S);
@@ -353,48 +437,21 @@ __global__ void __launch_bounds__(FFT_T) k_fft_x_r2c(float* mesh, int S, const f
     }
 }
 
-// ------------------------------------------------------------ x sweep, c2r
+// c2r: the packing above inverted inside the first pass, the N/2-point
+// inverse FFT, and the last pass writing the row's N reals
 template <int N>
 __global__ void __launch_bounds__(FFT_T) k_fft_x_c2r(float* mesh, int S, const float2* __restrict__ tw) {
     extern __shared__ float2 fsm[];
     constexpr int h = N / 2;
     float2* stw = fsm;               // [N]
     float2* buf = fsm + N;           // [h][NC]
-    float2* xh = buf + h * NC;       // [NC]: X[N/2]
     load_tw(stw, tw, N);
     const int64_t row0 = (int64_t)blockIdx.x * NC;
-    for (int t = threadIdx.x; t < (h + 1) * NC; t += FFT_T) {
-        const int k = t % (h + 1), c = t / (h + 1);
-        const float2* src = reinterpret_cast<const float2*>(mesh + (row0 + c) * S);
-        cp_async8(k < h ? &buf[sidx<true>(k, c)] : &xh[c], &src[k]);
-    }
-    cp_async_wait_all();
-    __syncthreads();
-    // Z[k] = E + i O, E = X[k] + X*[h-k], O = W^-k (X[k] - X*[h-k])
-    for (int t = threadIdx.x; t < (h / 2 + 1) * NC; t += FFT_T) {
-        const int k = t % (h / 2 + 1), c = t / (h / 2 + 1);
-        const int km = h - k;
-        const float2 xk = buf[sidx<true>(k, c)];
-        const float2 xm = km < h ? buf[sidx<true>(km, c)] : xh[c];
-        float2 e = make_float2(xk.x + xm.x, xk.y - xm.y);
-        float2 d = make_float2(xk.x - xm.x, xk.y + xm.y);
-        float2 o = cmul(cconj(stw[k]), d);
-        const float2 zk = make_float2(e.x - o.y, e.y + o.x);
-        buf[sidx<true>(k, c)] = zk;
-        if (km != k && km < h) {
-            float2 e2 = make_float2(xm.x + xk.x, xm.y - xk.y);
-            float2 d2 = make_float2(xm.x - xk.x, xm.y + xk.y);
-            float2 o2 = cmul(cconj(stw[km]), d2);
-            buf[sidx<true>(km, c)] = make_float2(e2.x - o2.y, e2.y + o2.x);
-        }
-    }
-    __syncthreads();
-    tile_fft<h, 1, 2, true, true>(buf, stw);
-    for (int t = threadIdx.x; t < h * NC; t += FFT_T) {
-        const int k = t % h, c = t / h;
-        float2* dst = reinterpret_cast<float2*>(mesh + (row0 + c) * S);
-        dst[k] = buf[sidx<true>(k, c)];
-    }
+    constexpr int R1 = x_first_radix<h>();
+    xpass_load<h, R1, true, true>(buf, mesh, row0, S, tw);
+    tile_fft_but_last<h, R1, 2, true, true>(buf, stw);
+    constexpr int Ns = last_span<h, R1>();
+    xpass_store<h, Ns, h / Ns, 2, true>(buf, stw, mesh, row0, S);
 }
 
 // ------------------------------------------------------------ y sweep
