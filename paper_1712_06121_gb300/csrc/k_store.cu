@@ -242,6 +242,10 @@ __global__ void __launch_bounds__(T_BRICK) k_decode(Geo g, StoreDev s, const flo
 // layer below it (a particle in fine cell i also feeds node i + 1).  Weights
 // are integers (numerators over 2^s per axis) summed in int64, so the result
 // is exact and independent of the summation order; rho = m * sum * 2^(-3s).
+__device__ __forceinline__ float node_value(unsigned lo, unsigned hi) {
+    return hi ? __ull2float_rn(((unsigned long long)hi << 32) | lo) : __uint2float_rn(lo);
+}
+
 template <int NX>
 __global__ void __launch_bounds__(T_BRICK) k_deposit(Geo g, StoreDev s, float* __restrict__ mesh, float fscale) {
     extern __shared__ unsigned long long dep_smem[];
@@ -254,7 +258,8 @@ __global__ void __launch_bounds__(T_BRICK) k_deposit(Geo g, StoreDev s, float* _
     int bx, by, bz;
     brick_coords(g, blockIdx.x, &bx, &by, &bz);
     const int c0[3] = {bx * g.B, by * g.B, bz * g.B};
-    for (int t = threadIdx.x; t < 2 * F3; t += blockDim.x) acc[t] = 0u;
+    for (int t = threadIdx.x; t < F3 / 2; t += blockDim.x)            // F3 is a multiple of 64
+        reinterpret_cast<uint4*>(acc)[t] = make_uint4(0u, 0u, 0u, 0u);
     for (int t = threadIdx.x; t < E3; t += blockDim.x) {
         const int lx = t % E - 1, ly = (t / E) % E - 1, lz = t / (E * E) - 1;
         const int L = cell_rank(g, wrapi(c0[0] + lx, g.Nc), wrapi(c0[1] + ly, g.Nc), wrapi(c0[2] + lz, g.Nc));
@@ -300,6 +305,8 @@ __global__ void __launch_bounds__(T_BRICK) k_deposit(Geo g, StoreDev s, float* _
             wn[d] = Q & wmask;
             wm[d] = wone - wn[d];
         }
+        // a particle of the layer below more than one fine cell from the brick feeds none of its nodes
+        if (nd[0] < -1 || nd[1] < -1 || nd[2] < -1) continue;
         // all 8 corners inside the brick's nodes: no per-corner range checks
         const bool inside = nd[0] >= 0 && nd[1] >= 0 && nd[2] >= 0 && nd[0] < F - 1 && nd[1] < F - 1 && nd[2] < F - 1;
 #pragma unroll
@@ -335,13 +342,18 @@ __global__ void __launch_bounds__(T_BRICK) k_deposit(Geo g, StoreDev s, float* _
         }
     }
     __syncthreads();
+    // four consecutive x nodes per thread: two 16-byte shared loads, one
+    // 16-byte store (F and the row stride S are multiples of 4)
     const int ox = c0[0] * g.R, oy = c0[1] * g.R, oz = c0[2] * g.R;
-    for (int t = threadIdx.x; t < F3; t += blockDim.x) {
+    for (int t4 = threadIdx.x; t4 < F3 / 4; t4 += blockDim.x) {
+        const int t = 4 * t4;
         const int x = t & (F - 1), y = (t >> lF) & (F - 1), z = t >> (2 * lF);
-        const unsigned lo = acc[2 * t], hi = acc[2 * t + 1];
+        const uint4 a = reinterpret_cast<const uint4*>(acc)[2 * t4];        // {lo, hi} of nodes t, t + 1
+        const uint4 b = reinterpret_cast<const uint4*>(acc)[2 * t4 + 1];    // nodes t + 2, t + 3
         // exact integer sum; one rounding when the scale is a power of two (mass 2^k)
-        const float v = (hi ? __ull2float_rn(((unsigned long long)hi << 32) | lo) : __uint2float_rn(lo)) * fscale;
-        mesh[((int64_t)(oz + z) * g.N + (oy + y)) * g.S + ox + x] = v;
+        const float4 v = make_float4(node_value(a.x, a.y) * fscale, node_value(a.z, a.w) * fscale,
+                                     node_value(b.x, b.y) * fscale, node_value(b.z, b.w) * fscale);
+        *reinterpret_cast<float4*>(&mesh[((int64_t)(oz + z) * g.N + (oy + y)) * g.S + ox + x]) = v;
     }
 }
 
