@@ -56,6 +56,18 @@ __host__ __device__ __forceinline__ int wrapi(int v, int n) {
 // periodic wrap of a coordinate known to lie in [-n, 2n)
 __host__ __device__ __forceinline__ int wrap1(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
 
+// Exact FP32 value of a 16-bit unsigned integer: 2^23 + u is a float, and
+// subtracting 2^23 is exact.
+__device__ __forceinline__ float u16_to_float(unsigned u) { return __int_as_float(0x4B000000 | u) - 8388608.0f; }
+
+// Nearest FP32 to a 32-bit unsigned integer, from FP32 arithmetic alone:
+// hi 2^16 + lo is formed exactly inside one fused multiply-add and rounded
+// once.  (The integer-to-float conversion instructions issue at the FP64
+// rate on this part.)
+__device__ __forceinline__ float u32_to_float_rn(unsigned u) {
+    return __fmaf_rn(u16_to_float(u >> 16), 65536.0f, u16_to_float(u & 0xffffu));
+}
+
 // 2^-24 fixed point of a velocity (round to nearest even); exact for |v| < 2^39
 __device__ __forceinline__ long long vel_fix(float v) {
     return __float2ll_rn(v * 16777216.0f);

@@ -243,7 +243,7 @@ __global__ void __launch_bounds__(T_BRICK) k_decode(Geo g, StoreDev s, const flo
 // are integers (numerators over 2^s per axis) summed in int64, so the result
 // is exact and independent of the summation order; rho = m * sum * 2^(-3s).
 __device__ __forceinline__ float node_value(unsigned lo, unsigned hi) {
-    return hi ? __ull2float_rn(((unsigned long long)hi << 32) | lo) : __uint2float_rn(lo);
+    return hi ? __ull2float_rn(((unsigned long long)hi << 32) | lo) : u32_to_float_rn(lo);
 }
 
 template <int NX>
@@ -351,8 +351,14 @@ __global__ void __launch_bounds__(T_BRICK) k_deposit(Geo g, StoreDev s, float* _
         const uint4 a = reinterpret_cast<const uint4*>(acc)[2 * t4];        // {lo, hi} of nodes t, t + 1
         const uint4 b = reinterpret_cast<const uint4*>(acc)[2 * t4 + 1];    // nodes t + 2, t + 3
         // exact integer sum; one rounding when the scale is a power of two (mass 2^k)
-        const float4 v = make_float4(node_value(a.x, a.y) * fscale, node_value(a.z, a.w) * fscale,
-                                     node_value(b.x, b.y) * fscale, node_value(b.z, b.w) * fscale);
+        float4 v;
+        if (small) {   // block-uniform: no node sum exceeds 32 bits
+            v = make_float4(u32_to_float_rn(a.x) * fscale, u32_to_float_rn(a.z) * fscale,
+                            u32_to_float_rn(b.x) * fscale, u32_to_float_rn(b.z) * fscale);
+        } else {
+            v = make_float4(node_value(a.x, a.y) * fscale, node_value(a.z, a.w) * fscale,
+                            node_value(b.x, b.y) * fscale, node_value(b.z, b.w) * fscale);
+        }
         *reinterpret_cast<float4*>(&mesh[((int64_t)(oz + z) * g.N + (oy + y)) * g.S + ox + x]) = v;
     }
 }
