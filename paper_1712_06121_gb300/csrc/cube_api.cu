@@ -317,7 +317,8 @@ cube_status cube_create(const cube_params* params, void* cuda_stream, cube_ctx**
         if (params->id_bytes) AL(c->id[k], Np * 4);
         AL(c->codec[k].dec, (size_t)(2 * g.nulim + 1) * 4);
         AL(c->codec[k].thr, (size_t)(g.nulim + 2) * 4);
-        AL(c->codec[k].est, 2 * 4);
+        AL(c->codec[k].est, 3 * 4);
+        AL(c->codec[k].vtab, VT_N);
         AL(c->codec[k].sigma, 8);
     }
     AL(c->tanv, (size_t)(g.nulim + 1) * 8);

@@ -122,6 +122,27 @@ __device__ __forceinline__ int nu_from_thresholds(float d, const float* __restri
     return d < 0.0f ? -k : k;
 }
 
+// Eq. nu for 1-byte codes through a bucket table.  Bucket i holds the |d|
+// whose float bit patterns share bits 31..(23 - VT_B) = key0 + i: 2^VT_B
+// buckets per octave, VT_N buckets (16 octaves) from just below thr[1].
+// vtab[i] is the code of the bucket's first value.  Consecutive thresholds
+// of 1-byte codes are at least 2.49% apart (relative; min over k of
+// tan(pi (k + 1/2) / 255) / tan(pi (k - 1/2) / 255)), more than a bucket's
+// width (at most 2^-6 = 1.56%), so a bucket holds at most one threshold and
+// one compare with the next threshold completes the code; thr[1 .. 127]
+// span 13.7 octaves, inside the table.  The result equals
+// nu_from_thresholds'.
+constexpr int VT_B = 6;
+constexpr int VT_N = 1024;
+__device__ __forceinline__ int nu_from_table(float d, const float* __restrict__ thr,
+                                             const unsigned char* __restrict__ vtab, int key0, int lim) {
+    const float a = fabsf(d);
+    const int i = min(max((int)(__float_as_uint(a) >> (23 - VT_B)) - key0, 0), VT_N - 1);
+    int k = vtab[i];
+    k = min(k + (a >= thr[k + 1] ? 1 : 0), lim);
+    return d < 0.0f ? -k : k;
+}
+
 // Starting guess for nu_from_thresholds: (M/pi) atan(|d| s) with the
 // arctangent from the polynomial of Abramowitz & Stegun 4.4.47 (Hastings),
 // |error| <= 1e-5 rad on [0, 1], and atan(x) = pi/2 - atan(1/x) above 1.

@@ -150,7 +150,7 @@ __global__ void k_sigma_finalize(const float* __restrict__ part, int nparts, dou
 
 __global__ void k_codec_tables(int lim, const double* __restrict__ tanv, const double* __restrict__ tanh_,
                                const double* __restrict__ sigma, float* __restrict__ dec, float* __restrict__ thr,
-                               float* __restrict__ est) {
+                               float* __restrict__ est, unsigned char* __restrict__ vtab) {
     const double sg = *sigma;
     const double s = sqrt(PI_D / (2.0 * sg * sg));
     const double gam = sqrt(2.0 * sg * sg / PI_D);
@@ -168,6 +168,21 @@ __global__ void k_codec_tables(int lim, const double* __restrict__ tanv, const d
             thr[k] = __double2float_ru(tanh_[k] / s);
         } else {
             thr[lim + 1] = __int_as_float(0x7f800000);   // +inf
+        }
+    }
+    if (vtab) {   // 1-byte codes, one block: the bucket table of nu_from_table
+        __syncthreads();
+        const int key0 = (int)(__float_as_uint(thr[1]) >> (23 - VT_B)) - 1;   // first bucket lies below thr[1]
+        if (threadIdx.x == 0) est[2] = __int_as_float(key0);
+        for (int i = threadIdx.x; i < VT_N; i += blockDim.x) {
+            const float A = __uint_as_float((unsigned)(key0 + i) << (23 - VT_B));
+            int lo = 0, hi = lim;                       // number of thresholds thr[1..lim] <= A
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (thr[mid] <= A) lo = mid;
+                else hi = mid - 1;
+            }
+            vtab[i] = (unsigned char)lo;
         }
     }
 }
@@ -384,13 +399,18 @@ __global__ void __launch_bounds__(T_BRICK, 4) k_passA(Geo g, StoreDev s, const f
     float* sdec = reinterpret_cast<float*>(sm_off + nbc + 1);               // NV == 1: [2 lim + 1]
     float* sthr = sdec + (NV == 1 ? 2 * lim + 1 : 0);                       // NV == 1: [lim + 2]
     float* svc = sthr + (NV == 1 ? lim + 2 : 0);                            // [3][nbc]: v_c of the brick
+    unsigned char* stab = reinterpret_cast<unsigned char*>(svc + 3 * nbc);  // NV == 1: [VT_N] bucket table
     const float* dec = cur.dec;
     const float* thr = cur.thr;
+    int key0 = 0;
     if (NV == 1) {
         for (int t = threadIdx.x; t < 2 * lim + 1; t += blockDim.x) sdec[t] = cur.dec[t];
         for (int t = threadIdx.x; t < lim + 2; t += blockDim.x) sthr[t] = cur.thr[t];
+        for (int t = threadIdx.x; t < VT_N / 4; t += blockDim.x)
+            reinterpret_cast<unsigned*>(stab)[t] = reinterpret_cast<const unsigned*>(cur.vtab)[t];
         dec = sdec;
         thr = sthr;
+        key0 = __float_as_int(cur.est[2]);
     }
     int bx, by, bz;
     brick_coords(g, blockIdx.x, &bx, &by, &bz);
@@ -514,7 +534,8 @@ __global__ void __launch_bounds__(T_BRICK, 4) k_passA(Geo g, StoreDev s, const f
             float v = vcd + dec[nu + lim];
             float p1 = __fmaf_rn(force[d], kick, v);
             float dd = p1 - vcd;
-            int nu1 = nu_from_thresholds(dd, thr, lim, nu_estimate(dd, e0, e1));
+            const int nu1 = NV == 1 ? nu_from_table(dd, thr, stab, key0, lim)
+                                    : nu_from_thresholds(dd, thr, lim, nu_estimate(dd, e0, e1));
             store_code<NV>(s.nu, d * g.Np + i, nu1);
             float p2 = vcd + dec[nu1 + lim];
             float r2 = p2 - vcd;
@@ -603,7 +624,7 @@ __global__ void k_cells(Geo g, StepScratch w, unsigned* __restrict__ off_new, fl
 constexpr int PB_WARPS = 8;
 
 template <int NX, int NV>
-__global__ void __launch_bounds__(PB_WARPS * 32, 6) k_passB(Geo g, StoreDev so, StoreDev sn, CodecDev cur, CodecDev next,
+__global__ void __launch_bounds__(PB_WARPS * 32, 5) k_passB(Geo g, StoreDev so, StoreDev sn, CodecDev cur, CodecDev next,
                                                         float dc, const unsigned* __restrict__ ghost,
                                                         const float* __restrict__ vc_new, unsigned* flags) {
     extern __shared__ unsigned pb_smem[];
@@ -612,18 +633,23 @@ __global__ void __launch_bounds__(PB_WARPS * 32, 6) k_passB(Geo g, StoreDev so, 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     float* sdec = reinterpret_cast<float*>(pb_smem);                       // NV == 1: [2 lim + 1]
     float* sthr = sdec + (NV == 1 ? 2 * lim + 1 : 0);                       // NV == 1: [lim + 2]
-    unsigned* wbase = reinterpret_cast<unsigned*>(sthr + (NV == 1 ? lim + 2 : 0));
+    unsigned char* stab = reinterpret_cast<unsigned char*>(sthr + (NV == 1 ? lim + 2 : 0));   // NV == 1: [VT_N]
+    unsigned* wbase = reinterpret_cast<unsigned*>(stab + (NV == 1 ? VT_N : 0));
     unsigned* sm_off = wbase + warp * (4 * nbc + 1 + 4 * H3);               // [nbc + 1] per warp
     unsigned* run = sm_off + nbc + 1;                                       // [H3] per warp
     float* svc = reinterpret_cast<float*>(run + H3);                        // [3][nbc]: v_c of the brick
     float* svn = svc + 3 * nbc;                                             // [3][H3]: v_c* of the halo region
     const float* dec = cur.dec;
     const float* thr = next.thr;
+    int key0 = 0;
     if (NV == 1) {
         for (int t = threadIdx.x; t < 2 * lim + 1; t += blockDim.x) sdec[t] = cur.dec[t];
         for (int t = threadIdx.x; t < lim + 2; t += blockDim.x) sthr[t] = next.thr[t];
+        for (int t = threadIdx.x; t < VT_N / 4; t += blockDim.x)
+            reinterpret_cast<unsigned*>(stab)[t] = reinterpret_cast<const unsigned*>(next.vtab)[t];
         dec = sdec;
         thr = sthr;
+        key0 = __float_as_int(next.est[2]);
     }
     __syncthreads();
     const int brick = blockIdx.x * PB_WARPS + warp;
@@ -706,7 +732,9 @@ __global__ void __launch_bounds__(PB_WARPS * 32, 6) k_passB(Geo g, StoreDev so, 
                 for (int d = 0; d < 3; ++d) {
                     store_code<NX>(sn.chi, d * g.Np + pos, chi[d]);
                     const float dd = pv[d] - svn[d * H3 + ei];
-                    store_code<NV>(sn.nu, d * g.Np + pos, nu_from_thresholds(dd, thr, lim, nu_estimate(dd, e0, e1)));
+                    store_code<NV>(sn.nu, d * g.Np + pos,
+                                   NV == 1 ? nu_from_table(dd, thr, stab, key0, lim)
+                                           : nu_from_thresholds(dd, thr, lim, nu_estimate(dd, e0, e1)));
                 }
                 if (sn.id) sn.id[pos] = cid;
             }
@@ -779,7 +807,10 @@ void launch_sigma_finalize(const float* part, int nparts, double count, double r
 }
 
 void launch_codec_tables(int nulim, const double* tanv, const double* tanh_, const CodecDev& c, cudaStream_t st) {
-    k_codec_tables<<<nblk(nulim + 2, 256), 256, 0, st>>>(nulim, tanv, tanh_, c.sigma, c.dec, c.thr, c.est);
+    // 1-byte codes (nulim 127) fit one block, which also builds the bucket table
+    const bool one = nulim + 2 <= 256;
+    k_codec_tables<<<nblk(nulim + 2, 256), 256, 0, st>>>(nulim, tanv, tanh_, c.sigma, c.dec, c.thr, c.est,
+                                                        one ? c.vtab : nullptr);
 }
 
 void launch_encode_scatter(const Geo& g, const float* pos, const float* vel, const unsigned* id_in,
@@ -821,7 +852,7 @@ static size_t passA_smem(const Geo& g) {
     const int T = g.F + 5, TS = g.F + 8, H3 = g.Bh * g.Bh * g.Bh, nbc = g.B * g.B * g.B;
     size_t sm = (((size_t)3 * H3 * 8 + 15) & ~(size_t)15) + (size_t)T * T * TS * 4 + (size_t)H3 * 4 +
                 (size_t)(nbc + 1) * 4;
-    if (g.nnu == 1) sm += (size_t)(3 * g.nulim + 3) * 4;
+    if (g.nnu == 1) sm += (size_t)(3 * g.nulim + 3) * 4 + VT_N;
     sm += (size_t)3 * nbc * 4;
     return (sm + 15) & ~(size_t)15;
 }
@@ -842,7 +873,7 @@ void launch_cells(const Geo& g, const StepScratch& w, unsigned* off_new, float* 
 static size_t passB_smem(const Geo& g) {
     const int H3 = g.Bh * g.Bh * g.Bh, nbc = g.B * g.B * g.B;
     size_t sm = (size_t)PB_WARPS * (4 * nbc + 1 + 4 * H3) * 4;
-    if (g.nnu == 1) sm += (size_t)(3 * g.nulim + 3) * 4;
+    if (g.nnu == 1) sm += (size_t)(3 * g.nulim + 3) * 4 + VT_N;
     return (sm + 15) & ~(size_t)15;
 }
 

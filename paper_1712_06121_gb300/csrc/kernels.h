@@ -64,7 +64,8 @@ struct StoreDev {
 struct CodecDev {
     float* dec;         // [2 lim + 1]: dec[nu + lim] = tan(pi nu / M) * sqrt(2 sigma^2 / pi)
     float* thr;         // [lim + 2]: encode thresholds (see nu_from_thresholds)
-    float* est;         // [2]: (M/pi) s and M/pi, for the starting guess
+    float* est;         // [3]: s and M/pi for the starting guess; [2] the first bucket key of vtab (int bits)
+    unsigned char* vtab;   // [VT_N] (1-byte codes): code at the start of each bucket of |d| (see nu_from_table)
     double* sigma;      // device scalar
 };
 
