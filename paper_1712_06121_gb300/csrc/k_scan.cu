@@ -39,15 +39,24 @@ __device__ unsigned block_inclusive_scan(unsigned v, unsigned* smem_warp, unsign
     return v + add;
 }
 
-__global__ void k_scan_reduce(const unsigned* __restrict__ in, int64_t n, unsigned* __restrict__ bsum) {
-    __shared__ unsigned sw[32];
-    int64_t base = (int64_t)blockIdx.x * SCAN_TILE;
-    unsigned s = 0;
+// SCAN_ITEMS = 4 consecutive items of one thread, as one 16-byte load when
+// the array is 16-byte aligned and the four items exist
+__device__ __forceinline__ void load4(const unsigned* __restrict__ in, int64_t base, int64_t n, bool vec,
+                                      unsigned* v) {
+    if (vec && base + 3 < n) {
+        const uint4 q = *reinterpret_cast<const uint4*>(in + base);
+        v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+    } else {
 #pragma unroll
-    for (int i = 0; i < SCAN_ITEMS; ++i) {
-        int64_t idx = base + (int64_t)i * SCAN_T + threadIdx.x;
-        if (idx < n) s += in[idx];
+        for (int i = 0; i < SCAN_ITEMS; ++i) v[i] = base + i < n ? in[base + i] : 0u;
     }
+}
+
+__global__ void k_scan_reduce(const unsigned* __restrict__ in, int64_t n, unsigned* __restrict__ bsum, bool vec) {
+    __shared__ unsigned sw[32];
+    unsigned v[SCAN_ITEMS];
+    load4(in, (int64_t)blockIdx.x * SCAN_TILE + (int64_t)threadIdx.x * SCAN_ITEMS, n, vec, v);
+    const unsigned s = v[0] + v[1] + v[2] + v[3];
     unsigned tot;
     block_inclusive_scan(s, sw, &tot);
     if (threadIdx.x == 0) bsum[blockIdx.x] = tot;
@@ -68,26 +77,25 @@ __global__ void k_scan_bsums(unsigned* bsum, int nb, unsigned* total_out) {
     if (threadIdx.x == 0 && total_out) *total_out = carry;
 }
 
-__global__ void k_scan_down(const unsigned* __restrict__ in, int64_t n, const unsigned* __restrict__ bsum,
-                            unsigned* __restrict__ out) {
+__global__ void k_scan_down(const unsigned* in, int64_t n, const unsigned* __restrict__ bsum, unsigned* out,
+                            bool vec) {
     __shared__ unsigned sw[32];
-    int64_t base = (int64_t)blockIdx.x * SCAN_TILE + (int64_t)threadIdx.x * SCAN_ITEMS;
+    const int64_t base = (int64_t)blockIdx.x * SCAN_TILE + (int64_t)threadIdx.x * SCAN_ITEMS;
     unsigned v[SCAN_ITEMS];
-    unsigned s = 0;
-#pragma unroll
-    for (int i = 0; i < SCAN_ITEMS; ++i) {
-        int64_t idx = base + i;
-        v[i] = idx < n ? in[idx] : 0u;
-        s += v[i];
-    }
+    load4(in, base, n, vec, v);
+    const unsigned s = v[0] + v[1] + v[2] + v[3];
     unsigned tot;
-    unsigned inc = block_inclusive_scan(s, sw, &tot);
-    unsigned run = bsum[blockIdx.x] + inc - s;
+    const unsigned inc = block_inclusive_scan(s, sw, &tot);
+    unsigned e[SCAN_ITEMS];
+    e[0] = bsum[blockIdx.x] + inc - s;
 #pragma unroll
-    for (int i = 0; i < SCAN_ITEMS; ++i) {
-        int64_t idx = base + i;
-        if (idx < n) out[idx] = run;
-        run += v[i];
+    for (int i = 1; i < SCAN_ITEMS; ++i) e[i] = e[i - 1] + v[i - 1];
+    if (vec && base + 3 < n) {
+        *reinterpret_cast<uint4*>(out + base) = make_uint4(e[0], e[1], e[2], e[3]);
+    } else {
+#pragma unroll
+        for (int i = 0; i < SCAN_ITEMS; ++i)
+            if (base + i < n) out[base + i] = e[i];
     }
 }
 
@@ -143,9 +151,10 @@ void exclusive_scan(const unsigned* in, unsigned* out, int64_t n, unsigned* tmp,
     int nb = (int)((n + SCAN_TILE - 1) / SCAN_TILE);
     if (nb == 0) nb = 1;
     unsigned* total = tmp + nb;
-    k_scan_reduce<<<nb, SCAN_T, 0, st>>>(in, n, tmp);
+    const bool vec = ((reinterpret_cast<uintptr_t>(in) | reinterpret_cast<uintptr_t>(out)) & 15) == 0;
+    k_scan_reduce<<<nb, SCAN_T, 0, st>>>(in, n, tmp, vec);
     k_scan_bsums<<<1, SCAN_T, 0, st>>>(tmp, nb, total);
-    k_scan_down<<<nb, SCAN_T, 0, st>>>(in, n, tmp, out);
+    k_scan_down<<<nb, SCAN_T, 0, st>>>(in, n, tmp, out, vec);
     k_write_total<<<1, 1, 0, st>>>(out, n, total);
 }
 
