@@ -150,12 +150,15 @@ __device__ __forceinline__ void tile_fft(float2* buf, const float2* tw) {
 }
 
 // First pass (span 1, no twiddles) of a column tile straight from global
-// memory: column c of element j + m n/R is src[(j + m n/R) rs + c0 + c], zero
-// at or past column ncol.  The caller's cp.async copies (twiddles, tables)
-// are waited for before the closing barrier.
+// memory: column c of element j + m n/R is src[(j + m n/R) rs + (c0 + c) cs],
+// zero at or past column ncol.  pack_off > 0: column 0 of the tile (c0 = 0)
+// becomes X + i Y, X its own values and Y those of the column pack_off
+// further (two real sequences in one complex transform).  The caller's
+// cp.async copies (twiddles, tables) are waited for before the closing
+// barrier.
 template <int n, int R, bool INV>
 __device__ __forceinline__ void fft_pass_load(float2* buf, const float2* __restrict__ src, int64_t rs, int c0,
-                                              int ncol) {
+                                              int ncol, int64_t cs = 1, int pack_off = 0) {
     constexpr int nq = n / R;
     constexpr int nbf = nq * NC;
     constexpr int KMAX = (nbf + FFT_T - 1) / FFT_T;
@@ -165,10 +168,16 @@ __device__ __forceinline__ void fft_pass_load(float2* buf, const float2* __restr
         if (nbf % FFT_T == 0 || b < nbf) {
             const int c = b & (NC - 1), j = b >> LOG_NC;
             const bool ok = c0 + c < ncol;
-            const float2* p = src + (int64_t)j * rs + c0 + c;
+            const float2* p = src + (int64_t)j * rs + (int64_t)(c0 + c) * cs;
             float2 v[R];
 #pragma unroll
             for (int m = 0; m < R; ++m) v[m] = ok ? p[(int64_t)m * nq * rs] : make_float2(0.f, 0.f);
+            if (pack_off > 0 && c0 + c == 0)
+#pragma unroll
+                for (int m = 0; m < R; ++m) {
+                    const float2 y = p[(int64_t)m * nq * rs + pack_off];
+                    v[m] = make_float2(v[m].x - y.y, v[m].y + y.x);
+                }
             dft<R, INV>(v);
 #pragma unroll
             for (int m = 0; m < R; ++m) buf[sidx<false>(j * R + m, c)] = v[m];
@@ -179,12 +188,14 @@ __device__ __forceinline__ void fft_pass_load(float2* buf, const float2* __restr
 }
 
 // Last pass of a column tile: results (natural order, element j + m Ns) go
-// straight to dst[(j + m Ns) rs + c0 + c] for columns below ncol, each first
-// passed through post(element, column, value).  Shared memory is only read:
-// the caller synchronises before reusing the tile.
+// straight to dst[(j + m Ns) rs + (c0 + c) cs] for columns below ncol, each
+// first passed through post(element, column, value).  split_off > 0: column
+// 0 of the tile (c0 = 0) holds x + i y of two real sequences; x goes to
+// column 0 and y to the column split_off further, both as (value, 0).
+// Shared memory is only read: the caller synchronises before reusing it.
 template <int n, int Ns, int R, int TWM, bool INV, class Post>
 __device__ __forceinline__ void fft_pass_store(const float2* buf, const float2* tw, float2* dst, int64_t rs, int c0,
-                                               int ncol, Post post) {
+                                               int ncol, Post post, int64_t cs = 1, int split_off = 0) {
     constexpr int nq = n / R;
     static_assert(nq == Ns, "the last pass has span n / R");
     constexpr int nbf = nq * NC;
@@ -207,8 +218,15 @@ __device__ __forceinline__ void fft_pass_store(const float2* buf, const float2* 
                 }
             }
             dft<R, INV>(v);
-            if (c0 + c < ncol) {
-                float2* p = dst + (int64_t)j * rs + c0 + c;
+            if (split_off > 0 && c0 + c == 0) {
+                float2* p = dst + (int64_t)j * rs;
+#pragma unroll
+                for (int m = 0; m < R; ++m) {
+                    p[(int64_t)m * Ns * rs] = make_float2(v[m].x, 0.f);
+                    p[(int64_t)m * Ns * rs + split_off] = make_float2(v[m].y, 0.f);
+                }
+            } else if (c0 + c < ncol) {
+                float2* p = dst + (int64_t)j * rs + (int64_t)(c0 + c) * cs;
 #pragma unroll
                 for (int m = 0; m < R; ++m) p[(int64_t)m * Ns * rs] = post(j + m * Ns, c, v[m]);
             }
@@ -223,15 +241,15 @@ struct NoPost {
 // passes from span Ns on, the last one through fft_pass_store
 template <int n, int Ns, int TWM, bool INV, class Post>
 __device__ __forceinline__ void tile_fft_to_global(float2* buf, const float2* tw, float2* dst, int64_t rs, int c0,
-                                                   int ncol, Post post) {
+                                                   int ncol, Post post, int64_t cs = 1, int split_off = 0) {
     constexpr int rem = n / Ns;
     constexpr int R = rem % 8 == 0 ? 8 : rem % 4 == 0 ? 4 : rem % 2 == 0 ? 2 : 3;
     static_assert(rem % R == 0, "length must be 2^a 3^b");
     if constexpr (Ns * R == n) {
-        fft_pass_store<n, Ns, R, TWM, INV>(buf, tw, dst, rs, c0, ncol, post);
+        fft_pass_store<n, Ns, R, TWM, INV>(buf, tw, dst, rs, c0, ncol, post, cs, split_off);
     } else {
         fft_pass<n, Ns, R, TWM, INV, false>(buf, tw);
-        tile_fft_to_global<n, Ns * R, TWM, INV>(buf, tw, dst, rs, c0, ncol, post);
+        tile_fft_to_global<n, Ns * R, TWM, INV>(buf, tw, dst, rs, c0, ncol, post, cs, split_off);
     }
 }
 
@@ -456,19 +474,44 @@ __global__ void __launch_bounds__(FFT_T) k_fft_x_c2r(float* mesh, int S, const f
 
 // ------------------------------------------------------------ y sweep
 // The tile's first pass reads global memory and its last pass writes it:
-// shared memory holds only the intermediate passes.
+// shared memory holds only the intermediate passes.  Columns kx = 0 and
+// kx = N/2 are real before the forward sweep and after the inverse one, so
+// they share one complex column (x + i y) in tile 0, and N/2 / NC tiles
+// cover the N/2 + 1 columns.  Forward, tile 0 separates the two transforms
+// by Hermitian symmetry, A(k) = (Z(k) + Z*(N-k)) / 2, B(k) = (Z(k) - Z*(N-k)) / 2i.
+template <int N>
+constexpr int ntile_x() { return (N / 2 + NC - 1) / NC; }
+
 template <int N, bool INV>
 __global__ void __launch_bounds__(FFT_T, N <= 512 ? 2 : 1) k_fft_y(float* mesh, int S, const float2* __restrict__ tw) {
     extern __shared__ float2 fsm[];
+    constexpr int h = N / 2;
     float2* stw = fsm;
     float2* buf = fsm + N;
     load_tw(stw, tw, N);
     const int Sc = S / 2;
-    constexpr int ncol = N / 2 + 1;
     const int c0 = blockIdx.x * NC;
     float2* slab = reinterpret_cast<float2*>(mesh) + (int64_t)blockIdx.y * N * Sc;
-    fft_pass_load<N, first_radix<N>(), INV>(buf, slab, Sc, c0, ncol);
-    tile_fft_to_global<N, first_radix<N>(), 1, INV>(buf, stw, slab, Sc, c0, ncol, NoPost{});
+    fft_pass_load<N, first_radix<N>(), INV>(buf, slab, Sc, c0, h, 1, h);
+    if (INV) {
+        tile_fft_to_global<N, first_radix<N>(), 1, INV>(buf, stw, slab, Sc, c0, h, NoPost{}, 1, h);
+    } else if (blockIdx.x > 0) {
+        tile_fft_to_global<N, first_radix<N>(), 1, INV>(buf, stw, slab, Sc, c0, h, NoPost{});
+    } else {
+        tile_fft<N, first_radix<N>(), 1, INV, false>(buf, stw);
+        for (int t = threadIdx.x; t < N * NC; t += FFT_T) {
+            const int c = t & (NC - 1), ky = t >> LOG_NC;
+            float2* row = slab + (int64_t)ky * Sc;
+            if (c == 0) {
+                const float2 zk = buf[sidx<false>(ky, 0)];
+                const float2 zm = buf[sidx<false>((N - ky) % N, 0)];
+                row[0] = make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y));
+                row[h] = make_float2(0.5f * (zk.y + zm.y), 0.5f * (zm.x - zk.x));
+            } else if (c < h) {
+                row[c] = buf[sidx<false>(ky, c)];
+            }
+        }
+    }
 }
 
 // ------------------------------------------------------------ z sweep (+ Green)
@@ -487,21 +530,21 @@ struct GreenPost {
     }
 };
 
+// One tile of 16 consecutive kx (0 .. N/2) at one ky.
 template <int N, int MODE>   // 0: forward only, 1: forward, Green, inverse
 __global__ void __launch_bounds__(FFT_T, N <= 512 ? 2 : 1) k_fft_z(float* mesh, int S, const float2* __restrict__ tw,
                                                  const float* __restrict__ k2, const float* __restrict__ wdec, float g0) {
     extern __shared__ float2 fsm[];
+    constexpr int ncol = N / 2 + 1;
     float2* stw = fsm;
     float2* buf = fsm + N;
     float* sk2 = reinterpret_cast<float*>(buf + N * NC + NC);     // [N]
     float* swd = sk2 + N;                                          // [N]
     load_tw(stw, tw, N);
     const int Sc = S / 2;
-    constexpr int ncol = N / 2 + 1;
-    const int c0 = blockIdx.x * NC;
-    const int ky = blockIdx.y;
-    float2* base = reinterpret_cast<float2*>(mesh) + (int64_t)ky * Sc;
     const int64_t zs = (int64_t)N * Sc;
+    const int c0 = blockIdx.x * NC, ky = blockIdx.y;
+    float2* base = reinterpret_cast<float2*>(mesh) + (int64_t)ky * Sc;
     if (MODE == 1)
         for (int i = threadIdx.x; i < N; i += blockDim.x) {
             cp_async4(&sk2[i], &k2[i]);
@@ -598,13 +641,13 @@ struct Sweeps {
     }
     static void y(const FftPlan& p, float* mesh, int S, bool inv, cudaStream_t st) {
         attrs();
-        dim3 gy((N / 2 + NC) / NC, N);
+        dim3 gy(ntile_x<N>(), N);
         if (inv) k_fft_y<N, true><<<gy, FFT_T, tile_smem(N, N), st>>>(mesh, S, p.tw);
         else k_fft_y<N, false><<<gy, FFT_T, tile_smem(N, N), st>>>(mesh, S, p.tw);
     }
     static void z(const FftPlan& p, float* mesh, int S, float g0, bool green, cudaStream_t st) {
         attrs();
-        dim3 gz((N / 2 + NC) / NC, N);
+        const dim3 gz((N / 2 + NC) / NC, N);
         if (green) k_fft_z<N, 1><<<gz, FFT_T, tile_smem(N, N), st>>>(mesh, S, p.tw, p.k2, p.wdec, g0);
         else k_fft_z<N, 0><<<gz, FFT_T, tile_smem(N, N), st>>>(mesh, S, p.tw, p.k2, p.wdec, g0);
     }
