@@ -38,6 +38,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="pm256")
+    ap.add_argument("--codes", default=None, choices=["x1v1", "x1v2", "x2v1", "x2v2", "fp32"],
+                    help="override the workload's code widths; fp32 = the uncompressed FP32 store")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--nps", type=int, default=0,
@@ -64,6 +66,10 @@ def phase_bytes(w, geo):
     nbr = Ncc // geo["brick"] ** 3
     half = N * N * (N // 2 + 1) * 8          # half-complex mesh bytes
     s_x, s_v = 3 * w.x_bytes, 3 * w.v_bytes
+    if w.x_bytes == 4:                       # uncompressed FP32 store: no codes, cells or re-sort
+        return {"deposit": 12 * Np + 4 * Nm, "fft_x_r2c": 4 * Nm + half, "fft_y_fwd": 2 * half,
+                "fft_z_green": 2 * half, "fft_y_inv": 2 * half, "fft_x_c2r": half + 4 * Nm,
+                "pass_a": 48 * Np + 4 * Nm}
     return {
         "deposit": 4 * Nm + s_x * Np + 4 * Ncc,
         "fft_x_r2c": 4 * Nm + half,
@@ -81,7 +87,11 @@ def phase_bytes(w, geo):
 
 def step_bytes(w):
     """Whole-step algorithmic bytes of the method's minimum model:
-    (3s + 3n_nu) N_p + 32 N_coarse + 32 N_mesh, s = 3 n_chi + 3 n_nu."""
+    (3s + 3n_nu) N_p + 32 N_coarse + 32 N_mesh, s = 3 n_chi + 3 n_nu; the
+    uncompressed FP32 store: 60 N_p (read 24 + write 24 + deposit read 12)
+    + 32 N_mesh."""
+    if w.x_bytes == 4:
+        return 60 * w.n_particles + 32 * w.n_fine ** 3
     s = 3 * w.x_bytes + 3 * w.v_bytes
     return (3 * s + 3 * w.v_bytes) * w.n_particles + 32 * (w.n_fine // w.ratio) ** 3 + 32 * w.n_fine ** 3
 
@@ -173,22 +183,34 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
+def oracle_state(w, ic, nps):
+    """The oracle's state and step function for the workload's store: the
+    compressed store (pm.encode / pm.step), or for the uncompressed FP32
+    store the oracle's uncompressed FP64 mode (pm.exact_from / exact_step)."""
+    import numpy as np
+    from oracle import pm
+    om, ol, _ = w.omega()
+    if w.x_bytes == 4:
+        P = pm.Params(n_fine=2 * nps, n_particles=nps ** 3, x_bytes=1, v_bytes=1, box=w.box, omega_m=om,
+                      omega_l=ol)
+        return pm.exact_from(P, np.mod(ic.pos.astype(np.float64), 2 * nps), ic.vel, w.a_init), pm.exact_step
+    P = pm.Params(n_fine=2 * nps, n_particles=nps ** 3, x_bytes=w.x_bytes, v_bytes=w.v_bytes, box=w.box,
+                  omega_m=om, omega_l=ol)
+    return pm.encode(P, ic.pos, ic.vel, ic.ids, w.a_init, ic.sigma_1d), pm.step
+
+
 def cpu_baseline(w, steps=1):
     """The FP64 oracle on the host cores: one step of the same workload at
     128^3 particles / 256^3 mesh (same seed and cosmology)."""
     import numpy as np
     import synth
-    from oracle import pm
     nps = min(128, w.n_part_side)
     ic = synth.make_ics(w, n_part_side=nps, n_fine=2 * nps)
-    om, ol, _ = w.omega()
-    P = pm.Params(n_fine=2 * nps, n_particles=nps ** 3, x_bytes=w.x_bytes, v_bytes=w.v_bytes, box=w.box,
-                  omega_m=om, omega_l=ol)
-    st = pm.encode(P, ic.pos, ic.vel, ic.ids, w.a_init, ic.sigma_1d)
+    st, step = oracle_state(w, ic, nps)
     sch = np.linspace(w.a_init, w.a_final, w.n_steps + 1)
     t0 = time.perf_counter()
     for i in range(steps):
-        st = pm.step(st, float(sch[i]), float(sch[i + 1]))
+        st = step(st, float(sch[i]), float(sch[i + 1]))
     dt = time.perf_counter() - t0
     return {"value": nps ** 3 * steps / dt, "unit": "particle-steps/s", "cores": 1, "kind": "oracle",
             "sample": f"{steps} oracle step(s) of {w.name} at {nps}^3 particles / {2 * nps}^3 mesh "
@@ -201,19 +223,15 @@ def run_reference(args, w):
         return
     import numpy as np
     import synth
-    from oracle import pm
     nps = min(128, w.n_part_side)
     ic = synth.make_ics(w, n_part_side=nps, n_fine=2 * nps)
-    om, ol, _ = w.omega()
-    P = pm.Params(n_fine=2 * nps, n_particles=nps ** 3, x_bytes=w.x_bytes, v_bytes=w.v_bytes, box=w.box,
-                  omega_m=om, omega_l=ol)
-    st = pm.encode(P, ic.pos, ic.vel, ic.ids, w.a_init, ic.sigma_1d)
+    st, step = oracle_state(w, ic, nps)
     sch = schedule(w, args.warmup + args.steps)
     for i in range(args.warmup):
-        st = pm.step(st, float(sch[i]), float(sch[i + 1]))
+        st = step(st, float(sch[i]), float(sch[i + 1]))
     t0 = time.perf_counter()
     for i in range(args.warmup, args.warmup + args.steps):
-        st = pm.step(st, float(sch[i]), float(sch[i + 1]))
+        st = step(st, float(sch[i]), float(sch[i + 1]))
     dt = time.perf_counter() - t0
     value = nps ** 3 * args.steps / dt
     sample = (f"oracle steps of {w.name} at {nps}^3 particles / {2 * nps}^3 mesh "
@@ -228,9 +246,17 @@ def run_reference(args, w):
     }), flush=True)
 
 
+def codes_of(w):
+    return "uncompressed FP32" if w.x_bytes == 4 else f"x{w.x_bytes}v{w.v_bytes}"
+
+
+def step_model(w):
+    return "60 N_p + 32 N_mesh" if w.x_bytes == 4 else "(3s+3n_nu)N_p + 32 N_coarse + 32 N_mesh"
+
+
 def config_of(w):
     return {"workload": f"{w.name}: {w.n_part_side}^3 particles, {w.n_fine}^3 FP32 mesh, {w.box:g} Mpc/h, "
-                        f"{'EdS' if w.cosmo_kind == 'eds' else 'LCDM BBKS'}, x{w.x_bytes}v{w.v_bytes}, "
+                        f"{'EdS' if w.cosmo_kind == 'eds' else 'LCDM BBKS'}, {codes_of(w)}, "
                         f"R={w.ratio}, steps uniform in a from z={1 / w.a_init - 1:g}",
             "l2": ("inputs larger than L2 (no flush)" if 4 * w.n_fine ** 3 > 129e6
                    else "L2-resident small workload"), "parallelism": "replicas"}
@@ -243,6 +269,9 @@ def main():
     w = synth.WORKLOADS[args.workload]
     if args.nps:
         w = dataclasses.replace(w, name=f"{w.name}@{args.nps}", n_part_side=args.nps, n_fine=2 * args.nps)
+    if args.codes:
+        xb, vb = (4, 4) if args.codes == "fp32" else (int(args.codes[1]), int(args.codes[3]))
+        w = dataclasses.replace(w, x_bytes=xb, v_bytes=vb)
     if args.impl == "reference":
         run_reference(args, w)
         return
@@ -357,8 +386,7 @@ def main():
         "data": "synthetic (seeded GRF Zel'dovich ICs)", "config": config_of(w),
         "roofline": {"bound": "hbm", "kernel": top, "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind},
-        "step_roofline": {"bytes": step_bytes(w), "frac": step_frac,
-                          "model": "(3s+3n_nu)N_p + 32 N_coarse + 32 N_mesh"},
+        "step_roofline": {"bytes": step_bytes(w), "frac": step_frac, "model": step_model(w)},
         "phases_ms_per_step": {k: v / max(1, nst) for k, v in phase_ms.items()},
         "gpu_launches": int(launches),
         "clocks": clk,

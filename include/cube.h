@@ -67,7 +67,9 @@ typedef struct {
     int32_t ratio;         /* R fine cells per coarse cell (Section 2.3.1): 1, 2,
                               4 or 8, with N_c = N_f / R >= 3                    */
     int64_t n_particles;   /* N_p >= 1 (< 2^31)                                 */
-    int32_t x_bytes;       /* n_chi in {1, 2}: position code width (Eq. chi)    */
+    int32_t x_bytes;       /* n_chi in {1, 2}: position code width (Eq. chi);
+                              4 together with v_bytes = 4: uncompressed FP32
+                              particles (see "Uncompressed store" below)       */
     int32_t v_bytes;       /* n_nu in {1, 2}: velocity code width (Eq. nu)      */
     int32_t id_bytes;      /* 0 (no particle IDs) or 4 (uint32 I_P)             */
     int32_t gradient;      /* CUBE_GRAD_FD4: 4th-order finite-difference force  */
@@ -82,6 +84,17 @@ typedef struct {
     double omega_m;        /* Omega_m: source term of lap Phi = 1.5 Om (rho-1)  */
     double omega_l;        /* Omega_Lambda: expansion rate E(a)                 */
 } cube_params;
+
+/* Uncompressed store (x_bytes = v_bytes = 4): the comparison arm of the
+   paper's precision study (Section 3: compressed runs against an
+   uncompressed PM code).  The store holds float positions (fine cells, in
+   [0, N_f)) and momenta in input order, updated in place; no codes, cells or
+   codec scale.  cube_pm_step runs the same mesh part, then per particle a
+   CIC gather of the FD4 force, the kick and the drift (periodic).  The
+   density is deposited with float atomics, so its last bits depend on the
+   summation order.  cube_state_view: chi and nu point to [3][N_p] floats
+   (positions, momenta), counts, offsets and vc are NULL, sigma 0.
+   cube_keep_drifted(ctx, 1) returns CUBE_E_STATE. */
 
 /* Message describing the calling thread's most recent error ("" if none).
    The pointer stays valid until the thread's next failing call. */
@@ -180,7 +193,8 @@ typedef struct {
     int32_t max_migration;   /* largest |cell shift| of the last step (<= 1)   */
     uint32_t error_flags;    /* bit 0 migration, bit 1 non-finite, bit 2 count  */
     double last_step_ms;     /* device time of the last step's kernels         */
-    int64_t kernel_launches; /* CUDA kernels this context has launched         */
+    int64_t kernel_launches; /* CUDA kernels this context launched before this
+                                call (the call's own reduction not counted)    */
 } cube_stats;
 
 /* Bookkeeping of Section 2.3.3 (particle count, mass, momentum, codec scale,

@@ -148,6 +148,7 @@ struct cube_ctx {
     double* tanv = nullptr;
     double* tanh_ = nullptr;
     CodecDev codec[2]{};
+    bool raw = false;               // uncompressed FP32 store: chi[0] = positions, nu[0] = momenta
     // per-step scratch
     long long* vsum = nullptr;
     unsigned* ghost = nullptr;
@@ -224,8 +225,9 @@ cube_status check_params(const cube_params* p, int* brick) {
     const int Nc = N / R;
     if (Nc < 3) return fail(CUBE_E_ARG, "need at least 3 coarse cells per side");
     if (p->n_particles < 1 || p->n_particles >= (1LL << 31)) return fail(CUBE_E_ARG, "n_particles out of range");
-    if ((p->x_bytes != 1 && p->x_bytes != 2) || (p->v_bytes != 1 && p->v_bytes != 2))
-        return fail(CUBE_E_ARG, "x_bytes and v_bytes must be 1 or 2");
+    const bool raw = p->x_bytes == 4 && p->v_bytes == 4;
+    if (!raw && ((p->x_bytes != 1 && p->x_bytes != 2) || (p->v_bytes != 1 && p->v_bytes != 2)))
+        return fail(CUBE_E_ARG, "x_bytes and v_bytes must be 1 or 2 (codes), or both 4 (uncompressed FP32)");
     if (p->id_bytes != 0 && p->id_bytes != 4) return fail(CUBE_E_ARG, "id_bytes must be 0 or 4");
     if (p->gradient != CUBE_GRAD_FD4) return fail(CUBE_E_ARG, "only CUBE_GRAD_FD4 is implemented");
     if (p->deconv_power < 0 || p->deconv_power > 2) return fail(CUBE_E_ARG, "deconv_power must be 0, 1 or 2");
@@ -286,15 +288,16 @@ cube_status cube_create(const cube_params* params, void* cuda_stream, cube_ctx**
     g.B = B;
     g.nb = g.Nc / B;
     g.Bh = B + 2;
-    g.nchi = params->x_bytes;
-    g.nnu = params->v_bytes;
+    c->raw = params->x_bytes == 4;
+    g.nchi = c->raw ? 4 : params->x_bytes;
+    g.nnu = c->raw ? 4 : params->v_bytes;
     g.sbits = 8 * g.nchi + 1 - g.r;
     g.F = B * g.R;
     g.S = g.N + 4;
     g.Ncc = g.Nc * g.Nc * g.Nc;
     g.nbricks = g.nb * g.nb * g.nb;
     g.Np = params->n_particles;
-    g.nulim = (1 << (8 * g.nnu - 1)) - 1;
+    g.nulim = c->raw ? 127 : (1 << (8 * g.nnu - 1)) - 1;   // (no codec tables are used uncompressed)
     g.lB = 0;
     while ((1 << g.lB) < g.B) ++g.lB;
     g.lF = 0;
@@ -312,9 +315,11 @@ cube_status cube_create(const cube_params* params, void* cuda_stream, cube_ctx**
         AL(c->counts[k], Ncc * 4);
         AL(c->offsets[k], (Ncc + 1) * 4);
         AL(c->vc[k], 3 * Ncc * 4);
-        AL(c->chi[k], 3 * Np * g.nchi);
-        AL(c->nu[k], 3 * Np * g.nnu);
-        if (params->id_bytes) AL(c->id[k], Np * 4);
+        if (k == 0 || !c->raw) {         // the uncompressed store is updated in place
+            AL(c->chi[k], 3 * Np * g.nchi);
+            AL(c->nu[k], 3 * Np * g.nnu);
+            if (params->id_bytes) AL(c->id[k], Np * 4);
+        }
         AL(c->codec[k].dec, (size_t)(2 * g.nulim + 1) * 4);
         AL(c->codec[k].thr, (size_t)(g.nulim + 2) * 4);
         AL(c->codec[k].est, 3 * 4);
@@ -374,6 +379,41 @@ cube_status cube_create(const cube_params* params, void* cuda_stream, cube_ctx**
     return CUBE_OK;
 }
 
+// Uncompressed store: copy (and wrap) the particles; momenta and positions share the epoch a.
+static cube_status raw_encode(cube_ctx* c, const float* pos, const float* vel, const uint32_t* id, double a,
+                              bool hpos, bool hvel, bool hid) {
+    const Geo& g = c->g;
+    const size_t Np = (size_t)g.Np;
+    const size_t need = (hpos ? 12 * Np : 0) + (hvel ? 12 * Np : 0) + (hid ? 4 * Np : 0);
+    char* sp = nullptr;
+    if (need) {
+        void* p = nullptr;
+        cube_status s = stage_bytes(c, need, &p);
+        if (s != CUBE_OK) return s;
+        sp = (char*)p;
+    }
+    const float* dpos = pos;
+    const float* dvel = vel;
+    const unsigned* did = id;
+    if (hpos) { CK(cudaMemcpyAsync(sp, pos, 12 * Np, cudaMemcpyHostToDevice, c->st)); dpos = (const float*)sp; sp += 12 * Np; }
+    if (hvel) { CK(cudaMemcpyAsync(sp, vel, 12 * Np, cudaMemcpyHostToDevice, c->st)); dvel = (const float*)sp; sp += 12 * Np; }
+    if (hid) { CK(cudaMemcpyAsync(sp, id, 4 * Np, cudaMemcpyHostToDevice, c->st)); did = (const unsigned*)sp; }
+    CK(cudaMemsetAsync(c->flags, 0, 4, c->st));
+    CK(cudaMemsetAsync(c->maxmig, 0, 4, c->st));
+    launch_raw_encode(g, dpos, dvel, did, (float*)c->chi[0], (float*)c->nu[0], c->id[0], c->flags, c->st);
+    c->launches += 1;
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(c->st));
+    c->cur = 0;
+    c->encoded = true;
+    c->a = a;
+    c->a_p = a;
+    c->steps = 0;
+    c->dbg_valid = false;
+    c->timed = false;
+    return CUBE_OK;
+}
+
 cube_status cube_encode(cube_ctx* c, const float* pos, const float* vel, const uint32_t* id, double a, double sigma) {
     if (!c) return fail(CUBE_E_ARG, "ctx is NULL");
     if (!pos || !vel) return fail(CUBE_E_ARG, "pos and vel are required");
@@ -381,6 +421,7 @@ cube_status cube_encode(cube_ctx* c, const float* pos, const float* vel, const u
     const Geo& g = c->g;
     const size_t Np = (size_t)g.Np;
     const bool hpos = !is_device_ptr(pos), hvel = !is_device_ptr(vel), hid = id && !is_device_ptr(id);
+    if (c->raw) return raw_encode(c, pos, vel, id, a, hpos, hvel, hid);
     // scratch: keys, perm, radix workspace, host staging
     const int key_bits = std::max(1, (int)std::ceil(std::log2((double)g.Ncc)));
     size_t words = (size_t)(2 * Np) + (size_t)radix_tmp_words(g.Np);
@@ -432,6 +473,10 @@ const int kPhaseKernels[CUBE_PHASES] = {0, 1, 1, 1, 1, 1, 1, 1, 2, 4, 1, 1};
 const char* kPhaseNames[CUBE_PHASES] = {"setup", "deposit", "fft_x_r2c", "fft_y_fwd", "fft_z_green", "fft_y_inv",
                                         "fft_x_c2r", "pass_a", "codec", "scan", "cells", "pass_b"};
 
+// the uncompressed store's step: mesh cleared in setup, one deposit, the FFT
+// sweeps, one kick-drift kernel in the pass_a slot
+const int kPhaseKernelsRaw[CUBE_PHASES] = {0, 1, 1, 1, 1, 1, 1, 1, 0, 0, 0, 0};
+
 static void mark(cube_ctx* c, int boundary) {
     if (c->prof_steps < c->prof_max) cudaEventRecord(c->prof_ev[(size_t)c->prof_steps * (CUBE_PHASES + 1) + boundary], c->st);
 }
@@ -440,7 +485,12 @@ static double particle_mass(const Geo& g) { return std::pow((double)g.N, 3) / (d
 
 static void deposit(cube_ctx* c) {
     const Geo& g = c->g;
-    launch_deposit(g, c->store(c->cur), c->mesh, particle_mass(g) * std::ldexp(1.0, -3 * g.sbits), c->st);
+    if (c->raw) {
+        cudaMemsetAsync(c->mesh, 0, (size_t)g.N * g.N * g.S * 4, c->st);
+        launch_raw_deposit(g, (const float*)c->chi[0], c->mesh, (float)particle_mass(g), c->st);
+    } else {
+        launch_deposit(g, c->store(c->cur), c->mesh, particle_mass(g) * std::ldexp(1.0, -3 * g.sbits), c->st);
+    }
     c->launches += 1;
 }
 
@@ -474,6 +524,24 @@ cube_status cube_pm_step(cube_ctx* c, double a_from, double a_to) {
     const float kick = (float)c->cosmo.kick(c->a_p, a_mid);
     const float dc = (float)(c->cosmo.drift(a_from, a_to) / g.R);
     const double ratio = c->cosmo.g(a_to) / c->cosmo.g(a_from);
+    if (c->raw) {
+        CK(cudaEventRecord(c->ev0, c->st));
+        mark(c, 0);
+        mark(c, 1);
+        mesh_potential(c);
+        launch_raw_kick_drift(g, (float*)c->chi[0], (float*)c->nu[0], c->mesh, kick,
+                              (float)c->cosmo.drift(a_from, a_to), c->flags, c->st);
+        for (int b = 8; b <= 12; ++b) mark(c, b);
+        CK(cudaEventRecord(c->ev1, c->st));
+        c->launches += 1;
+        if (c->prof_steps < c->prof_max) c->prof_steps += 1;
+        CK(cudaGetLastError());
+        c->a = a_to;
+        c->a_p = a_mid;
+        c->steps += 1;
+        c->timed = true;
+        return CUBE_OK;
+    }
     const int k = c->cur, kn = 1 - k;
     if (c->keep) {
         if (!c->dbg_cell) {
@@ -537,8 +605,17 @@ cube_status cube_decode(cube_ctx* c, float* pos, float* vel, uint32_t* id) {
     float* dpos = hpos ? (float*)sp : pos;
     float* dvel = hvel ? (float*)(sp + (hpos ? 12 * Np : 0)) : vel;
     unsigned* did = id ? (hid ? (unsigned*)(sp + (hpos ? 12 * Np : 0) + (hvel ? 12 * Np : 0)) : id) : nullptr;
-    launch_decode(g, c->store(c->cur), c->codec[c->cur].dec, dpos, dvel, did, c->st);
-    c->launches += 1;
+    if (c->raw) {                        // the store is the particles: copy them out
+        CK(cudaMemcpyAsync(dpos, c->chi[0], 12 * Np, cudaMemcpyDeviceToDevice, c->st));
+        CK(cudaMemcpyAsync(dvel, c->nu[0], 12 * Np, cudaMemcpyDeviceToDevice, c->st));
+        if (did) {
+            if (c->id[0]) CK(cudaMemcpyAsync(did, c->id[0], 4 * Np, cudaMemcpyDeviceToDevice, c->st));
+            else launch_iota(did, g.Np, c->st);
+        }
+    } else {
+        launch_decode(g, c->store(c->cur), c->codec[c->cur].dec, dpos, dvel, did, c->st);
+        c->launches += 1;
+    }
     CK(cudaGetLastError());
     cube_status s;
     if (hpos && (s = to_user(c, pos, dpos, 12 * Np, true)) != CUBE_OK) return s;
@@ -589,13 +666,14 @@ cube_status cube_state_view(cube_ctx* c, cube_state* out) {
     out->v_bytes = g.nnu;
     out->id_bytes = c->P.id_bytes;
     out->n_particles = g.Np;
-    out->counts = c->counts[k];
-    out->offsets = c->offsets[k];
-    out->vc = c->vc[k];
+    out->counts = c->raw ? nullptr : c->counts[k];
+    out->offsets = c->raw ? nullptr : c->offsets[k];
+    out->vc = c->raw ? nullptr : c->vc[k];
     out->chi = c->chi[k];
     out->nu = c->nu[k];
     out->id = c->id[k];
-    CK(cudaMemcpyAsync(&out->sigma, c->codec[k].sigma, 8, cudaMemcpyDeviceToHost, c->st));
+    out->sigma = 0.0;
+    if (!c->raw) CK(cudaMemcpyAsync(&out->sigma, c->codec[k].sigma, 8, cudaMemcpyDeviceToHost, c->st));
     out->a = c->a;
     out->a_p = c->a_p;
     return latched(c);
@@ -605,12 +683,16 @@ cube_status cube_stats_get(cube_ctx* c, cube_stats* out) {
     if (!c || !out) return fail(CUBE_E_ARG, "NULL argument");
     if (!c->encoded) return fail(CUBE_E_STATE, "no store: call cube_encode first");
     const Geo& g = c->g;
-    launch_momentum(g, c->vsum, c->mom, c->st);
+    const int64_t launched = c->launches;          // before this call's own reduction
+    if (c->raw) launch_raw_momentum(g, (const float*)c->nu[0], c->mom, c->st);
+    else launch_momentum(g, c->vsum, c->mom, c->st);
+    c->launches += 1;
     long long m[3] = {0, 0, 0};
     unsigned f = 0;
     int mig = 0;
+    out->sigma = 0.0;
     CK(cudaMemcpyAsync(m, c->mom, sizeof(m), cudaMemcpyDeviceToHost, c->st));
-    CK(cudaMemcpyAsync(&out->sigma, c->codec[c->cur].sigma, 8, cudaMemcpyDeviceToHost, c->st));
+    if (!c->raw) CK(cudaMemcpyAsync(&out->sigma, c->codec[c->cur].sigma, 8, cudaMemcpyDeviceToHost, c->st));
     CK(cudaMemcpyAsync(&f, c->flags, 4, cudaMemcpyDeviceToHost, c->st));
     CK(cudaMemcpyAsync(&mig, c->maxmig, 4, cudaMemcpyDeviceToHost, c->st));
     CK(cudaStreamSynchronize(c->st));
@@ -624,7 +706,7 @@ cube_status cube_stats_get(cube_ctx* c, cube_stats* out) {
     float ms = 0.0f;
     if (c->timed) cudaEventElapsedTime(&ms, c->ev0, c->ev1);
     out->last_step_ms = ms;
-    out->kernel_launches = c->launches;
+    out->kernel_launches = launched;
     return latched(c);
 }
 
@@ -665,6 +747,7 @@ cube_status cube_potential(cube_ctx* c, float* phi) {
 
 cube_status cube_keep_drifted(cube_ctx* c, int32_t enable) {
     if (!c) return fail(CUBE_E_ARG, "ctx is NULL");
+    if (c->raw && enable) return fail(CUBE_E_STATE, "the uncompressed store has no re-sort to inspect");
     c->keep = enable != 0;
     if (!c->keep) {
         CK(cudaStreamSynchronize(c->st));
@@ -717,7 +800,7 @@ cube_status cube_profile_read(cube_ctx* c, double* ms, int32_t* kernels, int32_t
             t += e;
         }
         ms[p] = t;
-        if (kernels) kernels[p] = kPhaseKernels[p];
+        if (kernels) kernels[p] = c->raw ? kPhaseKernelsRaw[p] : kPhaseKernels[p];
     }
     if (nsteps) *nsteps = c->prof_steps;
     return CUBE_OK;

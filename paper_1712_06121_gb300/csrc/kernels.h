@@ -107,6 +107,15 @@ void launch_passB(const Geo& g, const StoreDev& s_old, const StoreDev& s_new, co
                   const CodecDev& next, float dc, const StepScratch& w, cudaStream_t st);
 void launch_momentum(const Geo& g, const long long* vsum, long long* out3, cudaStream_t st);
 
+// uncompressed FP32 particles (k_raw.cu)
+void launch_raw_encode(const Geo& g, const float* pos, const float* vel, const unsigned* id_in, float* P, float* V,
+                       unsigned* I, unsigned* flags, cudaStream_t st);
+void launch_raw_deposit(const Geo& g, const float* P, float* mesh, float mass, cudaStream_t st);
+void launch_raw_kick_drift(const Geo& g, float* P, float* V, const float* phi, float kick, float drift,
+                           unsigned* flags, cudaStream_t st);
+void launch_raw_momentum(const Geo& g, const float* V, long long* out3, cudaStream_t st);
+void launch_iota(unsigned* out, int64_t n, cudaStream_t st);
+
 // ------------------------------------------------------------ k_fft.cu
 struct FftPlan {
     int N;              // transform length along every axis
