@@ -6,7 +6,7 @@ Bounds: the FP32 store differs from FP64 by rounding only (orders of
 magnitude below the codes' quantisation); x2v2 keeps 99% of the particles
 within a few hundredths of a fine cell of the uncompressed run (the paper
 reports almost all below 1/100 of a fine cell for x2v2 against its
-uncompressed reference, Section 3.1) and its P(k) within 0.1%; every store
+uncompressed reference, Section 3.2) and its P(k) within 0.1%; every store
 keeps the density field correlated (1 - r small) and the displacement error
 falls as code bytes are added to positions.  The seeds are fixed; the bounds
 leave an order of magnitude to the measured values (float atomics make the
