@@ -24,7 +24,8 @@ namespace {
 
 constexpr int NC = 16;          // columns per tile
 constexpr int LOG_NC = 4;
-constexpr int FFT_T = 512;      // threads per CTA
+constexpr int FFT_T = 512;      // threads per CTA of the column (y, z) sweeps
+constexpr int XFFT_T = 256;     // threads per CTA of the row (x) sweeps
 
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
     return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
@@ -97,17 +98,17 @@ __device__ __forceinline__ void dft(float2* v) {
 
 // one Stockham pass of radix R over the NC-column tile of length n, span Ns;
 // twiddles come from a table of TWN = n * TWM entries e^{-2 pi i k / TWN}
-template <int n, int Ns, int R, int TWM, bool INV, bool SWZ>
+template <int n, int Ns, int R, int TWM, bool INV, bool SWZ, int T = FFT_T>
 __device__ __forceinline__ void fft_pass(float2* buf, const float2* tw) {
     constexpr int nq = n / R;
     constexpr int nbf = nq * NC;
-    constexpr int KMAX = (nbf + FFT_T - 1) / FFT_T;
+    constexpr int KMAX = (nbf + T - 1) / T;
     constexpr int step = TWM * (n / (Ns * R));
     float2 v[KMAX][R];
 #pragma unroll
     for (int q = 0; q < KMAX; ++q) {
-        const int b = threadIdx.x + q * FFT_T;
-        if (nbf % FFT_T == 0 || b < nbf) {
+        const int b = threadIdx.x + q * T;
+        if (nbf % T == 0 || b < nbf) {
             const int c = b & (NC - 1), j = b >> LOG_NC;
 #pragma unroll
             for (int m = 0; m < R; ++m) v[q][m] = buf[sidx<SWZ>(j + m * nq, c)];
@@ -116,8 +117,8 @@ __device__ __forceinline__ void fft_pass(float2* buf, const float2* tw) {
     __syncthreads();
 #pragma unroll
     for (int q = 0; q < KMAX; ++q) {
-        const int b = threadIdx.x + q * FFT_T;
-        if (nbf % FFT_T == 0 || b < nbf) {
+        const int b = threadIdx.x + q * T;
+        if (nbf % T == 0 || b < nbf) {
             const int c = b & (NC - 1), j = b >> LOG_NC;
             const int k = j % Ns;
             if (Ns > 1) {                                  // span 1: all twiddles are 1
@@ -138,14 +139,14 @@ __device__ __forceinline__ void fft_pass(float2* buf, const float2* tw) {
 }
 
 // all passes of a length-n transform, radices 8, 4, 2, 3 taken greedily
-template <int n, int Ns, int TWM, bool INV, bool SWZ>
+template <int n, int Ns, int TWM, bool INV, bool SWZ, int T = FFT_T>
 __device__ __forceinline__ void tile_fft(float2* buf, const float2* tw) {
     if constexpr (Ns < n) {
         constexpr int rem = n / Ns;
         constexpr int R = rem % 8 == 0 ? 8 : rem % 4 == 0 ? 4 : rem % 2 == 0 ? 2 : 3;
         static_assert(rem % R == 0, "length must be 2^a 3^b");
-        fft_pass<n, Ns, R, TWM, INV, SWZ>(buf, tw);
-        tile_fft<n, Ns * R, TWM, INV, SWZ>(buf, tw);
+        fft_pass<n, Ns, R, TWM, INV, SWZ, T>(buf, tw);
+        tile_fft<n, Ns * R, TWM, INV, SWZ, T>(buf, tw);
     }
 }
 
@@ -254,13 +255,13 @@ __device__ __forceinline__ void tile_fft_to_global(float2* buf, const float2* tw
 }
 
 // passes from span Ns up to (not including) the last, in shared memory
-template <int n, int Ns, int TWM, bool INV, bool SWZ = false>
+template <int n, int Ns, int TWM, bool INV, bool SWZ = false, int T = FFT_T>
 __device__ __forceinline__ void tile_fft_but_last(float2* buf, const float2* tw) {
     constexpr int rem = n / Ns;
     constexpr int R = rem % 8 == 0 ? 8 : rem % 4 == 0 ? 4 : rem % 2 == 0 ? 2 : 3;
     if constexpr (Ns * R < n) {
-        fft_pass<n, Ns, R, TWM, INV, SWZ>(buf, tw);
-        tile_fft_but_last<n, Ns * R, TWM, INV, SWZ>(buf, tw);
+        fft_pass<n, Ns, R, TWM, INV, SWZ, T>(buf, tw);
+        tile_fft_but_last<n, Ns * R, TWM, INV, SWZ, T>(buf, tw);
     }
 }
 
@@ -359,11 +360,11 @@ __device__ __forceinline__ void xpass_load(float2* buf, const float* mesh, int64
                                            const float2* __restrict__ gtw) {
     constexpr int nq = n / R;
     constexpr int nbf = nq * NC;
-    constexpr int KMAX = (nbf + FFT_T - 1) / FFT_T;
+    constexpr int KMAX = (nbf + XFFT_T - 1) / XFFT_T;
 #pragma unroll 1
     for (int q = 0; q < KMAX; ++q) {
-        const int b = threadIdx.x + q * FFT_T;
-        if (nbf % FFT_T == 0 || b < nbf) {
+        const int b = threadIdx.x + q * XFFT_T;
+        if (nbf % XFFT_T == 0 || b < nbf) {
             const int j = b % nq, c = b / nq;
             const float2* row = reinterpret_cast<const float2*>(mesh + (row0 + c) * S);
             float2 v[R];
@@ -395,12 +396,12 @@ __device__ __forceinline__ void xpass_store(const float2* buf, const float2* tw,
     constexpr int nq = n / R;
     static_assert(nq == Ns, "the last pass has span n / R");
     constexpr int nbf = nq * NC;
-    constexpr int KMAX = (nbf + FFT_T - 1) / FFT_T;
+    constexpr int KMAX = (nbf + XFFT_T - 1) / XFFT_T;
     constexpr int step = TWM * (n / (Ns * R));
 #pragma unroll 1
     for (int q = 0; q < KMAX; ++q) {
-        const int b = threadIdx.x + q * FFT_T;
-        if (nbf % FFT_T == 0 || b < nbf) {
+        const int b = threadIdx.x + q * XFFT_T;
+        if (nbf % XFFT_T == 0 || b < nbf) {
             const int j = b % nq, c = b / nq;
             float2 v[R];
 #pragma unroll
@@ -424,7 +425,7 @@ __device__ __forceinline__ void xpass_store(const float2* buf, const float2* tw,
 // r2c: the N reals of a row as N/2 complex z[k] = x[2k] + i x[2k+1], an
 // N/2-point FFT Z, then X[k] = (Z[k] + Z*[h-k])/2 - i W^k (Z[k] - Z*[h-k])/2
 template <int N>
-__global__ void __launch_bounds__(FFT_T) k_fft_x_r2c(float* mesh, int S, const float2* __restrict__ tw) {
+__global__ void __launch_bounds__(XFFT_T) k_fft_x_r2c(float* mesh, int S, const float2* __restrict__ tw) {
     extern __shared__ float2 fsm[];
     constexpr int h = N / 2;
     float2* stw = fsm;               // [N]
@@ -433,8 +434,8 @@ __global__ void __launch_bounds__(FFT_T) k_fft_x_r2c(float* mesh, int S, const f
     const int64_t row0 = (int64_t)blockIdx.x * NC;
     constexpr int R1 = x_first_radix<h>();
     xpass_load<h, R1, false, false>(buf, mesh, row0, S, tw);
-    tile_fft<h, R1, 2, false, true>(buf, stw);
-    for (int t = threadIdx.x; t < (h / 2 + 1) * NC; t += FFT_T) {
+    tile_fft<h, R1, 2, false, true, XFFT_T>(buf, stw);
+    for (int t = threadIdx.x; t < (h / 2 + 1) * NC; t += XFFT_T) {
         const int k = t % (h / 2 + 1), c = t / (h / 2 + 1);
         float2* dst = reinterpret_cast<float2*>(mesh + (row0 + c) * S);
         const float2 zk = buf[sidx<true>(k % h, c)];
@@ -458,7 +459,7 @@ __global__ void __launch_bounds__(FFT_T) k_fft_x_r2c(float* mesh, int S, const f
 // c2r: the packing above inverted inside the first pass, the N/2-point
 // inverse FFT, and the last pass writing the row's N reals
 template <int N>
-__global__ void __launch_bounds__(FFT_T) k_fft_x_c2r(float* mesh, int S, const float2* __restrict__ tw) {
+__global__ void __launch_bounds__(XFFT_T) k_fft_x_c2r(float* mesh, int S, const float2* __restrict__ tw) {
     extern __shared__ float2 fsm[];
     constexpr int h = N / 2;
     float2* stw = fsm;               // [N]
@@ -467,7 +468,7 @@ __global__ void __launch_bounds__(FFT_T) k_fft_x_c2r(float* mesh, int S, const f
     const int64_t row0 = (int64_t)blockIdx.x * NC;
     constexpr int R1 = x_first_radix<h>();
     xpass_load<h, R1, true, true>(buf, mesh, row0, S, tw);
-    tile_fft_but_last<h, R1, 2, true, true>(buf, stw);
+    tile_fft_but_last<h, R1, 2, true, true, XFFT_T>(buf, stw);
     constexpr int Ns = last_span<h, R1>();
     xpass_store<h, Ns, h / Ns, 2, true>(buf, stw, mesh, row0, S);
 }
@@ -637,7 +638,7 @@ struct Sweeps {
     }
     static void x_r2c(const FftPlan& p, float* mesh, int S, cudaStream_t st) {
         attrs();
-        k_fft_x_r2c<N><<<(N * N) / NC, FFT_T, tile_smem(N, N / 2), st>>>(mesh, S, p.tw);
+        k_fft_x_r2c<N><<<(N * N) / NC, XFFT_T, tile_smem(N, N / 2), st>>>(mesh, S, p.tw);
     }
     static void y(const FftPlan& p, float* mesh, int S, bool inv, cudaStream_t st) {
         attrs();
@@ -653,7 +654,7 @@ struct Sweeps {
     }
     static void x_c2r(const FftPlan& p, float* mesh, int S, cudaStream_t st) {
         attrs();
-        k_fft_x_c2r<N><<<(N * N) / NC, FFT_T, tile_smem(N, N / 2), st>>>(mesh, S, p.tw);
+        k_fft_x_c2r<N><<<(N * N) / NC, XFFT_T, tile_smem(N, N / 2), st>>>(mesh, S, p.tw);
     }
 };
 
