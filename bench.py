@@ -389,6 +389,7 @@ def main():
         "step_roofline": {"bytes": step_bytes(w), "frac": step_frac, "model": step_model(w)},
         "phases_ms_per_step": {k: v / max(1, nst) for k, v in phase_ms.items()},
         "gpu_launches": int(launches),
+        "tile_load": "tma" if stats.features & 1 else "cp.async",
         "clocks": clk,
         "e2e": e2e,
     }

@@ -195,6 +195,8 @@ typedef struct {
     double last_step_ms;     /* device time of the last step's kernels         */
     int64_t kernel_launches; /* CUDA kernels this context launched before this
                                 call (the call's own reduction not counted)    */
+    uint32_t features;       /* bit 0: pass A loads its Phi tiles by TMA
+                                (cp.async.bulk.tensor) rather than cp.async   */
 } cube_stats;
 
 /* Bookkeeping of Section 2.3.3 (particle count, mass, momentum, codec scale,

@@ -51,7 +51,8 @@ class cube_stats(ctypes.Structure):
     _fields_ = [("mass", ctypes.c_double), ("momentum", ctypes.c_double * 3), ("sigma", ctypes.c_double),
                 ("a", ctypes.c_double), ("a_p", ctypes.c_double), ("steps", ctypes.c_int64),
                 ("max_migration", ctypes.c_int32), ("error_flags", ctypes.c_uint32),
-                ("last_step_ms", ctypes.c_double), ("kernel_launches", ctypes.c_int64)]
+                ("last_step_ms", ctypes.c_double), ("kernel_launches", ctypes.c_int64),
+                ("features", ctypes.c_uint32)]
 
 CUBE_PHASES = 12
 

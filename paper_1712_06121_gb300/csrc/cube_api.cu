@@ -6,6 +6,8 @@
 #include <string>
 #include <vector>
 
+#include <cudaTypedefs.h>
+
 #include "cube.h"
 #include "kernels.h"
 
@@ -159,6 +161,9 @@ struct cube_ctx {
     unsigned* scan_tmp = nullptr;
     long long* mom = nullptr;
     float* mesh = nullptr;
+    float* phig = nullptr;          // ghosted Phi, written by the c2r sweep
+    CUtensorMap phig_map{};         // TMA map of phig with pass A's tile as the box
+    bool tma = false;               // phig_map encoded (else pass A loads with cp.async)
     FftPlan fft{};
     // host-pointer staging (lazily allocated)
     void* stage = nullptr;
@@ -212,7 +217,32 @@ cube_status latched(cube_ctx* c) {
     if (f & ERR_MIGRATION) return fail(CUBE_E_MIGRATION, "a particle moved more than one coarse cell in a step");
     if (f & ERR_NONFINITE) return fail(CUBE_E_OVERFLOW, "non-finite particle position or velocity");
     if (f & ERR_COUNT) return fail(CUBE_E_OVERFLOW, "cell counts inconsistent with the particle total");
+    if (f & ERR_TIMEOUT) return fail(CUBE_E_TIMEOUT, "a bounded wait for an asynchronous tile copy gave up");
     return CUBE_OK;
+}
+
+// TMA descriptor of the ghosted Phi: a 3-D float tensor (x, y, z extents
+// N + 8, N + 5, N + 5) whose box is pass A's tile ((F + 8) x (F + 5) x (F + 5)).
+// The encoder comes from the driver through the runtime; any failure leaves
+// pass A on its cp.async path.
+bool encode_phig_map(cube_ctx* c) {
+    const Geo& g = c->g;
+    PFN_cuTensorMapEncodeTiled_v12000 enc = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", (void**)&enc, 12000, cudaEnableDefault, &q) !=
+            cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !enc) {
+        cudaGetLastError();
+        return false;
+    }
+    const cuuint64_t dims[3] = {(cuuint64_t)phig_nx(g.N), (cuuint64_t)phig_ny(g.N), (cuuint64_t)phig_ny(g.N)};
+    const cuuint64_t strides[2] = {(cuuint64_t)phig_nx(g.N) * 4, (cuuint64_t)phig_nx(g.N) * phig_ny(g.N) * 4};
+    const cuuint32_t box[3] = {(cuuint32_t)(g.F + 8), (cuuint32_t)(g.F + 5), (cuuint32_t)(g.F + 5)};
+    const cuuint32_t unit[3] = {1, 1, 1};
+    const CUresult r = enc(&c->phig_map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, c->phig, dims, strides, box, unit,
+                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
 }
 
 cube_status check_params(const cube_params* p, int* brick) {
@@ -337,6 +367,7 @@ cube_status cube_create(const cube_params* params, void* cuda_stream, cube_ctx**
     AL(c->scan_tmp, (size_t)scan_tmp_words(std::max<int64_t>(g.Ncc + 1, (int64_t)g.nbricks * H3 + 1)) * 4 + 64);
     AL(c->mom, 3 * 8);
     AL(c->mesh, (size_t)g.N * g.N * g.S * 4);
+    AL(c->phig, (size_t)phig_nx(g.N) * phig_ny(g.N) * phig_ny(g.N) * 4);
     FftPlan& f = c->fft;
     f.N = g.N;
     AL(f.tw, (size_t)g.N * 8);
@@ -375,6 +406,7 @@ cube_status cube_create(const cube_params* params, void* cuda_stream, cube_ctx**
         if (e == cudaSuccess) e = cudaEventCreate(&c->ev1);
         if (e != cudaSuccess) return bad(e, "table upload");
     }
+    c->tma = encode_phig_map(c);
     *out = c;
     return CUBE_OK;
 }
@@ -508,7 +540,7 @@ static void mesh_potential(cube_ctx* c) {
     mark(c, 5);
     fft_y(c->fft, c->mesh, g.S, true, c->st);
     mark(c, 6);
-    fft_x_c2r(c->fft, c->mesh, g.S, c->st);
+    fft_x_c2r(c->fft, c->mesh, g.S, c->phig, c->st);
     mark(c, 7);
     c->launches += 5;
 }
@@ -529,7 +561,7 @@ cube_status cube_pm_step(cube_ctx* c, double a_from, double a_to) {
         mark(c, 0);
         mark(c, 1);
         mesh_potential(c);
-        launch_raw_kick_drift(g, (float*)c->chi[0], (float*)c->nu[0], c->mesh, kick,
+        launch_raw_kick_drift(g, (float*)c->chi[0], (float*)c->nu[0], c->phig, kick,
                               (float)c->cosmo.drift(a_from, a_to), c->flags, c->st);
         for (int b = 8; b <= 12; ++b) mark(c, b);
         CK(cudaEventRecord(c->ev1, c->st));
@@ -558,7 +590,7 @@ cube_status cube_pm_step(cube_ctx* c, double a_from, double a_to) {
     mesh_potential(c);
     StepScratch w{c->counts[kn], c->vsum, c->ghost, c->part, c->flags, c->maxmig};
     DriftDebug dbg{c->keep ? c->dbg_cell : nullptr, c->dbg_u, c->dbg_p};
-    launch_passA(g, c->store(k), c->mesh, c->codec[k], kick, dc, w, dbg, c->st);
+    launch_passA(g, c->store(k), c->phig, c->tma ? &c->phig_map : nullptr, c->codec[k], kick, dc, w, dbg, c->st);
     mark(c, 8);
     launch_sigma_finalize(c->part, g.nbricks, 3.0 * (double)g.Np, ratio, 0.0, c->codec[kn].sigma, c->st);
     launch_codec_tables(g.nulim, c->tanv, c->tanh_, c->codec[kn], c->st);
@@ -707,10 +739,12 @@ cube_status cube_stats_get(cube_ctx* c, cube_stats* out) {
     if (c->timed) cudaEventElapsedTime(&ms, c->ev0, c->ev1);
     out->last_step_ms = ms;
     out->kernel_launches = launched;
+    out->features = c->tma ? 1u : 0u;
     return latched(c);
 }
 
-static cube_status mesh_out(cube_ctx* c, float* dst) {
+// unpadded N^3 copy of the mesh (density) or of the ghosted Phi
+static cube_status mesh_out(cube_ctx* c, float* dst, bool phi) {
     const Geo& g = c->g;
     const size_t bytes = (size_t)g.N * g.N * g.N * 4;
     const bool host = !is_device_ptr(dst);
@@ -721,7 +755,8 @@ static cube_status mesh_out(cube_ctx* c, float* dst) {
         if (s != CUBE_OK) return s;
         d = (float*)p;
     }
-    launch_unpad(c->mesh, g.N, g.S, d, c->st);
+    if (phi) launch_unpad_phig(c->phig, g.N, d, c->st);
+    else launch_unpad(c->mesh, g.N, g.S, d, c->st);
     c->launches += 1;
     if (host) CK(cudaMemcpyAsync(dst, d, bytes, cudaMemcpyDeviceToHost, c->st));
     CK(cudaGetLastError());
@@ -732,7 +767,7 @@ cube_status cube_density(cube_ctx* c, float* rho) {
     if (!c || !rho) return fail(CUBE_E_ARG, "NULL argument");
     if (!c->encoded) return fail(CUBE_E_STATE, "no store: call cube_encode first");
     deposit(c);
-    return mesh_out(c, rho);
+    return mesh_out(c, rho, false);
 }
 
 cube_status cube_potential(cube_ctx* c, float* phi) {
@@ -742,7 +777,7 @@ cube_status cube_potential(cube_ctx* c, float* phi) {
     c->prof_max = 0;                    // not a step: keep it out of the trace
     mesh_potential(c);
     c->prof_max = saved;
-    return mesh_out(c, phi);
+    return mesh_out(c, phi, true);
 }
 
 cube_status cube_keep_drifted(cube_ctx* c, int32_t enable) {

@@ -20,7 +20,56 @@ enum ErrFlag : uint32_t {
     ERR_MIGRATION = 1u,   // a particle moved more than one coarse cell
     ERR_NONFINITE = 2u,   // non-finite input position / velocity
     ERR_COUNT = 4u,       // counter overflow / inconsistent totals
+    ERR_TIMEOUT = 8u,     // a bounded wait for an asynchronous copy gave up
 };
+
+// Ghosted copy of the potential, written by the c2r sweep: x in [-4, N + 4),
+// y and z in [-2, N + 3), values periodic, row stride N + 8 floats (a
+// multiple of 16 bytes), so the Phi tile of any brick is one rectangular box.
+constexpr int PHIG_X0 = 4, PHIG_Y0 = 2;
+__host__ __device__ __forceinline__ int phig_nx(int N) { return N + 8; }
+__host__ __device__ __forceinline__ int phig_ny(int N) { return N + 5; }
+__host__ __device__ __forceinline__ int64_t phig_index(int N, int x, int y, int z) {
+    return ((int64_t)(z + PHIG_Y0) * phig_ny(N) + (y + PHIG_Y0)) * phig_nx(N) + (x + PHIG_X0);
+}
+
+// ---- mbarrier and TMA (cp.async.bulk.tensor) wrappers
+__device__ __forceinline__ unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_test(unsigned long long* bar, unsigned parity) {
+    unsigned done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(done)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+// waits at most ~2^20 polls (tens of milliseconds); false if the phase never completed
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* bar, unsigned parity) {
+    for (int it = 0; it < (1 << 20); ++it) {
+        if (mbar_test(bar, parity)) return true;
+        __nanosleep(32);
+    }
+    return false;
+}
+// 3-D tiled TMA load of the tensor map's box at (x, y, z) into shared memory,
+// completing on `bar`
+__device__ __forceinline__ void tma_load_3d(void* dst, const void* tmap, int x, int y, int z,
+                                            unsigned long long* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+        "[%5];" ::"r"(smem_addr(dst)),
+        "l"(tmap), "r"(x), "r"(y), "r"(z), "r"(smem_addr(bar))
+        : "memory");
+}
 
 struct Geo {
     int N;        // fine cells per side

@@ -390,9 +390,13 @@ __device__ __forceinline__ void xpass_load(float2* buf, const float* mesh, int64
     __syncthreads();
 }
 
-// Last pass (span n / R) of the row transforms, straight to global memory.
+// Last pass (span n / R) of the row transforms of N = 2n reals, straight to
+// the ghosted copy of Phi: every row lands at its place and, within the
+// ghost layers, at its periodic images (rows y < 3 also at y + N, y >= N - 2
+// also at y - N, the same in z; x < 4 also at x + N, x >= N - 4 at x - N).
 template <int n, int Ns, int R, int TWM, bool INV>
-__device__ __forceinline__ void xpass_store(const float2* buf, const float2* tw, float* mesh, int64_t row0, int S) {
+__device__ __forceinline__ void xpass_store(const float2* buf, const float2* tw, float* phig, int64_t row0) {
+    constexpr int N = 2 * n;
     constexpr int nq = n / R;
     static_assert(nq == Ns, "the last pass has span n / R");
     constexpr int nbf = nq * NC;
@@ -415,9 +419,25 @@ __device__ __forceinline__ void xpass_store(const float2* buf, const float2* tw,
                 }
             }
             dft<R, INV>(v);
-            float2* row = reinterpret_cast<float2*>(mesh + (row0 + c) * S);
+            const int64_t r = row0 + c;
+            const int z = (int)(r / N), y = (int)(r - (int64_t)z * N);
+            // element k = j + m Ns holds reals 2k, 2k + 1; k < 2 only for m = 0,
+            // k >= n - 2 only for m = R - 1 (Ns >= 2)
+            auto put = [&](int yy, int zz) {
+                float2* row = reinterpret_cast<float2*>(phig + phig_index(N, 0, yy, zz));
 #pragma unroll
-            for (int m = 0; m < R; ++m) row[j + m * Ns] = v[m];
+                for (int m = 0; m < R; ++m) row[j + m * Ns] = v[m];
+                if (j < 2) row[j + n] = v[0];
+                if (j >= Ns - 2) row[j + (R - 1) * Ns - n] = v[R - 1];
+            };
+            put(y, z);
+            const bool gy = y < 3 || y >= N - 2, gz = z < 3 || z >= N - 2;
+            if (gy || gz) {                      // rows with periodic images in the ghost layers
+                const int y2 = y < 3 ? y + N : y - N, z2 = z < 3 ? z + N : z - N;
+                if (gy) put(y2, z);
+                if (gz) put(y, z2);
+                if (gy && gz) put(y2, z2);
+            }
         }
     }
 }
@@ -459,7 +479,8 @@ __global__ void __launch_bounds__(XFFT_T) k_fft_x_r2c(float* mesh, int S, const 
 // c2r: the packing above inverted inside the first pass, the N/2-point
 // inverse FFT, and the last pass writing the row's N reals
 template <int N>
-__global__ void __launch_bounds__(XFFT_T) k_fft_x_c2r(float* mesh, int S, const float2* __restrict__ tw) {
+__global__ void __launch_bounds__(XFFT_T) k_fft_x_c2r(const float* mesh, int S, const float2* __restrict__ tw,
+                                                     float* __restrict__ phig) {
     extern __shared__ float2 fsm[];
     constexpr int h = N / 2;
     float2* stw = fsm;               // [N]
@@ -470,7 +491,7 @@ __global__ void __launch_bounds__(XFFT_T) k_fft_x_c2r(float* mesh, int S, const 
     xpass_load<h, R1, true, true>(buf, mesh, row0, S, tw);
     tile_fft_but_last<h, R1, 2, true, true, XFFT_T>(buf, stw);
     constexpr int Ns = last_span<h, R1>();
-    xpass_store<h, Ns, h / Ns, 2, true>(buf, stw, mesh, row0, S);
+    xpass_store<h, Ns, h / Ns, 2, true>(buf, stw, phig, row0);
 }
 
 // ------------------------------------------------------------ y sweep
@@ -610,6 +631,14 @@ __global__ void k_pk_reduce(const double* __restrict__ part, int nblocks, int nb
     pk[b] = w > 0 ? ps / w : nan("");
 }
 
+__global__ void k_unpad_phig(const float* __restrict__ phig, int N, float* __restrict__ out) {
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int64_t tot = (int64_t)N * N * N;
+    if (t >= tot) return;
+    const int x = (int)(t % N), y = (int)((t / N) % N), z = (int)(t / ((int64_t)N * N));
+    out[t] = phig[phig_index(N, x, y, z)];
+}
+
 __global__ void k_unpad(const float* __restrict__ mesh, int N, int S, float* __restrict__ out) {
     int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     int64_t tot = (int64_t)N * N * N;
@@ -652,9 +681,9 @@ struct Sweeps {
         if (green) k_fft_z<N, 1><<<gz, FFT_T, tile_smem(N, N), st>>>(mesh, S, p.tw, p.k2, p.wdec, g0);
         else k_fft_z<N, 0><<<gz, FFT_T, tile_smem(N, N), st>>>(mesh, S, p.tw, p.k2, p.wdec, g0);
     }
-    static void x_c2r(const FftPlan& p, float* mesh, int S, cudaStream_t st) {
+    static void x_c2r(const FftPlan& p, float* mesh, int S, float* phig, cudaStream_t st) {
         attrs();
-        k_fft_x_c2r<N><<<(N * N) / NC, XFFT_T, tile_smem(N, N / 2), st>>>(mesh, S, p.tw);
+        k_fft_x_c2r<N><<<(N * N) / NC, XFFT_T, tile_smem(N, N / 2), st>>>(mesh, S, p.tw, phig);
     }
 };
 
@@ -697,8 +726,8 @@ void fft_z(const FftPlan& p, float* mesh, int S, float g0, bool green, cudaStrea
 #undef DCASE
 }
 
-void fft_x_c2r(const FftPlan& p, float* mesh, int S, cudaStream_t st) {
-#define DCASE(n) case n: Sweeps<n>::x_c2r(p, mesh, S, st); break;
+void fft_x_c2r(const FftPlan& p, float* mesh, int S, float* phig, cudaStream_t st) {
+#define DCASE(n) case n: Sweeps<n>::x_c2r(p, mesh, S, phig, st); break;
     DISPATCH()
 #undef DCASE
 }
@@ -714,6 +743,11 @@ void launch_pk_bin(const FftPlan& p, const float* mesh, int S, int nbins, double
 
 void launch_pk_reduce(const double* part, int nblocks, int nbins, double* k, double* pk, double* nm, cudaStream_t st) {
     k_pk_reduce<<<(nbins + 127) / 128, 128, 0, st>>>(part, nblocks, nbins, k, pk, nm);
+}
+
+void launch_unpad_phig(const float* phig, int N, float* out, cudaStream_t st) {
+    int64_t tot = (int64_t)N * N * N;
+    k_unpad_phig<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(phig, N, out);
 }
 
 void launch_unpad(const float* mesh, int N, int S, float* out, cudaStream_t st) {

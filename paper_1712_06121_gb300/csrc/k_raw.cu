@@ -4,7 +4,7 @@
 // uncompressed PM code).  One thread per particle.
 //   deposit    CIC mass of each particle onto the fine mesh (float atomics;
 //              the summation order, and so the last bit, is not fixed)
-//   kick/drift CIC gather of the FD4 gradient of Phi from the mesh, kick,
+//   kick/drift CIC gather of the FD4 gradient of Phi (ghosted copy), kick,
 //              drift, periodic wrap
 #include "kernels.h"
 
@@ -89,7 +89,7 @@ __device__ __forceinline__ float fd4_line(const float* r, float w) {
 }
 
 __global__ void __launch_bounds__(RAW_T) k_raw_kick_drift(Geo g, float* __restrict__ P, float* __restrict__ V,
-                                                          const float* __restrict__ phi, float kick, float drift,
+                                                          const float* __restrict__ phig, float kick, float drift,
                                                           unsigned* flags) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= g.Np) return;
@@ -108,9 +108,7 @@ __global__ void __launch_bounds__(RAW_T) k_raw_kick_drift(Geo g, float* __restri
             k[d][m] = q;
         }
     }
-    auto at = [&](int ix, int iy, int iz) {
-        return __ldg(&phi[((int64_t)k[2][iz] * g.N + k[1][iy]) * g.S + k[0][ix]]);
-    };
+    auto at = [&](int ix, int iy, int iz) { return __ldg(&phig[phig_index(g.N, k[0][ix], k[1][iy], k[2][iz])]); };
     float gx = 0.0f, gy = 0.0f, gz = 0.0f;
 #pragma unroll
     for (int a = 0; a < 2; ++a)
@@ -170,9 +168,9 @@ void launch_raw_deposit(const Geo& g, const float* P, float* mesh, float mass, c
     k_raw_deposit<<<nblk(g.Np), RAW_T, 0, st>>>(g, P, mesh, mass);
 }
 
-void launch_raw_kick_drift(const Geo& g, float* P, float* V, const float* phi, float kick, float drift,
+void launch_raw_kick_drift(const Geo& g, float* P, float* V, const float* phig, float kick, float drift,
                            unsigned* flags, cudaStream_t st) {
-    k_raw_kick_drift<<<nblk(g.Np), RAW_T, 0, st>>>(g, P, V, phi, kick, drift, flags);
+    k_raw_kick_drift<<<nblk(g.Np), RAW_T, 0, st>>>(g, P, V, phig, kick, drift, flags);
 }
 
 void launch_iota(unsigned* out, int64_t n, cudaStream_t st) { k_iota<<<nblk(n), RAW_T, 0, st>>>(out, n); }

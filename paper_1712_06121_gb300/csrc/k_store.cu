@@ -384,16 +384,32 @@ __global__ void __launch_bounds__(T_BRICK) k_deposit(Geo g, StoreDev s, float* _
 // destination cells over the brick and its one-cell halo (Bh^3 cells) with
 // fixed-point momentum sums, and (1-byte velocities) the codec tables.
 template <int NX, int NV>
-__global__ void __launch_bounds__(T_BRICK, 4) k_passA(Geo g, StoreDev s, const float* __restrict__ phi, CodecDev cur,
-                                                   float kick, float dc, StepScratch w, DriftDebug dbg) {
+__global__ void __launch_bounds__(T_BRICK, 4) k_passA(Geo g, StoreDev s, const float* __restrict__ phig,
+                                                      const __grid_constant__ CUtensorMap tmap, int use_tma,
+                                                      CodecDev cur, float kick, float dc, StepScratch w,
+                                                      DriftDebug dbg) {
     extern __shared__ unsigned char pa_smem[];
+    __shared__ __align__(8) unsigned long long tile_bar;
     // Phi tile: T x T rows (y, z: [o - 2, o + F + 3)) of TX = F + 8 nodes
-    // (x: [o - 4, o + F + 4)), row stride TS = TX floats
+    // (x: [o - 4, o + F + 4)), row stride TS = TX floats, read from the
+    // ghosted Phi (no wrap): one TMA box, or 16-byte cp.async chunks
     const int F = g.F, T = F + 5, TX = F + 8, TS = TX, T3 = T * T * TS;
     const int nbc = g.B * g.B * g.B, Bh = g.Bh, H3 = Bh * Bh * Bh;
     const int lim = g.nulim;
+    int bx, by, bz;
+    brick_coords(g, blockIdx.x, &bx, &by, &bz);
+    const int ox = bx * F - 4, oy = by * F - 2, oz = bz * F - 2;      // tile origin
     long long* vs = reinterpret_cast<long long*>(pa_smem);                 // [3][H3]
-    float* tile = reinterpret_cast<float*>(pa_smem + ((3 * H3 * 8 + 15) & ~15));   // [T3], 16-byte aligned
+    const unsigned sbase = smem_addr(pa_smem);
+    float* tile = reinterpret_cast<float*>(pa_smem + (((sbase + 3 * H3 * 8 + 127) & ~127u) - sbase));   // [T3], 128-byte aligned
+    if (use_tma) {
+        if (threadIdx.x == 0) mbar_init(&tile_bar, 1);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            mbar_expect_tx(&tile_bar, (unsigned)T3 * 4u);
+            tma_load_3d(tile, &tmap, ox + PHIG_X0, oy + PHIG_Y0, oz + PHIG_Y0, &tile_bar);
+        }
+    }
     unsigned* hist = reinterpret_cast<unsigned*>(tile + T3);                // [H3]
     unsigned* sm_off = hist + H3;                                           // [nbc + 1]
     float* sdec = reinterpret_cast<float*>(sm_off + nbc + 1);               // NV == 1: [2 lim + 1]
@@ -412,8 +428,6 @@ __global__ void __launch_bounds__(T_BRICK, 4) k_passA(Geo g, StoreDev s, const f
         thr = sthr;
         key0 = __float_as_int(cur.est[2]);
     }
-    int bx, by, bz;
-    brick_coords(g, blockIdx.x, &bx, &by, &bz);
     const int L0 = blockIdx.x * nbc;
     for (int t = threadIdx.x; t < 3 * nbc; t += blockDim.x)
         cp_async4(&svc[t], &s.vc[(int64_t)(t >> (3 * g.lB)) * g.Ncc + L0 + (t & (nbc - 1))]);
@@ -424,22 +438,18 @@ __global__ void __launch_bounds__(T_BRICK, 4) k_passA(Geo g, StoreDev s, const f
         vs[H3 + t] = 0;
         vs[2 * H3 + t] = 0;
     }
-    // tile origin (o - 4, o - 2, o - 2): rows of TX = F + 8 nodes start on a
-    // 16-byte boundary, so they load as 4-node chunks, each wrapped on its own
-    const int ox = bx * F - 4, oy = by * F - 2, oz = bz * F - 2;
-    {
-        // thread t < RPI * CX owns chunk column cx of rows t / CX, + RPI, + 2 RPI, ...:
-        // the row's (y, z) advance by constants, with no division in the loop
+    if (!use_tma) {
+        // rows of TX = F + 8 nodes start on a 16-byte boundary: 4-node chunks;
+        // thread t < RPI * CX owns chunk column cx of rows t / CX, + RPI, ...
         const int CX = TX >> 2, nrow = T * T, RPI = T_BRICK / CX;
         if (threadIdx.x < RPI * CX) {
             const int cx = threadIdx.x % CX;
             int row = threadIdx.x / CX;
             int z = row / T, y = row - z * T;
             const int dz = RPI / T, dy = RPI - dz * T;
-            const float* xsrc = phi + wrap1(ox + 4 * cx, g.N);
             float* dst = tile + 4 * cx;
             for (; row < nrow; row += RPI) {
-                cp_async16(dst + row * TS, xsrc + ((int64_t)wrap1(oz + z, g.N) * g.N + wrap1(oy + y, g.N)) * g.S);
+                cp_async16(dst + row * TS, phig + phig_index(g.N, ox + 4 * cx, oy + y, oz + z));
                 y += dy;
                 z += dz;
                 if (y >= T) {
@@ -462,7 +472,12 @@ __global__ void __launch_bounds__(T_BRICK, 4) k_passA(Geo g, StoreDev s, const f
         }
     }
     cp_async_wait_all();
-    __syncthreads();
+    const bool tile_ok = !use_tma || mbar_wait_bounded(&tile_bar, 0);
+    if (__syncthreads_or(!tile_ok)) {       // the tile copy never completed: report, drain, leave
+        if (threadIdx.x == 0) atomicOr(w.flags, ERR_TIMEOUT);
+        mbar_wait_bounded(&tile_bar, 0);
+        return;
+    }
     const float e0 = cur.est[0], e1 = cur.est[1];
     const int nbits = 8 * NX, half = 1 << (nbits - 1);
     const int sb = g.sbits, wmask = (1 << sb) - 1;
@@ -757,9 +772,10 @@ __global__ void k_momentum(int ncc, const long long* __restrict__ vsum, long lon
 
 template <int NX, int NV>
 struct Disp {
-    static void passA(const Geo& g, const StoreDev& s, const float* phi, const CodecDev& cur, float kick, float dc,
-                      const StepScratch& w, const DriftDebug& dbg, size_t sm, cudaStream_t st) {
-        k_passA<NX, NV><<<g.nbricks, T_BRICK, sm, st>>>(g, s, phi, cur, kick, dc, w, dbg);
+    static void passA(const Geo& g, const StoreDev& s, const float* phig, const CUtensorMap& tmap, int use_tma,
+                      const CodecDev& cur, float kick, float dc, const StepScratch& w, const DriftDebug& dbg,
+                      size_t sm, cudaStream_t st) {
+        k_passA<NX, NV><<<g.nbricks, T_BRICK, sm, st>>>(g, s, phig, tmap, use_tma, cur, kick, dc, w, dbg);
     }
     static void passB(const Geo& g, const StoreDev& so, const StoreDev& sn, const CodecDev& cur,
                       const CodecDev& next, float dc, const unsigned* ghost, const float* vcn, unsigned* flags,
@@ -850,20 +866,23 @@ void launch_deposit(const Geo& g, const StoreDev& s, float* mesh, double scale, 
 
 static size_t passA_smem(const Geo& g) {
     const int T = g.F + 5, TS = g.F + 8, H3 = g.Bh * g.Bh * g.Bh, nbc = g.B * g.B * g.B;
-    size_t sm = (((size_t)3 * H3 * 8 + 15) & ~(size_t)15) + (size_t)T * T * TS * 4 + (size_t)H3 * 4 +
-                (size_t)(nbc + 1) * 4;
+    // + 128: the tile is placed on a 128-byte boundary at run time
+    size_t sm = (size_t)3 * H3 * 8 + 128 + (size_t)T * T * TS * 4 + (size_t)H3 * 4 + (size_t)(nbc + 1) * 4;
     if (g.nnu == 1) sm += (size_t)(3 * g.nulim + 3) * 4 + VT_N;
     sm += (size_t)3 * nbc * 4;
     return (sm + 15) & ~(size_t)15;
 }
 
-void launch_passA(const Geo& g, const StoreDev& s, const float* phi, const CodecDev& cur, float kick, float dc,
-                  const StepScratch& w, const DriftDebug& dbg, cudaStream_t st) {
+void launch_passA(const Geo& g, const StoreDev& s, const float* phig, const CUtensorMap* tmap, const CodecDev& cur,
+                  float kick, float dc, const StepScratch& w, const DriftDebug& dbg, cudaStream_t st) {
     size_t sm = passA_smem(g);
-    if (g.nchi == 1 && g.nnu == 1) { set_smem_attrs<1, 1>(); Disp<1, 1>::passA(g, s, phi, cur, kick, dc, w, dbg, sm, st); }
-    else if (g.nchi == 1) { set_smem_attrs<1, 2>(); Disp<1, 2>::passA(g, s, phi, cur, kick, dc, w, dbg, sm, st); }
-    else if (g.nnu == 1) { set_smem_attrs<2, 1>(); Disp<2, 1>::passA(g, s, phi, cur, kick, dc, w, dbg, sm, st); }
-    else { set_smem_attrs<2, 2>(); Disp<2, 2>::passA(g, s, phi, cur, kick, dc, w, dbg, sm, st); }
+    static const CUtensorMap none{};
+    const CUtensorMap& tm = tmap ? *tmap : none;
+    const int use = tmap != nullptr;
+    if (g.nchi == 1 && g.nnu == 1) { set_smem_attrs<1, 1>(); Disp<1, 1>::passA(g, s, phig, tm, use, cur, kick, dc, w, dbg, sm, st); }
+    else if (g.nchi == 1) { set_smem_attrs<1, 2>(); Disp<1, 2>::passA(g, s, phig, tm, use, cur, kick, dc, w, dbg, sm, st); }
+    else if (g.nnu == 1) { set_smem_attrs<2, 1>(); Disp<2, 1>::passA(g, s, phig, tm, use, cur, kick, dc, w, dbg, sm, st); }
+    else { set_smem_attrs<2, 2>(); Disp<2, 2>::passA(g, s, phig, tm, use, cur, kick, dc, w, dbg, sm, st); }
 }
 
 void launch_cells(const Geo& g, const StepScratch& w, unsigned* off_new, float* vc_new, cudaStream_t st) {

@@ -3,6 +3,8 @@
 
 #include <string>
 
+#include <cuda.h>
+
 #include "cube_common.cuh"
 
 namespace cube {
@@ -100,8 +102,9 @@ void launch_encode_scatter(const Geo& g, const float* pos, const float* vel, con
 void launch_decode(const Geo& g, const StoreDev& s, const float* dec, float* pos, float* vel, unsigned* id,
                    cudaStream_t st);
 void launch_deposit(const Geo& g, const StoreDev& s, float* mesh, double scale, cudaStream_t st);
-void launch_passA(const Geo& g, const StoreDev& s, const float* phi, const CodecDev& cur, float kick, float dc,
-                  const StepScratch& w, const DriftDebug& dbg, cudaStream_t st);
+// phig: ghosted Phi; tmap: TMA map of phig with the brick's tile as its box, or NULL (cp.async loads)
+void launch_passA(const Geo& g, const StoreDev& s, const float* phig, const CUtensorMap* tmap, const CodecDev& cur,
+                  float kick, float dc, const StepScratch& w, const DriftDebug& dbg, cudaStream_t st);
 void launch_cells(const Geo& g, const StepScratch& w, unsigned* off_new, float* vc_new, cudaStream_t st);
 void launch_passB(const Geo& g, const StoreDev& s_old, const StoreDev& s_new, const CodecDev& cur,
                   const CodecDev& next, float dc, const StepScratch& w, cudaStream_t st);
@@ -129,12 +132,13 @@ bool fft_size_supported(int N);                                                 
 void fft_x_r2c(const FftPlan& p, float* mesh, int S, cudaStream_t st);                 // rows: r2c
 void fft_y(const FftPlan& p, float* mesh, int S, bool inverse, cudaStream_t st);        // y columns
 void fft_z(const FftPlan& p, float* mesh, int S, float g0, bool green, cudaStream_t st); // z (+ Green, inverse)
-void fft_x_c2r(const FftPlan& p, float* mesh, int S, cudaStream_t st);                 // rows: c2r
+void fft_x_c2r(const FftPlan& p, float* mesh, int S, float* phig, cudaStream_t st);     // rows: c2r into ghosted Phi
 int pk_blocks(int N);
 void launch_pk_bin(const FftPlan& p, const float* mesh, int S, int nbins, double pfac, double kfund,
                    double* part, cudaStream_t st);
 void launch_pk_reduce(const double* part, int nblocks, int nbins, double* k, double* pk, double* nm,
                       cudaStream_t st);
 void launch_unpad(const float* mesh, int N, int S, float* out, cudaStream_t st);
+void launch_unpad_phig(const float* phig, int N, float* out, cudaStream_t st);
 
 }  // namespace cube
