@@ -161,6 +161,23 @@ cube_status cube_decode(cube_ctx* ctx, float* pos, float* vel, uint32_t* id);
    rebuilds it).  Synchronises.  Errors: CUBE_E_ARG, CUBE_E_STATE. */
 cube_status cube_power_spectrum(cube_ctx* ctx, int32_t n_bins, double* k, double* pk, double* nmodes);
 
+/* ---------------------------------------------------------------- time step */
+
+/* Largest |p| over the store's particles and the three axes (momenta as
+   decoded, Eq. v).  Synchronises.  Errors: CUBE_E_STATE (no store). */
+cube_status cube_max_speed(cube_ctx* ctx, double* p_max);
+
+/* Step-size control (Section 2.3.3: the time increment is limited by the
+   particles' velocities): the largest a_to <= a_max for which the fastest
+   particle of the current store, drifting with its present momentum,
+   moves at most `cells` coarse cells over [a, a_to] (a = the store's
+   epoch), i.e. p_max * int_a^a_to da / (a^3 E) <= cells * R fine cells.
+   The step's own kick changes the momenta before the drift, so keep
+   `cells` below 1 (0.5 leaves a factor 2) to stay within cube_pm_step's
+   one-cell migration limit.  Synchronises.
+   Errors: CUBE_E_ARG (a_max <= a, cells outside (0, 1]), CUBE_E_STATE. */
+cube_status cube_next_epoch(cube_ctx* ctx, double a_max, double cells, double* a_to);
+
 /* ---------------------------------------------------------------- inspection */
 
 typedef struct {

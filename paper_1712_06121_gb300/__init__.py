@@ -77,6 +77,8 @@ _sigs = {
                            ctypes.POINTER(ctypes.c_int32)], ctypes.c_int),
     "cube_phase_name": ([ctypes.c_int32], ctypes.c_char_p),
     "cube_counts_to_offsets_noalloc": ([_P, ctypes.c_int64, _P, _P], ctypes.c_int),
+    "cube_max_speed": ([_P, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
+    "cube_next_epoch": ([_P, ctypes.c_double, ctypes.c_double, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
 }
 for _name, (_args, _res) in _sigs.items():
     _f = getattr(_lib, _name)
@@ -155,6 +157,18 @@ def cube_stats_get(ctx):
     st = cube_stats()
     _check(_lib.cube_stats_get(ctx, ctypes.byref(st)))
     return st
+
+
+def cube_max_speed(ctx):
+    v = ctypes.c_double()
+    _check(_lib.cube_max_speed(ctx, ctypes.byref(v)))
+    return v.value
+
+
+def cube_next_epoch(ctx, a_max, cells=0.5):
+    v = ctypes.c_double()
+    _check(_lib.cube_next_epoch(ctx, float(a_max), float(cells), ctypes.byref(v)))
+    return v.value
 
 
 def cube_density(ctx, rho):

@@ -160,6 +160,7 @@ struct cube_ctx {
     int* maxmig = nullptr;
     unsigned* scan_tmp = nullptr;
     long long* mom = nullptr;
+    unsigned* vmax = nullptr;       // largest |p| of the store, float bits
     float* mesh = nullptr;
     float* phig = nullptr;          // ghosted Phi, written by the c2r sweep
     CUtensorMap phig_map{};         // TMA map of phig with pass A's tile as the box
@@ -366,6 +367,7 @@ cube_status cube_create(const cube_params* params, void* cuda_stream, cube_ctx**
     AL(c->maxmig, 4);
     AL(c->scan_tmp, (size_t)scan_tmp_words(std::max<int64_t>(g.Ncc + 1, (int64_t)g.nbricks * H3 + 1)) * 4 + 64);
     AL(c->mom, 3 * 8);
+    AL(c->vmax, 4);
     AL(c->mesh, (size_t)g.N * g.N * g.S * 4);
     AL(c->phig, (size_t)phig_nx(g.N) * phig_ny(g.N) * phig_ny(g.N) * 4);
     FftPlan& f = c->fft;
@@ -685,6 +687,46 @@ cube_status cube_power_spectrum(cube_ctx* c, int32_t n_bins, double* k, double* 
     CK(cudaGetLastError());
     if (s != CUBE_OK) return s;
     return latched(c);
+}
+
+cube_status cube_max_speed(cube_ctx* c, double* p_max) {
+    if (!c || !p_max) return fail(CUBE_E_ARG, "NULL argument");
+    if (!c->encoded) return fail(CUBE_E_STATE, "no store: call cube_encode first");
+    const Geo& g = c->g;
+    if (c->raw) launch_raw_max_speed(g, (const float*)c->nu[0], c->vmax, c->st);
+    else launch_max_speed(g, c->store(c->cur), c->codec[c->cur].dec, c->vmax, c->st);
+    c->launches += 1;
+    unsigned bits = 0;
+    CK(cudaMemcpyAsync(&bits, c->vmax, 4, cudaMemcpyDeviceToHost, c->st));
+    cube_status s = latched(c);
+    float f;
+    std::memcpy(&f, &bits, 4);
+    *p_max = f;
+    return s;
+}
+
+cube_status cube_next_epoch(cube_ctx* c, double a_max, double cells, double* a_to) {
+    if (!c || !a_to) return fail(CUBE_E_ARG, "NULL argument");
+    if (!c->encoded) return fail(CUBE_E_STATE, "no store: call cube_encode first");
+    if (!(a_max > c->a)) return fail(CUBE_E_ARG, "a_max must exceed the store's epoch");
+    if (!(cells > 0.0 && cells <= 1.0)) return fail(CUBE_E_ARG, "cells must be in (0, 1]");
+    double p = 0.0;
+    cube_status s = cube_max_speed(c, &p);
+    if (s != CUBE_OK) return s;
+    const double limit = cells * c->g.R;                 // fine cells
+    const double a0 = c->a;
+    if (p * c->cosmo.drift(a0, a_max) <= limit) {
+        *a_to = a_max;
+        return CUBE_OK;
+    }
+    double lo = a0, hi = a_max;                         // drift(a0, a) grows with a: bisect
+    for (int it = 0; it < 100 && hi - lo > 1e-15 * hi; ++it) {
+        const double mid = 0.5 * (lo + hi);
+        if (p * c->cosmo.drift(a0, mid) <= limit) lo = mid;
+        else hi = mid;
+    }
+    *a_to = lo;
+    return lo > a0 ? CUBE_OK : fail(CUBE_E_ARG, "no step keeps the fastest particle within the limit");
 }
 
 cube_status cube_state_view(cube_ctx* c, cube_state* out) {

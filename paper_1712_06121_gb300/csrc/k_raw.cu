@@ -150,6 +150,16 @@ __global__ void __launch_bounds__(RAW_T) k_raw_momentum(int64_t np, const float*
     }
 }
 
+// largest |p| over particles and axes, as the bits of a non-negative float
+__global__ void __launch_bounds__(RAW_T) k_raw_max_speed(int64_t np, const float* __restrict__ V,
+                                                         unsigned* __restrict__ vmax_bits) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    float m = 0.0f;
+    if (i < np) m = fmaxf(fmaxf(fabsf(V[i]), fabsf(V[np + i])), fabsf(V[2 * np + i]));
+    const unsigned b = __reduce_max_sync(0xffffffffu, __float_as_uint(m));
+    if ((threadIdx.x & 31) == 0) atomicMax(vmax_bits, b);
+}
+
 __global__ void k_iota(unsigned* out, int64_t n) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) out[i] = (unsigned)i;
@@ -174,6 +184,11 @@ void launch_raw_kick_drift(const Geo& g, float* P, float* V, const float* phig, 
 }
 
 void launch_iota(unsigned* out, int64_t n, cudaStream_t st) { k_iota<<<nblk(n), RAW_T, 0, st>>>(out, n); }
+
+void launch_raw_max_speed(const Geo& g, const float* V, unsigned* vmax_bits, cudaStream_t st) {
+    cudaMemsetAsync(vmax_bits, 0, sizeof(unsigned), st);
+    k_raw_max_speed<<<nblk(g.Np), RAW_T, 0, st>>>(g.Np, V, vmax_bits);
+}
 
 void launch_raw_momentum(const Geo& g, const float* V, long long* out3, cudaStream_t st) {
     cudaMemsetAsync(out3, 0, 3 * sizeof(long long), st);

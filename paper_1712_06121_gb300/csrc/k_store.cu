@@ -251,6 +251,31 @@ __global__ void __launch_bounds__(T_BRICK) k_decode(Geo g, StoreDev s, const flo
     }
 }
 
+// largest |p| over particles and axes of the store (momenta as decoded,
+// v_c + tan-table offset), as the bits of a non-negative float (order-
+// preserving as unsigned)
+template <int NV>
+__global__ void __launch_bounds__(T_BRICK) k_max_speed(Geo g, StoreDev s, const float* __restrict__ dec,
+                                                       unsigned* __restrict__ vmax_bits) {
+    extern __shared__ unsigned sm_off[];
+    const int nbc = g.B * g.B * g.B;
+    const int L0 = blockIdx.x * nbc;
+    for (int c = threadIdx.x; c <= nbc; c += blockDim.x) sm_off[c] = s.offsets[L0 + c];
+    __syncthreads();
+    const unsigned q1 = min(sm_off[nbc], (unsigned)g.Np);
+    float m = 0.0f;
+    for (unsigned i = min(sm_off[0], q1) + threadIdx.x; i < q1; i += blockDim.x) {
+        const int lc = upper_cell(sm_off, nbc, i);
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            const int nu = load_nu<NV>(s.nu, d * g.Np + i, g.nulim);
+            m = fmaxf(m, fabsf(s.vc[(int64_t)d * g.Ncc + L0 + lc] + dec[nu + g.nulim]));
+        }
+    }
+    const unsigned b = __reduce_max_sync(0xffffffffu, __float_as_uint(m));
+    if ((threadIdx.x & 31) == 0) atomicMax(vmax_bits, b);
+}
+
 // ------------------------------------------------------------------ CIC deposit
 // Owner computes: a CTA produces the density of its brick's fine nodes
 // [o, o + F)^3 from the particles of the brick's cells and of the one-cell
@@ -837,6 +862,13 @@ void launch_encode_scatter(const Geo& g, const float* pos, const float* vel, con
     else if (g.nchi == 1) k_encode_scatter<1, 2><<<nb, 256, 0, st>>>(g, pos, vel, id_in, key_sorted, perm, vc, c.thr, c.est, s);
     else if (g.nnu == 1) k_encode_scatter<2, 1><<<nb, 256, 0, st>>>(g, pos, vel, id_in, key_sorted, perm, vc, c.thr, c.est, s);
     else k_encode_scatter<2, 2><<<nb, 256, 0, st>>>(g, pos, vel, id_in, key_sorted, perm, vc, c.thr, c.est, s);
+}
+
+void launch_max_speed(const Geo& g, const StoreDev& s, const float* dec, unsigned* vmax_bits, cudaStream_t st) {
+    size_t sm = (size_t)(g.B * g.B * g.B + 1) * sizeof(unsigned);
+    cudaMemsetAsync(vmax_bits, 0, sizeof(unsigned), st);
+    if (g.nnu == 1) k_max_speed<1><<<g.nbricks, T_BRICK, sm, st>>>(g, s, dec, vmax_bits);
+    else k_max_speed<2><<<g.nbricks, T_BRICK, sm, st>>>(g, s, dec, vmax_bits);
 }
 
 void launch_decode(const Geo& g, const StoreDev& s, const float* dec, float* pos, float* vel, unsigned* id,

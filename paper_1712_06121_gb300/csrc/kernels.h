@@ -118,6 +118,8 @@ void launch_raw_kick_drift(const Geo& g, float* P, float* V, const float* phi, f
                            unsigned* flags, cudaStream_t st);
 void launch_raw_momentum(const Geo& g, const float* V, long long* out3, cudaStream_t st);
 void launch_iota(unsigned* out, int64_t n, cudaStream_t st);
+void launch_raw_max_speed(const Geo& g, const float* V, unsigned* vmax_bits, cudaStream_t st);
+void launch_max_speed(const Geo& g, const StoreDev& s, const float* dec, unsigned* vmax_bits, cudaStream_t st);
 
 // ------------------------------------------------------------ k_fft.cu
 struct FftPlan {

@@ -30,13 +30,14 @@ class Workload:
     n_steps: int
     seed: int
     ratio: int = 4
+    sigma8: float = 0.8
 
     @property
     def n_particles(self):
         return self.n_part_side ** 3
 
     def cosmology(self):
-        return einstein_de_sitter() if self.cosmo_kind == "eds" else lcdm_bbks()
+        return einstein_de_sitter(self.sigma8) if self.cosmo_kind == "eds" else lcdm_bbks(sigma8=self.sigma8)
 
     def omega(self):
         c = self.cosmology()
@@ -49,6 +50,19 @@ WORKLOADS = {
     "pm128o": Workload("pm128o", 128, 256, 300.0, "lcdm", 1, 1, 0.02, 1.0, 50, 1712002),
     "pm512": Workload("pm512", 512, 1024, 600.0, "lcdm", 1, 1, 0.02, 1.0, 50, 1712003),
 }
+
+
+def ensemble_c4(n=64, seed=1712004):
+    """An ensemble of uneven realisations: particles per side drawn from
+    {32, 48, 64, 96, 128}, mesh twice that, box uniform in [50, 400] Mpc/h,
+    sigma8 uniform in [0.7, 0.9], flat LCDM BBKS, x1v1, 30 steps uniform in a
+    from z = 49 to z = 0, IC seeds 0 .. n-1."""
+    rng = np.random.default_rng(seed)
+    sides = rng.choice([32, 48, 64, 96, 128], size=n)
+    boxes = rng.uniform(50.0, 400.0, size=n)
+    s8 = rng.uniform(0.7, 0.9, size=n)
+    return [Workload(f"c4_{i}", int(sides[i]), 2 * int(sides[i]), float(boxes[i]), "lcdm", 1, 1, 0.02, 1.0, 30, i,
+                     sigma8=float(s8[i])) for i in range(n)]
 
 
 def uniform_schedule(a_init, a_final, n_steps):
