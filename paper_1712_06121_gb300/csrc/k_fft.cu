@@ -157,13 +157,15 @@ __device__ __forceinline__ void tile_fft(float2* buf, const float2* tw) {
 // further (two real sequences in one complex transform).  The caller's
 // cp.async copies (twiddles, tables) are waited for before the closing
 // barrier.
-template <int n, int R, bool INV>
+// UNR = 1 keeps one butterfly's loads in flight per thread (fewer
+// registers); UNR = KMAX issues all of them first (more loads in flight)
+template <int n, int R, bool INV, int UNR = 1>
 __device__ __forceinline__ void fft_pass_load(float2* buf, const float2* __restrict__ src, int64_t rs, int c0,
                                               int ncol, int64_t cs = 1, int pack_off = 0) {
     constexpr int nq = n / R;
     constexpr int nbf = nq * NC;
     constexpr int KMAX = (nbf + FFT_T - 1) / FFT_T;
-#pragma unroll 1
+#pragma unroll UNR
     for (int q = 0; q < KMAX; ++q) {
         const int b = threadIdx.x + q * FFT_T;
         if (nbf % FFT_T == 0 || b < nbf) {
@@ -194,7 +196,7 @@ __device__ __forceinline__ void fft_pass_load(float2* buf, const float2* __restr
 // 0 of the tile (c0 = 0) holds x + i y of two real sequences; x goes to
 // column 0 and y to the column split_off further, both as (value, 0).
 // Shared memory is only read: the caller synchronises before reusing it.
-template <int n, int Ns, int R, int TWM, bool INV, class Post>
+template <int n, int Ns, int R, int TWM, bool INV, class Post, int UNR = 1>
 __device__ __forceinline__ void fft_pass_store(const float2* buf, const float2* tw, float2* dst, int64_t rs, int c0,
                                                int ncol, Post post, int64_t cs = 1, int split_off = 0) {
     constexpr int nq = n / R;
@@ -202,7 +204,7 @@ __device__ __forceinline__ void fft_pass_store(const float2* buf, const float2* 
     constexpr int nbf = nq * NC;
     constexpr int KMAX = (nbf + FFT_T - 1) / FFT_T;
     constexpr int step = TWM * (n / (Ns * R));
-#pragma unroll 1
+#pragma unroll UNR
     for (int q = 0; q < KMAX; ++q) {
         const int b = threadIdx.x + q * FFT_T;
         if (nbf % FFT_T == 0 || b < nbf) {
@@ -240,17 +242,17 @@ struct NoPost {
 };
 
 // passes from span Ns on, the last one through fft_pass_store
-template <int n, int Ns, int TWM, bool INV, class Post>
+template <int n, int Ns, int TWM, bool INV, class Post, int UNR = 1>
 __device__ __forceinline__ void tile_fft_to_global(float2* buf, const float2* tw, float2* dst, int64_t rs, int c0,
                                                    int ncol, Post post, int64_t cs = 1, int split_off = 0) {
     constexpr int rem = n / Ns;
     constexpr int R = rem % 8 == 0 ? 8 : rem % 4 == 0 ? 4 : rem % 2 == 0 ? 2 : 3;
     static_assert(rem % R == 0, "length must be 2^a 3^b");
     if constexpr (Ns * R == n) {
-        fft_pass_store<n, Ns, R, TWM, INV>(buf, tw, dst, rs, c0, ncol, post, cs, split_off);
+        fft_pass_store<n, Ns, R, TWM, INV, Post, UNR>(buf, tw, dst, rs, c0, ncol, post, cs, split_off);
     } else {
         fft_pass<n, Ns, R, TWM, INV, false>(buf, tw);
-        tile_fft_to_global<n, Ns * R, TWM, INV>(buf, tw, dst, rs, c0, ncol, post, cs, split_off);
+        tile_fft_to_global<n, Ns * R, TWM, INV, Post, UNR>(buf, tw, dst, rs, c0, ncol, post, cs, split_off);
     }
 }
 
@@ -361,7 +363,7 @@ __device__ __forceinline__ void xpass_load(float2* buf, const float* mesh, int64
     constexpr int nq = n / R;
     constexpr int nbf = nq * NC;
     constexpr int KMAX = (nbf + XFFT_T - 1) / XFFT_T;
-#pragma unroll 1
+#pragma unroll
     for (int q = 0; q < KMAX; ++q) {
         const int b = threadIdx.x + q * XFFT_T;
         if (nbf % XFFT_T == 0 || b < nbf) {
@@ -402,7 +404,7 @@ __device__ __forceinline__ void xpass_store(const float2* buf, const float2* tw,
     constexpr int nbf = nq * NC;
     constexpr int KMAX = (nbf + XFFT_T - 1) / XFFT_T;
     constexpr int step = TWM * (n / (Ns * R));
-#pragma unroll 1
+#pragma unroll
     for (int q = 0; q < KMAX; ++q) {
         const int b = threadIdx.x + q * XFFT_T;
         if (nbf % XFFT_T == 0 || b < nbf) {
@@ -514,11 +516,13 @@ __global__ void __launch_bounds__(FFT_T, N <= 512 ? 2 : 1) k_fft_y(float* mesh, 
     const int Sc = S / 2;
     const int c0 = blockIdx.x * NC;
     float2* slab = reinterpret_cast<float2*>(mesh) + (int64_t)blockIdx.y * N * Sc;
-    fft_pass_load<N, first_radix<N>(), INV>(buf, slab, Sc, c0, h, 1, h);
+    constexpr int R1 = first_radix<N>(), KMAX1 = (N / R1 * NC + FFT_T - 1) / FFT_T;
+    fft_pass_load<N, R1, INV, INV ? 1 : KMAX1>(buf, slab, Sc, c0, h, 1, h);
     if (INV) {
         tile_fft_to_global<N, first_radix<N>(), 1, INV>(buf, stw, slab, Sc, c0, h, NoPost{}, 1, h);
     } else if (blockIdx.x > 0) {
-        tile_fft_to_global<N, first_radix<N>(), 1, INV>(buf, stw, slab, Sc, c0, h, NoPost{});
+        constexpr int KL = (last_span<N>() * NC + FFT_T - 1) / FFT_T;
+        tile_fft_to_global<N, first_radix<N>(), 1, INV, NoPost, KL>(buf, stw, slab, Sc, c0, h, NoPost{});
     } else {
         tile_fft<N, first_radix<N>(), 1, INV, false>(buf, stw);
         for (int t = threadIdx.x; t < N * NC; t += FFT_T) {
