@@ -71,6 +71,19 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const void* tmap, int x, 
         : "memory");
 }
 
+// floor(t / d) for 0 <= t < 4096 and 2 <= d <= 8 as (t * ceil(2^16 / d)) >> 16
+// (checked exhaustively over that range); m = div_magic(d)
+__host__ __device__ __forceinline__ unsigned div_magic(int d) { return (65536u + (unsigned)d - 1u) / (unsigned)d; }
+__host__ __device__ __forceinline__ int div_small(int t, unsigned m) { return (int)(((unsigned)t * m) >> 16); }
+
+// the three coordinates of t = e0 + d (e1 + d e2), 0 <= t < d^3 <= 512
+__device__ __forceinline__ void split3(int t, int d, unsigned m, int* e) {
+    const int q = div_small(t, m);
+    e[0] = t - q * d;
+    e[2] = div_small(q, m);
+    e[1] = q - e[2] * d;
+}
+
 struct Geo {
     int N;        // fine cells per side
     int Nc;       // coarse cells per side

@@ -301,7 +301,9 @@ __global__ void __launch_bounds__(T_BRICK) k_deposit(Geo g, StoreDev s, float* _
     for (int t = threadIdx.x; t < F3 / 2; t += blockDim.x)            // F3 is a multiple of 64
         reinterpret_cast<uint4*>(acc)[t] = make_uint4(0u, 0u, 0u, 0u);
     for (int t = threadIdx.x; t < E3; t += blockDim.x) {
-        const int lx = t % E - 1, ly = (t / E) % E - 1, lz = t / (E * E) - 1;
+        int ec[3];
+        split3(t, E, div_magic(E), ec);
+        const int lx = ec[0] - 1, ly = ec[1] - 1, lz = ec[2] - 1;
         const int L = cell_rank(g, wrapi(c0[0] + lx, g.Nc), wrapi(c0[1] + ly, g.Nc), wrapi(c0[2] + lz, g.Nc));
         const unsigned a = s.offsets[L];
         cstart[t] = a;
@@ -420,6 +422,7 @@ __global__ void __launch_bounds__(T_BRICK, 4) k_passA(Geo g, StoreDev s, const f
     // ghosted Phi (no wrap): one TMA box, or 16-byte cp.async chunks
     const int F = g.F, T = F + 5, TX = F + 8, TS = TX, T3 = T * T * TS;
     const int nbc = g.B * g.B * g.B, Bh = g.Bh, H3 = Bh * Bh * Bh;
+    const unsigned mBh = div_magic(Bh);
     const int lim = g.nulim;
     int bx, by, bz;
     brick_coords(g, blockIdx.x, &bx, &by, &bz);
@@ -608,7 +611,8 @@ __global__ void __launch_bounds__(T_BRICK, 4) k_passA(Geo g, StoreDev s, const f
     const int bc[3] = {bx, by, bz};
     for (int t = threadIdx.x; t < H3; t += blockDim.x) {
         const unsigned h = hist[t];
-        const int e[3] = {t % Bh, (t / Bh) % Bh, t / (Bh * Bh)};
+        int e[3];
+        split3(t, Bh, mBh, e);
         w.ghost[flat_slot(g, bc, e)] = h;                 // every slot has exactly one writer
         if (h) {
             const int L = cell_rank(g, wrap1(bx * g.B - 1 + e[0], g.Nc), wrap1(by * g.B - 1 + e[1], g.Nc),
@@ -669,6 +673,7 @@ __global__ void __launch_bounds__(PB_WARPS * 32, 5) k_passB(Geo g, StoreDev so, 
                                                         const float* __restrict__ vc_new, unsigned* flags) {
     extern __shared__ unsigned pb_smem[];
     const int nbc = g.B * g.B * g.B, Bh = g.Bh, H3 = Bh * Bh * Bh;
+    const unsigned mBh = div_magic(Bh);
     const int lim = g.nulim;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     float* sdec = reinterpret_cast<float*>(pb_smem);                       // NV == 1: [2 lim + 1]
@@ -714,7 +719,8 @@ __global__ void __launch_bounds__(PB_WARPS * 32, 5) k_passB(Geo g, StoreDev so, 
     for (int c = lane; c <= nbc; c += 32) sm_off[c] = so.offsets[L0 + c];
     for (int t = lane; t < 3 * nbc; t += 32) svc[t] = so.vc[(int64_t)(t >> (3 * g.lB)) * g.Ncc + L0 + (t & (nbc - 1))];
     for (int t = lane; t < H3; t += 32) {
-        const int e[3] = {t % Bh, (t / Bh) % Bh, t / (Bh * Bh)};
+        int e[3];
+        split3(t, Bh, mBh, e);
         run[t] = ghost[flat_slot(g, bc, e)];
         const int L = cell_rank(g, wrap1(bx * g.B - 1 + e[0], g.Nc), wrap1(by * g.B - 1 + e[1], g.Nc),
                                 wrap1(bz * g.B - 1 + e[2], g.Nc));
