@@ -137,10 +137,10 @@ __global__ void k_encode_sigma(Geo g, const float* __restrict__ vel, const unsig
 __global__ void k_sigma_finalize(const float* __restrict__ part, int nparts, double count, double ratio,
                                  double fixed, double* sigma_out) {
     __shared__ double sh[32];
-    // contiguous chunk per thread in FP32, then a fixed tree in FP64
-    const int per = (nparts + blockDim.x - 1) / blockDim.x;
+    // strided FP32 sums per thread (coalesced loads, fixed order), then a fixed tree in FP64
     float acc = 0.0f;
-    for (int i = threadIdx.x * per, e = min(nparts, i + per); i < e; ++i) acc += part[i];
+#pragma unroll 8
+    for (int i = threadIdx.x; i < nparts; i += blockDim.x) acc += part[i];
     double s = block_sum_double((double)acc, sh);
     if (threadIdx.x == 0) {
         double x = fixed > 0.0 ? fixed : sqrt(s / count) * ratio;
@@ -148,10 +148,11 @@ __global__ void k_sigma_finalize(const float* __restrict__ part, int nparts, dou
     }
 }
 
-__global__ void k_codec_tables(int lim, const double* __restrict__ tanv, const double* __restrict__ tanh_,
-                               const double* __restrict__ sigma, float* __restrict__ dec, float* __restrict__ thr,
-                               float* __restrict__ est, unsigned char* __restrict__ vtab) {
-    const double sg = *sigma;
+// decode table, thresholds, starting-guess constants and (1-byte codes,
+// single block) the bucket table for the codec scale sg
+__device__ void codec_tables_body(int lim, const double* __restrict__ tanv, const double* __restrict__ tanh_,
+                                  double sg, float* __restrict__ dec, float* __restrict__ thr,
+                                  float* __restrict__ est, unsigned char* __restrict__ vtab) {
     const double s = sqrt(PI_D / (2.0 * sg * sg));
     const double gam = sqrt(2.0 * sg * sg / PI_D);
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k <= lim + 1; k += gridDim.x * blockDim.x) {
@@ -170,21 +171,30 @@ __global__ void k_codec_tables(int lim, const double* __restrict__ tanv, const d
             thr[lim + 1] = __int_as_float(0x7f800000);   // +inf
         }
     }
-    if (vtab) {   // 1-byte codes, one block: the bucket table of nu_from_table
+    if (vtab) {   // 1-byte codes (lim < 256), one block: the bucket table of nu_from_table
+        __shared__ float sthr[256];
         __syncthreads();
-        const int key0 = (int)(__float_as_uint(thr[1]) >> (23 - VT_B)) - 1;   // first bucket lies below thr[1]
+        for (int k = threadIdx.x; k <= lim; k += blockDim.x) sthr[k] = thr[k];
+        __syncthreads();
+        const int key0 = (int)(__float_as_uint(sthr[1]) >> (23 - VT_B)) - 1;   // first bucket lies below thr[1]
         if (threadIdx.x == 0) est[2] = __int_as_float(key0);
         for (int i = threadIdx.x; i < VT_N; i += blockDim.x) {
             const float A = __uint_as_float((unsigned)(key0 + i) << (23 - VT_B));
             int lo = 0, hi = lim;                       // number of thresholds thr[1..lim] <= A
             while (lo < hi) {
                 const int mid = (lo + hi + 1) >> 1;
-                if (thr[mid] <= A) lo = mid;
+                if (sthr[mid] <= A) lo = mid;
                 else hi = mid - 1;
             }
             vtab[i] = (unsigned char)lo;
         }
     }
+}
+
+__global__ void k_codec_tables(int lim, const double* __restrict__ tanv, const double* __restrict__ tanh_,
+                               const double* __restrict__ sigma, float* __restrict__ dec, float* __restrict__ thr,
+                               float* __restrict__ est, unsigned char* __restrict__ vtab) {
+    codec_tables_body(lim, tanv, tanh_, *sigma, dec, thr, est, vtab);
 }
 
 template <int NX, int NV>
