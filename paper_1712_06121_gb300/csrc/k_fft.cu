@@ -329,6 +329,47 @@ __device__ __forceinline__ void fft_pass_post(float2* buf, const float2* tw, Pos
     __syncthreads();
 }
 
+// The last forward pass (span n / R) and the first inverse pass (span 1)
+// of the same radix R touch the same R elements per thread (j + m n/R), so
+// they run back to back in registers: forward pass, post(element, column,
+// value) (the Green's function), inverse radix-R DFT, written where the
+// inverse first pass writes (j R + m).
+template <int n, int Ns, int R, int TWM, class Post>
+__device__ __forceinline__ void fft_pass_fwd_post_inv(float2* buf, const float2* tw, Post post) {
+    constexpr int nq = n / R;
+    static_assert(nq == Ns, "the last forward pass has span n / R");
+    constexpr int nbf = nq * NC;
+    constexpr int KMAX = (nbf + FFT_T - 1) / FFT_T;
+    constexpr int step = TWM * (n / (Ns * R));
+    float2 v[KMAX][R];
+#pragma unroll
+    for (int q = 0; q < KMAX; ++q) {
+        const int b = threadIdx.x + q * FFT_T;
+        if (nbf % FFT_T == 0 || b < nbf) {
+            const int c = b & (NC - 1), j = b >> LOG_NC;
+#pragma unroll
+            for (int m = 0; m < R; ++m) v[q][m] = buf[sidx<false>(j + m * nq, c)];
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < KMAX; ++q) {
+        const int b = threadIdx.x + q * FFT_T;
+        if (nbf % FFT_T == 0 || b < nbf) {
+            const int c = b & (NC - 1), j = b >> LOG_NC;
+#pragma unroll
+            for (int m = 1; m < R; ++m) v[q][m] = cmul(v[q][m], tw[j * m * step]);
+            dft<R, false>(v[q]);
+#pragma unroll
+            for (int m = 0; m < R; ++m) v[q][m] = post(j + m * Ns, c, v[q][m]);
+            dft<R, true>(v[q]);
+#pragma unroll
+            for (int m = 0; m < R; ++m) buf[sidx<false>(j * R + m, c)] = v[q][m];
+        }
+    }
+    __syncthreads();
+}
+
 // twiddle table into shared memory (asynchronous; waited for with the tile)
 __device__ __forceinline__ void load_tw(float2* stw, const float2* tw, int N) {
     for (int i = threadIdx.x; i < N; i += blockDim.x) cp_async8(&stw[i], &tw[i]);
@@ -581,8 +622,13 @@ __global__ void __launch_bounds__(FFT_T, N <= 512 ? 2 : 1) k_fft_z(float* mesh, 
         tile_fft_but_last<N, first_radix<N>(), 1, false>(buf, stw);
         constexpr int Ns = last_span<N>();
         const GreenPost gp{sk2, swd, g0, sk2[ky], swd[ky], c0, ky, ncol};
-        fft_pass_post<N, Ns, N / Ns, 1, false>(buf, stw, gp);
-        tile_fft_to_global<N, 1, 1, true>(buf, stw, base, zs, c0, ncol, NoPost{});
+        if constexpr (N / Ns == first_radix<N>()) {     // last forward radix = first inverse radix
+            fft_pass_fwd_post_inv<N, Ns, N / Ns, 1>(buf, stw, gp);
+            tile_fft_to_global<N, first_radix<N>(), 1, true>(buf, stw, base, zs, c0, ncol, NoPost{});
+        } else {
+            fft_pass_post<N, Ns, N / Ns, 1, false>(buf, stw, gp);
+            tile_fft_to_global<N, 1, 1, true>(buf, stw, base, zs, c0, ncol, NoPost{});
+        }
     } else {
         tile_fft_to_global<N, first_radix<N>(), 1, false>(buf, stw, base, zs, c0, ncol, NoPost{});
     }
