@@ -420,7 +420,7 @@ __global__ void __launch_bounds__(T_BRICK) k_deposit(Geo g, StoreDev s, float* _
 // ([o - 2, o + F + 3) per axis, periodic), brick offsets, the histogram of
 // destination cells over the brick and its one-cell halo (Bh^3 cells) with
 // fixed-point momentum sums, and (1-byte velocities) the codec tables.
-template <int NX, int NV>
+template <int NX, int NV, int FC>
 __global__ void __launch_bounds__(T_BRICK, 4) k_passA(Geo g, StoreDev s, const float* __restrict__ phig,
                                                       const __grid_constant__ CUtensorMap tmap, int use_tma,
                                                       CodecDev cur, float kick, float dc, StepScratch w,
@@ -430,7 +430,9 @@ __global__ void __launch_bounds__(T_BRICK, 4) k_passA(Geo g, StoreDev s, const f
     // Phi tile: T x T rows (y, z: [o - 2, o + F + 3)) of TX = F + 8 nodes
     // (x: [o - 4, o + F + 4)), row stride TS = TX floats, read from the
     // ghosted Phi (no wrap): one TMA box, or 16-byte cp.async chunks
-    const int F = g.F, T = F + 5, TX = F + 8, TS = TX, T3 = T * T * TS;
+    // FC > 0: the brick side in fine cells is the compile-time FC (every
+    // tile offset of the gather becomes an immediate), else g.F
+    const int F = FC > 0 ? FC : g.F, T = F + 5, TX = F + 8, TS = TX, T3 = T * T * TS;
     const int nbc = g.B * g.B * g.B, Bh = g.Bh, H3 = Bh * Bh * Bh;
     const unsigned mBh = div_magic(Bh);
     const int lim = g.nulim;
@@ -546,31 +548,58 @@ __global__ void __launch_bounds__(T_BRICK, 4) k_passA(Geo g, StoreDev s, const f
             n[d] = (d == 0 ? 4 : 2) + (l[d] << g.r) + (Q[d] >> sb);
             wv[d] = (float)(Q[d] & wmask) * winv;
         }
-        // CIC gather of the FD4 gradient: per axis, 4 rows of 6 nodes
+        // CIC gather of the FD4 gradient: per axis, 4 lines of 6 nodes, read
+        // as 28 pairs of x-adjacent nodes {o, o + 1}.  A particle with odd
+        // n_y / 2 reads each pair as {o + 1, o} and swaps it back: near a
+        // uniform lattice (two fine cells per particle spacing) every node
+        // index is even, so unswapped a warp's loads would fall on the 16 even
+        // banks only; the swap spreads them over all 32.
         const int base = (n[2] * T + n[1]) * TS + n[0];
+        const int sh = (n[1] >> 1) & 1;
+        const float* pa = tile + base + sh;
+        const float* pb = tile + base + 1 - sh;
+        auto pair = [&](int o, float& lo, float& hi) {
+            const float u = pa[o], v = pb[o];
+            lo = sh ? v : u;
+            hi = sh ? u : v;
+        };
         float gx = 0.0f, gy = 0.0f, gz = 0.0f;
 #pragma unroll
         for (int a = 0; a < 2; ++a) {
 #pragma unroll
             for (int b = 0; b < 2; ++b) {
+                float r[6];                            // r[j]: node j - 2 of the line
                 {   // x rows at (y + a, z + b)
-                    const float* r = tile + base + a * TS + b * TT;
-                    float g0 = 8.0f * (r[1] - r[-1]) - (r[2] - r[-2]);
-                    float g1 = 8.0f * (r[2] - r[0]) - (r[3] - r[-1]);
+                    const int o = a * TS + b * TT;
+                    pair(o - 2, r[0], r[1]);
+                    pair(o, r[2], r[3]);
+                    pair(o + 2, r[4], r[5]);
+                    float g0 = 8.0f * (r[3] - r[1]) - (r[4] - r[0]);
+                    float g1 = 8.0f * (r[4] - r[2]) - (r[5] - r[1]);
                     float wyz = (a ? wv[1] : 1.0f - wv[1]) * (b ? wv[2] : 1.0f - wv[2]);
                     gx += wyz * ((1.0f - wv[0]) * g0 + wv[0] * g1);
                 }
                 {   // y columns at (x + a, z + b)
-                    const float* r = tile + base + a + b * TT;
-                    float g0 = 8.0f * (r[TS] - r[-TS]) - (r[2 * TS] - r[-2 * TS]);
-                    float g1 = 8.0f * (r[2 * TS] - r[0]) - (r[3 * TS] - r[-TS]);
+#pragma unroll
+                    for (int k = 0; k < 6; ++k) {
+                        float lo, hi;
+                        pair(b * TT + (k - 2) * TS, lo, hi);
+                        r[k] = a ? hi : lo;
+                    }
+                    float g0 = 8.0f * (r[3] - r[1]) - (r[4] - r[0]);
+                    float g1 = 8.0f * (r[4] - r[2]) - (r[5] - r[1]);
                     float wxz = (a ? wv[0] : 1.0f - wv[0]) * (b ? wv[2] : 1.0f - wv[2]);
                     gy += wxz * ((1.0f - wv[1]) * g0 + wv[1] * g1);
                 }
                 {   // z columns at (x + a, y + b)
-                    const float* r = tile + base + a + b * TS;
-                    float g0 = 8.0f * (r[TT] - r[-TT]) - (r[2 * TT] - r[-2 * TT]);
-                    float g1 = 8.0f * (r[2 * TT] - r[0]) - (r[3 * TT] - r[-TT]);
+#pragma unroll
+                    for (int k = 0; k < 6; ++k) {
+                        float lo, hi;
+                        pair(b * TS + (k - 2) * TT, lo, hi);
+                        r[k] = a ? hi : lo;
+                    }
+                    float g0 = 8.0f * (r[3] - r[1]) - (r[4] - r[0]);
+                    float g1 = 8.0f * (r[4] - r[2]) - (r[5] - r[1]);
                     float wxy = (a ? wv[0] : 1.0f - wv[0]) * (b ? wv[1] : 1.0f - wv[1]);
                     gz += wxy * ((1.0f - wv[2]) * g0 + wv[2] * g1);
                 }
@@ -816,7 +845,10 @@ struct Disp {
     static void passA(const Geo& g, const StoreDev& s, const float* phig, const CUtensorMap& tmap, int use_tma,
                       const CodecDev& cur, float kick, float dc, const StepScratch& w, const DriftDebug& dbg,
                       size_t sm, cudaStream_t st) {
-        k_passA<NX, NV><<<g.nbricks, T_BRICK, sm, st>>>(g, s, phig, tmap, use_tma, cur, kick, dc, w, dbg);
+        if (g.F == 16)
+            k_passA<NX, NV, 16><<<g.nbricks, T_BRICK, sm, st>>>(g, s, phig, tmap, use_tma, cur, kick, dc, w, dbg);
+        else
+            k_passA<NX, NV, 0><<<g.nbricks, T_BRICK, sm, st>>>(g, s, phig, tmap, use_tma, cur, kick, dc, w, dbg);
     }
     static void passB(const Geo& g, const StoreDev& so, const StoreDev& sn, const CodecDev& cur,
                       const CodecDev& next, float dc, const unsigned* ghost, const float* vcn, unsigned* flags,
@@ -830,7 +862,8 @@ template <int NX, int NV>
 void set_smem_attrs() {
     static bool done = false;
     if (done) return;
-    cudaFuncSetAttribute(k_passA<NX, NV>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_passA<NX, NV, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_passA<NX, NV, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     cudaFuncSetAttribute(k_passB<NX, NV>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     cudaFuncSetAttribute(k_deposit<NX>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     done = true;
