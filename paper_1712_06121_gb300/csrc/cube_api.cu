@@ -333,6 +333,8 @@ cube_status cube_create(const cube_params* params, void* cuda_stream, cube_ctx**
     while ((1 << g.lB) < g.B) ++g.lB;
     g.lF = 0;
     while ((1 << g.lF) < g.F) ++g.lF;
+    g.nsm = 1;
+    cudaDeviceGetAttribute(&g.nsm, cudaDevAttrMultiProcessorCount, c->device);
 
     auto bad = [&](cudaError_t e, const char* what) -> cube_status {
         cube_destroy(c);
@@ -364,7 +366,7 @@ cube_status cube_create(const cube_params* params, void* cuda_stream, cube_ctx**
     c->npart = std::max(g.nbricks, 1024);
     AL(c->part, (size_t)c->npart * 4);
     AL(c->flags, 4);
-    AL(c->maxmig, 4);
+    AL(c->maxmig, ((size_t)g.nbricks + 2) * 4);    // [0] max migration, [1 ..] crowded-brick list
     AL(c->scan_tmp, (size_t)scan_tmp_words(std::max<int64_t>(g.Ncc + 1, (int64_t)g.nbricks * H3 + 1)) * 4 + 64);
     AL(c->mom, 3 * 8);
     AL(c->vmax, 4);
@@ -587,10 +589,10 @@ cube_status cube_pm_step(cube_ctx* c, double a_from, double a_to) {
     CK(cudaEventRecord(c->ev0, c->st));
     mark(c, 0);
     CK(cudaMemsetAsync(c->vsum, 0, (size_t)g.Ncc * 24, c->st));
-    CK(cudaMemsetAsync(c->maxmig, 0, 4, c->st));
+    CK(cudaMemsetAsync(c->maxmig, 0, 8, c->st));     // max migration, crowded-brick count
     mark(c, 1);
     mesh_potential(c);
-    StepScratch w{c->counts[kn], c->vsum, c->ghost, c->part, c->flags, c->maxmig};
+    StepScratch w{c->counts[kn], c->vsum, c->ghost, c->part, c->flags, c->maxmig, c->maxmig + 1};
     DriftDebug dbg{c->keep ? c->dbg_cell : nullptr, c->dbg_u, c->dbg_p};
     launch_passA(g, c->store(k), c->phig, c->tma ? &c->phig_map : nullptr, c->codec[k], kick, dc, w, dbg, c->st);
     mark(c, 8);

@@ -100,6 +100,7 @@ struct Geo {
     int64_t Np;
     int nulim;    // 2^(8 nnu - 1) - 1: largest |nu|
     int lB, lF;   // log2(B), log2(F): brick and fine-tile sides are powers of two
+    int nsm;      // SMs of the device (grid sizing)
 };
 
 // storage rank of coarse cell (cx, cy, cz), coordinates already in [0, Nc)

@@ -416,6 +416,9 @@ __global__ void __launch_bounds__(T_BRICK) k_deposit(Geo g, StoreDev s, float* _
 }
 
 // ------------------------------------------------------------------ pass A
+// (bricks of more than PB_BIG particles are listed for pass B's whole-CTA path)
+constexpr int PB_BIG = 1024;
+
 // One CTA per brick.  Shared memory: Phi tile of (F + 5)^3 fine nodes
 // ([o - 2, o + F + 3) per axis, periodic), brick offsets, the histogram of
 // destination cells over the brick and its one-cell halo (Bh^3 cells) with
@@ -503,6 +506,7 @@ __global__ void __launch_bounds__(T_BRICK, 4) k_passA(Geo g, StoreDev s, const f
     // while the tile is in flight
     const unsigned q1 = min(s.offsets[L0 + nbc], (unsigned)g.Np);
     unsigned i = min(s.offsets[L0], q1) + threadIdx.x;
+    if (threadIdx.x == 0 && q1 - (i - threadIdx.x) > (unsigned)PB_BIG) w.big[1 + atomicAdd(w.big, 1)] = blockIdx.x;
     int nchi[3] = {0, 0, 0}, nnu[3] = {0, 0, 0};
     if (i < q1) {
 #pragma unroll
@@ -704,47 +708,202 @@ __global__ void k_cells(Geo g, StepScratch w, unsigned* __restrict__ off_new, fl
 // at a time in index order; lanes moving to the same cell get consecutive
 // slots in lane order from the cell's running start (match + popc), so the
 // new order within a cell is the old index order.  No block barriers.
+//
+// A brick holding more than PB_BIG particles (clustering: late epochs reach
+// ~30x the mean) would make its warp the kernel's tail.  Pass A lists those
+// bricks; the first CTAs of the grid take them whole, 256 particles per
+// round: each warp's per-cell counts go to a shared table, and a lane's slot
+// is the cell's running start + the counts of the lower warps + its rank in
+// its warp, which is again the old index order.
 constexpr int PB_WARPS = 8;
+
+// what pass B needs of one particle: its new cell in the brick's halo
+// region (ei), new position code and momentum
+struct PbParticle {
+    int ei;
+    int chi[3];
+    float pv[3];
+};
+
+template <int NX, int NV>
+struct PassB {
+    Geo g;
+    const StoreDev& sn;
+    const float* dec;
+    const float* thr;
+    const unsigned char* stab;
+    int key0, lim;
+    float dc, e0, e1;
+
+    __device__ __forceinline__ PbParticle move(const unsigned* sm_off, const float* svc, unsigned i,
+                                               const int* cchi, const int* cnu) const {
+        const int nbc = g.B * g.B * g.B, Bh = g.Bh;
+        const int nbits = 8 * NX, half = 1 << (nbits - 1), bmask = (1 << nbits) - 1;
+        const float inv2q = ldexpf(1.0f, -(nbits + 1));
+        const float two8n = ldexpf(1.0f, nbits);
+        const int lc = upper_cell(sm_off, nbc, i);
+        const int l[3] = {lc & (g.B - 1), (lc >> g.lB) & (g.B - 1), lc >> (2 * g.lB)};
+        PbParticle r;
+        int e[3];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            const int Q = 2 * (cchi[d] + half) + 1;
+            const float p2 = svc[(d << (3 * g.lB)) + lc] + dec[cnu[d] + lim];
+            float un;
+            const int bin = drift_bin(Q, p2, dc, inv2q, two8n, &un);
+            const int sh = max(-1, min(1, bin >> nbits));
+            e[d] = l[d] + sh + 1;
+            r.chi[d] = (bin & bmask) - half;
+            r.pv[d] = p2;
+        }
+        r.ei = e[0] + Bh * (e[1] + Bh * e[2]);
+        return r;
+    }
+
+    __device__ __forceinline__ void put(const PbParticle& q, const float* svn, unsigned pos, unsigned cid,
+                                        unsigned* flags) const {
+        const int H3 = g.Bh * g.Bh * g.Bh;
+        if (pos >= (unsigned)g.Np) {
+            atomicOr(flags, ERR_COUNT);
+            return;
+        }
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            store_code<NX>(sn.chi, d * g.Np + pos, q.chi[d]);
+            const float dd = q.pv[d] - svn[d * H3 + q.ei];
+            store_code<NV>(sn.nu, d * g.Np + pos,
+                           NV == 1 ? nu_from_table(dd, thr, stab, key0, lim)
+                                   : nu_from_thresholds(dd, thr, lim, nu_estimate(dd, e0, e1)));
+        }
+        if (sn.id) sn.id[pos] = cid;
+    }
+};
+
+// brick offsets, v_c of the brick, running starts of the halo cells (this
+// brick's slots of the scanned histograms) and v_c* of the halo region,
+// staged by `nthr` threads from thread `t0`
+__device__ __forceinline__ void passB_stage(const Geo& g, const StoreDev& so, const unsigned* __restrict__ ghost,
+                                            const float* __restrict__ vc_new, int brick, int t0, int nthr,
+                                            unsigned* sm_off, unsigned* run, float* svc, float* svn) {
+    const int nbc = g.B * g.B * g.B, Bh = g.Bh, H3 = Bh * Bh * Bh;
+    const unsigned mBh = div_magic(Bh);
+    const int L0 = brick * nbc;
+    int bx, by, bz;
+    brick_coords(g, brick, &bx, &by, &bz);
+    const int bc[3] = {bx, by, bz};
+    for (int c = t0; c <= nbc; c += nthr) sm_off[c] = so.offsets[L0 + c];
+    for (int t = t0; t < 3 * nbc; t += nthr) svc[t] = so.vc[(int64_t)(t >> (3 * g.lB)) * g.Ncc + L0 + (t & (nbc - 1))];
+    for (int t = t0; t < H3; t += nthr) {
+        int e[3];
+        split3(t, Bh, mBh, e);
+        run[t] = ghost[flat_slot(g, bc, e)];
+        const int L = cell_rank(g, wrap1(bx * g.B - 1 + e[0], g.Nc), wrap1(by * g.B - 1 + e[1], g.Nc),
+                                wrap1(bz * g.B - 1 + e[2], g.Nc));
+#pragma unroll
+        for (int d = 0; d < 3; ++d) svn[d * H3 + t] = vc_new[(int64_t)d * g.Ncc + L];
+    }
+}
 
 template <int NX, int NV>
 __global__ void __launch_bounds__(PB_WARPS * 32, 5) k_passB(Geo g, StoreDev so, StoreDev sn, CodecDev cur, CodecDev next,
                                                         float dc, const unsigned* __restrict__ ghost,
-                                                        const float* __restrict__ vc_new, unsigned* flags) {
+                                                        const float* __restrict__ vc_new, unsigned* flags,
+                                                        const int* __restrict__ big, int nbig_ctas) {
     extern __shared__ unsigned pb_smem[];
-    const int nbc = g.B * g.B * g.B, Bh = g.Bh, H3 = Bh * Bh * Bh;
-    const unsigned mBh = div_magic(Bh);
+    const int nbc = g.B * g.B * g.B, H3 = g.Bh * g.Bh * g.Bh;
     const int lim = g.nulim;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const bool big_cta = (int)blockIdx.x < nbig_ctas;
+    const int nbig = big_cta ? big[0] : 0;
+    if (big_cta && (int)blockIdx.x >= nbig) return;          // no crowded brick left for this CTA
     float* sdec = reinterpret_cast<float*>(pb_smem);                       // NV == 1: [2 lim + 1]
     float* sthr = sdec + (NV == 1 ? 2 * lim + 1 : 0);                       // NV == 1: [lim + 2]
     unsigned char* stab = reinterpret_cast<unsigned char*>(sthr + (NV == 1 ? lim + 2 : 0));   // NV == 1: [VT_N]
     unsigned* wbase = reinterpret_cast<unsigned*>(stab + (NV == 1 ? VT_N : 0));
-    unsigned* sm_off = wbase + warp * (4 * nbc + 1 + 4 * H3);               // [nbc + 1] per warp
-    unsigned* run = sm_off + nbc + 1;                                       // [H3] per warp
-    float* svc = reinterpret_cast<float*>(run + H3);                        // [3][nbc]: v_c of the brick
-    float* svn = svc + 3 * nbc;                                             // [3][H3]: v_c* of the halo region
-    const float* dec = cur.dec;
-    const float* thr = next.thr;
-    int key0 = 0;
+    PassB<NX, NV> pb{g, sn, cur.dec, next.thr, stab, 0, lim, dc, next.est[0], next.est[1]};
     if (NV == 1) {
         for (int t = threadIdx.x; t < 2 * lim + 1; t += blockDim.x) sdec[t] = cur.dec[t];
         for (int t = threadIdx.x; t < lim + 2; t += blockDim.x) sthr[t] = next.thr[t];
         for (int t = threadIdx.x; t < VT_N / 4; t += blockDim.x)
             reinterpret_cast<unsigned*>(stab)[t] = reinterpret_cast<const unsigned*>(next.vtab)[t];
-        dec = sdec;
-        thr = sthr;
-        key0 = __float_as_int(next.est[2]);
+        pb.dec = sdec;
+        pb.thr = sthr;
+        pb.key0 = __float_as_int(next.est[2]);
+    }
+    if (big_cta) {
+        // whole CTA per crowded brick: [nbc + 1] offsets, [H3] running starts,
+        // [3][nbc] v_c, [3][H3] v_c*, [PB_WARPS][H3] per-warp cell counts
+        unsigned* sm_off = wbase;
+        unsigned* run = sm_off + nbc + 1;
+        float* svc = reinterpret_cast<float*>(run + H3);
+        float* svn = svc + 3 * nbc;
+        unsigned* wcnt = reinterpret_cast<unsigned*>(svn + 3 * H3);
+        for (int t = threadIdx.x; t < PB_WARPS * H3; t += blockDim.x) wcnt[t] = 0u;
+        for (int k = blockIdx.x; k < nbig; k += nbig_ctas) {
+            const int brick = big[1 + k];
+            __syncthreads();                 // the previous brick's tables are no longer read
+            passB_stage(g, so, ghost, vc_new, brick, threadIdx.x, blockDim.x, sm_off, run, svc, svn);
+            __syncthreads();
+            const unsigned p1 = min(sm_off[nbc], (unsigned)g.Np), p0 = min(sm_off[0], p1);
+            for (unsigned base = p0; base < p1; base += blockDim.x) {
+                const unsigned i = base + threadIdx.x;
+                const bool act = i < p1;
+                const unsigned am = __ballot_sync(0xffffffffu, act);
+                PbParticle q{};
+                unsigned cid = 0, peers = 0;
+                int leader = 0;
+                if (act) {
+                    int cchi[3], cnu[3];
+#pragma unroll
+                    for (int d = 0; d < 3; ++d) {
+                        cchi[d] = load_code<NX>(so.chi, d * g.Np + i);
+                        cnu[d] = load_nu<NV>(so.nu, d * g.Np + i, lim);
+                    }
+                    if (sn.id) cid = so.id[i];
+                    q = pb.move(sm_off, svc, i, cchi, cnu);
+                    peers = __match_any_sync(am, q.ei);
+                    leader = __ffs(peers) - 1;
+                    if (lane == leader) wcnt[warp * H3 + q.ei] = (unsigned)__popc(peers);
+                }
+                __syncthreads();
+                unsigned start = 0, total = 0;
+                bool last = true;
+                if (act) {
+                    if (lane == leader) {
+                        start = run[q.ei];
+#pragma unroll
+                        for (int v = 0; v < PB_WARPS; ++v) {
+                            const unsigned c = wcnt[v * H3 + q.ei];
+                            if (v < warp) start += c;
+                            if (v > warp && c) last = false;
+                            total += c;
+                        }
+                    }
+                    start = __shfl_sync(peers, start, leader);
+                }
+                __syncthreads();                 // every read of run and wcnt is done
+                if (act) {
+                    if (lane == leader) {
+                        if (last) run[q.ei] += total;
+                        wcnt[warp * H3 + q.ei] = 0u;
+                    }
+                    pb.put(q, svn, start + (unsigned)__popc(peers & ((1u << lane) - 1u)), cid, flags);
+                }
+            }
+        }
+        return;
     }
     __syncthreads();
-    const int brick = blockIdx.x * PB_WARPS + warp;
+    const int brick = ((int)blockIdx.x - nbig_ctas) * PB_WARPS + warp;
     if (brick >= g.nbricks) return;
     const int L0 = brick * nbc;
-    int bx, by, bz;
-    brick_coords(g, brick, &bx, &by, &bz);
-    const int bc[3] = {bx, by, bz};
-    // the brick's particle range and the first round's codes and ids first,
-    // so their latency overlaps the staging below
     const unsigned p1 = min(so.offsets[L0 + nbc], (unsigned)g.Np), p0 = min(so.offsets[L0], p1);
+    if (p1 - p0 > (unsigned)PB_BIG) return;              // a crowded brick: taken by a whole CTA
+    unsigned* sm_off = wbase + warp * (4 * nbc + 1 + 4 * H3);               // [nbc + 1] per warp
+    unsigned* run = sm_off + nbc + 1;                                       // [H3] per warp
+    float* svc = reinterpret_cast<float*>(run + H3);                        // [3][nbc]: v_c of the brick
+    float* svn = svc + 3 * nbc;                                             // [3][H3]: v_c* of the halo region
+    // the first round's codes and ids first, so their latency overlaps the staging
     int nchi[3] = {0, 0, 0}, nnu[3] = {0, 0, 0};
     unsigned nid = 0;
     if (p0 + lane < p1) {
@@ -755,22 +914,8 @@ __global__ void __launch_bounds__(PB_WARPS * 32, 5) k_passB(Geo g, StoreDev so, 
         }
         if (sn.id) nid = so.id[p0 + lane];
     }
-    for (int c = lane; c <= nbc; c += 32) sm_off[c] = so.offsets[L0 + c];
-    for (int t = lane; t < 3 * nbc; t += 32) svc[t] = so.vc[(int64_t)(t >> (3 * g.lB)) * g.Ncc + L0 + (t & (nbc - 1))];
-    for (int t = lane; t < H3; t += 32) {
-        int e[3];
-        split3(t, Bh, mBh, e);
-        run[t] = ghost[flat_slot(g, bc, e)];
-        const int L = cell_rank(g, wrap1(bx * g.B - 1 + e[0], g.Nc), wrap1(by * g.B - 1 + e[1], g.Nc),
-                                wrap1(bz * g.B - 1 + e[2], g.Nc));
-#pragma unroll
-        for (int d = 0; d < 3; ++d) svn[d * H3 + t] = vc_new[(int64_t)d * g.Ncc + L];
-    }
+    passB_stage(g, so, ghost, vc_new, brick, lane, 32, sm_off, run, svc, svn);
     __syncwarp();
-    const int nbits = 8 * NX, half = 1 << (nbits - 1), bmask = (1 << nbits) - 1;
-    const float inv2q = ldexpf(1.0f, -(nbits + 1));
-    const float two8n = ldexpf(1.0f, nbits);
-    const float e0 = next.est[0], e1 = next.est[1];
     for (unsigned base = p0; base < p1; base += 32) {
         const unsigned i = base + lane;
         const bool act = i < p1;
@@ -787,42 +932,14 @@ __global__ void __launch_bounds__(PB_WARPS * 32, 5) k_passB(Geo g, StoreDev so, 
             if (sn.id) nid = so.id[i + 32];
         }
         if (act) {
-            const int lc = upper_cell(sm_off, nbc, i);
-            const int l[3] = {lc & (g.B - 1), (lc >> g.lB) & (g.B - 1), lc >> (2 * g.lB)};
-            int e[3], chi[3];
-            float pv[3];
-#pragma unroll
-            for (int d = 0; d < 3; ++d) {
-                const int Q = 2 * (cchi[d] + half) + 1;
-                const float p2 = svc[(d << (3 * g.lB)) + lc] + dec[cnu[d] + lim];
-                float un;
-                const int bin = drift_bin(Q, p2, dc, inv2q, two8n, &un);
-                const int sh = max(-1, min(1, bin >> nbits));
-                e[d] = l[d] + sh + 1;
-                chi[d] = (bin & bmask) - half;
-                pv[d] = p2;
-            }
-            const int ei = e[0] + Bh * (e[1] + Bh * e[2]);
-            const unsigned peers = __match_any_sync(am, ei);
+            const PbParticle q = pb.move(sm_off, svc, i, cchi, cnu);
+            const unsigned peers = __match_any_sync(am, q.ei);
             const int leader = __ffs(peers) - 1;
             unsigned start = 0;
-            if (lane == leader) start = run[ei];
+            if (lane == leader) start = run[q.ei];
             start = __shfl_sync(peers, start, leader);
-            if (lane == leader) run[ei] = start + (unsigned)__popc(peers);
-            const unsigned pos = start + (unsigned)__popc(peers & ((1u << lane) - 1u));
-            if (pos >= (unsigned)g.Np) {
-                atomicOr(flags, ERR_COUNT);
-            } else {
-#pragma unroll
-                for (int d = 0; d < 3; ++d) {
-                    store_code<NX>(sn.chi, d * g.Np + pos, chi[d]);
-                    const float dd = pv[d] - svn[d * H3 + ei];
-                    store_code<NV>(sn.nu, d * g.Np + pos,
-                                   NV == 1 ? nu_from_table(dd, thr, stab, key0, lim)
-                                           : nu_from_thresholds(dd, thr, lim, nu_estimate(dd, e0, e1)));
-                }
-                if (sn.id) sn.id[pos] = cid;
-            }
+            if (lane == leader) run[q.ei] = start + (unsigned)__popc(peers);
+            pb.put(q, svn, start + (unsigned)__popc(peers & ((1u << lane) - 1u)), cid, flags);
         }
         __syncwarp();
     }
@@ -852,9 +969,11 @@ struct Disp {
     }
     static void passB(const Geo& g, const StoreDev& so, const StoreDev& sn, const CodecDev& cur,
                       const CodecDev& next, float dc, const unsigned* ghost, const float* vcn, unsigned* flags,
-                      size_t sm, cudaStream_t st) {
-        k_passB<NX, NV><<<(g.nbricks + PB_WARPS - 1) / PB_WARPS, PB_WARPS * 32, sm, st>>>(g, so, sn, cur, next, dc,
-                                                                                       ghost, vcn, flags);
+                      const int* big, size_t sm, cudaStream_t st) {
+        // CTAs for crowded bricks first (at most Np / (PB_BIG + 1) of them exist)
+        const int nbig_ctas = (int)std::min<int64_t>(2 * g.nsm, g.Np / (PB_BIG + 1));
+        const int grid = nbig_ctas + (g.nbricks + PB_WARPS - 1) / PB_WARPS;
+        k_passB<NX, NV><<<grid, PB_WARPS * 32, sm, st>>>(g, so, sn, cur, next, dc, ghost, vcn, flags, big, nbig_ctas);
     }
 };
 
@@ -981,10 +1100,10 @@ void launch_passB(const Geo& g, const StoreDev& so, const StoreDev& sn, const Co
                   float dc, const StepScratch& w, cudaStream_t st) {
     size_t sm = passB_smem(g);
     const float* vcn = sn.vc;
-    if (g.nchi == 1 && g.nnu == 1) { set_smem_attrs<1, 1>(); Disp<1, 1>::passB(g, so, sn, cur, next, dc, w.ghost, vcn, w.flags, sm, st); }
-    else if (g.nchi == 1) { set_smem_attrs<1, 2>(); Disp<1, 2>::passB(g, so, sn, cur, next, dc, w.ghost, vcn, w.flags, sm, st); }
-    else if (g.nnu == 1) { set_smem_attrs<2, 1>(); Disp<2, 1>::passB(g, so, sn, cur, next, dc, w.ghost, vcn, w.flags, sm, st); }
-    else { set_smem_attrs<2, 2>(); Disp<2, 2>::passB(g, so, sn, cur, next, dc, w.ghost, vcn, w.flags, sm, st); }
+    if (g.nchi == 1 && g.nnu == 1) { set_smem_attrs<1, 1>(); Disp<1, 1>::passB(g, so, sn, cur, next, dc, w.ghost, vcn, w.flags, w.big, sm, st); }
+    else if (g.nchi == 1) { set_smem_attrs<1, 2>(); Disp<1, 2>::passB(g, so, sn, cur, next, dc, w.ghost, vcn, w.flags, w.big, sm, st); }
+    else if (g.nnu == 1) { set_smem_attrs<2, 1>(); Disp<2, 1>::passB(g, so, sn, cur, next, dc, w.ghost, vcn, w.flags, w.big, sm, st); }
+    else { set_smem_attrs<2, 2>(); Disp<2, 2>::passB(g, so, sn, cur, next, dc, w.ghost, vcn, w.flags, w.big, sm, st); }
 }
 
 void launch_momentum(const Geo& g, const long long* vsum, long long* out3, cudaStream_t st) {

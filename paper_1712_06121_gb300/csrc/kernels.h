@@ -85,6 +85,8 @@ struct StepScratch {
     float* part;            // [max(nbricks, blocks)] partial sums
     unsigned* flags;        // device error flags
     int* maxmig;            // largest |cell shift| of the step
+    int* big;               // [1 + nbricks]: number of bricks with more than PB_BIG
+                            // particles, then their indices (listed by pass A)
 };
 
 void launch_encode_keys(const Geo& g, const float* pos, const float* vel, unsigned* key, unsigned* val,

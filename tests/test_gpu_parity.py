@@ -11,7 +11,7 @@ import numpy as np
 import pytest
 
 import synth
-from oracle import layout, mesh, pm
+from oracle import cosmo, layout, mesh, pm
 
 from gpu_util import assert_store_equal, oracle_params, read_store
 
@@ -222,6 +222,56 @@ def test_step_resort_is_bit_exact(cube, xb, vb, nps, nf, brick):
             assert np.array_equal(np.stack(old.cells()), cell)
             ref = pm.encode_drifted(P, cell, u, p, before["ids"], sig, g["a"], g["a_p"])
             assert_store_equal(g, ref, f"step {i} x{xb}v{vb}")
+    finally:
+        cube.cube_destroy(ctx)
+
+
+def _crowded_ics(nps, nf, w, a0, a1, seed=1712101):
+    """The pm64 generator's particles at a later epoch with two dense blobs:
+    3000 particles (sigma 1.5 fine cells) inside one brick of side 8 or 16
+    fine cells and 2000 (sigma 1.5) on a corner where eight bricks meet,
+    their momenta normal with a drift of half a fine cell per step.  Bricks
+    then hold far more than the mean (clustered late epochs)."""
+    ic = synth.make_ics(w, n_part_side=nps, n_fine=nf)
+    rng = np.random.default_rng(seed)
+    pos = ic.pos.astype(np.float64).copy()
+    vel = ic.vel.astype(np.float64).copy()
+    om, ol, _ = w.omega()
+    sp = 0.5 / cosmo.drift_factor(a0, a1, om, ol)
+    for (lo, hi), c, s in (((0, 3000), (44.2, 43.8, 44.5), 1.5), ((3000, 5000), (31.9, 32.1, 31.95), 1.5)):
+        pos[:, lo:hi] = np.asarray(c)[:, None] + s * rng.standard_normal((3, hi - lo))
+        vel[:, lo:hi] = sp * rng.standard_normal((3, hi - lo))
+    return np.mod(pos, nf).astype(np.float32), vel.astype(np.float32), ic.ids
+
+
+@pytest.mark.parametrize("xb,vb,brick", [(1, 1, 4), (2, 2, 4), (1, 2, 2)])
+def test_crowded_bricks_resort_is_bit_exact(cube, xb, vb, brick):
+    """Bricks with more particles than one warp's share (re-sorted by a whole
+    CTA) give the same store as the oracle's re-encode of the drifted
+    particles: codes, counts, order and v_c, for 3 steps."""
+    w = synth.WORKLOADS["pm64"]
+    nps, nf = 32, 64
+    n = nps ** 3
+    sched = synth.uniform_schedule(0.5, 0.515, 3)
+    pos, vel, ids = _crowded_ics(nps, nf, w, sched[0], sched[1])
+    prm, ctx = _ctx(cube, nf, n, xb, vb, w, brick=brick)
+    try:
+        cube.cube_encode(ctx, pos, vel, ids, sched[0], 0.0)
+        cube.cube_keep_drifted(ctx, True)
+        for i in range(3):
+            before = read_store(cube, ctx)
+            nbc = before["brick"] ** 3
+            assert before["counts"].reshape(-1, nbc).sum(axis=1).max() > 2048
+            cube.cube_pm_step(ctx, sched[i], sched[i + 1])
+            cell, u, p, sig = _drifted(cube, ctx, n)
+            g = read_store(cube, ctx)
+            P = oracle_params(pm, prm, g["brick"])
+            old = pm.Store(P, before["counts"], before["vc"], before["chi"], before["nu"], before["ids"],
+                           before["sigma"], before["a"], before["a_p"])
+            assert np.array_equal(np.stack(old.cells()), cell)
+            ref = pm.encode_drifted(P, cell, u, p, before["ids"], sig, g["a"], g["a_p"])
+            assert_store_equal(g, ref, f"crowded step {i} x{xb}v{vb} brick {brick}")
+        assert cube.cube_stats_get(ctx).max_migration <= 1
     finally:
         cube.cube_destroy(ctx)
 
