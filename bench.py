@@ -17,6 +17,7 @@ N > 1 runs independent replicas (one simulation per GPU, seed + rank); the
 path has no collective.
 """
 import argparse
+import dataclasses
 import json
 import os
 import statistics
@@ -44,7 +45,10 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--ensemble", type=int, default=0,
                     help="run the C4 ensemble of this many uneven realisations (sims/s) instead of pm256")
-    ap.add_argument("--streams", type=int, default=8, help="CUDA streams for --ensemble")
+    ap.add_argument("--streams", type=int, default=8, help="CUDA streams for --ensemble and --serve")
+    ap.add_argument("--serve", type=int, default=0,
+                    help="run the C5 serving stream of this many requests (latency, sims/s) instead of pm256")
+    ap.add_argument("--budget-gb", type=float, default=120.0, help="HBM budget of --serve")
     ap.add_argument("--nps", type=int, default=0,
                     help="particles per side (mesh = 2 x nps) instead of the workload's, for small profiling cases")
     return ap.parse_args()
@@ -351,10 +355,110 @@ def run_ensemble(args):
     }), flush=True)
 
 
+def run_serve(args):
+    """C5: a Poisson stream of simulation requests (sizes 64^3 .. 256^3,
+    10 .. 60 steps, own sigma8) through cube_server under an HBM budget,
+    continuous batching on several streams against the plain method (one
+    request at a time, same arrivals).  Latency = completion - arrival on the
+    server's clock; throughput = requests / (last completion - first arrival)."""
+    import numpy as np
+    import torch
+    import synth
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1712_06121_gb300 as cube
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    reqs = synth.serving_c5(args.serve)
+    # one base realisation per size; each request rescales it to its own sigma8
+    base = {}
+    for r in reqs:
+        w = r.workload
+        if w.n_part_side not in base:
+            bw = dataclasses.replace(w, sigma8=0.8, seed=1712005 + w.n_part_side)
+            base[w.n_part_side] = synth.make_ics(bw)
+    data = []
+    for r in reqs:
+        w = r.workload
+        ic = synth.rescaled_ics(base[w.n_part_side], w.sigma8 / 0.8)
+        om, ol, _ = w.omega()
+        prm = cube.make_params(w.n_fine, w.n_particles, x_bytes=w.x_bytes, v_bytes=w.v_bytes, box=w.box,
+                               omega_m=om, omega_l=ol)
+        host = tuple(torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+                     for a in (ic.pos, ic.vel, ic.ids.view(np.int32)))
+        data.append((prm, host, ic.sigma_1d, synth.uniform_schedule(w.a_init, w.a_final, w.n_steps)))
+    budget = int(args.budget_gb * (1 << 30))
+
+    def serve(n_streams, max_running, at_once=False):
+        srv = cube.cube_server_create(budget, n_streams, max_running)
+        try:
+            seen = set()                                    # warm-up: one short run per size
+            warm = []
+            for r, (prm, host, sig, sch) in zip(reqs, data):
+                if r.workload.n_part_side not in seen:
+                    seen.add(r.workload.n_part_side)
+                    warm.append(cube.cube_server_submit(srv, prm, *host, sig, sch[:3], 8))
+            cube.cube_server_drain(srv)
+            for t in warm:
+                cube.cube_server_release(srv, t)
+            torch.cuda.synchronize()
+            tickets, nxt, peak = [], 0, 0
+            t0 = time.perf_counter()
+            while True:
+                now = time.perf_counter() - t0
+                while nxt < len(reqs) and (at_once or reqs[nxt].arrival <= now):
+                    prm, host, sig, sch = data[nxt]
+                    tickets.append(cube.cube_server_submit(srv, prm, *host, sig, sch, 8))
+                    nxt += 1
+                nr, nq = cube.cube_server_pump(srv)
+                peak = max(peak, cube.cube_server_bytes(srv))
+                if nxt == len(reqs) and nr + nq == 0:
+                    break
+                time.sleep(5e-5)
+            infos = [cube.cube_server_info(srv, t) for t in tickets]
+            for t in tickets:
+                cube.cube_server_release(srv, t)
+        finally:
+            cube.cube_server_destroy(srv)
+        ok = [i for i in infos if i.state == cube.CUBE_REQ_DONE]
+        lat = np.array([i.t_done - i.t_submit for i in ok])
+        span = max(i.t_done for i in ok) - min(i.t_submit for i in infos)
+        steps = sum(i.n_steps for i in ok)
+        parts = sum(reqs[k].workload.n_particles * infos[k].n_steps for k in range(len(infos))
+                    if infos[k].state == cube.CUBE_REQ_DONE)
+        return {"sims_per_s": len(ok) / span, "latency_p50_s": float(np.percentile(lat, 50)),
+                "latency_p99_s": float(np.percentile(lat, 99)), "makespan_s": span, "failed": len(infos) - len(ok),
+                "steps": int(steps), "particle_steps_per_s": parts / span, "peak_device_gb": peak / (1 << 30),
+                "streams": n_streams, "max_running": max_running}
+
+    batched = serve(args.streams, 64)
+    sequential = serve(1, 1)
+    cap_b = serve(args.streams, 64, at_once=True)          # capacity: every request queued at t = 0
+    cap_s = serve(1, 1, at_once=True)
+    sizes = sorted({r.workload.n_part_side for r in reqs})
+    print(json.dumps({
+        "metric": "sims/s (served, all requests queued at once)", "value": cap_b["sims_per_s"], "unit": "sims/s",
+        "n_gpus": 1,
+        "higher_is_better": True, "dtype": "f32", "data": "synthetic (seeded GRF Zel'dovich ICs)",
+        "config": {"workload": f"C5 serving: {len(reqs)} requests, Poisson arrivals at 20/s, "
+                               f"{sizes[0]}^3..{sizes[-1]}^3 particles (mesh 2x, 300 Mpc/h per 256 particles), "
+                               "10-60 steps of Delta a 0.0196 from z=49, sigma8 0.7-0.9, LCDM BBKS, x1v1",
+                   "budget_gb": args.budget_gb,
+                   "ics": "one Zel'dovich realisation per size rescaled to each request's sigma8, pinned host "
+                          "memory, uploaded at admission"},
+        "latency_p50_s": batched["latency_p50_s"], "latency_p99_s": batched["latency_p99_s"],
+        "arrivals": {"rate_per_s": 20.0, "batched": batched, "sequential": sequential},
+        "capacity": {"batched": cap_b, "sequential": cap_s,
+                     "speedup_vs_sequential": cap_b["sims_per_s"] / cap_s["sims_per_s"]},
+    }), flush=True)
+
+
 def main():
     args = parse()
     if args.ensemble:
         run_ensemble(args)
+        return
+    if args.serve:
+        run_serve(args)
         return
     import dataclasses
     import synth

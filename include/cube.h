@@ -295,6 +295,97 @@ const char* cube_phase_name(int32_t phase);
 cube_status cube_counts_to_offsets_noalloc(const uint32_t* counts, int64_t n_cells, uint32_t* offsets,
                                            void* cuda_stream);
 
+/* ---------------------------------------------------------------- serving: many simulations on one GPU */
+
+/* A server runs many independent simulations ("requests") at once on one GPU
+   with continuous batching: requests arrive at any time, are admitted in
+   arrival order while an HBM budget allows, step concurrently on a few CUDA
+   streams (one step of each running request after another, at most two steps
+   of a request in flight), and finish with the power spectrum of their final
+   store.
+   Memory.  Between steps a simulation needs only its compressed store
+   (Section 2.3's point: a few bytes per particle) plus codec tables; the
+   mesh, the ghosted potential, the step histograms and the encode scratch
+   are needed only while one of its calls runs.  A request therefore holds
+   its state bytes from admission until cube_server_release, and each stream
+   holds one work area, sized for the largest request it has run and shared
+   by all requests on that stream.  cube_server_sizes gives both figures.
+   The budget bounds the sum of the resident states and the work areas.
+   Results.  Every kernel of the step is deterministic, so a request's store
+   and P(k) do not depend on what else runs beside it.
+   Threading.  A server must not be used by two threads at once.  Calls are
+   non-blocking except where noted; the server's clock is seconds since
+   cube_server_create (steady clock). */
+typedef struct cube_server cube_server;
+
+typedef enum {
+    CUBE_REQ_QUEUED = 0,     /* submitted, waiting for memory or a slot           */
+    CUBE_REQ_RUNNING = 1,    /* encoded and stepping                              */
+    CUBE_REQ_DONE = 2,       /* all steps and the final P(k) completed            */
+    CUBE_REQ_FAILED = 3      /* a device error was latched (see error)            */
+} cube_req_state;
+
+typedef struct {
+    int32_t state;            /* cube_req_state                                    */
+    int32_t steps_enqueued;   /* steps handed to the GPU so far                    */
+    int32_t n_steps;
+    int32_t max_migration;    /* after completion: largest |cell shift| of a step  */
+    double t_submit, t_admit, t_done;   /* server clock; -1 before the event       */
+    int64_t state_bytes;      /* device bytes held from admission to release       */
+    int32_t error;            /* cube_status of a failed request, else CUBE_OK      */
+} cube_request_info;
+
+/* Device bytes of one request with these parameters: its resident state and
+   the work area it needs on its stream.  Errors: CUBE_E_ARG as cube_create. */
+cube_status cube_server_sizes(const cube_params* params, int64_t* state_bytes, int64_t* work_bytes);
+
+/* budget_bytes: bound on resident states + work areas (device bytes);
+   n_streams in [1, 64]: CUDA streams (non-blocking, created by the server);
+   max_running >= 1: requests stepping at once (1 = one after another, the
+   plain sequential method; admission then waits for the running one). */
+cube_status cube_server_create(int64_t budget_bytes, int32_t n_streams, int32_t max_running, cube_server** out);
+
+/* Waits for the server's streams, then frees everything it holds. */
+cube_status cube_server_destroy(cube_server* srv);
+
+/* Queues a simulation: initial particles pos[3][N], vel[3][N] (host --
+   pinned for an asynchronous upload -- or device arrays) and id[N]
+   (nullable) at scale factor epochs[0], codec scale sigma as cube_encode,
+   then the n_steps steps epochs[i] -> epochs[i + 1] (epochs[n_steps + 1]
+   values, increasing, copied), then P(k) in n_bins bins as
+   cube_power_spectrum.  The caller keeps pos, vel and id valid until the
+   request is DONE or FAILED.  Returns a ticket (> 0).
+   Errors: CUBE_E_ARG (parameters, n_steps < 1, n_bins outside [1, 2048],
+   epochs not increasing), CUBE_E_NOMEM (the request alone exceeds the
+   budget, or pinned result memory). */
+cube_status cube_server_submit(cube_server* srv, const cube_params* params, const float* pos, const float* vel,
+                               const uint32_t* id, double sigma, const double* epochs, int32_t n_steps,
+                               int32_t n_bins, int64_t* ticket);
+
+/* Makes progress without blocking: retires finished requests, hands the next
+   steps of running requests to the GPU, admits queued requests that fit.
+   n_running, n_queued (nullable): requests in those states afterwards. */
+cube_status cube_server_pump(cube_server* srv, int32_t* n_running, int32_t* n_queued);
+
+/* Pumps until every submitted request is DONE or FAILED (blocking). */
+cube_status cube_server_drain(cube_server* srv);
+
+cube_status cube_server_info(cube_server* srv, int64_t ticket, cube_request_info* out);
+
+/* P(k) of a DONE request into caller arrays of n_bins doubles (host or device).
+   Errors: CUBE_E_STATE before DONE; CUBE_E_ARG for an unknown ticket. */
+cube_status cube_server_result(cube_server* srv, int64_t ticket, double* k, double* pk, double* nmodes);
+
+/* Decodes a DONE request's resident store as cube_decode (synchronises with
+   the request's stream). */
+cube_status cube_server_decode(cube_server* srv, int64_t ticket, float* pos, float* vel, uint32_t* id);
+
+/* Frees a DONE or FAILED request's state and returns its bytes to the budget. */
+cube_status cube_server_release(cube_server* srv, int64_t ticket);
+
+/* Device bytes held now: resident states plus work areas. */
+cube_status cube_server_bytes(cube_server* srv, int64_t* bytes_in_use);
+
 #ifdef __cplusplus
 }
 #endif

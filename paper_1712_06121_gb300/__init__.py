@@ -56,6 +56,14 @@ class cube_stats(ctypes.Structure):
 
 CUBE_PHASES = 12
 
+CUBE_REQ_QUEUED, CUBE_REQ_RUNNING, CUBE_REQ_DONE, CUBE_REQ_FAILED = range(4)
+
+
+class cube_request_info(ctypes.Structure):
+    _fields_ = [("state", ctypes.c_int32), ("steps_enqueued", ctypes.c_int32), ("n_steps", ctypes.c_int32),
+                ("max_migration", ctypes.c_int32), ("t_submit", ctypes.c_double), ("t_admit", ctypes.c_double),
+                ("t_done", ctypes.c_double), ("state_bytes", ctypes.c_int64), ("error", ctypes.c_int32)]
+
 
 _P = ctypes.c_void_p
 _sigs = {
@@ -79,6 +87,19 @@ _sigs = {
     "cube_counts_to_offsets_noalloc": ([_P, ctypes.c_int64, _P, _P], ctypes.c_int),
     "cube_max_speed": ([_P, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
     "cube_next_epoch": ([_P, ctypes.c_double, ctypes.c_double, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
+    "cube_server_sizes": ([ctypes.POINTER(cube_params), ctypes.POINTER(ctypes.c_int64),
+                           ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
+    "cube_server_create": ([ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(_P)], ctypes.c_int),
+    "cube_server_destroy": ([_P], ctypes.c_int),
+    "cube_server_submit": ([_P, ctypes.POINTER(cube_params), _P, _P, _P, ctypes.c_double, _P, ctypes.c_int32,
+                            ctypes.c_int32, ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
+    "cube_server_pump": ([_P, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)], ctypes.c_int),
+    "cube_server_drain": ([_P], ctypes.c_int),
+    "cube_server_info": ([_P, ctypes.c_int64, ctypes.POINTER(cube_request_info)], ctypes.c_int),
+    "cube_server_result": ([_P, ctypes.c_int64, _P, _P, _P], ctypes.c_int),
+    "cube_server_decode": ([_P, ctypes.c_int64, _P, _P, _P], ctypes.c_int),
+    "cube_server_release": ([_P, ctypes.c_int64], ctypes.c_int),
+    "cube_server_bytes": ([_P, ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
 }
 for _name, (_args, _res) in _sigs.items():
     _f = getattr(_lib, _name)
@@ -216,3 +237,69 @@ def cube_phase_name(phase):
 
 __all__ = [n for n in _sigs] + ["make_params", "cube_params", "cube_state", "cube_stats", "CubeError",
                                 "LIB_PATH", "CUBE_GRAD_FD4", "CUBE_PHASES"]
+
+
+# ---------------------------------------------------------------- serving
+def cube_server_sizes(params):
+    """(state bytes, work bytes) of one request with these parameters."""
+    a, b = ctypes.c_int64(), ctypes.c_int64()
+    _check(_lib.cube_server_sizes(ctypes.byref(params), ctypes.byref(a), ctypes.byref(b)))
+    return a.value, b.value
+
+
+def cube_server_create(budget_bytes, n_streams=4, max_running=64):
+    out = _P()
+    _check(_lib.cube_server_create(int(budget_bytes), int(n_streams), int(max_running), ctypes.byref(out)))
+    return out.value
+
+
+def cube_server_destroy(srv):
+    _check(_lib.cube_server_destroy(srv))
+
+
+def cube_server_submit(srv, params, pos, vel, ids, sigma, epochs, n_bins):
+    """Queues one simulation; epochs: n_steps + 1 increasing scale factors
+    (a float64 array kept alive by the caller only for this call).  pos, vel
+    and ids must stay alive until the request is done.  Returns the ticket."""
+    import numpy as np
+    ep = np.ascontiguousarray(epochs, dtype=np.float64)
+    t = ctypes.c_int64()
+    _check(_lib.cube_server_submit(srv, ctypes.byref(params), _ptr(pos), _ptr(vel), _ptr(ids), float(sigma),
+                                   ep.ctypes.data, len(ep) - 1, int(n_bins), ctypes.byref(t)))
+    return t.value
+
+
+def cube_server_pump(srv):
+    """Non-blocking progress; returns (running, queued)."""
+    nr, nq = ctypes.c_int32(), ctypes.c_int32()
+    _check(_lib.cube_server_pump(srv, ctypes.byref(nr), ctypes.byref(nq)))
+    return nr.value, nq.value
+
+
+def cube_server_drain(srv):
+    _check(_lib.cube_server_drain(srv))
+
+
+def cube_server_info(srv, ticket):
+    info = cube_request_info()
+    _check(_lib.cube_server_info(srv, int(ticket), ctypes.byref(info)))
+    return info
+
+
+def cube_server_result(srv, ticket, k, pk, nmodes):
+    _check(_lib.cube_server_result(srv, int(ticket), _ptr(k), _ptr(pk), _ptr(nmodes)))
+
+
+def cube_server_decode(srv, ticket, pos, vel, ids):
+    _check(_lib.cube_server_decode(srv, int(ticket), _ptr(pos), _ptr(vel), _ptr(ids)))
+
+
+def cube_server_release(srv, ticket):
+    _check(_lib.cube_server_release(srv, int(ticket)))
+
+
+def cube_server_bytes(srv):
+    v = ctypes.c_int64()
+    _check(_lib.cube_server_bytes(srv, ctypes.byref(v)))
+    return v.value
+

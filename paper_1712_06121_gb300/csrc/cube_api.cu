@@ -166,9 +166,22 @@ struct cube_ctx {
     CUtensorMap phig_map{};         // TMA map of phig with pass A's tile as the box
     bool tma = false;               // phig_map encoded (else pass A loads with cp.async)
     FftPlan fft{};
-    // host-pointer staging (lazily allocated)
+    // host-pointer staging (lazily allocated when the work slab's region is too small)
     void* stage = nullptr;
     size_t stage_bytes = 0;
+    // device memory in two slabs: the state kept between calls (store, codec
+    // tables, small results) and the work buffers of one call (mesh, ghosted
+    // Phi, histograms, scan scratch, host staging).  A standalone context owns
+    // both; a server's context owns its state slab (stream-ordered) and is
+    // bound to its stream's shared work slab before each use.
+    char* state_slab = nullptr;
+    size_t state_size = 0;
+    char* work_slab = nullptr;          // owned work slab (standalone contexts)
+    size_t work_size = 0;
+    char* work_base = nullptr;          // the work slab in use
+    void* stage_ws = nullptr;           // host-staging region of the work slab
+    size_t stage_ws_bytes = 0;
+    bool served = false;
     // drifted-state export
     bool keep = false;
     int* dbg_cell = nullptr;
@@ -185,21 +198,86 @@ struct cube_ctx {
     // per-kernel tracing: CUBE_PHASES + 1 boundary events per traced step
     int prof_max = 0, prof_steps = 0;
     std::vector<cudaEvent_t> prof_ev;
-    std::vector<void*> allocs;
 
     StoreDev store(int k) const { return StoreDev{counts[k], offsets[k], vc[k], chi[k], nu[k], id[k]}; }
 };
 
 namespace {
 
+// next 256-byte aligned piece of a slab (base == nullptr: sizing pass)
 template <class T>
-cudaError_t dalloc(cube_ctx* c, T** p, size_t bytes) {
-    cudaError_t e = cudaMalloc((void**)p, bytes ? bytes : 16);
-    if (e == cudaSuccess) c->allocs.push_back((void*)*p);
-    return e;
+void carve(char* base, size_t& off, T*& p, size_t bytes) {
+    off = (off + 255) & ~(size_t)255;
+    p = base ? reinterpret_cast<T*>(base + off) : nullptr;
+    off += bytes ? bytes : 16;
+}
+
+// device state of a context: both stores, codec tables and small results
+size_t state_layout(cube_ctx* c, char* base) {
+    const Geo& g = c->g;
+    const size_t Np = (size_t)g.Np, Ncc = (size_t)g.Ncc;
+    size_t off = 0;
+    for (int k = 0; k < 2; ++k) {
+        carve(base, off, c->counts[k], Ncc * 4);
+        carve(base, off, c->offsets[k], (Ncc + 1) * 4);
+        carve(base, off, c->vc[k], 3 * Ncc * 4);
+        if (k == 0 || !c->raw) {         // the uncompressed store is updated in place
+            carve(base, off, c->chi[k], 3 * Np * g.nchi);
+            carve(base, off, c->nu[k], 3 * Np * g.nnu);
+            if (c->P.id_bytes) carve(base, off, c->id[k], Np * 4);
+        }
+        carve(base, off, c->codec[k].dec, (size_t)(2 * g.nulim + 1) * 4);
+        carve(base, off, c->codec[k].thr, (size_t)(g.nulim + 2) * 4);
+        carve(base, off, c->codec[k].est, 3 * 4);
+        carve(base, off, c->codec[k].vtab, VT_N);
+        carve(base, off, c->codec[k].sigma, 8);
+    }
+    carve(base, off, c->tanv, (size_t)(g.nulim + 1) * 8);
+    carve(base, off, c->tanh_, (size_t)(g.nulim + 2) * 8);
+    carve(base, off, c->flags, 4);
+    carve(base, off, c->maxmig, ((size_t)g.nbricks + 2) * 4);    // [0] max migration, [1 ..] crowded-brick list
+    carve(base, off, c->mom, 3 * 8);
+    carve(base, off, c->vmax, 4);
+    FftPlan& f = c->fft;
+    carve(base, off, f.tw, (size_t)g.N * 8);
+    carve(base, off, f.k2, (size_t)g.N * 4);
+    carve(base, off, f.wdec, (size_t)g.N * 4);
+    carve(base, off, f.wpk, (size_t)g.N * 8);
+    return off;
+}
+
+// bytes of host staging and encode scratch: keys, permutation and radix
+// workspace, then the particles when they come from host memory
+size_t encode_scratch_bytes(const Geo& g, bool host) {
+    const size_t Np = (size_t)g.Np;
+    return (size_t)(2 * Np + radix_tmp_words(g.Np)) * 4 + (host ? 28 * Np : 0);
+}
+
+// work buffers of one call: mesh, ghosted Phi, step histograms and partial
+// sums, scan scratch, and a staging region for host-array encode and decode
+size_t work_layout(cube_ctx* c, char* base) {
+    const Geo& g = c->g;
+    const size_t Ncc = (size_t)g.Ncc;
+    const int H3 = g.Bh * g.Bh * g.Bh;
+    size_t off = 0;
+    carve(base, off, c->mesh, (size_t)g.N * g.N * g.S * 4);
+    carve(base, off, c->phig, (size_t)phig_nx(g.N) * phig_ny(g.N) * phig_ny(g.N) * 4);
+    carve(base, off, c->vsum, 3 * Ncc * 8);
+    carve(base, off, c->ghost, ((size_t)g.nbricks * H3 + 1) * 4);
+    c->npart = std::max(g.nbricks, 1024);
+    carve(base, off, c->part, (size_t)c->npart * 4);
+    carve(base, off, c->scan_tmp,
+          (size_t)scan_tmp_words(std::max<int64_t>(g.Ncc + 1, (int64_t)g.nbricks * H3 + 1)) * 4 + 64);
+    c->stage_ws_bytes = c->raw ? 28 * (size_t)g.Np : encode_scratch_bytes(g, true);
+    carve(base, off, c->stage_ws, c->stage_ws_bytes);
+    return off;
 }
 
 cube_status stage_bytes(cube_ctx* c, size_t bytes, void** out) {
+    if (c->stage_ws && bytes <= c->stage_ws_bytes) {   // the work slab's staging region
+        *out = c->stage_ws;
+        return CUBE_OK;
+    }
     if (c->stage_bytes < bytes) {
         if (c->stage) cudaFree(c->stage);
         c->stage = nullptr;
@@ -211,15 +289,19 @@ cube_status stage_bytes(cube_ctx* c, size_t bytes, void** out) {
     return CUBE_OK;
 }
 
-cube_status latched(cube_ctx* c) {
-    unsigned f = 0;
-    CK(cudaMemcpyAsync(&f, c->flags, sizeof(unsigned), cudaMemcpyDeviceToHost, c->st));
-    CK(cudaStreamSynchronize(c->st));
+cube_status flags_status(unsigned f) {
     if (f & ERR_MIGRATION) return fail(CUBE_E_MIGRATION, "a particle moved more than one coarse cell in a step");
     if (f & ERR_NONFINITE) return fail(CUBE_E_OVERFLOW, "non-finite particle position or velocity");
     if (f & ERR_COUNT) return fail(CUBE_E_OVERFLOW, "cell counts inconsistent with the particle total");
     if (f & ERR_TIMEOUT) return fail(CUBE_E_TIMEOUT, "a bounded wait for an asynchronous tile copy gave up");
     return CUBE_OK;
+}
+
+cube_status latched(cube_ctx* c) {
+    unsigned f = 0;
+    CK(cudaMemcpyAsync(&f, c->flags, sizeof(unsigned), cudaMemcpyDeviceToHost, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    return flags_status(f);
 }
 
 // TMA descriptor of the ghosted Phi: a 3-D float tensor (x, y, z extents
@@ -244,6 +326,36 @@ bool encode_phig_map(cube_ctx* c) {
                            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS;
+}
+
+// geometry and flags of a context from validated parameters (brick side B)
+void init_geo(cube_ctx* c, const cube_params* params, int B) {
+    c->P = *params;
+    c->cosmo = Cosmo{params->omega_m, params->omega_l};
+    Geo& g = c->g;
+    g.N = params->n_fine;
+    g.R = params->ratio;
+    g.r = g.R == 1 ? 0 : g.R == 2 ? 1 : g.R == 4 ? 2 : 3;
+    g.Nc = g.N / g.R;
+    g.B = B;
+    g.nb = g.Nc / B;
+    g.Bh = B + 2;
+    c->raw = params->x_bytes == 4;
+    g.nchi = c->raw ? 4 : params->x_bytes;
+    g.nnu = c->raw ? 4 : params->v_bytes;
+    g.sbits = 8 * g.nchi + 1 - g.r;
+    g.F = B * g.R;
+    g.S = g.N + 4;
+    g.Ncc = g.Nc * g.Nc * g.Nc;
+    g.nbricks = g.nb * g.nb * g.nb;
+    g.Np = params->n_particles;
+    g.nulim = c->raw ? 127 : (1 << (8 * g.nnu - 1)) - 1;   // (no codec tables are used uncompressed)
+    g.lB = 0;
+    while ((1 << g.lB) < g.B) ++g.lB;
+    g.lF = 0;
+    while ((1 << g.lF) < g.F) ++g.lF;
+    g.nsm = 1;
+    c->fft.N = g.N;
 }
 
 cube_status check_params(const cube_params* p, int* brick) {
@@ -285,8 +397,13 @@ const char* cube_last_error(void) { return g_err.c_str(); }
 
 cube_status cube_destroy(cube_ctx* c) {
     if (!c) return CUBE_OK;
-    cudaStreamSynchronize(c->st);
-    for (void* p : c->allocs) cudaFree(p);
+    if (c->served) {                     // stream-ordered: no device-wide synchronisation
+        if (c->state_slab) cudaFreeAsync(c->state_slab, c->st);
+    } else {
+        cudaStreamSynchronize(c->st);
+        if (c->state_slab) cudaFree(c->state_slab);
+        if (c->work_slab) cudaFree(c->work_slab);
+    }
     if (c->stage) cudaFree(c->stage);
     if (c->dbg_cell) cudaFree(c->dbg_cell);
     if (c->dbg_u) cudaFree(c->dbg_u);
@@ -298,7 +415,7 @@ cube_status cube_destroy(cube_ctx* c) {
     return CUBE_OK;
 }
 
-cube_status cube_create(const cube_params* params, void* cuda_stream, cube_ctx** out) {
+static cube_status create_ctx(const cube_params* params, void* cuda_stream, bool served, cube_ctx** out) {
     if (!out) return fail(CUBE_E_ARG, "out is NULL");
     *out = nullptr;
     int B = 0;
@@ -307,79 +424,34 @@ cube_status cube_create(const cube_params* params, void* cuda_stream, cube_ctx**
     int ndev = 0;
     CK(cudaGetDeviceCount(&ndev));
     cube_ctx* c = new cube_ctx();
-    c->P = *params;
     c->st = (cudaStream_t)cuda_stream;
-    c->cosmo = Cosmo{params->omega_m, params->omega_l};
+    c->served = served;
     cudaGetDevice(&c->device);
-    Geo& g = c->g;
-    g.N = params->n_fine;
-    g.R = params->ratio;
-    g.r = g.R == 1 ? 0 : g.R == 2 ? 1 : g.R == 4 ? 2 : 3;
-    g.Nc = g.N / g.R;
-    g.B = B;
-    g.nb = g.Nc / B;
-    g.Bh = B + 2;
-    c->raw = params->x_bytes == 4;
-    g.nchi = c->raw ? 4 : params->x_bytes;
-    g.nnu = c->raw ? 4 : params->v_bytes;
-    g.sbits = 8 * g.nchi + 1 - g.r;
-    g.F = B * g.R;
-    g.S = g.N + 4;
-    g.Ncc = g.Nc * g.Nc * g.Nc;
-    g.nbricks = g.nb * g.nb * g.nb;
-    g.Np = params->n_particles;
-    g.nulim = c->raw ? 127 : (1 << (8 * g.nnu - 1)) - 1;   // (no codec tables are used uncompressed)
-    g.lB = 0;
-    while ((1 << g.lB) < g.B) ++g.lB;
-    g.lF = 0;
-    while ((1 << g.lF) < g.F) ++g.lF;
-    g.nsm = 1;
-    cudaDeviceGetAttribute(&g.nsm, cudaDevAttrMultiProcessorCount, c->device);
+    init_geo(c, params, B);
+    const Geo& g = c->g;
+    cudaDeviceGetAttribute(&c->g.nsm, cudaDevAttrMultiProcessorCount, c->device);
 
     auto bad = [&](cudaError_t e, const char* what) -> cube_status {
         cube_destroy(c);
         return fail(e == cudaErrorMemoryAllocation ? CUBE_E_NOMEM : CUBE_E_CUDA,
                     std::string(what) + ": " + cudaGetErrorString(e));
     };
-#define AL(ptr, bytes) do { cudaError_t e_ = dalloc(c, &(ptr), (bytes)); if (e_ != cudaSuccess) return bad(e_, #ptr); } while (0)
-    const size_t Np = (size_t)g.Np, Ncc = (size_t)g.Ncc;
-    const int H3 = g.Bh * g.Bh * g.Bh;
-    for (int k = 0; k < 2; ++k) {
-        AL(c->counts[k], Ncc * 4);
-        AL(c->offsets[k], (Ncc + 1) * 4);
-        AL(c->vc[k], 3 * Ncc * 4);
-        if (k == 0 || !c->raw) {         // the uncompressed store is updated in place
-            AL(c->chi[k], 3 * Np * g.nchi);
-            AL(c->nu[k], 3 * Np * g.nnu);
-            if (params->id_bytes) AL(c->id[k], Np * 4);
-        }
-        AL(c->codec[k].dec, (size_t)(2 * g.nulim + 1) * 4);
-        AL(c->codec[k].thr, (size_t)(g.nulim + 2) * 4);
-        AL(c->codec[k].est, 3 * 4);
-        AL(c->codec[k].vtab, VT_N);
-        AL(c->codec[k].sigma, 8);
+    c->state_size = state_layout(c, nullptr);
+    c->work_size = work_layout(c, nullptr);
+    {
+        cudaError_t e = c->served ? cudaMallocAsync((void**)&c->state_slab, c->state_size, c->st)
+                                  : cudaMalloc((void**)&c->state_slab, c->state_size);
+        if (e == cudaSuccess && !c->served) e = cudaMalloc((void**)&c->work_slab, c->work_size);
+        if (e != cudaSuccess) return bad(e, "device memory");
     }
-    AL(c->tanv, (size_t)(g.nulim + 1) * 8);
-    AL(c->tanh_, (size_t)(g.nulim + 2) * 8);
-    AL(c->vsum, 3 * Ncc * 8);
-    AL(c->ghost, ((size_t)g.nbricks * H3 + 1) * 4);
-    c->npart = std::max(g.nbricks, 1024);
-    AL(c->part, (size_t)c->npart * 4);
-    AL(c->flags, 4);
-    AL(c->maxmig, ((size_t)g.nbricks + 2) * 4);    // [0] max migration, [1 ..] crowded-brick list
-    AL(c->scan_tmp, (size_t)scan_tmp_words(std::max<int64_t>(g.Ncc + 1, (int64_t)g.nbricks * H3 + 1)) * 4 + 64);
-    AL(c->mom, 3 * 8);
-    AL(c->vmax, 4);
-    AL(c->mesh, (size_t)g.N * g.N * g.S * 4);
-    AL(c->phig, (size_t)phig_nx(g.N) * phig_ny(g.N) * phig_ny(g.N) * 4);
+    state_layout(c, c->state_slab);
+    if (!c->served) {
+        c->work_base = c->work_slab;
+        work_layout(c, c->work_base);
+    }
     FftPlan& f = c->fft;
-    f.N = g.N;
-    AL(f.tw, (size_t)g.N * 8);
-    AL(f.k2, (size_t)g.N * 4);
-    AL(f.wdec, (size_t)g.N * 4);
-    AL(f.wpk, (size_t)g.N * 8);
-#undef AL
-    // host tables (FP64 libm), uploaded once
+    // host tables (FP64 libm), uploaded once (stream-ordered: pageable sources are
+    // staged before each call returns)
     {
         std::vector<float2> tw(g.N);
         std::vector<float> k2(g.N), wd(g.N);
@@ -399,25 +471,29 @@ cube_status cube_create(const cube_params* params, void* cuda_stream, cube_ctx**
         for (int k = 0; k <= g.nulim; ++k) tv[k] = std::tan(PI * k / M);
         for (int k = 0; k <= g.nulim + 1; ++k) th[k] = std::tan(PI * (k - 0.5) / M);
         cudaError_t e = cudaSuccess;
-        if (e == cudaSuccess) e = cudaMemcpy(f.tw, tw.data(), g.N * 8, cudaMemcpyHostToDevice);
-        if (e == cudaSuccess) e = cudaMemcpy(f.k2, k2.data(), g.N * 4, cudaMemcpyHostToDevice);
-        if (e == cudaSuccess) e = cudaMemcpy(f.wdec, wd.data(), g.N * 4, cudaMemcpyHostToDevice);
-        if (e == cudaSuccess) e = cudaMemcpy(f.wpk, wpk.data(), g.N * 8, cudaMemcpyHostToDevice);
-        if (e == cudaSuccess) e = cudaMemcpy(c->tanv, tv.data(), tv.size() * 8, cudaMemcpyHostToDevice);
-        if (e == cudaSuccess) e = cudaMemcpy(c->tanh_, th.data(), th.size() * 8, cudaMemcpyHostToDevice);
-        if (e == cudaSuccess) e = cudaMemset(c->flags, 0, 4);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(f.tw, tw.data(), g.N * 8, cudaMemcpyHostToDevice, c->st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(f.k2, k2.data(), g.N * 4, cudaMemcpyHostToDevice, c->st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(f.wdec, wd.data(), g.N * 4, cudaMemcpyHostToDevice, c->st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(f.wpk, wpk.data(), g.N * 8, cudaMemcpyHostToDevice, c->st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(c->tanv, tv.data(), tv.size() * 8, cudaMemcpyHostToDevice, c->st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(c->tanh_, th.data(), th.size() * 8, cudaMemcpyHostToDevice, c->st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(c->flags, 0, 4, c->st);
         if (e == cudaSuccess) e = cudaEventCreate(&c->ev0);
         if (e == cudaSuccess) e = cudaEventCreate(&c->ev1);
         if (e != cudaSuccess) return bad(e, "table upload");
     }
-    c->tma = encode_phig_map(c);
+    c->tma = c->phig ? encode_phig_map(c) : false;     // a server's context: at its first binding
     *out = c;
     return CUBE_OK;
 }
 
+cube_status cube_create(const cube_params* params, void* cuda_stream, cube_ctx** out) {
+    return create_ctx(params, cuda_stream, false, out);
+}
+
 // Uncompressed store: copy (and wrap) the particles; momenta and positions share the epoch a.
 static cube_status raw_encode(cube_ctx* c, const float* pos, const float* vel, const uint32_t* id, double a,
-                              bool hpos, bool hvel, bool hid) {
+                              bool hpos, bool hvel, bool hid, bool sync) {
     const Geo& g = c->g;
     const size_t Np = (size_t)g.Np;
     const size_t need = (hpos ? 12 * Np : 0) + (hvel ? 12 * Np : 0) + (hid ? 4 * Np : 0);
@@ -439,7 +515,7 @@ static cube_status raw_encode(cube_ctx* c, const float* pos, const float* vel, c
     launch_raw_encode(g, dpos, dvel, did, (float*)c->chi[0], (float*)c->nu[0], c->id[0], c->flags, c->st);
     c->launches += 1;
     CK(cudaGetLastError());
-    CK(cudaStreamSynchronize(c->st));
+    if (sync) CK(cudaStreamSynchronize(c->st));
     c->cur = 0;
     c->encoded = true;
     c->a = a;
@@ -450,14 +526,17 @@ static cube_status raw_encode(cube_ctx* c, const float* pos, const float* vel, c
     return CUBE_OK;
 }
 
-cube_status cube_encode(cube_ctx* c, const float* pos, const float* vel, const uint32_t* id, double a, double sigma) {
+// encode, enqueued on the context's stream; sync: wait for it (host arrays
+// may then be released and the staging reused at once)
+static cube_status encode_impl(cube_ctx* c, const float* pos, const float* vel, const uint32_t* id, double a,
+                               double sigma, bool sync) {
     if (!c) return fail(CUBE_E_ARG, "ctx is NULL");
     if (!pos || !vel) return fail(CUBE_E_ARG, "pos and vel are required");
     if (!(a > 0.0)) return fail(CUBE_E_ARG, "a must be > 0");
     const Geo& g = c->g;
     const size_t Np = (size_t)g.Np;
     const bool hpos = !is_device_ptr(pos), hvel = !is_device_ptr(vel), hid = id && !is_device_ptr(id);
-    if (c->raw) return raw_encode(c, pos, vel, id, a, hpos, hvel, hid);
+    if (c->raw) return raw_encode(c, pos, vel, id, a, hpos, hvel, hid, sync);
     // scratch: keys, perm, radix workspace, host staging
     const int key_bits = std::max(1, (int)std::ceil(std::log2((double)g.Ncc)));
     size_t words = (size_t)(2 * Np) + (size_t)radix_tmp_words(g.Np);
@@ -494,7 +573,7 @@ cube_status cube_encode(cube_ctx* c, const float* pos, const float* vel, const u
     launch_encode_scatter(g, dpos, dvel, did, keys, perm, c->vc[k], c->codec[k], c->store(k), c->st);
     c->launches += 1 + 4 + 1 + (sigma > 0.0 ? 1 : 2) + 1 + (int64_t)((key_bits + 7) / 8) * 6 + 1;
     CK(cudaGetLastError());
-    CK(cudaStreamSynchronize(c->st));
+    if (sync) CK(cudaStreamSynchronize(c->st));
     c->encoded = true;
     c->a = a;
     c->a_p = a;
@@ -502,6 +581,10 @@ cube_status cube_encode(cube_ctx* c, const float* pos, const float* vel, const u
     c->dbg_valid = false;
     c->timed = false;
     return CUBE_OK;
+}
+
+cube_status cube_encode(cube_ctx* c, const float* pos, const float* vel, const uint32_t* id, double a, double sigma) {
+    return encode_impl(c, pos, vel, id, a, sigma, true);
 }
 
 // kernels launched per phase of a step (see cube_phase_name)
@@ -660,7 +743,9 @@ cube_status cube_decode(cube_ctx* c, float* pos, float* vel, uint32_t* id) {
     return latched(c);
 }
 
-cube_status cube_power_spectrum(cube_ctx* c, int32_t n_bins, double* k, double* pk, double* nmodes) {
+// P(k) of the current store, enqueued; k, pk, nmodes copied out (host copies
+// are asynchronous only into pinned memory)
+static cube_status pk_enqueue(cube_ctx* c, int32_t n_bins, double* k, double* pk, double* nmodes) {
     if (!c) return fail(CUBE_E_ARG, "ctx is NULL");
     if (!c->encoded) return fail(CUBE_E_STATE, "no store: call cube_encode first");
     if (n_bins < 1 || n_bins > 2048 || !k || !pk || !nmodes) return fail(CUBE_E_ARG, "n_bins in [1, 2048] and outputs required");
@@ -687,6 +772,11 @@ cube_status cube_power_spectrum(cube_ctx* c, int32_t n_bins, double* k, double* 
         s = to_user(c, nmodes, outk + 2 * n_bins, n_bins * 8, hn);
     cudaFreeAsync(part, c->st);
     CK(cudaGetLastError());
+    return s;
+}
+
+cube_status cube_power_spectrum(cube_ctx* c, int32_t n_bins, double* k, double* pk, double* nmodes) {
+    cube_status s = pk_enqueue(c, n_bins, k, pk, nmodes);
     if (s != CUBE_OK) return s;
     return latched(c);
 }
@@ -890,3 +980,47 @@ const char* cube_phase_name(int32_t phase) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------- hooks for the server (serve.cu)
+namespace cube {
+
+cube_status served_sizes(const cube_params* p, size_t* state, size_t* work) {
+    int B = 0;
+    cube_status s = check_params(p, &B);
+    if (s != CUBE_OK) return s;
+    cube_ctx c;
+    init_geo(&c, p, B);
+    *state = state_layout(&c, nullptr);
+    *work = work_layout(&c, nullptr);
+    return CUBE_OK;
+}
+
+cube_status served_create(const cube_params* p, cudaStream_t st, cube_ctx** out) {
+    return create_ctx(p, st, true, out);
+}
+
+void served_bind(cube_ctx* c, char* work) {
+    if (c->work_base == work) return;
+    c->work_base = work;
+    work_layout(c, work);
+    c->tma = encode_phig_map(c);
+}
+
+cube_status served_encode(cube_ctx* c, const float* pos, const float* vel, const uint32_t* id, double a,
+                          double sigma) {
+    return encode_impl(c, pos, vel, id, a, sigma, false);
+}
+
+cube_status served_finish(cube_ctx* c, int32_t n_bins, double* pk3, unsigned* flags2) {
+    cube_status s = pk_enqueue(c, n_bins, pk3, pk3 + n_bins, pk3 + 2 * n_bins);
+    if (s != CUBE_OK) return s;
+    CK(cudaMemcpyAsync(flags2, c->flags, 4, cudaMemcpyDeviceToHost, c->st));
+    CK(cudaMemcpyAsync(flags2 + 1, c->maxmig, 4, cudaMemcpyDeviceToHost, c->st));
+    return CUBE_OK;
+}
+
+cube_status served_flags_status(unsigned flags) { return flags_status(flags); }
+
+cube_status served_fail(cube_status s, const char* msg) { return fail(s, msg); }
+
+}  // namespace cube

@@ -9,6 +9,7 @@ pm128o : the 128^3-particle / 256^3-mesh version of pm256 with the same seed
 pm512  : 512^3 particles, 1024^3 mesh, 600 Mpc/h, same LCDM, code widths varied.
 All use a coarse cell of 4 fine cells and two fine cells per particle spacing.
 """
+import dataclasses
 from dataclasses import dataclass
 
 import numpy as np
@@ -63,6 +64,52 @@ def ensemble_c4(n=64, seed=1712004):
     s8 = rng.uniform(0.7, 0.9, size=n)
     return [Workload(f"c4_{i}", int(sides[i]), 2 * int(sides[i]), float(boxes[i]), "lcdm", 1, 1, 0.02, 1.0, 30, i,
                      sigma8=float(s8[i])) for i in range(n)]
+
+
+@dataclass(frozen=True)
+class Request:
+    """One simulation request of the serving stream."""
+    arrival: float               # seconds after the stream starts
+    workload: Workload
+
+
+def serving_c5(n=40, rate=20.0, seed=1712005):
+    """A Poisson-arrival stream of simulation requests (mean `rate` per
+    second): particles per side drawn from {64, 96, 128, 192, 256} (mesh
+    twice that; 2^a 3^b sides), box 300 Mpc/h x side / 256 (the 256^3
+    workload's resolution), sigma8 uniform in [0.7, 0.9], flat LCDM BBKS,
+    x1v1, a step count uniform in 10 .. 60 with the 256^3 workload's step
+    Delta a = 0.0196 from z = 49 (a_final = min(1, 0.02 + 0.0196 n)), IC
+    seed per request."""
+    rng = np.random.default_rng(seed)
+    t = np.cumsum(rng.exponential(1.0 / rate, size=n))
+    sides = rng.choice([64, 96, 128, 192, 256], size=n)
+    s8 = rng.uniform(0.7, 0.9, size=n)
+    steps = rng.integers(10, 61, size=n)
+    out = []
+    for i in range(n):
+        ns = int(sides[i])
+        a_final = min(1.0, 0.02 + 0.0196 * int(steps[i]))
+        out.append(Request(float(t[i]), Workload(f"c5_{i}", ns, 2 * ns, 300.0 * ns / 256, "lcdm", 1, 1, 0.02,
+                                                 a_final, int(steps[i]), 2000 + i, sigma8=float(s8[i]))))
+    return out
+
+
+def rescaled_ics(ic, factor):
+    """The same Zel'dovich realisation with its amplitude (sigma8) times
+    `factor`: displacements from the Lagrangian lattice, momenta and the
+    velocity scale are linear in the amplitude."""
+    nf = ic.n_fine
+    ng = round(len(ic.ids) ** (1.0 / 3.0))
+    s = nf / ng
+    i = ic.ids.astype(np.int64)
+    q = np.stack([(i % ng) * s + 0.5, ((i // ng) % ng) * s + 0.5, (i // (ng * ng)) * s + 0.5])
+    d = ic.pos.astype(np.float64) - q
+    d -= nf * np.round(d / nf)
+    pos = np.mod(q + factor * d, float(nf)).astype(np.float32)
+    pos[pos >= np.float32(nf)] = 0.0
+    vel = (ic.vel.astype(np.float64) * factor).astype(np.float32)
+    return dataclasses.replace(ic, pos=pos, vel=vel, sigma_1d=ic.sigma_1d * factor)
 
 
 def uniform_schedule(a_init, a_final, n_steps):
