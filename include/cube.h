@@ -295,6 +295,23 @@ const char* cube_phase_name(int32_t phase);
 cube_status cube_counts_to_offsets_noalloc(const uint32_t* counts, int64_t n_cells, uint32_t* offsets,
                                            void* cuda_stream);
 
+/* ---------------------------------------------------------------- autotuning */
+
+/* Picks the storage-order brick (cube_params.brick: 1, 2 or 4 coarse cells)
+   that steps fastest for these parameters on this GPU.  The brick is the
+   tile shape of the deposit, of the force gather's potential tile and of the
+   re-sort; every valid brick gives bit-identical results, so the choice
+   changes speed only.  For each valid brick: a context on cuda_stream, an
+   encode of pos/vel (as cube_encode, ids by index) at epoch a with codec
+   scale sigma, one untimed step, then n_steps (1 .. 100) steps of
+   Delta a = 1e-4 a timed with CUDA events.  Blocks until done.
+   best_brick: the fastest brick side; ms_per_step (nullable): [3] times for
+   bricks 1, 2, 4, -1 where a brick is not valid.
+   Errors: CUBE_E_ARG, or any error of the calls above. */
+cube_status cube_autotune_brick(const cube_params* params, const float* pos, const float* vel, double a,
+                                double sigma, int32_t n_steps, void* cuda_stream, int32_t* best_brick,
+                                double* ms_per_step);
+
 /* ---------------------------------------------------------------- serving: many simulations on one GPU */
 
 /* A server runs many independent simulations ("requests") at once on one GPU

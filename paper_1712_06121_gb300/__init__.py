@@ -87,6 +87,8 @@ _sigs = {
     "cube_counts_to_offsets_noalloc": ([_P, ctypes.c_int64, _P, _P], ctypes.c_int),
     "cube_max_speed": ([_P, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
     "cube_next_epoch": ([_P, ctypes.c_double, ctypes.c_double, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
+    "cube_autotune_brick": ([ctypes.POINTER(cube_params), _P, _P, ctypes.c_double, ctypes.c_double, ctypes.c_int32,
+                             _P, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
     "cube_server_sizes": ([ctypes.POINTER(cube_params), ctypes.POINTER(ctypes.c_int64),
                            ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
     "cube_server_create": ([ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(_P)], ctypes.c_int),
@@ -237,6 +239,17 @@ def cube_phase_name(phase):
 
 __all__ = [n for n in _sigs] + ["make_params", "cube_params", "cube_state", "cube_stats", "CubeError",
                                 "LIB_PATH", "CUBE_GRAD_FD4", "CUBE_PHASES"]
+
+
+def cube_autotune_brick(params, pos, vel, a, sigma, n_steps=5, stream=None):
+    """(fastest brick side, [ms per step for bricks 1, 2, 4; -1 where invalid])."""
+    if stream is not None and hasattr(stream, "cuda_stream"):
+        stream = stream.cuda_stream
+    best = ctypes.c_int32()
+    ms = (ctypes.c_double * 3)()
+    _check(_lib.cube_autotune_brick(ctypes.byref(params), _ptr(pos), _ptr(vel), float(a), float(sigma),
+                                    int(n_steps), stream, ctypes.byref(best), ms))
+    return best.value, list(ms)
 
 
 # ---------------------------------------------------------------- serving

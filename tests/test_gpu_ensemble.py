@@ -3,7 +3,8 @@ each in its own context, spread over several CUDA streams and stepped in
 interleaved order, give stores bit-identical to the same runs made one after
 another on one stream (every sum that decides the store is an integer, so
 the overlap cannot change a result).  Each run's own parity with the oracle
-is the subject of the step tests.
+is the subject of the step tests.  The brick autotuner returns the fastest
+valid brick side (results are brick-invariant: test_gpu_parity).
 """
 import dataclasses
 
@@ -70,3 +71,22 @@ def test_concurrent_streams_match_sequential(cube):
         assert gs["sigma"] == gc["sigma"]
         assert int(gc["counts"].sum()) == w.n_particles
         assert np.array_equal(np.sort(gc["ids"]), np.arange(w.n_particles, dtype=np.uint32))
+
+
+def test_autotuned_brick_is_the_fastest_valid_one(cube):
+    """cube_autotune_brick times each valid brick side and returns the
+    fastest; sides that do not fit the mesh report -1."""
+    w = dataclasses.replace(synth.ensemble_c4(1)[0], n_part_side=16, n_fine=32)
+    ic = synth.make_ics(w)
+    om, ol, _ = w.omega()
+    prm = cube.make_params(w.n_fine, w.n_particles, box=w.box, omega_m=om, omega_l=ol)
+    best, ms = cube.cube_autotune_brick(prm, ic.pos, ic.vel, w.a_init, ic.sigma_1d, 3)
+    assert ms[2] == -1.0                      # 8 coarse cells per side: 2 bricks of 4, fewer than 3
+    valid = {b: t for b, t in zip((1, 2, 4), ms) if t >= 0}
+    assert best in valid and valid[best] == min(valid.values()) and all(t > 0 for t in valid.values())
+    # a mesh of 4 coarse cells per side admits brick 1 only
+    w2 = dataclasses.replace(w, n_part_side=8, n_fine=16)
+    ic2 = synth.make_ics(w2)
+    prm2 = cube.make_params(16, 8 ** 3, box=w.box, omega_m=om, omega_l=ol)
+    best2, ms2 = cube.cube_autotune_brick(prm2, ic2.pos, ic2.vel, w.a_init, ic2.sigma_1d, 2)
+    assert best2 == 1 and ms2[1] == -1.0 and ms2[2] == -1.0 and ms2[0] > 0
