@@ -49,6 +49,17 @@ __device__ __forceinline__ int sidx(int k, int c) {
     return SWZ ? (k << LOG_NC) + (c ^ ((k ^ (k >> 3)) & (NC - 1))) : (k << LOG_NC) + c;
 }
 
+// sidx(k_lo + k_hi, c) from base = sidx(k_lo, c) when the set bits of the
+// compile-time k_hi lie above those of k_lo: the swizzle is XOR-linear in k,
+// so the sum is base XOR a constant plus a constant (one logic op and an
+// immediate offset per access)
+template <bool SWZ>
+__device__ __forceinline__ int sidx_add(int base, int k_hi) {
+    return SWZ ? (base ^ ((k_hi ^ (k_hi >> 3)) & (NC - 1))) + (k_hi << LOG_NC) : base + (k_hi << LOG_NC);
+}
+
+constexpr bool pow2(int x) { return x > 0 && (x & (x - 1)) == 0; }
+
 template <int RAD, bool INV>
 __device__ __forceinline__ void dft(float2* v) {
     if (RAD == 2) {
@@ -104,14 +115,17 @@ __device__ __forceinline__ void fft_pass(float2* buf, const float2* tw) {
     constexpr int nbf = nq * NC;
     constexpr int KMAX = (nbf + T - 1) / T;
     constexpr int step = TWM * (n / (Ns * R));
+    constexpr bool lin = pow2(nq) && pow2(Ns) && pow2(R);   // bit-disjoint element offsets
     float2 v[KMAX][R];
 #pragma unroll
     for (int q = 0; q < KMAX; ++q) {
         const int b = threadIdx.x + q * T;
         if (nbf % T == 0 || b < nbf) {
             const int c = b & (NC - 1), j = b >> LOG_NC;
+            const int base = sidx<SWZ>(j, c);
 #pragma unroll
-            for (int m = 0; m < R; ++m) v[q][m] = buf[sidx<SWZ>(j + m * nq, c)];
+            for (int m = 0; m < R; ++m)
+                v[q][m] = buf[lin ? sidx_add<SWZ>(base, m * nq) : sidx<SWZ>(j + m * nq, c)];
         }
     }
     __syncthreads();
@@ -131,8 +145,10 @@ __device__ __forceinline__ void fft_pass(float2* buf, const float2* tw) {
             }
             dft<R, INV>(v[q]);
             const int idxD = (j / Ns) * Ns * R + k;
+            const int base = sidx<SWZ>(idxD, c);
 #pragma unroll
-            for (int m = 0; m < R; ++m) buf[sidx<SWZ>(idxD + m * Ns, c)] = v[q][m];
+            for (int m = 0; m < R; ++m)
+                buf[lin ? sidx_add<SWZ>(base, m * Ns) : sidx<SWZ>(idxD + m * Ns, c)] = v[q][m];
         }
     }
     __syncthreads();
@@ -425,8 +441,9 @@ __device__ __forceinline__ void xpass_load(float2* buf, const float* mesh, int64
                 }
             }
             dft<R, INV>(v);
+            const int base = sidx<true>(j * R, c);
 #pragma unroll
-            for (int m = 0; m < R; ++m) buf[sidx<true>(j * R + m, c)] = v[m];
+            for (int m = 0; m < R; ++m) buf[pow2(R) ? sidx_add<true>(base, m) : sidx<true>(j * R + m, c)] = v[m];
         }
     }
     cp_async_wait_all();
@@ -451,8 +468,10 @@ __device__ __forceinline__ void xpass_store(const float2* buf, const float2* tw,
         if (nbf % XFFT_T == 0 || b < nbf) {
             const int j = b % nq, c = b / nq;
             float2 v[R];
+            const int base = sidx<true>(j, c);
 #pragma unroll
-            for (int m = 0; m < R; ++m) v[m] = buf[sidx<true>(j + m * nq, c)];
+            for (int m = 0; m < R; ++m)
+                v[m] = buf[pow2(nq) ? sidx_add<true>(base, m * nq) : sidx<true>(j + m * nq, c)];
             if (Ns > 1) {
 #pragma unroll
                 for (int m = 1; m < R; ++m) {
