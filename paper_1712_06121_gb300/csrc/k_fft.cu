@@ -611,7 +611,8 @@ struct GreenPost {
         const int kx = c0 + c;
         if (kx >= ncol) return v;
         const float kk = sk2[kx] + ky2 + sk2[z];
-        const float gr = (kx == 0 && ky == 0 && z == 0) ? 0.0f : g0 / kk * (swd[kx] * wy * swd[z]);
+        // approximate division: within 2 ulp for kk below 2^126 (here kk < 3 pi^2)
+        const float gr = (kx == 0 && ky == 0 && z == 0) ? 0.0f : __fdividef(g0, kk) * (swd[kx] * wy * swd[z]);
         return make_float2(v.x * gr, v.y * gr);
     }
 };
