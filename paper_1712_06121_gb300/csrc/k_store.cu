@@ -296,15 +296,21 @@ __device__ __forceinline__ float node_value(unsigned lo, unsigned hi) {
     return hi ? __ull2float_rn(((unsigned long long)hi << 32) | lo) : u32_to_float_rn(lo);
 }
 
-template <int NX>
+// slots of the per-particle cell table: bricks whose particles and layer
+// fit look their cell up in it, larger ones (crowded late epochs) search
+constexpr int DEP_QCAP = 2048;
+
+template <int NX, int FC>
 __global__ void __launch_bounds__(T_BRICK) k_deposit(Geo g, StoreDev s, float* __restrict__ mesh, float fscale) {
     extern __shared__ unsigned long long dep_smem[];
-    const int F = g.F, lF = g.lF, F3 = 1 << (3 * lF);
+    // FC > 0: the brick side in fine cells is the compile-time FC, else g.F
+    const int lF = FC == 16 ? 4 : FC == 8 ? 3 : FC == 4 ? 2 : g.lF, F = 1 << lF, F3 = 1 << (3 * lF);
     const int E = g.B + 1, E3 = E * E * E;
     unsigned* acc = reinterpret_cast<unsigned*>(dep_smem);          // [F3] {lo, hi} words
     unsigned* cstart = acc + 2 * F3;                                 // [E3]
     unsigned* cpref = cstart + E3;                                   // [E3 + 1]
     int* cpack = reinterpret_cast<int*>(cpref + E3 + 1);             // [E3] packed cell offsets
+    unsigned char* qcell = reinterpret_cast<unsigned char*>(cpack + E3);   // [DEP_QCAP] cell of each slot
     int bx, by, bz;
     brick_coords(g, blockIdx.x, &bx, &by, &bz);
     const int c0[3] = {bx * g.B, by * g.B, bz * g.B};
@@ -343,8 +349,14 @@ __global__ void __launch_bounds__(T_BRICK) k_deposit(Geo g, StoreDev s, float* _
     // a node's 32-bit sum of 1-byte-code weights (each < 2^(3 s)) cannot wrap
     // when fewer than 2^(32 - 3 s) particles feed the brick
     const bool small = 3 * sb < 32 && total < (1u << (32 - 3 * sb));
+    const bool table = total <= (unsigned)DEP_QCAP && E3 <= 256;    // block-uniform
+    if (table) {
+        for (int t = threadIdx.x; t < E3; t += blockDim.x)
+            for (unsigned q = cpref[t], q1 = min(cpref[t + 1], total); q < q1; ++q) qcell[q] = (unsigned char)t;
+        __syncthreads();
+    }
     for (unsigned q = threadIdx.x; q < total; q += blockDim.x) {
-        const int t = upper_cell(cpref, E3, q);
+        const int t = table ? (int)qcell[q] : upper_cell(cpref, E3, q);
         const unsigned i = cstart[t] + (q - cpref[t]);
         if (i >= (unsigned)g.Np) continue;
         const int pk = cpack[t];
@@ -984,7 +996,8 @@ void set_smem_attrs() {
     cudaFuncSetAttribute(k_passA<NX, NV, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     cudaFuncSetAttribute(k_passA<NX, NV, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     cudaFuncSetAttribute(k_passB<NX, NV>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    cudaFuncSetAttribute(k_deposit<NX>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_deposit<NX, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_deposit<NX, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     done = true;
 }
 
@@ -1050,17 +1063,20 @@ void launch_decode(const Geo& g, const StoreDev& s, const float* dec, float* pos
 
 static size_t deposit_smem(const Geo& g) {
     const int F3 = g.F * g.F * g.F, E = g.B + 1, E3 = E * E * E;
-    return (size_t)F3 * 8 + (size_t)(3 * E3 + 1) * 4;
+    return (size_t)F3 * 8 + (size_t)(3 * E3 + 1) * 4 + DEP_QCAP;
 }
 
 void launch_deposit(const Geo& g, const StoreDev& s, float* mesh, double scale, cudaStream_t st) {
     size_t sm = deposit_smem(g);
+    const bool f16 = g.F == 16;
     if (g.nchi == 1) {
         set_smem_attrs<1, 1>(); set_smem_attrs<1, 2>();
-        k_deposit<1><<<g.nbricks, T_BRICK, sm, st>>>(g, s, mesh, (float)scale);
+        if (f16) k_deposit<1, 16><<<g.nbricks, T_BRICK, sm, st>>>(g, s, mesh, (float)scale);
+        else k_deposit<1, 0><<<g.nbricks, T_BRICK, sm, st>>>(g, s, mesh, (float)scale);
     } else {
         set_smem_attrs<2, 1>(); set_smem_attrs<2, 2>();
-        k_deposit<2><<<g.nbricks, T_BRICK, sm, st>>>(g, s, mesh, (float)scale);
+        if (f16) k_deposit<2, 16><<<g.nbricks, T_BRICK, sm, st>>>(g, s, mesh, (float)scale);
+        else k_deposit<2, 0><<<g.nbricks, T_BRICK, sm, st>>>(g, s, mesh, (float)scale);
     }
 }
 
