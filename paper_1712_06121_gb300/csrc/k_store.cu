@@ -471,6 +471,7 @@ __global__ void __launch_bounds__(T_BRICK, 4) k_passA(Geo g, StoreDev s, const f
     float* sthr = sdec + (NV == 1 ? 2 * lim + 1 : 0);                       // NV == 1: [lim + 2]
     float* svc = sthr + (NV == 1 ? lim + 2 : 0);                            // [3][nbc]: v_c of the brick
     unsigned char* stab = reinterpret_cast<unsigned char*>(svc + 3 * nbc);  // NV == 1: [VT_N] bucket table
+    unsigned char* qcell = stab + (NV == 1 ? VT_N : 0);                     // [DEP_QCAP] cell of each particle
     const float* dec = cur.dec;
     const float* thr = cur.thr;
     int key0 = 0;
@@ -534,6 +535,15 @@ __global__ void __launch_bounds__(T_BRICK, 4) k_passA(Geo g, StoreDev s, const f
         mbar_wait_bounded(&tile_bar, 0);
         return;
     }
+    // the cell of every particle of the brick, when they fit the table
+    const unsigned q0 = i - threadIdx.x;
+    const bool table = q1 - q0 <= (unsigned)DEP_QCAP;                  // block-uniform
+    if (table) {
+        for (int c = threadIdx.x; c < nbc; c += blockDim.x)
+            for (unsigned q = max(sm_off[c], q0), qe = min(sm_off[c + 1], q1); q < qe; ++q)
+                qcell[q - q0] = (unsigned char)c;
+        __syncthreads();
+    }
     const float e0 = cur.est[0], e1 = cur.est[1];
     const int nbits = 8 * NX, half = 1 << (nbits - 1);
     const int sb = g.sbits, wmask = (1 << sb) - 1;
@@ -554,7 +564,7 @@ __global__ void __launch_bounds__(T_BRICK, 4) k_passA(Geo g, StoreDev s, const f
                 nnu[d] = load_nu<NV>(s.nu, d * g.Np + i + blockDim.x, lim);
             }
         }
-        int lc = upper_cell(sm_off, nbc, i);
+        int lc = table ? (int)qcell[i - q0] : upper_cell(sm_off, nbc, i);
         int l[3] = {lc & (g.B - 1), (lc >> g.lB) & (g.B - 1), lc >> (2 * g.lB)};
         int Q[3], n[3];
         float wv[3];
@@ -747,13 +757,12 @@ struct PassB {
     int key0, lim;
     float dc, e0, e1;
 
-    __device__ __forceinline__ PbParticle move(const unsigned* sm_off, const float* svc, unsigned i,
-                                               const int* cchi, const int* cnu) const {
-        const int nbc = g.B * g.B * g.B, Bh = g.Bh;
+    // lc: the particle's coarse cell in the brick
+    __device__ __forceinline__ PbParticle move(int lc, const float* svc, const int* cchi, const int* cnu) const {
+        const int Bh = g.Bh;
         const int nbits = 8 * NX, half = 1 << (nbits - 1), bmask = (1 << nbits) - 1;
         const float inv2q = ldexpf(1.0f, -(nbits + 1));
         const float two8n = ldexpf(1.0f, nbits);
-        const int lc = upper_cell(sm_off, nbc, i);
         const int l[3] = {lc & (g.B - 1), (lc >> g.lB) & (g.B - 1), lc >> (2 * g.lB)};
         PbParticle r;
         int e[3];
@@ -872,7 +881,7 @@ __global__ void __launch_bounds__(PB_WARPS * 32, 5) k_passB(Geo g, StoreDev so, 
                         cnu[d] = load_nu<NV>(so.nu, d * g.Np + i, lim);
                     }
                     if (sn.id) cid = so.id[i];
-                    q = pb.move(sm_off, svc, i, cchi, cnu);
+                    q = pb.move(upper_cell(sm_off, nbc, i), svc, cchi, cnu);
                     peers = __match_any_sync(am, q.ei);
                     leader = __ffs(peers) - 1;
                     if (lane == leader) wcnt[warp * H3 + q.ei] = (unsigned)__popc(peers);
@@ -944,7 +953,7 @@ __global__ void __launch_bounds__(PB_WARPS * 32, 5) k_passB(Geo g, StoreDev so, 
             if (sn.id) nid = so.id[i + 32];
         }
         if (act) {
-            const PbParticle q = pb.move(sm_off, svc, i, cchi, cnu);
+            const PbParticle q = pb.move(upper_cell(sm_off, nbc, i), svc, cchi, cnu);
             const unsigned peers = __match_any_sync(am, q.ei);
             const int leader = __ffs(peers) - 1;
             unsigned start = 0;
@@ -1085,7 +1094,7 @@ static size_t passA_smem(const Geo& g) {
     // + 128: the tile is placed on a 128-byte boundary at run time
     size_t sm = (size_t)3 * H3 * 8 + 128 + (size_t)T * T * TS * 4 + (size_t)H3 * 4 + (size_t)(nbc + 1) * 4;
     if (g.nnu == 1) sm += (size_t)(3 * g.nulim + 3) * 4 + VT_N;
-    sm += (size_t)3 * nbc * 4;
+    sm += (size_t)3 * nbc * 4 + DEP_QCAP;
     return (sm + 15) & ~(size_t)15;
 }
 
