@@ -345,7 +345,7 @@ typedef enum {
 typedef struct {
     int32_t state;            /* cube_req_state                                    */
     int32_t steps_enqueued;   /* steps handed to the GPU so far                    */
-    int32_t n_steps;
+    int32_t n_steps;          /* scheduled steps (waypoints when adaptive)         */
     int32_t max_migration;    /* after completion: largest |cell shift| of a step  */
     double t_submit, t_admit, t_done;   /* server clock; -1 before the event       */
     int64_t state_bytes;      /* device bytes held from admission to release       */
@@ -368,16 +368,22 @@ cube_status cube_server_destroy(cube_server* srv);
 /* Queues a simulation: initial particles pos[3][N], vel[3][N] (host --
    pinned for an asynchronous upload -- or device arrays) and id[N]
    (nullable) at scale factor epochs[0], codec scale sigma as cube_encode,
-   then the n_steps steps epochs[i] -> epochs[i + 1] (epochs[n_steps + 1]
-   values, increasing, copied), then P(k) in n_bins bins as
-   cube_power_spectrum.  The caller keeps pos, vel and id valid until the
-   request is DONE or FAILED.  Returns a ticket (> 0).
+   then steps through epochs[1 .. n_steps] (n_steps + 1 values, increasing,
+   copied), then P(k) in n_bins bins as cube_power_spectrum.
+   max_drift_cells = 0: exactly the n_steps steps epochs[i] -> epochs[i + 1].
+   max_drift_cells in (0, 1]: the epochs are waypoints and every step is cut
+   as cube_next_epoch does, so that the fastest particle drifts at most that
+   many coarse cells (the velocity limit of Section 2.3.3's time step); the
+   server reads the largest |p| back asynchronously after each step, so a
+   request has one step in flight.
+   The caller keeps pos, vel and id valid until the request is DONE or
+   FAILED.  Returns a ticket (> 0).
    Errors: CUBE_E_ARG (parameters, n_steps < 1, n_bins outside [1, 2048],
-   epochs not increasing), CUBE_E_NOMEM (the request alone exceeds the
-   budget, or pinned result memory). */
+   epochs not increasing, max_drift_cells outside [0, 1]), CUBE_E_NOMEM (the
+   request alone exceeds the budget, or pinned result memory). */
 cube_status cube_server_submit(cube_server* srv, const cube_params* params, const float* pos, const float* vel,
                                const uint32_t* id, double sigma, const double* epochs, int32_t n_steps,
-                               int32_t n_bins, int64_t* ticket);
+                               double max_drift_cells, int32_t n_bins, int64_t* ticket);
 
 /* Makes progress without blocking: retires finished requests, hands the next
    steps of running requests to the GPU, admits queued requests that fit.

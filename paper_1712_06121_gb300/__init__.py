@@ -94,7 +94,7 @@ _sigs = {
     "cube_server_create": ([ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(_P)], ctypes.c_int),
     "cube_server_destroy": ([_P], ctypes.c_int),
     "cube_server_submit": ([_P, ctypes.POINTER(cube_params), _P, _P, _P, ctypes.c_double, _P, ctypes.c_int32,
-                            ctypes.c_int32, ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
+                            ctypes.c_double, ctypes.c_int32, ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
     "cube_server_pump": ([_P, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)], ctypes.c_int),
     "cube_server_drain": ([_P], ctypes.c_int),
     "cube_server_info": ([_P, ctypes.c_int64, ctypes.POINTER(cube_request_info)], ctypes.c_int),
@@ -270,15 +270,17 @@ def cube_server_destroy(srv):
     _check(_lib.cube_server_destroy(srv))
 
 
-def cube_server_submit(srv, params, pos, vel, ids, sigma, epochs, n_bins):
+def cube_server_submit(srv, params, pos, vel, ids, sigma, epochs, n_bins, max_drift_cells=0.0):
     """Queues one simulation; epochs: n_steps + 1 increasing scale factors
-    (a float64 array kept alive by the caller only for this call).  pos, vel
-    and ids must stay alive until the request is done.  Returns the ticket."""
+    (copied); max_drift_cells > 0 makes them waypoints of velocity-limited
+    steps.  pos, vel and ids must stay alive until the request is done.
+    Returns the ticket."""
     import numpy as np
     ep = np.ascontiguousarray(epochs, dtype=np.float64)
     t = ctypes.c_int64()
     _check(_lib.cube_server_submit(srv, ctypes.byref(params), _ptr(pos), _ptr(vel), _ptr(ids), float(sigma),
-                                   ep.ctypes.data, len(ep) - 1, int(n_bins), ctypes.byref(t)))
+                                   ep.ctypes.data, len(ep) - 1, float(max_drift_cells), int(n_bins),
+                                   ctypes.byref(t)))
     return t.value
 
 

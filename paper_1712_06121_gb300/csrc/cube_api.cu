@@ -797,6 +797,21 @@ cube_status cube_max_speed(cube_ctx* c, double* p_max) {
     return s;
 }
 
+// largest a_to <= a_max with p * int_a^a_to da / (a^3 E) <= cells coarse cells
+// (a = the store's epoch; drift(a, .) grows: bisection); a when none is
+static double epoch_limit(const cube_ctx* c, double p, double a_max, double cells) {
+    const double limit = cells * c->g.R;                 // fine cells
+    const double a0 = c->a;
+    if (p * c->cosmo.drift(a0, a_max) <= limit) return a_max;
+    double lo = a0, hi = a_max;
+    for (int it = 0; it < 100 && hi - lo > 1e-15 * hi; ++it) {
+        const double mid = 0.5 * (lo + hi);
+        if (p * c->cosmo.drift(a0, mid) <= limit) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
 cube_status cube_next_epoch(cube_ctx* c, double a_max, double cells, double* a_to) {
     if (!c || !a_to) return fail(CUBE_E_ARG, "NULL argument");
     if (!c->encoded) return fail(CUBE_E_STATE, "no store: call cube_encode first");
@@ -805,20 +820,8 @@ cube_status cube_next_epoch(cube_ctx* c, double a_max, double cells, double* a_t
     double p = 0.0;
     cube_status s = cube_max_speed(c, &p);
     if (s != CUBE_OK) return s;
-    const double limit = cells * c->g.R;                 // fine cells
-    const double a0 = c->a;
-    if (p * c->cosmo.drift(a0, a_max) <= limit) {
-        *a_to = a_max;
-        return CUBE_OK;
-    }
-    double lo = a0, hi = a_max;                         // drift(a0, a) grows with a: bisect
-    for (int it = 0; it < 100 && hi - lo > 1e-15 * hi; ++it) {
-        const double mid = 0.5 * (lo + hi);
-        if (p * c->cosmo.drift(a0, mid) <= limit) lo = mid;
-        else hi = mid;
-    }
-    *a_to = lo;
-    return lo > a0 ? CUBE_OK : fail(CUBE_E_ARG, "no step keeps the fastest particle within the limit");
+    *a_to = epoch_limit(c, p, a_max, cells);
+    return *a_to > c->a ? CUBE_OK : fail(CUBE_E_ARG, "no step keeps the fastest particle within the limit");
 }
 
 cube_status cube_state_view(cube_ctx* c, cube_state* out) {
@@ -1020,6 +1023,22 @@ cube_status served_finish(cube_ctx* c, int32_t n_bins, double* pk3, unsigned* fl
 }
 
 cube_status served_flags_status(unsigned flags) { return flags_status(flags); }
+
+// largest |p| of the store into pinned host memory (float bits), enqueued
+cube_status served_vmax_enqueue(cube_ctx* c, unsigned* pinned_bits) {
+    const Geo& g = c->g;
+    if (c->raw) launch_raw_max_speed(g, (const float*)c->nu[0], c->vmax, c->st);
+    else launch_max_speed(g, c->store(c->cur), c->codec[c->cur].dec, c->vmax, c->st);
+    c->launches += 1;
+    CK(cudaMemcpyAsync(pinned_bits, c->vmax, 4, cudaMemcpyDeviceToHost, c->st));
+    return CUBE_OK;
+}
+
+double served_epoch_limit(cube_ctx* c, double p_max, double a_max, double cells) {
+    return epoch_limit(c, p_max, a_max, cells);
+}
+
+double served_epoch(cube_ctx* c) { return c->a; }
 
 cube_status served_fail(cube_status s, const char* msg) { return fail(s, msg); }
 

@@ -10,6 +10,7 @@
 // until cube_server_release.  The host never waits on the GPU in pump().
 #include <algorithm>
 #include <chrono>
+#include <cstring>
 #include <deque>
 #include <map>
 #include <string>
@@ -28,6 +29,9 @@ cube_status served_encode(cube_ctx* c, const float* pos, const float* vel, const
 cube_status served_finish(cube_ctx* c, int32_t n_bins, double* pk3, unsigned* flags2);
 cube_status served_flags_status(unsigned flags);
 cube_status served_fail(cube_status s, const char* msg);
+cube_status served_vmax_enqueue(cube_ctx* c, unsigned* pinned_bits);
+double served_epoch_limit(cube_ctx* c, double p_max, double a_max, double cells);
+double served_epoch(cube_ctx* c);
 }  // namespace cube
 
 using namespace cube;
@@ -43,8 +47,12 @@ struct Request {
     const float* vel = nullptr;
     const uint32_t* id = nullptr;
     double sigma = 0.0;
-    std::vector<double> epochs;
+    std::vector<double> epochs;           // fixed steps, or the waypoints of adaptive ones
+    double cells = 0.0;                   // > 0: each step cut so the fastest particle drifts <= cells
     int n_bins = 0;
+    int waypoint = 1;                     // adaptive: next epochs[] index to reach
+    bool vmax_pending = false;            // adaptive: the max-speed copy of the current state is queued
+    cudaEvent_t vmax_ev = nullptr;
     size_t state_bytes = 0, work_bytes = 0;
     int state = CUBE_REQ_QUEUED;
     int next = 0;                         // steps enqueued
@@ -54,7 +62,7 @@ struct Request {
     std::deque<cudaEvent_t> inflight;     // one event per enqueued step
     cudaEvent_t done = nullptr;
     double* pk = nullptr;                 // pinned [3][n_bins]
-    unsigned* flags = nullptr;            // pinned {error flags, max migration}
+    unsigned* flags = nullptr;            // pinned {error flags, max migration, max |p| bits}
     double t_submit = -1.0, t_admit = -1.0, t_done = -1.0;
     cube_status err = CUBE_OK;
 };
@@ -121,7 +129,46 @@ cube_status advance(cube_server* s, Request* r) {
         r->inflight.pop_front();
     }
     const int n_steps = (int)r->epochs.size() - 1;
-    while (r->next < n_steps && (int)r->inflight.size() < kDepth) {
+    if (r->cells > 0.0) {                 // adaptive: one step per max-speed read-back
+        if (r->finishing) goto finish;
+        if (!r->vmax_pending) {
+            served_bind(r->ctx, sl.work);
+            cube_status st = served_vmax_enqueue(r->ctx, &r->flags[2]);
+            if (st != CUBE_OK) {
+                fail_request(s, r, st);
+                return CUBE_OK;
+            }
+            if (!r->vmax_ev) SCK(cudaEventCreateWithFlags(&r->vmax_ev, cudaEventDisableTiming));
+            SCK(cudaEventRecord(r->vmax_ev, sl.st));
+            r->vmax_pending = true;
+            return CUBE_OK;
+        }
+        const cudaError_t q = cudaEventQuery(r->vmax_ev);
+        if (q == cudaErrorNotReady) return CUBE_OK;
+        if (q != cudaSuccess) return served_fail(CUBE_E_CUDA, cudaGetErrorString(q));
+        r->vmax_pending = false;
+        const double a = served_epoch(r->ctx);
+        if (a < r->epochs[n_steps]) {
+            float p;
+            std::memcpy(&p, &r->flags[2], 4);
+            const double a_to = served_epoch_limit(r->ctx, (double)p, r->epochs[r->waypoint], r->cells);
+            if (!(a_to > a)) {
+                fail_request(s, r, served_fail(CUBE_E_ARG, "no step keeps the fastest particle within the limit"));
+                return CUBE_OK;
+            }
+            served_bind(r->ctx, sl.work);
+            cube_status st = cube_pm_step(r->ctx, a, a_to);
+            if (st != CUBE_OK) {
+                fail_request(s, r, st);
+                return CUBE_OK;
+            }
+            ++r->next;
+            if (a_to >= r->epochs[r->waypoint]) ++r->waypoint;
+            if (a_to < r->epochs[n_steps]) return advance(s, r);     // queue the next read-back
+        }
+        r->waypoint = n_steps + 1;
+    }
+    while (r->cells <= 0.0 && r->next < n_steps && (int)r->inflight.size() < kDepth) {
         served_bind(r->ctx, sl.work);
         cube_status st = cube_pm_step(r->ctx, r->epochs[r->next], r->epochs[r->next + 1]);
         if (st != CUBE_OK) {
@@ -133,7 +180,7 @@ cube_status advance(cube_server* s, Request* r) {
         r->inflight.push_back(e);
         ++r->next;
     }
-    if (r->next == n_steps && !r->finishing) {
+    if ((r->cells > 0.0 ? r->waypoint > n_steps : r->next == n_steps) && !r->finishing) {
         served_bind(r->ctx, sl.work);
         cube_status st = served_finish(r->ctx, r->n_bins, r->pk, r->flags);
         if (st != CUBE_OK) {
@@ -144,6 +191,7 @@ cube_status advance(cube_server* s, Request* r) {
         SCK(cudaEventRecord(r->done, sl.st));
         r->finishing = true;
     }
+finish:
     if (r->finishing) {
         const cudaError_t q = cudaEventQuery(r->done);
         if (q == cudaSuccess) {
@@ -253,6 +301,7 @@ cube_status cube_server_destroy(cube_server* s) {
         if (r->ctx) cube_destroy(r->ctx);
         for (cudaEvent_t e : r->inflight) cudaEventDestroy(e);
         if (r->done) cudaEventDestroy(r->done);
+        if (r->vmax_ev) cudaEventDestroy(r->vmax_ev);
         if (r->pk) cudaFreeHost(r->pk);
         delete r;
     }
@@ -270,8 +319,10 @@ cube_status cube_server_destroy(cube_server* s) {
 
 cube_status cube_server_submit(cube_server* s, const cube_params* params, const float* pos, const float* vel,
                                const uint32_t* id, double sigma, const double* epochs, int32_t n_steps,
-                               int32_t n_bins, int64_t* ticket) {
+                               double max_drift_cells, int32_t n_bins, int64_t* ticket) {
     if (!s || !params || !pos || !vel || !epochs || !ticket) return served_fail(CUBE_E_ARG, "NULL argument");
+    if (!(max_drift_cells >= 0.0 && max_drift_cells <= 1.0))
+        return served_fail(CUBE_E_ARG, "max_drift_cells must be 0 (fixed steps) or in (0, 1]");
     if (n_steps < 1) return served_fail(CUBE_E_ARG, "n_steps must be >= 1");
     if (n_bins < 1 || n_bins > 2048) return served_fail(CUBE_E_ARG, "n_bins in [1, 2048]");
     if (!(epochs[0] > 0.0)) return served_fail(CUBE_E_ARG, "epochs[0] must be > 0");
@@ -282,13 +333,13 @@ cube_status cube_server_submit(cube_server* s, const cube_params* params, const 
     if (st != CUBE_OK) return st;
     if ((int64_t)(sb + wb) > s->budget) return served_fail(CUBE_E_NOMEM, "the request alone exceeds the budget");
     Request* r = new Request();
-    const size_t pinned = (size_t)3 * n_bins * 8 + 2 * sizeof(unsigned);
+    const size_t pinned = (size_t)3 * n_bins * 8 + 3 * sizeof(unsigned);
     if (cudaMallocHost((void**)&r->pk, pinned) != cudaSuccess) {
         delete r;
         return served_fail(CUBE_E_NOMEM, "pinned result memory");
     }
     r->flags = reinterpret_cast<unsigned*>(r->pk + 3 * (size_t)n_bins);
-    r->flags[0] = r->flags[1] = 0;
+    r->flags[0] = r->flags[1] = r->flags[2] = 0;
     r->ticket = s->next_ticket++;
     r->prm = *params;
     r->pos = pos;
@@ -296,6 +347,7 @@ cube_status cube_server_submit(cube_server* s, const cube_params* params, const 
     r->id = id;
     r->sigma = sigma;
     r->epochs.assign(epochs, epochs + n_steps + 1);
+    r->cells = max_drift_cells;
     r->n_bins = n_bins;
     r->state_bytes = sb;
     r->work_bytes = wb;
@@ -391,6 +443,7 @@ cube_status cube_server_release(cube_server* s, int64_t ticket) {
     }
     for (cudaEvent_t e : r->inflight) s->spare.push_back(e);
     if (r->done) cudaEventDestroy(r->done);
+    if (r->vmax_ev) cudaEventDestroy(r->vmax_ev);
     if (r->pk) cudaFreeHost(r->pk);
     s->reqs.erase(ticket);
     delete r;

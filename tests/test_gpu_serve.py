@@ -13,6 +13,8 @@ cube_server on several streams.
   releasing a request returns its state bytes.
 * Arguments: bad epochs, step counts and bins are refused; a request larger
   than the whole budget is refused with CUBE_E_NOMEM.
+* Velocity-limited steps: a request whose epochs are waypoints takes the
+  same steps, and gives the same particles, as the cube_next_epoch loop.
 """
 import dataclasses
 
@@ -197,5 +199,57 @@ def test_submit_rejects_bad_requests(cube):
         assert e.value.status == cube.CUBE_E_STATE
         cube.cube_server_drain(srv)
         cube.cube_server_release(srv, t)
+    finally:
+        cube.cube_server_destroy(srv)
+
+
+def test_adaptive_requests_equal_the_velocity_limited_run_alone(cube):
+    """max_drift_cells > 0: the server cuts every step as cube_next_epoch
+    does (fastest particle within half a coarse cell), reading the largest |p|
+    back asynchronously.  The finest-cell ensemble realisation (whose uniform
+    steps clamp a migration with 1-byte codes) completes, with the same steps
+    and the same particles as the cube_next_epoch loop on a plain context."""
+    ens = synth.ensemble_c4(64)
+    w = min(ens, key=lambda x: x.box / x.n_part_side)
+    w = dataclasses.replace(w, n_part_side=32, n_fine=64, box=w.box * 32 / w.n_part_side)
+    ic = synth.make_ics(w)
+    p = _params(cube, w)
+    targets = synth.uniform_schedule(w.a_init, w.a_final, w.n_steps)
+    n = w.n_particles
+    # alone
+    ctx = cube.cube_create(p, torch.cuda.current_stream())
+    try:
+        cube.cube_encode(ctx, ic.pos, ic.vel, ic.ids, w.a_init, ic.sigma_1d)
+        a, steps = w.a_init, 0
+        for t in targets[1:]:
+            while a < t:
+                a_to = cube.cube_next_epoch(ctx, t, 0.5)
+                cube.cube_pm_step(ctx, a, a_to)
+                a, steps = a_to, steps + 1
+        want = (np.empty((3, n), np.float32), np.empty((3, n), np.float32), np.empty(n, np.uint32))
+        cube.cube_decode(ctx, *want)
+    finally:
+        cube.cube_destroy(ctx)
+    srv = cube.cube_server_create(8 << 30, n_streams=2, max_running=4)
+    try:
+        host = (_pinned(ic.pos), _pinned(ic.vel), _pinned(ic.ids.view(np.int32)))
+        t = cube.cube_server_submit(srv, p, *host, ic.sigma_1d, targets, 4, max_drift_cells=0.5)
+        other = _mix()[1]                                   # a fixed-step request beside it
+        oic = synth.make_ics(other)
+        ohost = (_pinned(oic.pos), _pinned(oic.vel), _pinned(oic.ids.view(np.int32)))
+        t2 = cube.cube_server_submit(srv, _params(cube, other), *ohost, oic.sigma_1d,
+                                     synth.uniform_schedule(other.a_init, other.a_final, other.n_steps), 4)
+        cube.cube_server_drain(srv)
+        info = cube.cube_server_info(srv, t)
+        assert info.state == cube.CUBE_REQ_DONE, info.error
+        assert info.steps_enqueued == steps > w.n_steps and info.max_migration <= 1
+        assert cube.cube_server_info(srv, t2).state == cube.CUBE_REQ_DONE
+        got = (np.empty((3, n), np.float32), np.empty((3, n), np.float32), np.empty(n, np.uint32))
+        cube.cube_server_decode(srv, t, *got)
+        for g, e in zip(got, want):
+            assert np.array_equal(g, e)
+        with pytest.raises(cube.CubeError) as e:
+            cube.cube_server_submit(srv, p, *host, ic.sigma_1d, targets, 4, max_drift_cells=1.5)
+        assert e.value.status == cube.CUBE_E_ARG
     finally:
         cube.cube_server_destroy(srv)
