@@ -113,6 +113,20 @@ def peaks():
         return 6800.0, "fallback"
 
 
+def kernel_source_hash():
+    """First 16 hex digits of the SHA-256 of the device-code sources (the
+    kernel files, their shared header and declarations; host-only files such
+    as the C-ABI glue, the server and the tuner are left out)."""
+    import hashlib
+    src = os.path.join(ROOT, "paper_1712_06121_gb300", "csrc")
+    h = hashlib.sha256()
+    for f in sorted(os.listdir(src)):
+        if f.startswith("k_") or f in ("cube_common.cuh", "kernels.h"):
+            with open(os.path.join(src, f), "rb") as fh:
+                h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
 def measured_traffic(kernel, workload):
     """DRAM bytes per launch of `kernel` from the committed ncu summary, if it
     was taken on the current kernel source; else None."""
@@ -120,12 +134,7 @@ def measured_traffic(kernel, workload):
     path = os.path.join(ROOT, "profiles", f"dram_traffic_{workload}.txt")
     if not os.path.exists(path):
         return None
-    src = os.path.join(ROOT, "paper_1712_06121_gb300", "csrc")
-    h = hashlib.sha256()
-    for f in sorted(os.listdir(src)):
-        with open(os.path.join(src, f), "rb") as fh:
-            h.update(fh.read())
-    cur = h.hexdigest()[:16]
+    cur = kernel_source_hash()
     rec = {}
     with open(path) as f:
         for line in f:
@@ -554,6 +563,7 @@ def main():
     # end to end through the C ABI with pinned host buffers: H2D of the
     # particles, encode, one step, decode, D2H, every iteration
     e2e = None
+    e2e_ck = None
     if not args.no_e2e:
         pos_h = torch.from_numpy(ic.pos).pin_memory()
         vel_h = torch.from_numpy(ic.vel).pin_memory()
@@ -584,6 +594,34 @@ def main():
                "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
                "what": "per iteration: pinned host pos/vel/ids -> cube_encode -> cube_pm_step -> "
                        "cube_decode -> pinned host"}
+        # the same loop on the compressed store's checkpoint (Section 2.3.1) instead of float particles
+        ck = cube.cube_checkpoint_size(prm)
+        ck_in = torch.empty(ck, dtype=torch.uint8).pin_memory()
+        ck_out = torch.empty(ck, dtype=torch.uint8).pin_memory()
+        cube.cube_encode(ctx, pos_h, vel_h, ids_h, w.a_init, ic.sigma_1d)
+        cube.cube_pm_step(ctx, sch[0], sch[1])
+        cube.cube_checkpoint_save(ctx, ck_in)
+        for it in range(2):
+            cube.cube_checkpoint_load(ctx, ck_in)
+            cube.cube_pm_step(ctx, sch[1], sch[2])
+            cube.cube_checkpoint_save(ctx, ck_out)
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for it in range(n_e2e):
+            cube.cube_checkpoint_load(ctx, ck_in)
+            cube.cube_pm_step(ctx, sch[1], sch[2])
+            cube.cube_checkpoint_save(ctx, ck_out)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        te = torch.tensor([dt], dtype=torch.float64, device="cuda")
+        if dist:
+            dist.all_reduce(te, op=dist.ReduceOp.MAX)
+        e2e_ck = {"value": world * w.n_particles * n_e2e / float(te.item()), "unit": "particle-steps/s",
+                  "h2d_bytes_per_step": ck, "d2h_bytes_per_step": ck,
+                  "what": "per iteration: pinned host checkpoint of the compressed store -> cube_checkpoint_load "
+                          "-> cube_pm_step -> cube_checkpoint_save -> pinned host"}
     cube.cube_destroy(ctx)
     if rank != 0:
         if dist:
@@ -610,6 +648,7 @@ def main():
         "tile_load": "tma" if stats.features & 1 else "cp.async",
         "clocks": clk,
         "e2e": e2e,
+        "e2e_checkpoint": e2e_ck,
     }
     if world == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(w)

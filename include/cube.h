@@ -295,6 +295,36 @@ const char* cube_phase_name(int32_t phase);
 cube_status cube_counts_to_offsets_noalloc(const uint32_t* counts, int64_t n_cells, uint32_t* offsets,
                                            void* cuda_stream);
 
+/* ---------------------------------------------------------------- checkpoint */
+
+/* The compressed store as one buffer -- the paper's checkpoint {rho_c, v_c,
+   chi_d, nu_d, I_P} (Section 2.3.1), plus the codec scale and the leapfrog
+   epochs needed to continue.  Layout (little-endian): a 64-byte header
+   {"CUBECKP1", n_fine, ratio, n_particles, x_bytes, v_bytes, id_bytes,
+   brick, a, a_p, sigma}, then 16-byte aligned sections: counts u32[N_c^3],
+   v_c f32[3][N_c^3], chi [3][N] and nu [3][N] codes of x_bytes / v_bytes,
+   ids u32[N] when id_bytes = 4.  The uncompressed store (x_bytes = 4)
+   stores positions f32[3][N] and momenta f32[3][N] instead of the first four
+   sections.  12 bytes per particle for x1v1 with ids (6 of codes, 4 of
+   ids, 2 of coarse fields at 8 particles per coarse cell), against 28 for
+   float positions, momenta and ids.
+
+   cube_checkpoint_size: buffer bytes for these parameters (no device needed).
+   cube_checkpoint_save: writes the current store into buf (host or device,
+   caller-owned, cube_checkpoint_size bytes); synchronises; reports latched
+   device errors like cube_decode.
+   cube_checkpoint_load: replaces the context's store with the checkpoint in
+   buf (host or device); the header's parameters must equal the context's
+   (CUBE_E_ARG otherwise, as for a wrong magic, non-positive epochs or codec
+   scale, or counts that do not add up to n_particles); rebuilds the offsets
+   (scan of the counts) and the codec tables; synchronises.  The next
+   cube_pm_step continues from the saved epochs a and a_p.  A load that
+   fails after the header checks leaves the context without a store
+   (CUBE_E_STATE until the next encode or load). */
+cube_status cube_checkpoint_size(const cube_params* params, int64_t* bytes);
+cube_status cube_checkpoint_save(cube_ctx* ctx, void* buf);
+cube_status cube_checkpoint_load(cube_ctx* ctx, const void* buf);
+
 /* ---------------------------------------------------------------- autotuning */
 
 /* Picks the storage-order brick (cube_params.brick: 1, 2 or 4 coarse cells)

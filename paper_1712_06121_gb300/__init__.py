@@ -87,6 +87,9 @@ _sigs = {
     "cube_counts_to_offsets_noalloc": ([_P, ctypes.c_int64, _P, _P], ctypes.c_int),
     "cube_max_speed": ([_P, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
     "cube_next_epoch": ([_P, ctypes.c_double, ctypes.c_double, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
+    "cube_checkpoint_size": ([ctypes.POINTER(cube_params), ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
+    "cube_checkpoint_save": ([_P, _P], ctypes.c_int),
+    "cube_checkpoint_load": ([_P, _P], ctypes.c_int),
     "cube_autotune_brick": ([ctypes.POINTER(cube_params), _P, _P, ctypes.c_double, ctypes.c_double, ctypes.c_int32,
                              _P, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
     "cube_server_sizes": ([ctypes.POINTER(cube_params), ctypes.POINTER(ctypes.c_int64),
@@ -239,6 +242,20 @@ def cube_phase_name(phase):
 
 __all__ = [n for n in _sigs] + ["make_params", "cube_params", "cube_state", "cube_stats", "CubeError",
                                 "LIB_PATH", "CUBE_GRAD_FD4", "CUBE_PHASES"]
+
+
+def cube_checkpoint_size(params):
+    v = ctypes.c_int64()
+    _check(_lib.cube_checkpoint_size(ctypes.byref(params), ctypes.byref(v)))
+    return v.value
+
+
+def cube_checkpoint_save(ctx, buf):
+    _check(_lib.cube_checkpoint_save(ctx, _ptr(buf)))
+
+
+def cube_checkpoint_load(ctx, buf):
+    _check(_lib.cube_checkpoint_load(ctx, _ptr(buf)))
 
 
 def cube_autotune_brick(params, pos, vel, a, sigma, n_steps=5, stream=None):

@@ -169,6 +169,7 @@ struct cube_ctx {
     // host-pointer staging (lazily allocated when the work slab's region is too small)
     void* stage = nullptr;
     size_t stage_bytes = 0;
+    double stage_sigma = 0.0;           // host copy of a loaded codec scale (source of its upload)
     // device memory in two slabs: the state kept between calls (store, codec
     // tables, small results) and the work buffers of one call (mesh, ghosted
     // Phi, histograms, scan scratch, host staging).  A standalone context owns
@@ -822,6 +823,139 @@ cube_status cube_next_epoch(cube_ctx* c, double a_max, double cells, double* a_t
     if (s != CUBE_OK) return s;
     *a_to = epoch_limit(c, p, a_max, cells);
     return *a_to > c->a ? CUBE_OK : fail(CUBE_E_ARG, "no step keeps the fastest particle within the limit");
+}
+
+// ---------------------------------------------------------------- checkpoint (Section 2.3.1)
+// Layout: a 64-byte header, then 16-byte aligned sections.  Compressed store:
+// counts u32[Ncc] (rho_c), v_c f32[3][Ncc], chi [3][N] codes, nu [3][N]
+// codes, ids u32[N] (id_bytes 4).  Uncompressed store: positions f32[3][N],
+// momenta f32[3][N], ids.
+namespace {
+
+struct CkptHeader {
+    char magic[8];                       // "CUBECKP1"
+    int32_t n_fine, ratio;
+    int64_t n_particles;
+    int32_t x_bytes, v_bytes, id_bytes, brick;
+    double a, a_p, sigma;
+};
+static_assert(sizeof(CkptHeader) == 64, "checkpoint header is 64 bytes");
+
+size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
+
+// byte offsets of the sections (sec[0..4]) and the total
+size_t ckpt_layout(const Geo& g, bool raw, int id_bytes, size_t sec[5]) {
+    const size_t N = (size_t)g.Np, Ncc = (size_t)g.Ncc;
+    size_t off = sizeof(CkptHeader);
+    const size_t sz[5] = {raw ? 12 * N : 4 * Ncc, raw ? 12 * N : 12 * Ncc, raw ? 0 : 3 * N * g.nchi,
+                          raw ? 0 : 3 * N * g.nnu, id_bytes ? 4 * N : 0};
+    for (int i = 0; i < 5; ++i) {
+        sec[i] = off;
+        off = align16(off + sz[i]);
+    }
+    return off;
+}
+
+}  // namespace
+
+cube_status cube_checkpoint_size(const cube_params* params, int64_t* bytes) {
+    if (!bytes) return fail(CUBE_E_ARG, "NULL argument");
+    int B = 0;
+    cube_status s = check_params(params, &B);
+    if (s != CUBE_OK) return s;
+    cube_ctx c;
+    init_geo(&c, params, B);
+    size_t sec[5];
+    *bytes = (int64_t)ckpt_layout(c.g, c.raw, params->id_bytes, sec);
+    return CUBE_OK;
+}
+
+cube_status cube_checkpoint_save(cube_ctx* c, void* buf) {
+    if (!c || !buf) return fail(CUBE_E_ARG, "NULL argument");
+    if (!c->encoded) return fail(CUBE_E_STATE, "no store: call cube_encode first");
+    const Geo& g = c->g;
+    const int k = c->cur;
+    size_t sec[5];
+    ckpt_layout(g, c->raw, c->P.id_bytes, sec);
+    CkptHeader h{};
+    std::memcpy(h.magic, "CUBECKP1", 8);
+    h.n_fine = g.N;
+    h.ratio = g.R;
+    h.n_particles = g.Np;
+    h.x_bytes = c->raw ? 4 : g.nchi;
+    h.v_bytes = c->raw ? 4 : g.nnu;
+    h.id_bytes = c->P.id_bytes;
+    h.brick = g.B;
+    h.a = c->a;
+    h.a_p = c->a_p;
+    h.sigma = 0.0;
+    if (!c->raw) CK(cudaMemcpyAsync(&h.sigma, c->codec[k].sigma, 8, cudaMemcpyDeviceToHost, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    char* b = (char*)buf;
+    const size_t N = (size_t)g.Np, Ncc = (size_t)g.Ncc;
+    CK(cudaMemcpyAsync(b, &h, sizeof(h), cudaMemcpyDefault, c->st));
+    if (c->raw) {
+        CK(cudaMemcpyAsync(b + sec[0], c->chi[0], 12 * N, cudaMemcpyDefault, c->st));
+        CK(cudaMemcpyAsync(b + sec[1], c->nu[0], 12 * N, cudaMemcpyDefault, c->st));
+    } else {
+        CK(cudaMemcpyAsync(b + sec[0], c->counts[k], 4 * Ncc, cudaMemcpyDefault, c->st));
+        CK(cudaMemcpyAsync(b + sec[1], c->vc[k], 12 * Ncc, cudaMemcpyDefault, c->st));
+        CK(cudaMemcpyAsync(b + sec[2], c->chi[k], 3 * N * g.nchi, cudaMemcpyDefault, c->st));
+        CK(cudaMemcpyAsync(b + sec[3], c->nu[k], 3 * N * g.nnu, cudaMemcpyDefault, c->st));
+    }
+    if (c->P.id_bytes) CK(cudaMemcpyAsync(b + sec[4], c->id[k], 4 * N, cudaMemcpyDefault, c->st));
+    return latched(c);
+}
+
+cube_status cube_checkpoint_load(cube_ctx* c, const void* buf) {
+    if (!c || !buf) return fail(CUBE_E_ARG, "NULL argument");
+    const Geo& g = c->g;
+    CkptHeader h{};
+    CK(cudaMemcpyAsync(&h, buf, sizeof(h), cudaMemcpyDefault, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    if (std::memcmp(h.magic, "CUBECKP1", 8) != 0) return fail(CUBE_E_ARG, "not a checkpoint (magic)");
+    if (h.n_fine != g.N || h.ratio != g.R || h.n_particles != g.Np || h.brick != g.B ||
+        h.x_bytes != (c->raw ? 4 : g.nchi) || h.v_bytes != (c->raw ? 4 : g.nnu) || h.id_bytes != c->P.id_bytes)
+        return fail(CUBE_E_ARG, "checkpoint parameters differ from the context's");
+    if (!(h.a > 0.0) || !(h.a_p > 0.0) || (!c->raw && !(h.sigma > 0.0)))
+        return fail(CUBE_E_ARG, "checkpoint epochs or codec scale invalid");
+    size_t sec[5];
+    ckpt_layout(g, c->raw, c->P.id_bytes, sec);
+    const char* b = (const char*)buf;
+    const size_t N = (size_t)g.Np, Ncc = (size_t)g.Ncc;
+    const int k = c->cur;
+    if (c->raw) {
+        CK(cudaMemcpyAsync(c->chi[0], b + sec[0], 12 * N, cudaMemcpyDefault, c->st));
+        CK(cudaMemcpyAsync(c->nu[0], b + sec[1], 12 * N, cudaMemcpyDefault, c->st));
+    } else {
+        CK(cudaMemcpyAsync(c->counts[k], b + sec[0], 4 * Ncc, cudaMemcpyDefault, c->st));
+        CK(cudaMemcpyAsync(c->vc[k], b + sec[1], 12 * Ncc, cudaMemcpyDefault, c->st));
+        CK(cudaMemcpyAsync(c->chi[k], b + sec[2], 3 * N * g.nchi, cudaMemcpyDefault, c->st));
+        CK(cudaMemcpyAsync(c->nu[k], b + sec[3], 3 * N * g.nnu, cudaMemcpyDefault, c->st));
+        exclusive_scan(c->counts[k], c->offsets[k], g.Ncc, c->scan_tmp, c->st);
+        c->stage_sigma = h.sigma;
+        CK(cudaMemcpyAsync(c->codec[k].sigma, &c->stage_sigma, 8, cudaMemcpyHostToDevice, c->st));
+        launch_codec_tables(g.nulim, c->tanv, c->tanh_, c->codec[k], c->st);
+        c->launches += 4 + 1;
+    }
+    if (c->P.id_bytes) CK(cudaMemcpyAsync(c->id[k], b + sec[4], 4 * N, cudaMemcpyDefault, c->st));
+    CK(cudaMemsetAsync(c->flags, 0, 4, c->st));
+    CK(cudaMemsetAsync(c->maxmig, 0, 4, c->st));
+    unsigned total = (unsigned)g.Np;
+    if (!c->raw) CK(cudaMemcpyAsync(&total, c->offsets[k] + g.Ncc, 4, cudaMemcpyDeviceToHost, c->st));
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(c->st));
+    c->encoded = true;
+    c->a = h.a;
+    c->a_p = h.a_p;
+    c->steps = 0;
+    c->dbg_valid = false;
+    c->timed = false;
+    if (total != (unsigned)g.Np) {
+        c->encoded = false;
+        return fail(CUBE_E_ARG, "checkpoint cell counts do not add up to the particle count");
+    }
+    return CUBE_OK;
 }
 
 cube_status cube_state_view(cube_ctx* c, cube_state* out) {
