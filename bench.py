@@ -113,6 +113,18 @@ def peaks():
         return 6800.0, "fallback"
 
 
+def max_over_ranks(x, dist):
+    """The largest x over all ranks of the process group (x itself without
+    one): the job's time is its slowest rank's."""
+    if dist is None:
+        return float(x)
+    import torch
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def kernel_source_hash():
     """First 16 hex digits of the SHA-256 of the device-code sources (the
     kernel files, their shared header and declarations; host-only files such
@@ -554,10 +566,7 @@ def main():
     launches = stats.kernel_launches - launches0
     phase_ms, phase_kernels, nst = cube.cube_profile_read(ctx)
     cube.cube_profile(ctx, 0)
-    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-    if dist:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
+    ms_max = max_over_ranks(ms, dist)
     value = world * w.n_particles * args.steps / (ms_max / 1e3)
 
     # end to end through the C ABI with pinned host buffers: H2D of the
@@ -586,11 +595,8 @@ def main():
             cube.cube_decode(ctx, out_p, out_v, out_i)
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
-        te = torch.tensor([dt], dtype=torch.float64, device="cuda")
-        if dist:
-            dist.all_reduce(te, op=dist.ReduceOp.MAX)
         nbytes = 28 * w.n_particles
-        e2e = {"value": world * w.n_particles * n_e2e / float(te.item()), "unit": "particle-steps/s",
+        e2e = {"value": world * w.n_particles * n_e2e / max_over_ranks(dt, dist), "unit": "particle-steps/s",
                "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
                "what": "per iteration: pinned host pos/vel/ids -> cube_encode -> cube_pm_step -> "
                        "cube_decode -> pinned host"}
@@ -615,10 +621,7 @@ def main():
             cube.cube_checkpoint_save(ctx, ck_out)
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
-        te = torch.tensor([dt], dtype=torch.float64, device="cuda")
-        if dist:
-            dist.all_reduce(te, op=dist.ReduceOp.MAX)
-        e2e_ck = {"value": world * w.n_particles * n_e2e / float(te.item()), "unit": "particle-steps/s",
+        e2e_ck = {"value": world * w.n_particles * n_e2e / max_over_ranks(dt, dist), "unit": "particle-steps/s",
                   "h2d_bytes_per_step": ck, "d2h_bytes_per_step": ck,
                   "what": "per iteration: pinned host checkpoint of the compressed store -> cube_checkpoint_load "
                           "-> cube_pm_step -> cube_checkpoint_save -> pinned host"}
