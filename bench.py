@@ -376,8 +376,31 @@ def run_ensemble(args):
     make_ctxs(False)
     for c in ctxs:
         cube.cube_destroy(c)
+
+    # the same realisations through cube_server: velocity-limited steps with
+    # the largest |p| read back asynchronously, so no host wait per step
+    def served():
+        srv = cube.cube_server_create(64 << 30, args.streams, len(ens))
+        try:
+            tickets = [cube.cube_server_submit(srv, params(w, tuned[w.n_part_side]), d[0], d[1], d[2], ic.sigma_1d,
+                                               sch, 8, max_drift_cells=0.5)
+                       for w, ic, d, sch in zip(ens, ics, dev, scheds)]
+            cube.cube_server_drain(srv)
+            infos = [cube.cube_server_info(srv, t) for t in tickets]
+            for t in tickets:
+                cube.cube_server_release(srv, t)
+        finally:
+            cube.cube_server_destroy(srv)
+        assert all(i.state == cube.CUBE_REQ_DONE for i in infos)
+        return infos
+    served()                                                # warm-up pass
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    infos = served()
+    t_srv = time.perf_counter() - t0
+    times[("served", True)] = t_srv
     sizes = sorted({w.n_part_side for w in ens})
-    best = times[(True, True)]
+    best = min(times[(True, True)], t_srv)
     print(json.dumps({
         "metric": "sims/s", "value": len(ens) / best, "unit": "sims/s", "n_gpus": 1,
         "higher_is_better": True, "dtype": "f32", "data": "synthetic (seeded GRF Zel'dovich ICs)",
@@ -387,6 +410,10 @@ def run_ensemble(args):
         "sequential": {"value": len(ens) / times[(False, False)], "unit": "sims/s",
                        "what": "the same contexts run one after another, default bricks"},
         "concurrent_default_bricks": {"value": len(ens) / times[(True, False)], "unit": "sims/s"},
+        "concurrent_tuned_bricks": {"value": len(ens) / times[(True, True)], "unit": "sims/s"},
+        "served": {"value": len(ens) / t_srv, "unit": "sims/s", "steps": int(sum(i.steps_enqueued for i in infos)),
+                   "what": "cube_server, all realisations admitted at once, velocity-limited steps with "
+                           "asynchronous max-|p| read-back (no host wait per step), tuned bricks"},
         "tuned_bricks": {str(k): v for k, v in sorted(tuned.items())},
         "tuner_ms_per_step_b1_b2_b4": {str(k): [round(x, 4) for x in v] for k, v in sorted(tune_ms.items())},
         "steps_total": int(sum(nsteps)),
