@@ -29,7 +29,6 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-PHASE_BYTES_DOC = "algorithmic bytes per launch: see DESIGN.md, section Measurement"
 
 
 def parse():
@@ -63,8 +62,10 @@ def schedule(w, n):
 
 
 def phase_bytes(w, geo):
-    """Algorithmic HBM bytes per launch of each traced kernel (minimum the
-    operation must move; the model is stated in the design doc)."""
+    """Algorithmic HBM bytes per launch of each traced kernel: the minimum
+    the operation must move (each input read once, each output written
+    once), from the particle count, mesh and coarse-grid sizes, code widths
+    and brick geometry."""
     N = w.n_fine
     Np = w.n_particles
     Nm = N ** 3

@@ -19,7 +19,7 @@ argsort and bincount as library steps:
              update_vp, Section 2.3.3), plus an uncompressed FP64 mode
   pp.py      brute-force pairwise force (used only to pin mesh.py)
 
-Readings of passages the paper leaves open are listed in the design doc; every
-function states the one it takes.
+Where the paper leaves a passage open, the function that depends on it
+states the reading it takes.
 """
 from . import codec, layout, mesh, cosmo, pm, pp  # noqa: F401
