@@ -178,6 +178,36 @@ cube_status cube_max_speed(cube_ctx* ctx, double* p_max);
    Errors: CUBE_E_ARG (a_max <= a, cells outside (0, 1]), CUBE_E_STATE. */
 cube_status cube_next_epoch(cube_ctx* ctx, double a_max, double cells, double* a_to);
 
+/* Largest force component on the mesh: max over nodes and axes of the 4th-
+   order gradient -(8 (Phi(+1) - Phi(-1)) - (Phi(+2) - Phi(-2))) / 12 of the
+   potential of the context's last step or cube_potential call (momentum per
+   unit kick integral, the units of cube_pm_step's kick).  Each particle's
+   force component interpolates these node values with CIC weights, so f_max
+   bounds every particle's.  0 before any step or cube_potential.  One pass
+   over the mesh (about 0.1 ms at 512^3); synchronises.
+   Errors: CUBE_E_STATE (no store). */
+cube_status cube_max_force(cube_ctx* ctx, double* f_max);
+
+/* The time step of Section 2.3.3's timestep: the increment is limited by the
+   particles' velocities, their accelerations and the cosmic expansion.
+   drift_cells in (0, 1]: the fastest particle's drift over the step, with
+   its momentum kicked by the largest force component (cube_max_force),
+   (p_max + F_max int_{a_p}^{(a + a_to)/2} da / (a^2 E)) int_a^{a_to} da / (a^3 E),
+   stays within drift_cells coarse cells (F_max = 0 before any step);
+   max_dlna >= 0: ln(a_to / a) <= max_dlna (0: no expansion limit). */
+typedef struct {
+    double drift_cells;
+    double max_dlna;
+} cube_step_limits;
+
+/* The largest a_to <= a_max within every limit (bisection on the host's
+   integrals; synchronises like cube_next_epoch).  binding (nullable): 0 if
+   a_max, 1 if the drift, 2 if the expansion limit set a_to.
+   Errors: CUBE_E_ARG (limits out of range, a_max not after the store's
+   epoch, no positive step possible), CUBE_E_STATE before cube_encode. */
+cube_status cube_next_epoch_limited(cube_ctx* ctx, double a_max, const cube_step_limits* lim, double* a_to,
+                                    int32_t* binding);
+
 /* ---------------------------------------------------------------- inspection */
 
 typedef struct {

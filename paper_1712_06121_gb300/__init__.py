@@ -54,6 +54,10 @@ class cube_stats(ctypes.Structure):
                 ("last_step_ms", ctypes.c_double), ("kernel_launches", ctypes.c_int64),
                 ("features", ctypes.c_uint32)]
 
+
+class cube_step_limits(ctypes.Structure):
+    _fields_ = [("drift_cells", ctypes.c_double), ("max_dlna", ctypes.c_double)]
+
 CUBE_PHASES = 12
 
 CUBE_REQ_QUEUED, CUBE_REQ_RUNNING, CUBE_REQ_DONE, CUBE_REQ_FAILED = range(4)
@@ -87,6 +91,9 @@ _sigs = {
     "cube_counts_to_offsets_noalloc": ([_P, ctypes.c_int64, _P, _P], ctypes.c_int),
     "cube_max_speed": ([_P, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
     "cube_next_epoch": ([_P, ctypes.c_double, ctypes.c_double, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
+    "cube_max_force": ([_P, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
+    "cube_next_epoch_limited": ([_P, ctypes.c_double, ctypes.POINTER(cube_step_limits), ctypes.POINTER(ctypes.c_double),
+                                 ctypes.POINTER(ctypes.c_int32)], ctypes.c_int),
     "cube_checkpoint_size": ([ctypes.POINTER(cube_params), ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
     "cube_checkpoint_save": ([_P, _P], ctypes.c_int),
     "cube_checkpoint_load": ([_P, _P], ctypes.c_int),
@@ -195,6 +202,23 @@ def cube_next_epoch(ctx, a_max, cells=0.5):
     v = ctypes.c_double()
     _check(_lib.cube_next_epoch(ctx, float(a_max), float(cells), ctypes.byref(v)))
     return v.value
+
+
+def cube_max_force(ctx):
+    v = ctypes.c_double()
+    _check(_lib.cube_max_force(ctx, ctypes.byref(v)))
+    return v.value
+
+
+def cube_next_epoch_limited(ctx, a_max, drift_cells=0.5, max_dlna=0.0):
+    """(a_to, binding): the largest a_to <= a_max within the drift limit (the
+    fastest particle, kicked by the largest force of cube_max_force) and
+    ln(a_to / a) <= max_dlna; binding 0 a_max, 1 drift, 2 expansion."""
+    lim = cube_step_limits(float(drift_cells), float(max_dlna))
+    out = ctypes.c_double()
+    why = ctypes.c_int32()
+    _check(_lib.cube_next_epoch_limited(ctx, float(a_max), ctypes.byref(lim), ctypes.byref(out), ctypes.byref(why)))
+    return out.value, why.value
 
 
 def cube_density(ctx, rho):

@@ -158,6 +158,7 @@ struct cube_ctx {
     int npart = 0;
     unsigned* flags = nullptr;
     int* maxmig = nullptr;
+    bool phig_valid = false;        // phig holds the potential of the last step or cube_potential call
     unsigned* scan_tmp = nullptr;
     long long* mom = nullptr;
     unsigned* vmax = nullptr;       // largest |p| of the store, float bits
@@ -519,6 +520,7 @@ static cube_status raw_encode(cube_ctx* c, const float* pos, const float* vel, c
     if (sync) CK(cudaStreamSynchronize(c->st));
     c->cur = 0;
     c->encoded = true;
+    c->phig_valid = false;
     c->a = a;
     c->a_p = a;
     c->steps = 0;
@@ -576,6 +578,7 @@ static cube_status encode_impl(cube_ctx* c, const float* pos, const float* vel, 
     CK(cudaGetLastError());
     if (sync) CK(cudaStreamSynchronize(c->st));
     c->encoded = true;
+    c->phig_valid = false;
     c->a = a;
     c->a_p = a;
     c->steps = 0;
@@ -649,6 +652,7 @@ cube_status cube_pm_step(cube_ctx* c, double a_from, double a_to) {
         mark(c, 0);
         mark(c, 1);
         mesh_potential(c);
+        c->phig_valid = true;
         launch_raw_kick_drift(g, (float*)c->chi[0], (float*)c->nu[0], c->phig, kick,
                               (float)c->cosmo.drift(a_from, a_to), c->flags, c->st);
         for (int b = 8; b <= 12; ++b) mark(c, b);
@@ -676,6 +680,7 @@ cube_status cube_pm_step(cube_ctx* c, double a_from, double a_to) {
     CK(cudaMemsetAsync(c->maxmig, 0, 8, c->st));     // max migration, crowded-brick count
     mark(c, 1);
     mesh_potential(c);
+    c->phig_valid = true;
     StepScratch w{c->counts[kn], c->vsum, c->ghost, c->part, c->flags, c->maxmig, c->maxmig + 1};
     DriftDebug dbg{c->keep ? c->dbg_cell : nullptr, c->dbg_u, c->dbg_p};
     launch_passA(g, c->store(k), c->phig, c->tma ? &c->phig_map : nullptr, c->codec[k], kick, dc, w, dbg, c->st);
@@ -813,6 +818,62 @@ static double epoch_limit(const cube_ctx* c, double p, double a_max, double cell
     return lo;
 }
 
+cube_status cube_max_force(cube_ctx* c, double* f_max) {
+    if (!c || !f_max) return fail(CUBE_E_ARG, "NULL argument");
+    if (!c->encoded) return fail(CUBE_E_STATE, "no store: call cube_encode first");
+    *f_max = 0.0;
+    if (!c->phig_valid) return CUBE_OK;
+    launch_grad_max(c->phig, c->g.N, c->vmax, c->st);
+    c->launches += 1;
+    unsigned bits = 0;
+    CK(cudaMemcpyAsync(&bits, c->vmax, 4, cudaMemcpyDeviceToHost, c->st));
+    cube_status s = latched(c);
+    float f;
+    std::memcpy(&f, &bits, 4);
+    *f_max = f;
+    return s;
+}
+
+cube_status cube_next_epoch_limited(cube_ctx* c, double a_max, const cube_step_limits* lim, double* a_to,
+                                    int32_t* binding) {
+    if (!c || !a_to || !lim) return fail(CUBE_E_ARG, "NULL argument");
+    if (!c->encoded) return fail(CUBE_E_STATE, "no store: call cube_encode first");
+    if (!(a_max > c->a)) return fail(CUBE_E_ARG, "a_max must exceed the store's epoch");
+    if (!(lim->drift_cells > 0.0 && lim->drift_cells <= 1.0)) return fail(CUBE_E_ARG, "drift_cells must be in (0, 1]");
+    if (!(lim->max_dlna >= 0.0)) return fail(CUBE_E_ARG, "max_dlna must be >= 0");
+    double p = 0.0, f = 0.0;
+    cube_status s = cube_max_speed(c, &p);
+    if (s == CUBE_OK) s = cube_max_force(c, &f);
+    if (s != CUBE_OK) return s;
+    const double a0 = c->a, limit = lim->drift_cells * c->g.R;
+    // expansion: Delta ln a <= max_dlna
+    double hi = a_max;
+    int why = 0;
+    if (lim->max_dlna > 0.0 && a0 * std::exp(lim->max_dlna) < hi) {
+        hi = a0 * std::exp(lim->max_dlna);
+        why = 2;
+    }
+    // drift of the fastest particle after the kick of the largest force, per axis:
+    // (p_max + F_max int_{a_p}^{a_mid} da / (a^2 E)) int_a^{a_to} da / (a^3 E), increasing in a_to
+    auto drift = [&](double at) {
+        return (p + f * c->cosmo.kick(c->a_p, 0.5 * (a0 + at))) * c->cosmo.drift(a0, at);
+    };
+    if (drift(hi) <= limit) {
+        *a_to = hi;
+    } else {
+        double lo = a0;
+        for (int it = 0; it < 100 && hi - lo > 1e-15 * hi; ++it) {
+            const double mid = 0.5 * (lo + hi);
+            if (drift(mid) <= limit) lo = mid;
+            else hi = mid;
+        }
+        *a_to = lo;
+        why = 1;
+    }
+    if (binding) *binding = why;
+    return *a_to > a0 ? CUBE_OK : fail(CUBE_E_ARG, "no step keeps the fastest particle within the limit");
+}
+
 cube_status cube_next_epoch(cube_ctx* c, double a_max, double cells, double* a_to) {
     if (!c || !a_to) return fail(CUBE_E_ARG, "NULL argument");
     if (!c->encoded) return fail(CUBE_E_STATE, "no store: call cube_encode first");
@@ -946,6 +1007,7 @@ cube_status cube_checkpoint_load(cube_ctx* c, const void* buf) {
     CK(cudaGetLastError());
     CK(cudaStreamSynchronize(c->st));
     c->encoded = true;
+    c->phig_valid = false;
     c->a = h.a;
     c->a_p = h.a_p;
     c->steps = 0;
@@ -1047,6 +1109,7 @@ cube_status cube_potential(cube_ctx* c, float* phi) {
     const int saved = c->prof_max;
     c->prof_max = 0;                    // not a step: keep it out of the trace
     mesh_potential(c);
+    c->phig_valid = true;
     c->prof_max = saved;
     return mesh_out(c, phi, true);
 }

@@ -654,6 +654,26 @@ __global__ void __launch_bounds__(FFT_T, N <= 512 ? 2 : 1) k_fft_z(float* mesh, 
     }
 }
 
+// ------------------------------------------------------------ largest force component
+// max over mesh nodes and axes of |8 (f(+1) - f(-1)) - (f(+2) - f(-2))| / 12 of
+// the ghosted potential (the FD4 gradient the force gather interpolates), as
+// the bits of a non-negative float
+__global__ void k_grad_max(const float* __restrict__ phig, int N, unsigned* __restrict__ out_bits) {
+    const int64_t n3 = (int64_t)N * N * N;
+    const int64_t sy = phig_nx(N), sz = sy * phig_ny(N);
+    float m = 0.0f;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n3; t += (int64_t)gridDim.x * blockDim.x) {
+        const int x = (int)(t % N), y = (int)((t / N) % N), z = (int)(t / ((int64_t)N * N));
+        const float* c = phig + phig_index(N, x, y, z);
+        const float gx = 8.0f * (c[1] - c[-1]) - (c[2] - c[-2]);
+        const float gy = 8.0f * (c[sy] - c[-sy]) - (c[2 * sy] - c[-2 * sy]);
+        const float gz = 8.0f * (c[sz] - c[-sz]) - (c[2 * sz] - c[-2 * sz]);
+        m = fmaxf(m, fmaxf(fabsf(gx), fmaxf(fabsf(gy), fabsf(gz))));
+    }
+    const unsigned b = __reduce_max_sync(0xffffffffu, __float_as_uint(m / 12.0f));
+    if ((threadIdx.x & 31) == 0 && b) atomicMax(out_bits, b);
+}
+
 // ------------------------------------------------------------ power spectrum
 __global__ void k_pk_bin(const float* __restrict__ mesh, int N, int S, int nbins, double pfac, double kfund,
                          const double* __restrict__ wpk, double* __restrict__ part) {
@@ -813,6 +833,11 @@ void launch_pk_bin(const FftPlan& p, const float* mesh, int S, int nbins, double
 
 void launch_pk_reduce(const double* part, int nblocks, int nbins, double* k, double* pk, double* nm, cudaStream_t st) {
     k_pk_reduce<<<(nbins + 127) / 128, 128, 0, st>>>(part, nblocks, nbins, k, pk, nm);
+}
+
+void launch_grad_max(const float* phig, int N, unsigned* out_bits, cudaStream_t st) {
+    cudaMemsetAsync(out_bits, 0, sizeof(unsigned), st);
+    k_grad_max<<<4 * 152, 256, 0, st>>>(phig, N, out_bits);
 }
 
 void launch_unpad_phig(const float* phig, int N, float* out, cudaStream_t st) {

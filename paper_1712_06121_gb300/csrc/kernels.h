@@ -143,6 +143,10 @@ void launch_pk_bin(const FftPlan& p, const float* mesh, int S, int nbins, double
 void launch_pk_reduce(const double* part, int nblocks, int nbins, double* k, double* pk, double* nm,
                       cudaStream_t st);
 void launch_unpad(const float* mesh, int N, int S, float* out, cudaStream_t st);
+// largest |component| of the FD4 gradient / 12 of the ghosted potential over
+// all mesh nodes (float bits): an upper bound of every particle's force
+// component, which the gather interpolates from these values with CIC weights
+void launch_grad_max(const float* phig, int N, unsigned* out_bits, cudaStream_t st);
 void launch_unpad_phig(const float* phig, int N, float* out, cudaStream_t st);
 
 }  // namespace cube

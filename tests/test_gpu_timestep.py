@@ -1,4 +1,4 @@
-"""Step-size control (cube_max_speed, cube_next_epoch).
+"""Step-size control (cube_max_speed, cube_next_epoch, cube_next_epoch_limited).
 
 cube_max_speed equals the largest |p| of the decoded momenta (the same FP32
 values cube_decode returns); cube_next_epoch's epoch makes the fastest
@@ -106,5 +106,58 @@ def test_adaptive_steps_keep_every_move_within_a_cell(cube):
         st = cube.cube_stats_get(ctx)                    # raises if a migration was clamped
         assert st.max_migration <= 1 and st.a == w.a_final
         assert steps >= w.n_steps
+    finally:
+        cube.cube_destroy(ctx)
+
+
+def test_limited_epoch_accounts_for_force_and_expansion(cube):
+    """cube_max_force and cube_next_epoch_limited (Section 2.3.3: velocity,
+    acceleration and expansion limits).  The force bound equals the largest
+    FD4 gradient component of the oracle's FP64 potential of the same store
+    (1e-4) and bounds the oracle's particle forces; the returned epoch puts
+    the kicked fastest particle's drift (p_max + F_max K(a_p, a_mid)) D(a, a_to)
+    exactly at the limit when that binds (oracle integrals, 1e-9), is
+    a * exp(max_dlna) when expansion binds, and equals cube_next_epoch before
+    any step (no potential yet: F_max = 0)."""
+    from oracle import mesh, pm
+    from gpu_util import oracle_params, read_store
+    w = dict_replace(synth.WORKLOADS["pm256"], n_part_side=32, n_fine=64, box=60.0)
+    ic = synth.make_ics(w)
+    om, ol, _ = w.omega()
+    ctx = _ctx(cube, w, 1, 1)
+    try:
+        # the ICs' momenta scaled to those of a later epoch, so that the limits bind
+        cube.cube_encode(ctx, ic.pos, ic.vel * 200.0, ic.ids, 0.3, ic.sigma_1d * 200.0)
+        cells = 0.05
+        assert cube.cube_max_force(ctx) == 0.0
+        a_v = cube.cube_next_epoch(ctx, 1.0, cells)
+        a_l, why = cube.cube_next_epoch_limited(ctx, 1.0, cells, 0.0)
+        assert a_l == a_v < 1.0 and why == 1
+        g = read_store(cube, ctx)
+        prm = cube.make_params(64, 32 ** 3, box=w.box, omega_m=om, omega_l=ol)
+        st = pm.Store(oracle_params(pm, prm, g["brick"]), g["counts"], g["vc"], g["chi"], g["nu"], g["ids"],
+                      g["sigma"], g["a"], g["a_p"])
+        ref = pm.step(st, 0.3, 0.31, keep_drifted=True)
+        cube.cube_pm_step(ctx, 0.3, 0.31)
+        f = cube.cube_max_force(ctx)
+        phi = mesh.potential(pm.density(st), om, prm.deconv_power)
+        want = max(float(np.max(np.abs(gr))) for gr in mesh.fd4_gradient(phi))
+        assert f == pytest.approx(want, rel=1e-4)
+        assert f >= float(np.max(np.abs(ref.extra["force"]))) * (1 - 1e-4)
+        s = cube.cube_stats_get(ctx)
+        p = cube.cube_max_speed(ctx)
+        a0, ap = s.a, s.a_p
+        a_to, why = cube.cube_next_epoch_limited(ctx, 1.0, cells, 0.0)
+        assert why == 1 and a0 < a_to < cube.cube_next_epoch(ctx, 1.0, cells)
+        d = (p + f * cosmo.kick_factor(ap, 0.5 * (a0 + a_to), om, ol)) * cosmo.drift_factor(a0, a_to, om, ol)
+        assert d == pytest.approx(cells * 4, rel=1e-9)
+        # expansion limit
+        a_to, why = cube.cube_next_epoch_limited(ctx, 1.0, 1.0, 1e-3)
+        assert why == 2 and a_to == pytest.approx(a0 * np.exp(1e-3), rel=1e-15)
+        # a_max itself
+        a_to, why = cube.cube_next_epoch_limited(ctx, a0 + 1e-6, 1.0, 0.0)
+        assert why == 0 and a_to == a0 + 1e-6
+        with pytest.raises(cube.CubeError):
+            cube.cube_next_epoch_limited(ctx, 1.0, 0.0, 0.0)
     finally:
         cube.cube_destroy(ctx)
