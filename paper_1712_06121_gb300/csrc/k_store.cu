@@ -306,7 +306,9 @@ __global__ void __launch_bounds__(T_BRICK) k_deposit(Geo g, StoreDev s, float* _
     // FC > 0: the brick side in fine cells is the compile-time FC, else g.F
     const int lF = FC == 16 ? 4 : FC == 8 ? 3 : FC == 4 ? 2 : g.lF, F = 1 << lF, F3 = 1 << (3 * lF);
     const int E = g.B + 1, E3 = E * E * E;
-    unsigned* acc = reinterpret_cast<unsigned*>(dep_smem);          // [F3] {lo, hi} words
+    // node sums: [F3] 32-bit words when no sum can exceed 32 bits ("small",
+    // block-uniform), else [F3] {lo, hi} pairs
+    unsigned* acc = reinterpret_cast<unsigned*>(dep_smem);
     unsigned* cstart = acc + 2 * F3;                                 // [E3]
     unsigned* cpref = cstart + E3;                                   // [E3 + 1]
     int* cpack = reinterpret_cast<int*>(cpref + E3 + 1);             // [E3] packed cell offsets
@@ -314,8 +316,6 @@ __global__ void __launch_bounds__(T_BRICK) k_deposit(Geo g, StoreDev s, float* _
     int bx, by, bz;
     brick_coords(g, blockIdx.x, &bx, &by, &bz);
     const int c0[3] = {bx * g.B, by * g.B, bz * g.B};
-    for (int t = threadIdx.x; t < F3 / 2; t += blockDim.x)            // F3 is a multiple of 64
-        reinterpret_cast<uint4*>(acc)[t] = make_uint4(0u, 0u, 0u, 0u);
     for (int t = threadIdx.x; t < E3; t += blockDim.x) {
         int ec[3];
         split3(t, E, div_magic(E), ec);
@@ -349,12 +349,14 @@ __global__ void __launch_bounds__(T_BRICK) k_deposit(Geo g, StoreDev s, float* _
     // a node's 32-bit sum of 1-byte-code weights (each < 2^(3 s)) cannot wrap
     // when fewer than 2^(32 - 3 s) particles feed the brick
     const bool small = 3 * sb < 32 && total < (1u << (32 - 3 * sb));
+    const int ws = small ? 0 : 1;                                   // log2 words per node
+    for (int t = threadIdx.x; t < (F3 << ws) / 4; t += blockDim.x)  // F3 is a multiple of 64
+        reinterpret_cast<uint4*>(acc)[t] = make_uint4(0u, 0u, 0u, 0u);
     const bool table = total <= (unsigned)DEP_QCAP && E3 <= 256;    // block-uniform
-    if (table) {
+    if (table)
         for (int t = threadIdx.x; t < E3; t += blockDim.x)
             for (unsigned q = cpref[t], q1 = min(cpref[t + 1], total); q < q1; ++q) qcell[q] = (unsigned char)t;
-        __syncthreads();
-    }
+    __syncthreads();
     for (unsigned q = threadIdx.x; q < total; q += blockDim.x) {
         const int t = table ? (int)qcell[q] : upper_cell(cpref, E3, q);
         const unsigned i = cstart[t] + (q - cpref[t]);
@@ -385,7 +387,7 @@ __global__ void __launch_bounds__(T_BRICK) k_deposit(Geo g, StoreDev s, float* _
                 for (int dx = 0; dx < 2; ++dx) {
                     const int x = nd[0] + dx;
                     if (!inside && (x < 0 || x >= F)) continue;
-                    unsigned* a = &acc[2 * ((((z << lF) + y) << lF) + x)];
+                    unsigned* a = &acc[((((z << lF) + y) << lF) + x) << ws];
                     if (NX == 1) {   // weight numerators of 1-byte codes: product < 2^27
                         const unsigned w = (unsigned)(dz ? wn[2] : wm[2]) * (unsigned)(dy ? wn[1] : wm[1]) *
                                            (unsigned)(dx ? wn[0] : wm[0]);
@@ -406,20 +408,21 @@ __global__ void __launch_bounds__(T_BRICK) k_deposit(Geo g, StoreDev s, float* _
         }
     }
     __syncthreads();
-    // four consecutive x nodes per thread: two 16-byte shared loads, one
-    // 16-byte store (F and the row stride S are multiples of 4)
+    // four consecutive x nodes per thread: one or two 16-byte shared loads,
+    // one 16-byte store (F and the row stride S are multiples of 4)
     const int ox = c0[0] * g.R, oy = c0[1] * g.R, oz = c0[2] * g.R;
     for (int t4 = threadIdx.x; t4 < F3 / 4; t4 += blockDim.x) {
         const int t = 4 * t4;
         const int x = t & (F - 1), y = (t >> lF) & (F - 1), z = t >> (2 * lF);
-        const uint4 a = reinterpret_cast<const uint4*>(acc)[2 * t4];        // {lo, hi} of nodes t, t + 1
-        const uint4 b = reinterpret_cast<const uint4*>(acc)[2 * t4 + 1];    // nodes t + 2, t + 3
         // exact integer sum; one rounding when the scale is a power of two (mass 2^k)
         float4 v;
-        if (small) {   // block-uniform: no node sum exceeds 32 bits
-            v = make_float4(u32_to_float_rn(a.x) * fscale, u32_to_float_rn(a.z) * fscale,
-                            u32_to_float_rn(b.x) * fscale, u32_to_float_rn(b.z) * fscale);
+        if (small) {   // block-uniform: 32-bit sums of nodes t .. t + 3
+            const uint4 a = reinterpret_cast<const uint4*>(acc)[t4];
+            v = make_float4(u32_to_float_rn(a.x) * fscale, u32_to_float_rn(a.y) * fscale,
+                            u32_to_float_rn(a.z) * fscale, u32_to_float_rn(a.w) * fscale);
         } else {
+            const uint4 a = reinterpret_cast<const uint4*>(acc)[2 * t4];        // {lo, hi} of nodes t, t + 1
+            const uint4 b = reinterpret_cast<const uint4*>(acc)[2 * t4 + 1];    // nodes t + 2, t + 3
             v = make_float4(node_value(a.x, a.y) * fscale, node_value(a.z, a.w) * fscale,
                             node_value(b.x, b.y) * fscale, node_value(b.z, b.w) * fscale);
         }
