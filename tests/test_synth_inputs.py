@@ -1,0 +1,43 @@
+"""The seeded input generators (no PM arithmetic) behind the ensemble and
+serving workloads: the serving request stream has the stated distribution,
+and rescaling a Zel'dovich realisation's amplitude equals generating it with
+the scaled sigma8 (displacements, momenta and the velocity scale are linear
+in the amplitude), to FP32 rounding."""
+import dataclasses
+
+import numpy as np
+
+import synth
+
+
+def test_serving_stream_follows_its_recipe():
+    reqs = synth.serving_c5(400, rate=20.0, seed=7)
+    t = np.array([r.arrival for r in reqs])
+    assert np.all(np.diff(t) > 0)
+    gaps = np.diff(np.concatenate([[0.0], t]))
+    assert abs(gaps.mean() - 1 / 20.0) < 0.01                    # Poisson: mean gap 1/rate
+    ws = [r.workload for r in reqs]
+    assert {w.n_part_side for w in ws} == {64, 96, 128, 192, 256}
+    for w in ws:
+        assert w.n_fine == 2 * w.n_part_side and w.box == 300.0 * w.n_part_side / 256
+        assert 10 <= w.n_steps <= 60 and 0.7 <= w.sigma8 <= 0.9
+        assert w.a_final == min(1.0, 0.02 + 0.0196 * w.n_steps) and w.x_bytes == w.v_bytes == 1
+    assert len({w.seed for w in ws}) == len(ws)
+    assert synth.serving_c5(400, rate=20.0, seed=7) == reqs      # seeded
+
+
+def test_rescaled_realisation_equals_the_regenerated_one():
+    w = dataclasses.replace(synth.WORKLOADS["pm64"], n_part_side=16, n_fine=32)
+    ic = synth.make_ics(w)
+    same = synth.rescaled_ics(ic, 1.0)
+    assert np.array_equal(same.pos, ic.pos) and np.array_equal(same.vel, ic.vel)
+    for f in (0.75, 1.1):
+        got = synth.rescaled_ics(ic, f)
+        want = synth.make_ics(dataclasses.replace(w, sigma8=w.sigma8 * f))
+        d = got.pos.astype(np.float64) - want.pos
+        d -= 32 * np.round(d / 32)
+        assert np.max(np.abs(d)) <= 1e-5
+        assert np.max(np.abs(got.vel - want.vel)) <= 1e-6 * np.max(np.abs(want.vel))
+        assert abs(got.sigma_1d / want.sigma_1d - 1) < 1e-12
+        assert np.array_equal(got.ids, ic.ids)
+        assert np.all((got.pos >= 0) & (got.pos < 32))
