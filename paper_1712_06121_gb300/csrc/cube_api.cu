@@ -985,6 +985,7 @@ cube_status cube_checkpoint_load(cube_ctx* c, const void* buf) {
     const char* b = (const char*)buf;
     const size_t N = (size_t)g.Np, Ncc = (size_t)g.Ncc;
     const int k = c->cur;
+    c->encoded = false;                  // until the whole store is in place
     if (c->raw) {
         CK(cudaMemcpyAsync(c->chi[0], b + sec[0], 12 * N, cudaMemcpyDefault, c->st));
         CK(cudaMemcpyAsync(c->nu[0], b + sec[1], 12 * N, cudaMemcpyDefault, c->st));
@@ -1006,17 +1007,14 @@ cube_status cube_checkpoint_load(cube_ctx* c, const void* buf) {
     if (!c->raw) CK(cudaMemcpyAsync(&total, c->offsets[k] + g.Ncc, 4, cudaMemcpyDeviceToHost, c->st));
     CK(cudaGetLastError());
     CK(cudaStreamSynchronize(c->st));
-    c->encoded = true;
     c->phig_valid = false;
     c->a = h.a;
     c->a_p = h.a_p;
     c->steps = 0;
     c->dbg_valid = false;
     c->timed = false;
-    if (total != (unsigned)g.Np) {
-        c->encoded = false;
-        return fail(CUBE_E_ARG, "checkpoint cell counts do not add up to the particle count");
-    }
+    if (total != (unsigned)g.Np) return fail(CUBE_E_ARG, "checkpoint cell counts do not add up to the particle count");
+    c->encoded = true;
     return CUBE_OK;
 }
 
