@@ -355,6 +355,20 @@ cube_status cube_checkpoint_size(const cube_params* params, int64_t* bytes);
 cube_status cube_checkpoint_save(cube_ctx* ctx, void* buf);
 cube_status cube_checkpoint_load(cube_ctx* ctx, const void* buf);
 
+/* The coarse density field in one byte per cell (Section 2.1): a count below
+   255 as itself, 255 for a cell of 255 or more particles, whose count
+   follows in `overflow` (4-byte integers, in cell order).  Host arrays;
+   no device is needed.
+   cube_counts_pack: counts[n_cells] -> bytes[n_cells] and overflow[..];
+   *n_overflow receives the list's length; CUBE_E_ARG when it exceeds
+   overflow_cap (call again with a list that long).
+   cube_counts_unpack: the inverse; CUBE_E_ARG when the 255 bytes and the
+   overflow entries do not correspond one to one or an entry is below 255. */
+cube_status cube_counts_pack(const uint32_t* counts, int64_t n_cells, uint8_t* bytes, uint32_t* overflow,
+                             int64_t overflow_cap, int64_t* n_overflow);
+cube_status cube_counts_unpack(const uint8_t* bytes, int64_t n_cells, const uint32_t* overflow, int64_t n_overflow,
+                               uint32_t* counts);
+
 /* ---------------------------------------------------------------- autotuning */
 
 /* Picks the storage-order brick (cube_params.brick: 1, 2 or 4 coarse cells)

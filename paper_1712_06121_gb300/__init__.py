@@ -94,6 +94,8 @@ _sigs = {
     "cube_max_force": ([_P, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
     "cube_next_epoch_limited": ([_P, ctypes.c_double, ctypes.POINTER(cube_step_limits), ctypes.POINTER(ctypes.c_double),
                                  ctypes.POINTER(ctypes.c_int32)], ctypes.c_int),
+    "cube_counts_pack": ([_P, ctypes.c_int64, _P, _P, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
+    "cube_counts_unpack": ([_P, ctypes.c_int64, _P, ctypes.c_int64, _P], ctypes.c_int),
     "cube_checkpoint_size": ([ctypes.POINTER(cube_params), ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
     "cube_checkpoint_save": ([_P, _P], ctypes.c_int),
     "cube_checkpoint_load": ([_P, _P], ctypes.c_int),
@@ -266,6 +268,30 @@ def cube_phase_name(phase):
 
 __all__ = [n for n in _sigs] + ["make_params", "cube_params", "cube_state", "cube_stats", "CubeError",
                                 "LIB_PATH", "CUBE_GRAD_FD4", "CUBE_PHASES"]
+
+
+def cube_counts_pack(counts):
+    """(bytes uint8[n], overflow uint32[k]) of host uint32 counts (Section 2.1's 1-byte field)."""
+    import numpy as np
+    c = np.ascontiguousarray(counts, dtype=np.uint32)
+    b = np.empty(c.size, np.uint8)
+    k = ctypes.c_int64()
+    st = _lib.cube_counts_pack(c.ctypes.data, c.size, b.ctypes.data, None, 0, ctypes.byref(k))
+    ov = np.empty(k.value, np.uint32)
+    if st != CUBE_OK or k.value:
+        _check(_lib.cube_counts_pack(c.ctypes.data, c.size, b.ctypes.data, ov.ctypes.data if k.value else None,
+                                     k.value, ctypes.byref(k)))
+    return b, ov
+
+
+def cube_counts_unpack(bytes_, overflow):
+    import numpy as np
+    b = np.ascontiguousarray(bytes_, dtype=np.uint8)
+    ov = np.ascontiguousarray(overflow, dtype=np.uint32)
+    out = np.empty(b.size, np.uint32)
+    _check(_lib.cube_counts_unpack(b.ctypes.data, b.size, ov.ctypes.data if ov.size else None, ov.size,
+                                   out.ctypes.data))
+    return out
 
 
 def cube_checkpoint_size(params):

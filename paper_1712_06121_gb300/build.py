@@ -16,7 +16,8 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "libcube.so")
-SOURCES = ["cube_api.cu", "k_scan.cu", "k_store.cu", "k_fft.cu", "k_raw.cu", "noalloc.cu", "serve.cu", "tune.cu"]
+SOURCES = ["cube_api.cu", "k_scan.cu", "k_store.cu", "k_fft.cu", "k_raw.cu", "noalloc.cu", "serve.cu", "tune.cu",
+           "counts_pack.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off",
          "--expt-relaxed-constexpr", "-I", INCLUDE, "-I", CSRC]
