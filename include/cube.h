@@ -208,6 +208,29 @@ typedef struct {
 cube_status cube_next_epoch_limited(cube_ctx* ctx, double a_max, const cube_step_limits* lim, double* a_to,
                                     int32_t* binding);
 
+/* The same bound for given maxima, on the host with no context or GPU:
+   positions at epoch a, momenta at a_p (0 < a_p <= a; a_p = a right after
+   cube_encode, (a_prev + a) / 2 after a step), fastest momentum component
+   p_max >= 0, largest force component f_max >= 0, `ratio` fine cells per
+   coarse cell, cosmology (omega_m > 0, omega_l >= 0).  cube_next_epoch_limited
+   is this call with the context's cosmology, epochs and measured maxima.
+   Errors: CUBE_E_ARG (arguments out of range, no positive step possible). */
+cube_status cube_epoch_bound(double omega_m, double omega_l, int32_t ratio, double a, double a_p, double a_max,
+                             double p_max, double f_max, const cube_step_limits* lim, double* a_to,
+                             int32_t* binding);
+
+/* The host integrals of the KD step (Section 2.3.3) and of the codec-scale
+   update (Section 2.2), as cube_pm_step evaluates them; no context or GPU.
+   kick = int_{a0}^{a1} da / (a^2 E), drift = int_{a0}^{a1} da / (a^3 E),
+   growth_ratio = g(a1) / g(a0) with g = a^2 E f D the linear growth of the
+   momenta; E(a)^2 = omega_m a^-3 + (1 - omega_m - omega_l) a^-2 + omega_l.
+   EdS (omega_m = 1, omega_l = 0) uses the closed forms, other cosmologies
+   Gauss-Legendre quadrature (16 panels of 64 nodes; D from Heath's
+   integral).  Outputs may be NULL.  Errors: CUBE_E_ARG (omega_m <= 0,
+   omega_l < 0, a0 or a1 <= 0). */
+cube_status cube_leapfrog_factors(double omega_m, double omega_l, double a0, double a1, double* kick,
+                                  double* drift, double* growth_ratio);
+
 /* ---------------------------------------------------------------- inspection */
 
 typedef struct {

@@ -94,6 +94,12 @@ _sigs = {
     "cube_max_force": ([_P, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
     "cube_next_epoch_limited": ([_P, ctypes.c_double, ctypes.POINTER(cube_step_limits), ctypes.POINTER(ctypes.c_double),
                                  ctypes.POINTER(ctypes.c_int32)], ctypes.c_int),
+    "cube_epoch_bound": ([ctypes.c_double, ctypes.c_double, ctypes.c_int32, ctypes.c_double, ctypes.c_double,
+                          ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.POINTER(cube_step_limits),
+                          ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int32)], ctypes.c_int),
+    "cube_leapfrog_factors": ([ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                               ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                               ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
     "cube_counts_pack": ([_P, ctypes.c_int64, _P, _P, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
     "cube_counts_unpack": ([_P, ctypes.c_int64, _P, ctypes.c_int64, _P], ctypes.c_int),
     "cube_checkpoint_size": ([ctypes.POINTER(cube_params), ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
@@ -221,6 +227,24 @@ def cube_next_epoch_limited(ctx, a_max, drift_cells=0.5, max_dlna=0.0):
     why = ctypes.c_int32()
     _check(_lib.cube_next_epoch_limited(ctx, float(a_max), ctypes.byref(lim), ctypes.byref(out), ctypes.byref(why)))
     return out.value, why.value
+
+
+def cube_epoch_bound(omega_m, omega_l, ratio, a, a_p, a_max, p_max, f_max, drift_cells=0.5, max_dlna=0.0):
+    """(a_to, binding) of cube_next_epoch_limited for given maxima, host only."""
+    lim = cube_step_limits(float(drift_cells), float(max_dlna))
+    out = ctypes.c_double()
+    why = ctypes.c_int32()
+    _check(_lib.cube_epoch_bound(float(omega_m), float(omega_l), int(ratio), float(a), float(a_p), float(a_max),
+                                 float(p_max), float(f_max), ctypes.byref(lim), ctypes.byref(out), ctypes.byref(why)))
+    return out.value, why.value
+
+
+def cube_leapfrog_factors(omega_m, omega_l, a0, a1):
+    """(kick, drift, growth_ratio) as the step evaluates them, host only."""
+    k, d, g = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    _check(_lib.cube_leapfrog_factors(float(omega_m), float(omega_l), float(a0), float(a1), ctypes.byref(k),
+                                      ctypes.byref(d), ctypes.byref(g)))
+    return k.value, d.value, g.value
 
 
 def cube_density(ctx, rho):

@@ -834,18 +834,18 @@ cube_status cube_max_force(cube_ctx* c, double* f_max) {
     return s;
 }
 
-cube_status cube_next_epoch_limited(cube_ctx* c, double a_max, const cube_step_limits* lim, double* a_to,
-                                    int32_t* binding) {
-    if (!c || !a_to || !lim) return fail(CUBE_E_ARG, "NULL argument");
-    if (!c->encoded) return fail(CUBE_E_STATE, "no store: call cube_encode first");
-    if (!(a_max > c->a)) return fail(CUBE_E_ARG, "a_max must exceed the store's epoch");
+static cube_status check_limits(const cube_step_limits* lim) {
     if (!(lim->drift_cells > 0.0 && lim->drift_cells <= 1.0)) return fail(CUBE_E_ARG, "drift_cells must be in (0, 1]");
     if (!(lim->max_dlna >= 0.0)) return fail(CUBE_E_ARG, "max_dlna must be >= 0");
-    double p = 0.0, f = 0.0;
-    cube_status s = cube_max_speed(c, &p);
-    if (s == CUBE_OK) s = cube_max_force(c, &f);
-    if (s != CUBE_OK) return s;
-    const double a0 = c->a, limit = lim->drift_cells * c->g.R;
+    return CUBE_OK;
+}
+
+// Largest a_to <= a_max within the limits for positions at a0, momenta at
+// a_p, fastest momentum p and largest force component f; R fine cells per
+// coarse cell.  `why`: 0 a_max, 1 the drift, 2 the expansion limit.
+static cube_status limited_epoch(const Cosmo& cosmo, int R, double a0, double a_p, double a_max, double p, double f,
+                                 const cube_step_limits* lim, double* a_to, int32_t* binding) {
+    const double limit = lim->drift_cells * R;
     // expansion: Delta ln a <= max_dlna
     double hi = a_max;
     int why = 0;
@@ -855,9 +855,7 @@ cube_status cube_next_epoch_limited(cube_ctx* c, double a_max, const cube_step_l
     }
     // drift of the fastest particle after the kick of the largest force, per axis:
     // (p_max + F_max int_{a_p}^{a_mid} da / (a^2 E)) int_a^{a_to} da / (a^3 E), increasing in a_to
-    auto drift = [&](double at) {
-        return (p + f * c->cosmo.kick(c->a_p, 0.5 * (a0 + at))) * c->cosmo.drift(a0, at);
-    };
+    auto drift = [&](double at) { return (p + f * cosmo.kick(a_p, 0.5 * (a0 + at))) * cosmo.drift(a0, at); };
     if (drift(hi) <= limit) {
         *a_to = hi;
     } else {
@@ -872,6 +870,45 @@ cube_status cube_next_epoch_limited(cube_ctx* c, double a_max, const cube_step_l
     }
     if (binding) *binding = why;
     return *a_to > a0 ? CUBE_OK : fail(CUBE_E_ARG, "no step keeps the fastest particle within the limit");
+}
+
+cube_status cube_next_epoch_limited(cube_ctx* c, double a_max, const cube_step_limits* lim, double* a_to,
+                                    int32_t* binding) {
+    if (!c || !a_to || !lim) return fail(CUBE_E_ARG, "NULL argument");
+    if (!c->encoded) return fail(CUBE_E_STATE, "no store: call cube_encode first");
+    if (!(a_max > c->a)) return fail(CUBE_E_ARG, "a_max must exceed the store's epoch");
+    cube_status s = check_limits(lim);
+    if (s != CUBE_OK) return s;
+    double p = 0.0, f = 0.0;
+    s = cube_max_speed(c, &p);
+    if (s == CUBE_OK) s = cube_max_force(c, &f);
+    if (s != CUBE_OK) return s;
+    return limited_epoch(c->cosmo, c->g.R, c->a, c->a_p, a_max, p, f, lim, a_to, binding);
+}
+
+cube_status cube_epoch_bound(double omega_m, double omega_l, int32_t ratio, double a, double a_p, double a_max,
+                             double p_max, double f_max, const cube_step_limits* lim, double* a_to,
+                             int32_t* binding) {
+    if (!a_to || !lim) return fail(CUBE_E_ARG, "NULL argument");
+    if (!(omega_m > 0.0) || !(omega_l >= 0.0)) return fail(CUBE_E_ARG, "omega_m must be > 0, omega_l >= 0");
+    if (ratio < 1) return fail(CUBE_E_ARG, "ratio must be >= 1");
+    if (!(a > 0.0) || !(a_p > 0.0) || !(a_p <= a)) return fail(CUBE_E_ARG, "need 0 < a_p <= a");
+    if (!(a_max > a)) return fail(CUBE_E_ARG, "a_max must exceed a");
+    if (!(p_max >= 0.0) || !(f_max >= 0.0)) return fail(CUBE_E_ARG, "p_max and f_max must be >= 0");
+    cube_status s = check_limits(lim);
+    if (s != CUBE_OK) return s;
+    return limited_epoch(Cosmo{omega_m, omega_l}, ratio, a, a_p, a_max, p_max, f_max, lim, a_to, binding);
+}
+
+cube_status cube_leapfrog_factors(double omega_m, double omega_l, double a0, double a1, double* kick,
+                                  double* drift, double* growth_ratio) {
+    if (!(omega_m > 0.0) || !(omega_l >= 0.0)) return fail(CUBE_E_ARG, "omega_m must be > 0, omega_l >= 0");
+    if (!(a0 > 0.0) || !(a1 > 0.0)) return fail(CUBE_E_ARG, "scale factors must be > 0");
+    const Cosmo cosmo{omega_m, omega_l};
+    if (kick) *kick = cosmo.kick(a0, a1);
+    if (drift) *drift = cosmo.drift(a0, a1);
+    if (growth_ratio) *growth_ratio = cosmo.g(a1) / cosmo.g(a0);
+    return CUBE_OK;
 }
 
 cube_status cube_next_epoch(cube_ctx* c, double a_max, double cells, double* a_to) {
