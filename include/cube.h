@@ -392,6 +392,48 @@ cube_status cube_counts_pack(const uint32_t* counts, int64_t n_cells, uint8_t* b
 cube_status cube_counts_unpack(const uint8_t* bytes, int64_t n_cells, const uint32_t* overflow, int64_t n_overflow,
                                uint32_t* counts);
 
+/* ---------------------------------------------------------------- memory model */
+
+/* The paper's memory model of one image (Section 2.3, memory layout; Eqs.
+   npmax, nptile, Mp_particle, Mp_coarse, Mp_fine and Table t.memory): the
+   bytes of each array an image of a multi-image, tiled CUBE run keeps, for
+   sizing runs and comparing layouts.  Host only, no device. */
+typedef struct {
+    int32_t x_bytes, v_bytes;     /* n_chi, n_nu in {1, 2}                          */
+    int32_t id_bytes;             /* n_I in {0, 4}                                  */
+    int32_t ratio;                /* R: fine cells per coarse cell, >= 1            */
+    int32_t coarse_per_image;     /* N_c / M_g: coarse cells per image side, >= 1   */
+    int32_t buffer;               /* N_b: buffer depth in coarse cells, >= 0        */
+    int32_t tiles;                /* M_t: tiles per image side, divides N_c / M_g   */
+    double eps_image;             /* inhomogeneity margin of an image, >= 0         */
+    double eps_tile;              /* inhomogeneity margin of a tile, >= 0           */
+    double particles_per_image;   /* <P_local> > 0                                  */
+} cube_memory_config;
+
+/* Bytes per image; divide by particles_per_image for bytes per particle.
+   With N_t = (N_c/M_g) / M_t, N_e = N_t + 2 N_b, b = (1 + 2 N_b / N_t)^3,
+   P_max = <P_local> b (1 + eps_image) and
+   P*_max = <P_local> b (1 + eps_tile) / M_t^3:
+     chi_nu      = (3 n_chi + 3 n_nu) P_max      chi_d, nu_d
+     chi_nu_tile = (3 n_chi + 3 n_nu) P*_max     chi*_d, nu*_d (tile)
+     ids         = n_I (P_max + P*_max)          I_P, I_P*
+     rho_c, v_c  = 4, 12 bytes x (N_e M_t)^3     coarse counts and velocities
+     k_c         = 12 (N_c/M_g)^3 / 2            coarse force kernel
+     k_f         = 12 (R N_e / 2 + 1)(R N_e)^2   fine force kernel of one tile
+   The buffer factor in P*_max and the tile-sized K_f are the readings under
+   which the equations reproduce Table t.memory (Eq. nptile omits b; Eq.
+   Mp_fine's N_t^-3 is garbled).  Arrays that share memory with these
+   (F_c, F_f, the FFT work arrays) are not counted, as in the table.
+   Errors: CUBE_E_ARG for a NULL pointer or a field out of range. */
+typedef struct {
+    double chi_nu, chi_nu_tile, ids;
+    double rho_c, v_c, k_c;
+    double k_f;
+    double total;                 /* sum of the rows above                          */
+} cube_memory_layout;
+
+cube_status cube_memory_model(const cube_memory_config* cfg, cube_memory_layout* bytes);
+
 /* ---------------------------------------------------------------- autotuning */
 
 /* Picks the storage-order brick (cube_params.brick: 1, 2 or 4 coarse cells)

@@ -58,6 +58,18 @@ class cube_stats(ctypes.Structure):
 class cube_step_limits(ctypes.Structure):
     _fields_ = [("drift_cells", ctypes.c_double), ("max_dlna", ctypes.c_double)]
 
+
+class cube_memory_config(ctypes.Structure):
+    _fields_ = [("x_bytes", ctypes.c_int32), ("v_bytes", ctypes.c_int32), ("id_bytes", ctypes.c_int32),
+                ("ratio", ctypes.c_int32), ("coarse_per_image", ctypes.c_int32), ("buffer", ctypes.c_int32),
+                ("tiles", ctypes.c_int32), ("eps_image", ctypes.c_double), ("eps_tile", ctypes.c_double),
+                ("particles_per_image", ctypes.c_double)]
+
+
+class cube_memory_layout(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_double) for n in ("chi_nu", "chi_nu_tile", "ids", "rho_c", "v_c", "k_c", "k_f", "total")]
+
+
 CUBE_PHASES = 12
 
 CUBE_REQ_QUEUED, CUBE_REQ_RUNNING, CUBE_REQ_DONE, CUBE_REQ_FAILED = range(4)
@@ -100,6 +112,7 @@ _sigs = {
     "cube_leapfrog_factors": ([ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
                                ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
+    "cube_memory_model": ([ctypes.POINTER(cube_memory_config), ctypes.POINTER(cube_memory_layout)], ctypes.c_int),
     "cube_counts_pack": ([_P, ctypes.c_int64, _P, _P, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
     "cube_counts_unpack": ([_P, ctypes.c_int64, _P, ctypes.c_int64, _P], ctypes.c_int),
     "cube_checkpoint_size": ([ctypes.POINTER(cube_params), ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
@@ -292,6 +305,17 @@ def cube_phase_name(phase):
 
 __all__ = [n for n in _sigs] + ["make_params", "cube_params", "cube_state", "cube_stats", "CubeError",
                                 "LIB_PATH", "CUBE_GRAD_FD4", "CUBE_PHASES"]
+
+
+def cube_memory_model(x_bytes=1, v_bytes=1, id_bytes=0, ratio=4, coarse_per_image=384, buffer=6, tiles=3,
+                      eps_image=0.05, eps_tile=2.0, particles_per_image=1536.0 ** 3):
+    """Bytes per image of each array of the paper's memory model, as a dict
+    (host only; defaults are the configuration of its memory table)."""
+    cfg = cube_memory_config(int(x_bytes), int(v_bytes), int(id_bytes), int(ratio), int(coarse_per_image),
+                             int(buffer), int(tiles), float(eps_image), float(eps_tile), float(particles_per_image))
+    out = cube_memory_layout()
+    _check(_lib.cube_memory_model(ctypes.byref(cfg), ctypes.byref(out)))
+    return {n: getattr(out, n) for n, _ in cube_memory_layout._fields_}
 
 
 def cube_counts_pack(counts):

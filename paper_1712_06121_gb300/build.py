@@ -17,7 +17,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "libcube.so")
 SOURCES = ["cube_api.cu", "k_scan.cu", "k_store.cu", "k_fft.cu", "k_raw.cu", "noalloc.cu", "serve.cu", "tune.cu",
-           "counts_pack.cu"]
+           "counts_pack.cu", "memory_model.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off",
          "--expt-relaxed-constexpr", "-I", INCLUDE, "-I", CSRC]

@@ -1,0 +1,108 @@
+"""The paper's memory model (cube_memory_model, host only) against its own
+worked table (tests/golden/table_memory.txt, Table t.memory of Section 2.3):
+every listed array to the printed digits, the per-particle Eqs. Mp_particle
+(with the tile term's buffer factor the table uses) and Mp_coarse, the
+6-bytes-per-particle optimal limit, and the paper's statement that M_t = 3
+tiles per side minimises the memory of that configuration."""
+import os
+
+import pytest
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "table_memory.txt")
+
+
+@pytest.fixture(scope="module")
+def cube():
+    from conftest import build_lib
+    build_lib()
+    import paper_1712_06121_gb300 as c
+    return c
+
+
+def _golden():
+    cfg, rows = {}, {}
+    for line in open(GOLDEN):
+        line = line.strip()
+        if not line or line.startswith("#"):
+            continue
+        head, *rest = line.split()
+        if head == "config":
+            for kv in rest:
+                k, v = kv.split("=")
+                cfg[k] = float(v) if "." in v or k == "particles_per_image" else int(v)
+        else:
+            rows[head] = (rest[0], rest[1])
+    return cfg, rows
+
+
+def _half_unit(printed):
+    """Half a unit in the last printed digit ('0.0818' -> 5e-5, '6' -> 0.5)."""
+    if "." not in printed:
+        return 0.5
+    return 0.5 * 10.0 ** -len(printed.split(".")[1])
+
+
+def test_table_rows_to_the_printed_digits(cube):
+    cfg, rows = _golden()
+    assert cfg["particles_per_image"] == 1536 ** 3
+    m = cube.cube_memory_model(**cfg)
+    P = cfg["particles_per_image"]
+    got = dict(m)
+    got["particles_subtotal"] = m["chi_nu"] + m["chi_nu_tile"] + m["ids"]
+    got["optimal"] = cube.cube_memory_model(**{**cfg, "buffer": 0, "eps_image": 0.0})["chi_nu"]
+    for name, (gb, bpp) in rows.items():
+        if name == "total":
+            continue
+        assert abs(got[name] / 1e9 - float(gb)) <= _half_unit(gb) + 1e-12, name
+        if name == "k_c":
+            # the table's own 0.340 GB is 0.0938 bytes per particle; its 0.0939 is one unit above that
+            assert abs(float(gb) * 1e9 / P - float(bpp)) <= 2e-4
+            assert abs(got[name] / P - float(bpp)) <= 2e-4
+        else:
+            assert abs(got[name] / P - float(bpp)) <= _half_unit(bpp) + 1e-12, name
+    # the printed total also counts memory-light arrays the table does not list
+    gb, bpp = rows["total"]
+    assert abs(m["total"] / 1e9 - float(gb)) <= _half_unit(gb)
+    assert m["total"] / P == pytest.approx(float(bpp), rel=2e-3)
+    assert m["total"] == pytest.approx(sum(v for k, v in m.items() if k != "total"), rel=1e-15)
+
+
+@pytest.mark.parametrize("nb,mt,ei,et", [(6, 3, 0.05, 2.0), (0, 1, 0.0, 0.0), (4, 8, 0.1, 0.5), (12, 2, 0.2, 1.0)])
+def test_per_particle_equations(cube, nb, mt, ei, et):
+    """Eq. Mp_particle: 6 [b (1 + eps_image) + b M_t^-3 (1 + eps_tile)] with
+    b = (1 + 2 N_b / N_t)^3; Eq. Mp_coarse: P_c^-1 [16 b + 6] with P_c the
+    particles per coarse cell of the image."""
+    nc, P = 384, 1536.0 ** 3
+    m = cube.cube_memory_model(coarse_per_image=nc, buffer=nb, tiles=mt, eps_image=ei, eps_tile=et,
+                               particles_per_image=P)
+    b = (1 + 2 * nb / (nc / mt)) ** 3
+    assert (m["chi_nu"] + m["chi_nu_tile"]) / P == pytest.approx(6 * (b * (1 + ei) + b * (1 + et) / mt ** 3),
+                                                                 rel=1e-13)
+    pc = P / nc ** 3
+    assert (m["rho_c"] + m["v_c"] + m["k_c"]) / P == pytest.approx((16 * b + 6) / pc, rel=1e-13)
+
+
+def test_code_widths_and_ids_scale_the_particle_rows(cube):
+    base = cube.cube_memory_model()
+    wide = cube.cube_memory_model(x_bytes=2, v_bytes=2, id_bytes=4)
+    assert wide["chi_nu"] == pytest.approx(2 * base["chi_nu"], rel=1e-15)
+    assert wide["chi_nu_tile"] == pytest.approx(2 * base["chi_nu_tile"], rel=1e-15)
+    assert wide["ids"] == pytest.approx(4 / 6 * (base["chi_nu"] + base["chi_nu_tile"]), rel=1e-14)
+    assert base["ids"] == 0.0
+    for k in ("rho_c", "v_c", "k_c", "k_f"):
+        assert wide[k] == base[k]
+
+
+def test_three_tiles_per_side_minimise_the_table_configuration(cube):
+    cfg, _ = _golden()
+    totals = {mt: cube.cube_memory_model(**{**cfg, "tiles": mt})["total"] for mt in (1, 2, 3, 4, 6, 8, 12, 16)}
+    assert min(totals, key=totals.get) == 3
+
+
+@pytest.mark.parametrize("field,value", [("x_bytes", 3), ("v_bytes", 0), ("id_bytes", 2), ("ratio", 0),
+                                         ("coarse_per_image", 0), ("buffer", -1), ("tiles", 5),
+                                         ("eps_image", -0.1), ("particles_per_image", 0.0)])
+def test_bad_configurations_are_refused(cube, field, value):
+    with pytest.raises(cube.CubeError) as e:
+        cube.cube_memory_model(**{field: value})
+    assert e.value.status == cube.CUBE_E_ARG
