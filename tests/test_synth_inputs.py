@@ -41,3 +41,14 @@ def test_rescaled_realisation_equals_the_regenerated_one():
         assert abs(got.sigma_1d / want.sigma_1d - 1) < 1e-12
         assert np.array_equal(got.ids, ic.ids)
         assert np.all((got.pos >= 0) & (got.pos < 32))
+
+
+def test_ensemble_follows_its_recipe():
+    ws = synth.ensemble_c4(64)
+    assert len(ws) == 64 and [w.seed for w in ws] == list(range(64))
+    assert {w.n_part_side for w in ws} == {32, 48, 64, 96, 128}
+    for w in ws:
+        assert w.n_fine == 2 * w.n_part_side and 50.0 <= w.box <= 400.0 and 0.7 <= w.sigma8 <= 0.9
+        assert (w.a_init, w.a_final, w.n_steps, w.x_bytes, w.v_bytes, w.cosmo_kind) == (0.02, 1.0, 30, 1, 1, "lcdm")
+    assert len({(w.box, w.sigma8) for w in ws}) == 64                # every realisation differs
+    assert synth.ensemble_c4(64) == ws                                # seeded
