@@ -57,7 +57,8 @@ typedef enum {
     CUBE_E_STATE = 4,      /* call out of order, e.g. a step before cube_encode  */
     CUBE_E_MIGRATION = 5,  /* a particle moved more than one coarse cell         */
     CUBE_E_OVERFLOW = 6,   /* non-finite input or a counter overflow             */
-    CUBE_E_TIMEOUT = 7     /* a bounded device-side wait gave up (reserved)      */
+    CUBE_E_TIMEOUT = 7     /* a bounded device-side wait (the force pass's tile
+                              copy) gave up; the context stays usable        */
 } cube_status;
 
 enum { CUBE_GRAD_FD4 = 0 };
@@ -104,8 +105,11 @@ const char* cube_last_error(void);
    FFT tables, force-kernel factors).  `cuda_stream` is a cudaStream_t (NULL =
    the legacy default stream) on which every later call enqueues its work; the
    current CUDA device at this call is the context's device.  Allocates all
-   device memory the context needs: about (2 (3 n_chi + 3 n_nu + n_I) + 16) N_p
-   + 4.2 N_f^3 + 96 N_c^3 bytes.
+   device memory the context needs: about (2 (3 n_chi + 3 n_nu + n_I) + 45) N_p
+   + 8.2 N_f^3 + 78 N_c^3 bytes (both stores, the padded mesh, the ghosted
+   potential, histograms, scratch and staging for host arrays; 2.35 GB at
+   256^3 particles, 512^3 mesh, x1v1 with IDs).  cube_server_sizes gives the
+   exact figures, split into the resident state and the per-call work area.
    Errors: CUBE_E_ARG (params), CUBE_E_NOMEM, CUBE_E_CUDA. */
 cube_status cube_create(const cube_params* params, void* cuda_stream, cube_ctx** out);
 
