@@ -265,7 +265,8 @@ typedef struct {
     double a, a_p;           /* epochs of positions and momenta                */
     int64_t steps;           /* cube_pm_step calls since cube_encode           */
     int32_t max_migration;   /* largest |cell shift| of the last step (<= 1)   */
-    uint32_t error_flags;    /* bit 0 migration, bit 1 non-finite, bit 2 count  */
+    uint32_t error_flags;    /* bit 0 migration, bit 1 non-finite, bit 2 count,
+                                bit 3 a bounded tile-copy wait gave up         */
     double last_step_ms;     /* device time of the last step's kernels         */
     int64_t kernel_launches; /* CUDA kernels this context launched before this
                                 call (the call's own reduction not counted)    */
