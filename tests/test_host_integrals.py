@@ -6,9 +6,9 @@ of their definitions and the EdS closed forms, and the step-size bound
 closed form in EdS and its defining equation in LCDM."""
 import math
 
-import mpmath
 import pytest
 
+mpmath = pytest.importorskip("mpmath")
 mpmath.mp.dps = 30
 
 
