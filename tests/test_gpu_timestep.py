@@ -151,6 +151,8 @@ def test_limited_epoch_accounts_for_force_and_expansion(cube):
         assert why == 1 and a0 < a_to < cube.cube_next_epoch(ctx, 1.0, cells)
         d = (p + f * cosmo.kick_factor(ap, 0.5 * (a0 + a_to), om, ol)) * cosmo.drift_factor(a0, a_to, om, ol)
         assert d == pytest.approx(cells * 4, rel=1e-9)
+        # the host-only bound with the context's epochs and maxima is the same call
+        assert cube.cube_epoch_bound(om, ol, 4, a0, ap, 1.0, p, f, cells, 0.0) == (a_to, why)
         # expansion limit
         a_to, why = cube.cube_next_epoch_limited(ctx, 1.0, 1.0, 1e-3)
         assert why == 2 and a_to == pytest.approx(a0 * np.exp(1e-3), rel=1e-15)
