@@ -143,7 +143,6 @@ def kernel_source_hash():
 def measured_traffic(kernel, workload):
     """DRAM bytes per launch of `kernel` from the committed ncu summary, if it
     was taken on the current kernel source; else None."""
-    import hashlib
     path = os.path.join(ROOT, "profiles", f"dram_traffic_{workload}.txt")
     if not os.path.exists(path):
         return None
