@@ -106,3 +106,20 @@ def test_bad_configurations_are_refused(cube, field, value):
     with pytest.raises(cube.CubeError) as e:
         cube.cube_memory_model(**{field: value})
     assert e.value.status == cube.CUBE_E_ARG
+
+
+@pytest.mark.parametrize("nps,xb,vb,idb", [(256, 1, 1, 4), (128, 1, 2, 0), (64, 2, 2, 4)])
+def test_resident_state_is_the_models_single_image_particle_arrays(cube, nps, xb, vb, idb):
+    """One GPU holds the whole periodic box: one image, no buffer, the
+    re-sorted store full size (N_b = 0, M_t = 1, no margins).  There the
+    model's particle rows are exactly the resident state's particle arrays;
+    the rest of the state is the coarse fields of both stores (counts,
+    offsets, v_c: 40 bytes per coarse cell) and codec tables."""
+    nf, n = 2 * nps, nps ** 3
+    m = cube.cube_memory_model(x_bytes=xb, v_bytes=vb, id_bytes=idb, ratio=4, coarse_per_image=nf // 4, buffer=0,
+                               tiles=1, eps_image=0.0, eps_tile=0.0, particles_per_image=float(n))
+    state, _ = cube.cube_server_sizes(cube.make_params(nf, n, x_bytes=xb, v_bytes=vb, id_bytes=idb))
+    particles = m["chi_nu"] + m["chi_nu_tile"] + m["ids"]
+    assert particles == 2 * (3 * xb + 3 * vb + idb) * n
+    coarse = 40 * (nf // 4) ** 3
+    assert particles + coarse <= state <= particles + coarse + (2 << 20)
