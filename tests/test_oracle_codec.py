@@ -8,6 +8,8 @@ zero, and brute-force checks of the sort.
 import os
 
 import mpmath
+from fractions import Fraction
+
 import numpy as np
 import pytest
 
@@ -199,3 +201,48 @@ def test_cell_mean_velocity_is_mean_and_order_free():
     perm = rng.permutation(n)
     assert np.array_equal(pm.cell_mean_velocity(key[perm], vel[:, perm], cells), vc)
     assert np.all(vc[:, np.bincount(key, minlength=cells) == 0] == 0)
+
+
+def _round_f32_exact(x):
+    """x (a Fraction) rounded to the nearest float32, ties to even, by exact
+    comparison with its two float32 neighbours."""
+    f = np.float32(float(x))
+    while Fraction(float(f)) > x:
+        f = np.nextafter(f, np.float32(-np.inf))
+    while Fraction(float(np.nextafter(f, np.float32(np.inf)))) <= x:
+        f = np.nextafter(f, np.float32(np.inf))
+    hi = np.nextafter(f, np.float32(np.inf))
+    lo_gap, hi_gap = x - Fraction(float(f)), Fraction(float(hi)) - x
+    if lo_gap < hi_gap:
+        return f
+    if hi_gap < lo_gap:
+        return hi
+    return f if int(f.view(np.uint32)) % 2 == 0 else hi
+
+
+def test_cell_mean_velocity_is_the_correctly_rounded_fixed_point_mean():
+    """v_c = the exact rational mean of the 2^-24 fixed-point velocities,
+    rounded once to float32 (ties to even), for random cells and for sums
+    built to land next to a float32 rounding midpoint, where rounding twice
+    (or summing in floating point) would differ."""
+    rng = np.random.default_rng(11)
+    cases = []
+    for _ in range(300):                                    # random cells
+        n = int(rng.integers(1, 400))
+        q = rng.integers(-2 ** 24 + 1, 2 ** 24, n)          # |v| < 1: every 2^-24 multiple is a float32
+        cases.append(q)
+    for _ in range(300):                                    # next to a midpoint
+        n = int(rng.integers(2, 2000))
+        m = np.float32(rng.uniform(-0.9, 0.9))
+        mid = (Fraction(float(m)) + Fraction(float(np.nextafter(m, np.float32(np.inf))))) / 2
+        total = round(mid * n * 2 ** 24) + int(rng.integers(-1, 2))
+        q = np.full(n, total // n, dtype=np.int64)
+        q[: total - int(q.sum())] += 1
+        cases.append(q)
+    for q in cases:
+        vel = (q.astype(np.float64) / 2 ** 24).astype(np.float32)
+        assert np.array_equal(np.rint(vel.astype(np.float64) * 2 ** 24).astype(np.int64), q)   # representable
+        key = np.zeros(len(q), np.int64)
+        got = pm.cell_mean_velocity(key, np.stack([vel] * 3), 1)[0, 0]
+        want = _round_f32_exact(Fraction(int(q.sum()), len(q) * 2 ** 24))
+        assert got == want, (len(q), int(q.sum()))
