@@ -52,3 +52,16 @@ def test_ensemble_follows_its_recipe():
         assert (w.a_init, w.a_final, w.n_steps, w.x_bytes, w.v_bytes, w.cosmo_kind) == (0.02, 1.0, 30, 1, 1, "lcdm")
     assert len({(w.box, w.sigma8) for w in ws}) == 64                # every realisation differs
     assert synth.ensemble_c4(64) == ws                                # seeded
+
+
+def test_philox_known_answers():
+    """The initial conditions' noise generator reproduces the published
+    Philox-4x32-10 known-answer vectors (tests/golden/philox4x32_10_kat.txt)."""
+    import os
+    from synth.philox import philox4x32
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "philox4x32_10_kat.txt")
+    rows = [[int(x, 16) for x in line.split()] for line in open(path) if line.strip() and not line.startswith("#")]
+    assert len(rows) == 3
+    for r in rows:
+        got = philox4x32(*[np.array([x], np.uint32) for x in r[:4]], r[4], r[5])
+        assert [int(g[0]) for g in got] == r[6:]
