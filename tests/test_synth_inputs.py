@@ -65,3 +65,23 @@ def test_philox_known_answers():
     for r in rows:
         got = philox4x32(*[np.array([x], np.uint32) for x in r[:4]], r[4], r[5])
         assert [int(g[0]) for g in got] == r[6:]
+
+
+def test_white_noise_is_keyed_by_wave_vector():
+    """A Fourier mode draws the same noise at every grid size (the counter is
+    the integer wave-vector), the kx = 0 plane is Hermitian, and DC and the
+    Nyquist planes are zero."""
+    from synth.ics import white_noise_modes
+    a, b = white_noise_modes(16, 1712002), white_noise_modes(32, 1712002)
+    f16 = np.fft.fftfreq(16, 1.0 / 16).astype(int)
+    for iz, nz in enumerate(f16):
+        for iy, ny in enumerate(f16):
+            for nx in range(8):
+                if max(abs(nz), abs(ny), nx) < 8:
+                    assert a[iz, iy, nx] == b[nz % 32, ny % 32, nx]
+    for iz, nz in enumerate(f16):
+        for iy, ny in enumerate(f16):
+            assert a[(-nz) % 16, (-ny) % 16, 0] == np.conj(a[iz, iy, 0])
+    assert a[0, 0, 0] == 0 and np.all(a[8] == 0) and np.all(a[:, 8] == 0) and np.all(a[:, :, 8] == 0)
+    live = np.abs(b[b != 0]) ** 2
+    assert abs(live.mean() - 1.0) < 0.05
