@@ -82,6 +82,32 @@ def f32(x):
     return np.asarray(x, dtype=np.float64).astype(np.float32)
 
 
+def fma_f32(a, b, c):
+    """fl32(a * b + c) with a single rounding, for FP32 a, b, c: the drifted
+    offset u + p * dc of Fig. update_xp as an FP32 value (reading: the
+    position code is decided on that FP32 value, rounded once).
+
+    a * b is exact in FP64 (two 24-bit significands).  The sum with c is
+    s + e exactly, s = fl64(a b + c) and e its rounding error (Knuth's
+    TwoSum); s is then rounded to odd (moved one FP64 ulp toward e when e is
+    non-zero and s is even), after which rounding to FP32 gives the correctly
+    rounded value: rounding to odd at 53 bits followed by rounding to nearest
+    at 24 <= 53 - 2 bits is a single rounding (Boldo & Melquiond, 2008).
+    A plain FP64 add followed by an FP32 conversion rounds twice and can
+    land one FP32 ulp away on a tie.
+    """
+    a = np.asarray(a, np.float32).astype(np.float64)
+    b = np.asarray(b, np.float32).astype(np.float64)
+    c = np.asarray(c, np.float32).astype(np.float64)
+    prod = a * b
+    s = prod + c
+    bv = s - prod
+    e = (prod - (s - bv)) + (c - bv)
+    even = (np.asarray(s).view(np.int64) & 1) == 0
+    odd = np.where((e != 0) & even, np.nextafter(s, np.where(e > 0, np.inf, -np.inf)), s)
+    return np.asarray(odd, np.float64).astype(np.float32)
+
+
 def cell_mean_velocity(key, vel32, n_cells):
     """v_c of each cell: mean of its particles' FP32 velocities (Eq. deltav).
 
@@ -216,7 +242,7 @@ def step(store, a_from, a_to, keep_drifted=False):
     sigma_new = codec.snap_sigma(measured_sigma(p2, vc_old) * ratio)
     # 5: drift inside the old cell (coarse units), decided in FP32
     dc = np.float32(cosmo.drift_factor(a_from, a_to, om, ol) / P.ratio)
-    u_new = f32(u + p2.astype(np.float64) * np.float64(dc))
+    u_new = fma_f32(p2, np.broadcast_to(dc, p2.shape), u)
     # 6: rebuild
     out = encode_drifted(P, cells, u_new, p2, store.ids, sigma_new, a_to, a_mid)
     if keep_drifted:

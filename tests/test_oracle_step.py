@@ -157,3 +157,54 @@ def test_one_step_matches_the_uncompressed_step_within_code_bins(xb, vb, om, ol)
         target = 16 * np.log2(disp * (a1 / a0) ** 1.5)
         m = np.round(16 * np.log2(st1.sigma))
         assert st1.sigma == pytest.approx(2.0 ** (m / 16), rel=1e-14) and abs(m - target) <= 0.5 + 1e-9
+
+
+# ---------------------------------------------------------------- the drift's single rounding
+def _round_f32(x):
+    """Nearest FP32 to the rational x, ties to even (x normal in FP32)."""
+    from fractions import Fraction
+    if x == 0:
+        return 0.0
+    sgn = -1 if x < 0 else 1
+    m = abs(Fraction(x))
+    e = 0
+    while m >= 2 ** 24:
+        m /= 2
+        e += 1
+    while m < 2 ** 23:
+        m *= 2
+        e -= 1
+    q, r = divmod(m.numerator, m.denominator)
+    rem = Fraction(r, m.denominator)
+    if rem > Fraction(1, 2) or (rem == Fraction(1, 2) and q % 2 == 1):
+        q += 1
+    return float(sgn * Fraction(q) * Fraction(2) ** e)
+
+
+def test_drift_offset_is_rounded_once():
+    """The drifted offset u + p dc (Fig. update_xp) is the FP32 value of the
+    exact sum, rounded once, as a fused multiply-add forms it.  Random FP32
+    triples against exact rational rounding, and a tie that an FP64 add
+    followed by an FP32 conversion rounds the wrong way: u = 1/2, p dc =
+    3 2^-25 - 12 2^-71 lies just below the midpoint 1/2 + 3 2^-25, so the
+    answer is 1/2 + 2^-24, while FP64 first rounds to the midpoint and the
+    tie then goes to 1/2 + 2^-23."""
+    from fractions import Fraction
+    rng = np.random.default_rng(1712)
+    n = 4000
+    u = (2.0 * rng.integers(0, 256, n) + 1) / 512.0 * rng.choice([1, -1], n)
+    p = (rng.standard_normal(n) * 10.0 ** rng.uniform(-3, 2, n)).astype(np.float32)
+    dc = (rng.uniform(0.01, 2.0, n) * 10.0 ** rng.uniform(-4, 0, n)).astype(np.float32)
+    got = pm.fma_f32(p, dc, u)
+    want = np.array([_round_f32(Fraction(float(a)) * Fraction(float(b)) + Fraction(float(c)))
+                     for a, b, c in zip(p, dc, u.astype(np.float32))], np.float32)
+    assert np.array_equal(got, want)
+    p1 = np.float32((3 * 2 ** 22 + 3) * 2.0 ** -22)
+    d1 = np.float32((2 ** 24 - 4) * 2.0 ** -49)
+    exact = Fraction(float(p1)) * Fraction(float(d1)) + Fraction(1, 2)
+    assert exact == Fraction(1, 2) + 3 * Fraction(1, 2 ** 25) - 12 * Fraction(1, 2 ** 71)
+    assert _round_f32(exact) == 0.5 + 2.0 ** -24
+    assert pm.fma_f32(p1, d1, np.float32(0.5)) == np.float32(0.5 + 2.0 ** -24)
+    assert np.float32(np.float64(p1) * np.float64(d1) + 0.5) == np.float32(0.5 + 2.0 ** -23)
+    # the same tie mirrored below zero
+    assert pm.fma_f32(-p1, d1, np.float32(-0.5)) == np.float32(-(0.5 + 2.0 ** -24))
