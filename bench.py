@@ -14,7 +14,13 @@ Timing: W untimed steps, then exactly K steps between a barrier +
 synchronize on both sides, CUDA events on the library's stream; max over
 ranks.  Inputs exceed L2 (the 512^3 mesh alone is 537 MB), so no L2 flush.
 N > 1 runs independent replicas (one simulation per GPU, seed + rank); the
-path has no collective.
+path has no collective.  The K timed steps start at z = 49, where the store
+is nearly uniform; `whole_run` times the workload's whole run to z = 0 step
+by step beside them (late epochs are clustered and slower).
+
+The CPU baseline and the reference arm (--impl reference) run the FP64
+oracle as it stands at 128^3 particles / 256^3 mesh, one independent
+replica per host core (processes started with spawn).
 """
 import argparse
 import dataclasses
@@ -42,6 +48,8 @@ def parse():
                     help="override the workload's code widths; fp32 = the uncompressed FP32 store")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-whole-run", action="store_true",
+                    help="skip the whole z_init -> z_final run timed step by step beside the K timed steps")
     ap.add_argument("--ensemble", type=int, default=0,
                     help="run the C4 ensemble of this many uneven realisations (sims/s) instead of pm256")
     ap.add_argument("--streams", type=int, default=8, help="CUDA streams for --ensemble and --serve")
@@ -227,51 +235,151 @@ def oracle_state(w, ic, nps):
     return pm.encode(P, ic.pos, ic.vel, ic.ids, w.a_init, ic.sigma_1d), pm.step
 
 
-def cpu_baseline(w, steps=1):
-    """The FP64 oracle on the host cores: one step of the same workload at
-    128^3 particles / 256^3 mesh (same seed and cosmology)."""
-    import numpy as np
+ORACLE_NPS = 128            # the oracle's sample size: 128^3 particles, 256^3 mesh
+
+
+def _oracle_replica(wname, nps, codes, sched, warm, barrier, out):
+    """One oracle replica in its own process: the workload's ICs at nps^3
+    particles, `warm` untimed steps, then (after every replica is ready)
+    the remaining steps of `sched`, timed on the host clock."""
+    for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ.setdefault(var, "1")
+    import dataclasses
     import synth
-    nps = min(128, w.n_part_side)
+    w = synth.WORKLOADS[wname]
+    if codes:
+        w = dataclasses.replace(w, x_bytes=codes[0], v_bytes=codes[1])
     ic = synth.make_ics(w, n_part_side=nps, n_fine=2 * nps)
     st, step = oracle_state(w, ic, nps)
-    sch = np.linspace(w.a_init, w.a_final, w.n_steps + 1)
+    for i in range(warm):
+        st = step(st, float(sched[i]), float(sched[i + 1]))
+    barrier.wait()
     t0 = time.perf_counter()
-    for i in range(steps):
-        st = step(st, float(sch[i]), float(sch[i + 1]))
-    dt = time.perf_counter() - t0
-    return {"value": nps ** 3 * steps / dt, "unit": "particle-steps/s", "cores": 1, "kind": "oracle",
-            "sample": f"{steps} oracle step(s) of {w.name} at {nps}^3 particles / {2 * nps}^3 mesh "
-                      f"(numpy FP64, single-threaded), {dt:.1f} s"}
+    for i in range(warm, len(sched) - 1):
+        st = step(st, float(sched[i]), float(sched[i + 1]))
+    out.put(time.perf_counter() - t0)
+
+
+def oracle_replicas(w, sched, warm, workers=None):
+    """The oracle as it stands, on the host's cores: `workers` independent
+    replicas (one process each, started with spawn, numpy single-threaded),
+    each stepping the workload at 128^3 particles / 256^3 mesh through
+    `sched`.  Returns (particle-steps/s over all replicas, workers, wall s)."""
+    import multiprocessing as mp
+    if workers is None:
+        cores = os.cpu_count() or 1
+        try:                                              # each replica peaks near 2 GB
+            mem_gb = os.sysconf("SC_PAGE_SIZE") * os.sysconf("SC_AVPHYS_PAGES") / 2 ** 30
+        except (ValueError, OSError):
+            mem_gb = 16.0
+        workers = max(1, min(cores, int(mem_gb // 3)))
+    nps = min(ORACLE_NPS, w.n_part_side)
+    ctx = mp.get_context("spawn")
+    barrier = ctx.Barrier(workers)
+    out = ctx.Queue()
+    codes = (w.x_bytes, w.v_bytes)
+    procs = [ctx.Process(target=_oracle_replica, args=(w.name.split("@")[0], nps, codes, list(sched), warm, barrier,
+                                                     out)) for _ in range(workers)]
+    for p in procs:
+        p.start()
+    times = [out.get() for _ in procs]
+    for p in procs:
+        p.join()
+    dt = max(times)
+    steps = len(sched) - 1 - warm
+    return workers * nps ** 3 * steps / dt, workers, dt
+
+
+def cpu_baseline(w):
+    """The FP64 oracle on the host cores: one step of the same workload at
+    128^3 particles / 256^3 mesh (same seed and cosmology) in every replica."""
+    import numpy as np
+    sch = np.linspace(w.a_init, w.a_final, w.n_steps + 1)[:2]
+    value, workers, dt = oracle_replicas(w, sch, 0)
+    nps = min(ORACLE_NPS, w.n_part_side)
+    return {"value": value, "unit": "particle-steps/s", "cores": workers, "kind": "oracle",
+            "sample": f"one oracle step of {w.name} at {nps}^3 particles / {2 * nps}^3 mesh in each of {workers} "
+                      f"independent replicas (numpy FP64, one process and one thread per core), {dt:.1f} s"}
 
 
 def run_reference(args, w):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    import numpy as np
-    import synth
-    nps = min(128, w.n_part_side)
-    ic = synth.make_ics(w, n_part_side=nps, n_fine=2 * nps)
-    st, step = oracle_state(w, ic, nps)
+    import dataclasses
+    nps = min(ORACLE_NPS, w.n_part_side)
     sch = schedule(w, args.warmup + args.steps)
-    for i in range(args.warmup):
-        st = step(st, float(sch[i]), float(sch[i + 1]))
-    t0 = time.perf_counter()
-    for i in range(args.warmup, args.warmup + args.steps):
-        st = step(st, float(sch[i]), float(sch[i + 1]))
-    dt = time.perf_counter() - t0
-    value = nps ** 3 * args.steps / dt
-    sample = (f"oracle steps of {w.name} at {nps}^3 particles / {2 * nps}^3 mesh "
-              f"(numpy FP64, single-threaded)")
+    value, workers, dt = oracle_replicas(w, sch, args.warmup)
+    ws = dataclasses.replace(w, n_part_side=nps, n_fine=2 * nps)
+    sample = (f"{args.steps} oracle steps after {args.warmup} warm-up steps of {w.name} at {nps}^3 particles / "
+              f"{2 * nps}^3 mesh in each of {workers} independent replicas (numpy FP64, one process and one "
+              f"thread per core)")
     print(json.dumps({
         "impl": "reference", "metric": "particle-steps/s", "value": value, "unit": "particle-steps/s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": config_of(w),
-        "cpu_baseline": {"value": value, "unit": "particle-steps/s", "cores": 1, "kind": "oracle", "sample": sample},
+        "config": config_of(ws, mesh="FP64 (oracle)"),
+        "cpu_baseline": {"value": value, "unit": "particle-steps/s", "cores": workers, "kind": "oracle",
+                         "sample": sample},
         "e2e": {"value": value, "unit": "particle-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
+
+
+def whole_run(cube, ctx, ic, w, stream):
+    """The workload's whole run, z_init -> z_final, timed step by step with
+    CUDA events on the library's stream (no host synchronisation inside).
+    The schedule is the workload's uniform one unless it moves a particle
+    more than one coarse cell in a step (the library clamps the move and
+    reports CUBE_E_MIGRATION); then every step is cut by the velocity and
+    acceleration limit of cube_next_epoch_limited (the fastest particle
+    drifts at most half a coarse cell), with the uniform epochs as
+    waypoints.  An untimed pass over the schedule comes first (it also
+    fixes the limited schedule's epochs, which the timed pass replays)."""
+    import numpy as np
+    import torch
+    uniform = list(np.linspace(w.a_init, w.a_final, w.n_steps + 1))
+
+    def replay(sch, events=None):
+        cube.cube_encode(ctx, torch.from_numpy(ic.pos).cuda(), torch.from_numpy(ic.vel).cuda(),
+                         torch.from_numpy(ic.ids.view(np.int32)).cuda(), w.a_init, ic.sigma_1d)
+        torch.cuda.synchronize()
+        if events:
+            events[0].record(stream)
+        for i in range(len(sch) - 1):
+            cube.cube_pm_step(ctx, sch[i], sch[i + 1])
+            if events:
+                events[i + 1].record(stream)
+        torch.cuda.synchronize()
+        return cube.cube_stats_get(ctx)              # raises on a latched device error
+
+    kind = "uniform"
+    try:
+        replay(uniform)
+        sch = uniform
+    except cube.CubeError as e:
+        if e.status != cube.CUBE_E_MIGRATION:
+            raise
+        kind = "velocity-limited"
+        cube.cube_encode(ctx, torch.from_numpy(ic.pos).cuda(), torch.from_numpy(ic.vel).cuda(),
+                         torch.from_numpy(ic.ids.view(np.int32)).cuda(), w.a_init, ic.sigma_1d)
+        sch, a = [w.a_init], w.a_init
+        for t in uniform[1:]:
+            while a < t:
+                a_to, _ = cube.cube_next_epoch_limited(ctx, t, 0.5)
+                cube.cube_pm_step(ctx, a, a_to)
+                sch.append(a_to)
+                a = a_to
+        cube.cube_stats_get(ctx)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in sch]
+    st = replay(sch, ev)
+    ms = np.array([ev[i].elapsed_time(ev[i + 1]) for i in range(len(sch) - 1)])
+    k = len(ms) // 3
+    return {"schedule": f"{kind}, {len(ms)} steps z={1 / w.a_init - 1:g} -> {1 / w.a_final - 1:g}",
+            "steps": len(ms), "ms_per_step": float(ms.mean()),
+            "early_third_ms_per_step": float(ms[:k].mean()), "middle_third_ms_per_step": float(ms[k:-k].mean()),
+            "late_third_ms_per_step": float(ms[-k:].mean()), "max_ms": float(ms.max()),
+            "value": w.n_particles * len(ms) / (ms.sum() / 1e3), "unit": "particle-steps/s",
+            "max_migration": int(st.max_migration)}
 
 
 def codes_of(w):
@@ -282,8 +390,8 @@ def step_model(w):
     return "60 N_p + 32 N_mesh" if w.x_bytes == 4 else "(3s+3n_nu)N_p + 32 N_coarse + 32 N_mesh"
 
 
-def config_of(w):
-    return {"workload": f"{w.name}: {w.n_part_side}^3 particles, {w.n_fine}^3 FP32 mesh, {w.box:g} Mpc/h, "
+def config_of(w, mesh="FP32"):
+    return {"workload": f"{w.name}: {w.n_part_side}^3 particles, {w.n_fine}^3 {mesh} mesh, {w.box:g} Mpc/h, "
                         f"{'EdS' if w.cosmo_kind == 'eds' else 'LCDM BBKS'}, {codes_of(w)}, "
                         f"R={w.ratio}, steps uniform in a from z={1 / w.a_init - 1:g}",
             "l2": ("inputs larger than L2 (no flush)" if 4 * w.n_fine ** 3 > 129e6
@@ -595,6 +703,7 @@ def main():
     cube.cube_profile(ctx, 0)
     ms_max = max_over_ranks(ms, dist)
     value = world * w.n_particles * args.steps / (ms_max / 1e3)
+    run = None if args.no_whole_run else whole_run(cube, ctx, ic, w, stream)
 
     # end to end through the C ABI with pinned host buffers: H2D of the
     # particles, encode, one step, decode, D2H, every iteration
@@ -679,6 +788,7 @@ def main():
         "clocks": clk,
         "e2e": e2e,
         "e2e_checkpoint": e2e_ck,
+        "whole_run": run,
     }
     if world == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(w)

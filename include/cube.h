@@ -258,9 +258,16 @@ typedef struct {
 cube_status cube_state_view(cube_ctx* ctx, cube_state* out);
 
 typedef struct {
-    double mass;             /* total particle mass (= N_f^3)                   */
-    double momentum[3];      /* sum of p over particles, from the 2^-24 fixed-
-                                point cell sums of the last store build        */
+    double mass;             /* total particle mass: (sum of the cell counts,
+                                reduced on the device) x N_f^3 / N_p, i.e.
+                                N_f^3 for a consistent store; the
+                                uncompressed store counts N_p particles      */
+    double momentum[3];      /* sum over the current store's particles of the
+                                momenta as cube_decode returns them (FP32),
+                                each rounded to a multiple of 2^-24 and summed
+                                exactly in int64 on the device: within
+                                N_p 2^-25 of the exact sum, independent of
+                                the summation order                           */
     double sigma;            /* current codec scale                            */
     double a, a_p;           /* epochs of positions and momenta                */
     int64_t steps;           /* cube_pm_step calls since cube_encode           */
@@ -290,7 +297,8 @@ cube_status cube_density(cube_ctx* ctx, float* rho);
 cube_status cube_potential(cube_ctx* ctx, float* phi);
 
 /* Keep (1) or stop keeping (0) each step's drifted particles before the
-   re-sort, for cube_debug_drifted.  Costs 28 bytes per particle per step. */
+   re-sort, for cube_debug_drifted and cube_debug_force.  Costs 40 bytes per
+   particle per step. */
 cube_status cube_keep_drifted(cube_ctx* ctx, int32_t enable);
 
 /* Drifted particles of the last step, in the old storage order: the state
@@ -302,6 +310,16 @@ cube_status cube_keep_drifted(cube_ctx* ctx, int32_t enable);
    Errors: CUBE_E_STATE (not kept, or no step yet). */
 cube_status cube_debug_drifted(cube_ctx* ctx, int32_t* cell_old, float* u_new, float* p,
                                double* sigma_next);
+
+/* Force of the last step at each particle, in the old storage order (the
+   order of cube_debug_drifted): F [3][N_p] float = -grad Phi by the 4th-order
+   central difference on the fine mesh, interpolated to the particle by CIC
+   (the PM force of Section 2.3.3's update_vp, before it is multiplied by the
+   kick factor), in the units of the potential: lap Phi = (3/2) Omega_m
+   (rho - 1) with lengths in fine cells.  `force` may be host or device
+   memory, caller-owned.  Synchronises.
+   Errors: CUBE_E_ARG (NULL), CUBE_E_STATE (not kept, or no step yet). */
+cube_status cube_debug_force(cube_ctx* ctx, float* force);
 
 /* ---------------------------------------------------------------- tracing */
 
@@ -552,6 +570,14 @@ cube_status cube_server_release(cube_server* srv, int64_t ticket);
 
 /* Device bytes held now: resident states plus work areas. */
 cube_status cube_server_bytes(cube_server* srv, int64_t* bytes_in_use);
+
+/* Test hook for the admission path: the next n allocations of a larger
+   stream work area report "out of memory" without calling CUDA.  When a
+   work area cannot grow, the stream keeps its current area (its running
+   requests continue) and the request being admitted alone ends FAILED with
+   CUBE_E_NOMEM.  Not part of the paper (its memory model, Section 2.3, has
+   no allocator).  Errors: CUBE_E_ARG (NULL server, n < 0). */
+cube_status cube_server_inject_alloc_failures(cube_server* srv, int32_t n);
 
 #ifdef __cplusplus
 }

@@ -104,6 +104,34 @@ def force_at(pos, rho, omega_m, deconv_power=2):
     return np.stack([-cic_gather(g, pos) for g in fd4_gradient(phi)])
 
 
+def force_at_points(phi, pos):
+    """-grad Phi (FD4) interpolated by CIC at the particles `pos`, with the
+    difference evaluated only at the 8 nodes around each particle: the same
+    sums as the gather of fd4_gradient's meshes, for a sample of particles on
+    a mesh too large to difference whole."""
+    n = phi.shape[0]
+    flat = np.asarray(phi, dtype=np.float64).reshape(-1)
+    (ix, iy, iz), (wx, wy, wz) = _split(pos, n)
+    out = np.zeros((3, ix.size), dtype=np.float64)
+
+    def at(x, y, z):
+        return flat[((z % n) * n + (y % n)) * n + (x % n)]
+
+    for dz in (0, 1):
+        fz = wz if dz else 1.0 - wz
+        for dy in (0, 1):
+            fy = wy if dy else 1.0 - wy
+            for dx in (0, 1):
+                fx = wx if dx else 1.0 - wx
+                x, y, z = ix + dx, iy + dy, iz + dz
+                wt = fx * fy * fz
+                for d, (ex, ey, ez) in enumerate(((1, 0, 0), (0, 1, 0), (0, 0, 1))):
+                    d1 = at(x + ex, y + ey, z + ez) - at(x - ex, y - ey, z - ez)
+                    d2 = at(x + 2 * ex, y + 2 * ey, z + 2 * ez) - at(x - 2 * ex, y - 2 * ey, z - 2 * ez)
+                    out[d] -= wt * (8.0 * d1 - d2) / 12.0
+    return out
+
+
 # ---------------------------------------------------------------- power spectrum
 def shell_index(n2):
     """Shell i with i - 1/2 <= |n| < i + 1/2, decided in integers:

@@ -214,6 +214,22 @@ def density(store):
     return mesh.cic_deposit(pos, store.params.n_fine, store.params.mass)
 
 
+def kick_drift(P, u, vc_old, nu, sigma, force, kf, dc):
+    """Steps 3 and 5 of `step` for the given particles ([3][n] arrays): the
+    decoded momentum (Eq. v) kicked by force * kf and stored as an FP32
+    value, re-coded against the same v_c (Eq. nu, Fig. update_vp) and
+    decoded again; then the in-cell offset u (coarse units) drifted by that
+    momentum times dc, as the FP32 value of one rounding (Fig. update_xp).
+    Returns (p2, u_new), both FP32."""
+    v = np.stack([codec.vel_decode(nu[d], vc_old[d], sigma, P.v_bytes) for d in range(3)])
+    p1 = f32(v + force * kf)
+    nu1 = np.stack([codec.vel_encode((p1[d] - vc_old[d]).astype(np.float32), sigma, P.v_bytes)
+                    for d in range(3)])
+    p2 = f32(np.stack([codec.vel_decode(nu1[d], vc_old[d], sigma, P.v_bytes) for d in range(3)]))
+    u_new = fma_f32(p2, np.broadcast_to(np.float32(dc), p2.shape), np.asarray(u, np.float32))
+    return p2, u_new
+
+
 def step(store, a_from, a_to, keep_drifted=False):
     """One KD step of the compressed store (module docstring, steps 1-6)."""
     P = store.params
@@ -228,21 +244,15 @@ def step(store, a_from, a_to, keep_drifted=False):
     pos = np.stack([P.ratio * (cells[d] + u[d]) for d in range(3)])
     rho = mesh.cic_deposit(pos, P.n_fine, P.mass)
     force = mesh.force_at(pos, rho, om, P.deconv_power)
-    # 3: kick, re-quantised relative to the same v_c
+    # 3, 5: kick, re-quantised relative to the same v_c; drift
     a_mid = 0.5 * (a_from + a_to)
     kf = cosmo.kick_factor(store.a_p, a_mid, om, ol)
+    dc = np.float32(cosmo.drift_factor(a_from, a_to, om, ol) / P.ratio)
     vc_old = store.vc[:, key]
-    v = np.stack([codec.vel_decode(store.nu[d], vc_old[d], store.sigma, P.v_bytes) for d in range(3)])
-    p1 = f32(v + force * kf)
-    nu1 = np.stack([codec.vel_encode((p1[d] - vc_old[d]).astype(np.float32), store.sigma, P.v_bytes)
-                    for d in range(3)])
-    p2 = f32(np.stack([codec.vel_decode(nu1[d], vc_old[d], store.sigma, P.v_bytes) for d in range(3)]))
+    p2, u_new = kick_drift(P, u, vc_old, store.nu, store.sigma, force, kf, dc)
     # 4: codec scale for the new store
     ratio = cosmo.momentum_growth(a_to, om, ol) / cosmo.momentum_growth(a_from, om, ol)
     sigma_new = codec.snap_sigma(measured_sigma(p2, vc_old) * ratio)
-    # 5: drift inside the old cell (coarse units), decided in FP32
-    dc = np.float32(cosmo.drift_factor(a_from, a_to, om, ol) / P.ratio)
-    u_new = fma_f32(p2, np.broadcast_to(dc, p2.shape), u)
     # 6: rebuild
     out = encode_drifted(P, cells, u_new, p2, store.ids, sigma_new, a_to, a_mid)
     if keep_drifted:

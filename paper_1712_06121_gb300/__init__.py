@@ -96,6 +96,7 @@ _sigs = {
     "cube_potential": ([_P, _P], ctypes.c_int),
     "cube_keep_drifted": ([_P, ctypes.c_int32], ctypes.c_int),
     "cube_debug_drifted": ([_P, _P, _P, _P, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
+    "cube_debug_force": ([_P, _P], ctypes.c_int),
     "cube_profile": ([_P, ctypes.c_int32], ctypes.c_int),
     "cube_profile_read": ([_P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int32),
                            ctypes.POINTER(ctypes.c_int32)], ctypes.c_int),
@@ -133,6 +134,7 @@ _sigs = {
     "cube_server_decode": ([_P, ctypes.c_int64, _P, _P, _P], ctypes.c_int),
     "cube_server_release": ([_P, ctypes.c_int64], ctypes.c_int),
     "cube_server_bytes": ([_P, ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
+    "cube_server_inject_alloc_failures": ([_P, ctypes.c_int32], ctypes.c_int),
 }
 for _name, (_args, _res) in _sigs.items():
     _f = getattr(_lib, _name)
@@ -276,6 +278,10 @@ def cube_debug_drifted(ctx, cell_old, u_new, p):
     s = ctypes.c_double()
     _check(_lib.cube_debug_drifted(ctx, _ptr(cell_old), _ptr(u_new), _ptr(p), ctypes.byref(s)))
     return s.value
+
+
+def cube_debug_force(ctx, force):
+    _check(_lib.cube_debug_force(ctx, _ptr(force)))
 
 
 def cube_profile(ctx, max_steps):
@@ -432,4 +438,8 @@ def cube_server_bytes(srv):
     v = ctypes.c_int64()
     _check(_lib.cube_server_bytes(srv, ctypes.byref(v)))
     return v.value
+
+
+def cube_server_inject_alloc_failures(srv, n):
+    _check(_lib.cube_server_inject_alloc_failures(srv, int(n)))
 

@@ -189,6 +189,7 @@ struct cube_ctx {
     int* dbg_cell = nullptr;
     float* dbg_u = nullptr;
     float* dbg_p = nullptr;
+    float* dbg_f = nullptr;
     bool dbg_valid = false;
     // host mirror of the state
     bool encoded = false;
@@ -238,7 +239,7 @@ size_t state_layout(cube_ctx* c, char* base) {
     carve(base, off, c->tanh_, (size_t)(g.nulim + 2) * 8);
     carve(base, off, c->flags, 4);
     carve(base, off, c->maxmig, ((size_t)g.nbricks + 2) * 4);    // [0] max migration, [1 ..] crowded-brick list
-    carve(base, off, c->mom, 3 * 8);
+    carve(base, off, c->mom, 4 * 8);
     carve(base, off, c->vmax, 4);
     FftPlan& f = c->fft;
     carve(base, off, f.tw, (size_t)g.N * 8);
@@ -410,6 +411,7 @@ cube_status cube_destroy(cube_ctx* c) {
     if (c->dbg_cell) cudaFree(c->dbg_cell);
     if (c->dbg_u) cudaFree(c->dbg_u);
     if (c->dbg_p) cudaFree(c->dbg_p);
+    if (c->dbg_f) cudaFree(c->dbg_f);
     for (cudaEvent_t e : c->prof_ev) cudaEventDestroy(e);
     if (c->ev0) cudaEventDestroy(c->ev0);
     if (c->ev1) cudaEventDestroy(c->ev1);
@@ -672,6 +674,7 @@ cube_status cube_pm_step(cube_ctx* c, double a_from, double a_to) {
             CK(cudaMalloc((void**)&c->dbg_cell, 12 * (size_t)g.Np));
             CK(cudaMalloc((void**)&c->dbg_u, 12 * (size_t)g.Np));
             CK(cudaMalloc((void**)&c->dbg_p, 12 * (size_t)g.Np));
+            CK(cudaMalloc((void**)&c->dbg_f, 12 * (size_t)g.Np));
         }
     }
     CK(cudaEventRecord(c->ev0, c->st));
@@ -682,7 +685,7 @@ cube_status cube_pm_step(cube_ctx* c, double a_from, double a_to) {
     mesh_potential(c);
     c->phig_valid = true;
     StepScratch w{c->counts[kn], c->vsum, c->ghost, c->part, c->flags, c->maxmig, c->maxmig + 1};
-    DriftDebug dbg{c->keep ? c->dbg_cell : nullptr, c->dbg_u, c->dbg_p};
+    DriftDebug dbg{c->keep ? c->dbg_cell : nullptr, c->dbg_u, c->dbg_p, c->dbg_f};
     launch_passA(g, c->store(k), c->phig, c->tma ? &c->phig_map : nullptr, c->codec[k], kick, dc, w, dbg, c->st);
     mark(c, 8);
     launch_sigma_finalize(c->part, g.nbricks, 3.0 * (double)g.Np, ratio, 0.0, c->codec[kn].sigma, c->st);
@@ -1040,8 +1043,14 @@ cube_status cube_checkpoint_load(cube_ctx* c, const void* buf) {
     if (c->P.id_bytes) CK(cudaMemcpyAsync(c->id[k], b + sec[4], 4 * N, cudaMemcpyDefault, c->st));
     CK(cudaMemsetAsync(c->flags, 0, 4, c->st));
     CK(cudaMemsetAsync(c->maxmig, 0, 4, c->st));
-    unsigned total = (unsigned)g.Np;
-    if (!c->raw) CK(cudaMemcpyAsync(&total, c->offsets[k] + g.Ncc, 4, cudaMemcpyDeviceToHost, c->st));
+    // the counts must add up to N_p in 64 bits, none above N_p (a sum that
+    // only matches modulo 2^32 would pass a 32-bit check)
+    unsigned long long tot[2] = {(unsigned long long)g.Np, 0ull};
+    if (!c->raw) {
+        count_totals(c->counts[k], g.Ncc, reinterpret_cast<unsigned long long*>(c->mom), c->st);
+        c->launches += 1;
+        CK(cudaMemcpyAsync(tot, c->mom, sizeof(tot), cudaMemcpyDeviceToHost, c->st));
+    }
     CK(cudaGetLastError());
     CK(cudaStreamSynchronize(c->st));
     c->phig_valid = false;
@@ -1050,7 +1059,8 @@ cube_status cube_checkpoint_load(cube_ctx* c, const void* buf) {
     c->steps = 0;
     c->dbg_valid = false;
     c->timed = false;
-    if (total != (unsigned)g.Np) return fail(CUBE_E_ARG, "checkpoint cell counts do not add up to the particle count");
+    if (tot[0] != (unsigned long long)g.Np || tot[1] > (unsigned long long)g.Np)
+        return fail(CUBE_E_ARG, "checkpoint cell counts do not add up to the particle count");
     c->encoded = true;
     return CUBE_OK;
 }
@@ -1085,18 +1095,18 @@ cube_status cube_stats_get(cube_ctx* c, cube_stats* out) {
     const Geo& g = c->g;
     const int64_t launched = c->launches;          // before this call's own reduction
     if (c->raw) launch_raw_momentum(g, (const float*)c->nu[0], c->mom, c->st);
-    else launch_momentum(g, c->vsum, c->mom, c->st);
+    else launch_store_sums(g, c->store(c->cur), c->codec[c->cur].dec, c->mom, c->st);
     c->launches += 1;
-    long long m[3] = {0, 0, 0};
+    long long m[4] = {0, 0, 0, g.Np};
     unsigned f = 0;
     int mig = 0;
     out->sigma = 0.0;
-    CK(cudaMemcpyAsync(m, c->mom, sizeof(m), cudaMemcpyDeviceToHost, c->st));
+    CK(cudaMemcpyAsync(m, c->mom, (c->raw ? 3 : 4) * sizeof(long long), cudaMemcpyDeviceToHost, c->st));
     if (!c->raw) CK(cudaMemcpyAsync(&out->sigma, c->codec[c->cur].sigma, 8, cudaMemcpyDeviceToHost, c->st));
     CK(cudaMemcpyAsync(&f, c->flags, 4, cudaMemcpyDeviceToHost, c->st));
     CK(cudaMemcpyAsync(&mig, c->maxmig, 4, cudaMemcpyDeviceToHost, c->st));
     CK(cudaStreamSynchronize(c->st));
-    out->mass = std::pow((double)g.N, 3);
+    out->mass = (double)m[3] * particle_mass(g);
     for (int d = 0; d < 3; ++d) out->momentum[d] = (double)m[d] * std::ldexp(1.0, -24);
     out->a = c->a;
     out->a_p = c->a_p;
@@ -1158,8 +1168,9 @@ cube_status cube_keep_drifted(cube_ctx* c, int32_t enable) {
         cudaFree(c->dbg_cell);
         cudaFree(c->dbg_u);
         cudaFree(c->dbg_p);
+        cudaFree(c->dbg_f);
         c->dbg_cell = nullptr;
-        c->dbg_u = c->dbg_p = nullptr;
+        c->dbg_u = c->dbg_p = c->dbg_f = nullptr;
         c->dbg_valid = false;
     }
     return CUBE_OK;
@@ -1174,6 +1185,14 @@ cube_status cube_debug_drifted(cube_ctx* c, int32_t* cell_old, float* u_new, flo
     if ((s = to_user(c, u_new, c->dbg_u, b, !is_device_ptr(u_new))) != CUBE_OK) return s;
     if ((s = to_user(c, p, c->dbg_p, b, !is_device_ptr(p))) != CUBE_OK) return s;
     if (sigma_next) CK(cudaMemcpyAsync(sigma_next, c->codec[c->cur].sigma, 8, cudaMemcpyDeviceToHost, c->st));
+    return latched(c);
+}
+
+cube_status cube_debug_force(cube_ctx* c, float* force) {
+    if (!c || !force) return fail(CUBE_E_ARG, "NULL argument");
+    if (!c->dbg_valid) return fail(CUBE_E_STATE, "no drifted state kept: enable cube_keep_drifted before the step");
+    cube_status s = to_user(c, force, c->dbg_f, 12 * (size_t)c->g.Np, !is_device_ptr(force));
+    if (s != CUBE_OK) return s;
     return latched(c);
 }
 
@@ -1234,11 +1253,13 @@ cube_status served_create(const cube_params* p, cudaStream_t st, cube_ctx** out)
     return create_ctx(p, st, true, out);
 }
 
-void served_bind(cube_ctx* c, char* work) {
-    if (c->work_base == work) return;
+cube_status served_bind(cube_ctx* c, char* work) {
+    if (!work) return fail(CUBE_E_NOMEM, "the request's stream has no work area");
+    if (c->work_base == work) return CUBE_OK;
     c->work_base = work;
     work_layout(c, work);
     c->tma = encode_phig_map(c);
+    return CUBE_OK;
 }
 
 cube_status served_encode(cube_ctx* c, const float* pos, const float* vel, const uint32_t* id, double a,

@@ -101,6 +101,25 @@ __global__ void k_scan_down(const unsigned* in, int64_t n, const unsigned* __res
 
 __global__ void k_write_total(unsigned* out, int64_t n, const unsigned* total) { out[n] = *total; }
 
+// 64-bit sum and maximum of n 32-bit counts: out2[0] += sum, out2[1] = max(out2[1], max)
+__global__ void k_count_totals(const unsigned* __restrict__ c, int64_t n, unsigned long long* out2) {
+    unsigned long long s = 0;
+    unsigned m = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        s += c[i];
+        m = max(m, c[i]);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        s += __shfl_down_sync(0xffffffffu, s, o);
+        m = max(m, __shfl_down_sync(0xffffffffu, m, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(&out2[0], s);
+        atomicMax(&out2[1], (unsigned long long)m);
+    }
+}
+
 // ------------------------------------------------------------ radix sort
 constexpr int RX_T = 256;
 constexpr int RX_ITEMS = 8;
@@ -156,6 +175,12 @@ void exclusive_scan(const unsigned* in, unsigned* out, int64_t n, unsigned* tmp,
     k_scan_bsums<<<1, SCAN_T, 0, st>>>(tmp, nb, total);
     k_scan_down<<<nb, SCAN_T, 0, st>>>(in, n, tmp, out, vec);
     k_write_total<<<1, 1, 0, st>>>(out, n, total);
+}
+
+void count_totals(const unsigned* counts, int64_t n, unsigned long long* out2, cudaStream_t st) {
+    cudaMemsetAsync(out2, 0, 2 * sizeof(unsigned long long), st);
+    const int64_t nb = (n + 255) / 256;
+    k_count_totals<<<(int)(nb < 1024 ? (nb < 1 ? 1 : nb) : 1024), 256, 0, st>>>(counts, n, out2);
 }
 
 int64_t radix_tmp_words(int64_t n) {

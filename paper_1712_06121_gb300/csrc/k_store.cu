@@ -671,6 +671,7 @@ __global__ void __launch_bounds__(T_BRICK, 4) k_passA(Geo g, StoreDev s, const f
                 dbg.cell_old[d * g.Np + i] = cg[d];
                 dbg.u_new[d * g.Np + i] = un[d];
                 dbg.p[d * g.Np + i] = pv[d];
+                dbg.force[d * g.Np + i] = force[d];
             }
         }
     }
@@ -969,15 +970,39 @@ __global__ void __launch_bounds__(PB_WARPS * 32, 5) k_passB(Geo g, StoreDev so, 
     }
 }
 
-__global__ void k_momentum(int ncc, const long long* __restrict__ vsum, long long* out3) {
-    // exact integer sums of the fixed-point cell momenta
-    for (int d = 0; d < 3; ++d) {
-        long long s = 0;
-        for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < ncc; c += gridDim.x * blockDim.x)
-            s += vsum[(int64_t)d * ncc + c];
+// Global sums of the current store (Section 2.3.3's bookkeeping): the
+// momenta exactly as cube_decode returns them (v_c + decoded offset, FP32),
+// each rounded to a multiple of 2^-24 and summed exactly in int64, so the
+// result is independent of the summation order and within N 2^-25 of the
+// exact sum of the decoded values; and the particle count as the sum of the
+// cell counts.  One CTA per brick, one 64-bit atomic per warp and quantity.
+template <int NV>
+__global__ void __launch_bounds__(T_BRICK) k_store_sums(Geo g, StoreDev s, const float* __restrict__ dec,
+                                                        long long* __restrict__ out4) {
+    extern __shared__ unsigned sm_off[];
+    const int nbc = g.B * g.B * g.B;
+    const int L0 = blockIdx.x * nbc;
+    for (int c = threadIdx.x; c <= nbc; c += blockDim.x) sm_off[c] = s.offsets[L0 + c];
+    long long cnt = 0;
+    for (int c = threadIdx.x; c < nbc; c += blockDim.x) cnt += s.counts[L0 + c];
+    __syncthreads();
+    const unsigned q1 = min(sm_off[nbc], (unsigned)g.Np);
+    long long m[3] = {0, 0, 0};
+    for (unsigned i = min(sm_off[0], q1) + threadIdx.x; i < q1; i += blockDim.x) {
+        const int lc = upper_cell(sm_off, nbc, i);
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-        if ((threadIdx.x & 31) == 0) atomicAdd(reinterpret_cast<unsigned long long*>(&out3[d]), (unsigned long long)s);
+        for (int d = 0; d < 3; ++d) {
+            const int nu = load_nu<NV>(s.nu, d * g.Np + i, g.nulim);
+            m[d] += vel_fix(s.vc[(int64_t)d * g.Ncc + L0 + lc] + dec[nu + g.nulim]);
+        }
+    }
+    long long v[4] = {m[0], m[1], m[2], cnt};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
+        if ((threadIdx.x & 31) == 0 && v[k])
+            atomicAdd(reinterpret_cast<unsigned long long*>(&out4[k]), (unsigned long long)v[k]);
     }
 }
 
@@ -1134,9 +1159,11 @@ void launch_passB(const Geo& g, const StoreDev& so, const StoreDev& sn, const Co
     else { set_smem_attrs<2, 2>(); Disp<2, 2>::passB(g, so, sn, cur, next, dc, w.ghost, vcn, w.flags, w.big, sm, st); }
 }
 
-void launch_momentum(const Geo& g, const long long* vsum, long long* out3, cudaStream_t st) {
-    cudaMemsetAsync(out3, 0, 3 * sizeof(long long), st);
-    k_momentum<<<std::min(1024, nblk(g.Ncc, 256)), 256, 0, st>>>(g.Ncc, vsum, out3);
+void launch_store_sums(const Geo& g, const StoreDev& s, const float* dec, long long* out4, cudaStream_t st) {
+    size_t sm = (size_t)(g.B * g.B * g.B + 1) * sizeof(unsigned);
+    cudaMemsetAsync(out4, 0, 4 * sizeof(long long), st);
+    if (g.nnu == 1) k_store_sums<1><<<g.nbricks, T_BRICK, sm, st>>>(g, s, dec, out4);
+    else k_store_sums<2><<<g.nbricks, T_BRICK, sm, st>>>(g, s, dec, out4);
 }
 
 }  // namespace cube

@@ -50,6 +50,8 @@ void set_last_error(const std::string& msg);     // message for cube_last_error(
 // ------------------------------------------------------------ k_scan.cu
 int scan_tmp_words(int64_t n);
 void exclusive_scan(const unsigned* in, unsigned* out, int64_t n, unsigned* tmp, cudaStream_t st);
+// out2[0] = 64-bit sum, out2[1] = maximum of n counts
+void count_totals(const unsigned* counts, int64_t n, unsigned long long* out2, cudaStream_t st);
 int64_t radix_tmp_words(int64_t n);
 void radix_sort_pairs(unsigned* keys, unsigned* vals, int64_t n, int key_bits, unsigned* tmp, cudaStream_t st);
 
@@ -75,6 +77,7 @@ struct DriftDebug {
     int* cell_old;      // [3][Np] or null
     float* u_new;       // [3][Np]
     float* p;           // [3][Np]
+    float* force;       // [3][Np]: gathered -grad Phi before the kick
 };
 
 struct StepScratch {
@@ -110,7 +113,9 @@ void launch_passA(const Geo& g, const StoreDev& s, const float* phig, const CUte
 void launch_cells(const Geo& g, const StepScratch& w, unsigned* off_new, float* vc_new, cudaStream_t st);
 void launch_passB(const Geo& g, const StoreDev& s_old, const StoreDev& s_new, const CodecDev& cur,
                   const CodecDev& next, float dc, const StepScratch& w, cudaStream_t st);
-void launch_momentum(const Geo& g, const long long* vsum, long long* out3, cudaStream_t st);
+// sums over the current store: out[0..2] momentum of the decoded particles in
+// 2^-24 fixed point, out[3] the particle count (sum of the cell counts)
+void launch_store_sums(const Geo& g, const StoreDev& s, const float* dec, long long* out4, cudaStream_t st);
 
 // uncompressed FP32 particles (k_raw.cu)
 void launch_raw_encode(const Geo& g, const float* pos, const float* vel, const unsigned* id_in, float* P, float* V,

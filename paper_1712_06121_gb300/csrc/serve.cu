@@ -23,7 +23,7 @@
 namespace cube {
 cube_status served_sizes(const cube_params* p, size_t* state, size_t* work);
 cube_status served_create(const cube_params* p, cudaStream_t st, cube_ctx** out);
-void served_bind(cube_ctx* c, char* work);
+cube_status served_bind(cube_ctx* c, char* work);
 cube_status served_encode(cube_ctx* c, const float* pos, const float* vel, const uint32_t* id, double a,
                           double sigma);
 cube_status served_finish(cube_ctx* c, int32_t n_bins, double* pk3, unsigned* flags2);
@@ -94,6 +94,7 @@ struct cube_server {
     std::map<int64_t, Request*> reqs;
     std::vector<cudaEvent_t> spare;       // recycled step events
     int64_t next_ticket = 1;
+    int inject_alloc_failures = 0;        // test hook: work-area allocations to refuse
     std::chrono::steady_clock::time_point t0;
 
     double now() const { return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count(); }
@@ -132,8 +133,8 @@ cube_status advance(cube_server* s, Request* r) {
     if (r->cells > 0.0) {                 // adaptive: one step per max-speed read-back
         if (r->finishing) goto finish;
         if (!r->vmax_pending) {
-            served_bind(r->ctx, sl.work);
-            cube_status st = served_vmax_enqueue(r->ctx, &r->flags[2]);
+            cube_status st = served_bind(r->ctx, sl.work);
+            if (st == CUBE_OK) st = served_vmax_enqueue(r->ctx, &r->flags[2]);
             if (st != CUBE_OK) {
                 fail_request(s, r, st);
                 return CUBE_OK;
@@ -156,8 +157,8 @@ cube_status advance(cube_server* s, Request* r) {
                 fail_request(s, r, served_fail(CUBE_E_ARG, "no step keeps the fastest particle within the limit"));
                 return CUBE_OK;
             }
-            served_bind(r->ctx, sl.work);
-            cube_status st = cube_pm_step(r->ctx, a, a_to);
+            cube_status st = served_bind(r->ctx, sl.work);
+            if (st == CUBE_OK) st = cube_pm_step(r->ctx, a, a_to);
             if (st != CUBE_OK) {
                 fail_request(s, r, st);
                 return CUBE_OK;
@@ -169,8 +170,8 @@ cube_status advance(cube_server* s, Request* r) {
         r->waypoint = n_steps + 1;
     }
     while (r->cells <= 0.0 && r->next < n_steps && (int)r->inflight.size() < kDepth) {
-        served_bind(r->ctx, sl.work);
-        cube_status st = cube_pm_step(r->ctx, r->epochs[r->next], r->epochs[r->next + 1]);
+        cube_status st = served_bind(r->ctx, sl.work);
+        if (st == CUBE_OK) st = cube_pm_step(r->ctx, r->epochs[r->next], r->epochs[r->next + 1]);
         if (st != CUBE_OK) {
             fail_request(s, r, st);
             return CUBE_OK;
@@ -181,8 +182,8 @@ cube_status advance(cube_server* s, Request* r) {
         ++r->next;
     }
     if ((r->cells > 0.0 ? r->waypoint > n_steps : r->next == n_steps) && !r->finishing) {
-        served_bind(r->ctx, sl.work);
-        cube_status st = served_finish(r->ctx, r->n_bins, r->pk, r->flags);
+        cube_status st = served_bind(r->ctx, sl.work);
+        if (st == CUBE_OK) st = served_finish(r->ctx, r->n_bins, r->pk, r->flags);
         if (st != CUBE_OK) {
             fail_request(s, r, st);
             return CUBE_OK;
@@ -224,13 +225,28 @@ cube_status admit(cube_server* s) {
         }
         if (k < 0) break;                 // in arrival order: wait for memory
         Slot& sl = s->slots[k];
-        if (grow) {                       // stream-ordered: the old area's last user runs first
-            if (sl.work) SCK(cudaFreeAsync(sl.work, sl.st));
-            sl.work = nullptr;
-            sl.bytes = 0;
-            SCK(cudaMallocAsync((void**)&sl.work, r->work_bytes, sl.st));
+        if (grow) {
+            // the larger area is allocated before the old one is released, so
+            // the stream's running requests keep a valid work area whatever
+            // happens; without memory, this request alone fails
+            char* fresh = nullptr;
+            cudaError_t e = cudaErrorMemoryAllocation;
+            if (s->inject_alloc_failures > 0) --s->inject_alloc_failures;
+            else e = cudaMallocAsync((void**)&fresh, r->work_bytes, sl.st);
+            if (e != cudaSuccess) {
+                cudaGetLastError();
+                s->queue.pop_front();
+                if (e != cudaErrorMemoryAllocation) {
+                    fail_request(s, r, CUBE_E_CUDA);
+                    return served_fail(CUBE_E_CUDA, cudaGetErrorString(e));
+                }
+                fail_request(s, r, served_fail(CUBE_E_NOMEM, "no device memory for the stream's larger work area"));
+                continue;
+            }
+            if (sl.work) SCK(cudaFreeAsync(sl.work, sl.st));   // stream-ordered: its last user runs first
+            s->used += (int64_t)r->work_bytes - (int64_t)sl.bytes;
+            sl.work = fresh;
             sl.bytes = r->work_bytes;
-            s->used += grow;
         }
         s->queue.pop_front();
         r->slot = k;
@@ -238,8 +254,8 @@ cube_status admit(cube_server* s) {
         cube_status st = served_create(&r->prm, sl.st, &r->ctx);
         if (st == CUBE_OK) {
             s->used += (int64_t)r->state_bytes;
-            served_bind(r->ctx, sl.work);
-            st = served_encode(r->ctx, r->pos, r->vel, r->id, r->epochs[0], r->sigma);
+            st = served_bind(r->ctx, sl.work);
+            if (st == CUBE_OK) st = served_encode(r->ctx, r->pos, r->vel, r->id, r->epochs[0], r->sigma);
         }
         if (st != CUBE_OK) {
             fail_request(s, r, st);
@@ -427,7 +443,8 @@ cube_status cube_server_decode(cube_server* s, int64_t ticket, float* pos, float
     Request* r = find(s, ticket);
     if (!r) return served_fail(CUBE_E_ARG, "unknown ticket");
     if (r->state != CUBE_REQ_DONE) return served_fail(CUBE_E_STATE, "request not done");
-    served_bind(r->ctx, s->slots[r->slot].work);
+    cube_status st = served_bind(r->ctx, s->slots[r->slot].work);
+    if (st != CUBE_OK) return st;
     return cube_decode(r->ctx, pos, vel, id);
 }
 
@@ -447,6 +464,12 @@ cube_status cube_server_release(cube_server* s, int64_t ticket) {
     if (r->pk) cudaFreeHost(r->pk);
     s->reqs.erase(ticket);
     delete r;
+    return CUBE_OK;
+}
+
+cube_status cube_server_inject_alloc_failures(cube_server* s, int32_t n) {
+    if (!s || n < 0) return served_fail(CUBE_E_ARG, "server is NULL or n < 0");
+    s->inject_alloc_failures = n;
     return CUBE_OK;
 }
 

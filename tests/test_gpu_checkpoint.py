@@ -98,6 +98,15 @@ def test_bad_checkpoints_are_refused(cube):
         with pytest.raises(cube.CubeError) as e:
             cube.cube_checkpoint_load(a, bad)
         assert e.value.status == cube.CUBE_E_ARG
+        bad = good.copy()
+        cnt = bad[64:64 + 8].view(np.uint32)                   # the first two cells' counts
+        cnt[0] = np.uint32(int(cnt[0]) + 2 ** 31)
+        cnt[1] = np.uint32(int(cnt[1]) + 2 ** 31)              # + 2^32: the 32-bit sum still equals N
+        assert int(good[64:].view(np.uint32)[:prm.n_fine ** 3 // 64].sum(dtype=np.uint32)) == \
+            int(bad[64:].view(np.uint32)[:prm.n_fine ** 3 // 64].sum(dtype=np.uint32))
+        with pytest.raises(cube.CubeError) as e:
+            cube.cube_checkpoint_load(a, bad)
+        assert e.value.status == cube.CUBE_E_ARG
         other = cube.make_params(64, 32 ** 3, x_bytes=1, v_bytes=2, box=prm.box, omega_m=prm.omega_m,
                                  omega_l=prm.omega_l)
         c2 = cube.cube_create(other, torch.cuda.current_stream())

@@ -346,6 +346,83 @@ def test_step_matches_oracle_step(cube):
         cube.cube_destroy(ctx)
 
 
+@pytest.mark.parametrize("name,nps,nf,brick,deconv", [("pm64", 32, 64, 4, 2), ("pm64", 32, 64, 2, 2),
+                                                      ("pm64", 32, 64, 1, 1), ("pm64", 24, 48, 0, 2),
+                                                      ("pm256", 64, 128, 0, 2), ("pm256", 48, 96, 2, 0)])
+def test_force_matches_oracle(cube, name, nps, nf, brick, deconv):
+    """Pass A's gathered force (Section 2.3.3, update_vp: -grad Phi by FD4,
+    CIC-interpolated) at every particle, element by element against the
+    oracle's FP64 force_at from the same store's positions: within 1e-4 of
+    the largest |F| (FP32 FFTs and differences), for brick sides 1, 2, 4, a
+    3 * 2^a mesh and every deconvolution power."""
+    w, ic = _ics(nps, nf, name)
+    n = nps ** 3
+    prm, ctx = _ctx(cube, nf, n, 1, 1, w, brick=brick, deconv=deconv)
+    try:
+        cube.cube_encode(ctx, ic.pos, ic.vel, ic.ids, w.a_init, ic.sigma_1d)
+        before = read_store(cube, ctx)
+        cube.cube_keep_drifted(ctx, True)
+        cube.cube_pm_step(ctx, w.a_init, w.a_init + 0.004)
+        f = np.empty((3, n), np.float32)
+        cube.cube_debug_force(ctx, f)
+    finally:
+        cube.cube_destroy(ctx)
+    P = oracle_params(pm, prm, before["brick"])
+    st = pm.Store(P, before["counts"], before["vc"], before["chi"], before["nu"], before["ids"], before["sigma"],
+                  before["a"], before["a_p"])
+    pos, _, _ = pm.decode(st)
+    want = mesh.force_at(pos, mesh.cic_deposit(pos, nf, P.mass), prm.omega_m, deconv)
+    scale = np.max(np.abs(want))
+    assert scale > 0
+    err = np.max(np.abs(f - want)) / scale
+    assert err <= 1e-4, err
+
+
+def _decoded_momentum_bound(st):
+    """(FP64 sum of the oracle-decoded momenta, bound on the GPU's sum): the
+    GPU sums FP32 decodes (v_c + table offset, each within one FP32 rounding
+    of its value and one of the offset) rounded to multiples of 2^-24."""
+    key = layout.particle_cells(st.counts)
+    p = st.params
+    off = np.stack([pm.codec.vel_decode_offset(st.nu[d], st.sigma, p.v_bytes) for d in range(3)])
+    v = st.vc[:, key].astype(np.float64) + off
+    tot = v.sum(axis=1)
+    ulp = np.spacing(np.abs(v).astype(np.float32)).astype(np.float64)
+    ulo = np.spacing(np.abs(off).astype(np.float32)).astype(np.float64)
+    bound = 0.5 * (ulp + ulo).sum(axis=1) + v.shape[1] * 2.0 ** -25 + 1e-12 * np.abs(v).sum(axis=1)
+    return tot, bound
+
+
+@pytest.mark.parametrize("xb,vb", [(1, 1), (2, 2), (1, 2)])
+def test_store_sums_match_oracle(cube, xb, vb):
+    """cube_stats (Section 2.3.3 bookkeeping): the mass is the reduction of
+    the cell counts times the particle mass, N_f^3 exactly; the momentum is
+    the device reduction of the decoded momenta, against the FP64 sum of the
+    oracle's decode of the same store within the FP32-decode and 2^-24
+    fixed-point bounds, after the encode and after each of 3 steps."""
+    w, ic = _ics(32, 64)
+    n = 32 ** 3
+    prm, ctx = _ctx(cube, 64, n, xb, vb, w)
+    sched = synth.uniform_schedule(w.a_init, 0.05, 3)
+    vel = (ic.vel + np.array([[0.3], [-0.2], [0.15]], np.float32)).astype(np.float32)  # a bulk flow
+    try:
+        cube.cube_encode(ctx, ic.pos, vel, ic.ids, w.a_init, ic.sigma_1d)
+        for i in range(4):
+            if i:
+                cube.cube_pm_step(ctx, sched[i - 1], sched[i])
+            stats = cube.cube_stats_get(ctx)
+            g = read_store(cube, ctx)
+            st = pm.Store(oracle_params(pm, prm, g["brick"]), g["counts"], g["vc"], g["chi"], g["nu"], g["ids"],
+                          g["sigma"], g["a"], g["a_p"])
+            assert stats.mass == 64.0 ** 3
+            want, bound = _decoded_momentum_bound(st)
+            got = np.array(stats.momentum)
+            assert np.all(np.abs(got - want) <= bound), (i, got, want, bound)
+            assert np.max(np.abs(want)) > 100 * np.max(bound)       # the sums are far from trivial
+    finally:
+        cube.cube_destroy(ctx)
+
+
 def test_full_run_pm64_matches_oracle(cube):
     """The 64^3 / 128^3 EdS x1v2 workload, 10 steps a = 0.02 -> 0.1: RMS
     displacement difference (matched by id) <= 1e-3 fine cells and P(k)

@@ -253,3 +253,57 @@ def test_adaptive_requests_equal_the_velocity_limited_run_alone(cube):
         assert e.value.status == cube.CUBE_E_ARG
     finally:
         cube.cube_server_destroy(srv)
+
+
+def test_a_work_area_that_cannot_grow_fails_only_the_new_request(cube):
+    """Admission needs a larger work area for a bigger request on a stream
+    whose area is in use.  When that allocation fails (made to fail on the
+    host by the server's test hook), the stream keeps its old area, the
+    running request finishes with the same result as alone, the new request
+    ends FAILED with CUBE_E_NOMEM, the bytes held stay exact, and a later
+    request of the same size is admitted and completes."""
+    mix = _mix()
+    small, big = mix[0], mix[3]                       # 16^3 and 48^3 particles
+    ics = {w.n_part_side: synth.make_ics(w) for w in (small, big)}
+    nb = 4
+    s_sb, s_wb = cube.cube_server_sizes(_params(cube, small))
+    b_sb, b_wb = cube.cube_server_sizes(_params(cube, big))
+    assert b_wb > s_wb
+    srv = cube.cube_server_create(8 << 30, n_streams=1, max_running=4)
+    keep = []
+
+    def submit(w):
+        ic = ics[w.n_part_side]
+        host = (_pinned(ic.pos), _pinned(ic.vel), _pinned(ic.ids.view(np.int32)))
+        keep.append(host)
+        sch = synth.uniform_schedule(w.a_init, w.a_final, w.n_steps)
+        return cube.cube_server_submit(srv, _params(cube, w), *host, ic.sigma_1d, sch, nb)
+    try:
+        ta = submit(small)
+        cube.cube_server_pump(srv)
+        assert cube.cube_server_info(srv, ta).state == cube.CUBE_REQ_RUNNING
+        assert cube.cube_server_bytes(srv) == s_sb + s_wb
+        cube.cube_server_inject_alloc_failures(srv, 1)
+        tb = submit(big)
+        cube.cube_server_pump(srv)
+        ib = cube.cube_server_info(srv, tb)
+        assert ib.state == cube.CUBE_REQ_FAILED and ib.error == cube.CUBE_E_NOMEM
+        assert cube.cube_server_bytes(srv) == s_sb + s_wb        # the old area is kept, nothing leaked
+        cube.cube_server_drain(srv)
+        assert cube.cube_server_info(srv, ta).state == cube.CUBE_REQ_DONE
+        n = small.n_particles
+        got = (np.empty((3, n), np.float32), np.empty((3, n), np.float32), np.empty(n, np.uint32))
+        cube.cube_server_decode(srv, ta, *got)
+        want = _alone(cube, small, ics[small.n_part_side], nb)
+        for g, e in zip(got, want[3:]):
+            assert np.array_equal(g, e)
+        cube.cube_server_release(srv, tb)
+        tc = submit(big)                                          # the allocation now succeeds
+        cube.cube_server_drain(srv)
+        assert cube.cube_server_info(srv, tc).state == cube.CUBE_REQ_DONE
+        assert cube.cube_server_bytes(srv) == s_sb + b_sb + b_wb
+        cube.cube_server_release(srv, ta)
+        cube.cube_server_release(srv, tc)
+        assert cube.cube_server_bytes(srv) == b_wb
+    finally:
+        cube.cube_server_destroy(srv)

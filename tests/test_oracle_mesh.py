@@ -131,6 +131,26 @@ def test_pm_force_matches_pairwise_sum(deconv):
         assert np.median(err) < 0.03 and np.percentile(err, 90) < 0.10
 
 
+def test_sampled_force_equals_the_whole_mesh_gather():
+    """force_at_points (the FD4 difference at the 8 nodes around each
+    particle only) gives the same force as differencing the whole mesh and
+    gathering (force_at's path), including particles across the periodic
+    edge; a dropped sign or a swapped axis fails it."""
+    rng = np.random.default_rng(31)
+    n = 24
+    phi = rng.standard_normal((n, n, n))
+    pos = rng.uniform(0, n, (3, 500))
+    pos[:, :8] = np.array([[0.0, n - 1e-9, 0.5, n - 0.5, 1.0, 23.0, 0.0, 12.25]] * 3)
+    want = np.stack([-mesh.cic_gather(g, pos) for g in mesh.fd4_gradient(phi)])
+    got = mesh.force_at_points(phi, pos)
+    assert np.max(np.abs(got - want)) <= 1e-12 * np.max(np.abs(want))
+    # a potential that varies along y only pushes along y only
+    y = np.arange(n)
+    phi_y = np.broadcast_to(np.cos(2 * np.pi * 3 * y / n)[None, :, None], (n, n, n))
+    f = mesh.force_at_points(phi_y, pos)
+    assert np.max(np.abs(f[0])) <= 1e-12 and np.max(np.abs(f[2])) <= 1e-12 and np.max(np.abs(f[1])) > 0.1
+
+
 # ---------------------------------------------------------------- time integration
 def test_leapfrog_factors_eds_closed_form():
     for a0, a1 in [(0.02, 0.028), (0.1, 1.0), (0.5, 0.51)]:
