@@ -52,12 +52,24 @@ __device__ __forceinline__ bool mbar_test(unsigned long long* bar, unsigned pari
         : "memory");
     return done != 0;
 }
-// waits at most ~2^20 polls (tens of milliseconds); false if the phase never completed
+// one potentially blocking test: the thread is suspended until the phase
+// completes or about `hint_ns` nanoseconds pass (the hardware may wake it
+// earlier); true if the phase completed
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned parity, unsigned hint_ns) {
+    unsigned done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(done)
+        : "r"(smem_addr(bar)), "r"(parity), "r"(hint_ns)
+        : "memory");
+    return done != 0;
+}
+// waits at most 256 suspensions of up to 0.1 ms each (tens of milliseconds in
+// all); false if the phase never completed.  A suspended thread issues no
+// instructions, so waiting warps leave the issue slots to the SM's others.
 __device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* bar, unsigned parity) {
-    for (int it = 0; it < (1 << 20); ++it) {
-        if (mbar_test(bar, parity)) return true;
-        __nanosleep(32);
-    }
+    for (int it = 0; it < 256; ++it)
+        if (mbar_try_wait(bar, parity, 100000u)) return true;
     return false;
 }
 // 3-D tiled TMA load of the tensor map's box at (x, y, z) into shared memory,
@@ -227,6 +239,51 @@ __device__ __forceinline__ int nu_estimate(float d, float s, float m_over_pi) {
     if (big) a = 1.57079633f - a;
     return __float2int_rn(m_over_pi * a);
 }
+
+// Packed FP32 pairs (Blackwell's two-wide FP32 instructions): each lane of a
+// pair is rounded exactly as the scalar operation would round it.
+__device__ __forceinline__ float2 pk2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 padd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 pmul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 pfma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 psub(float2 a, float2 b) {
+    float2 r;
+    asm("{\n .reg .b64 x, y, z;\n mov.b64 x, {%2, %3};\n mov.b64 y, {%4, %5};\n sub.rn.f32x2 z, x, y;\n"
+        " mov.b64 {%0, %1}, z;\n}"
+        : "=f"(r.x), "=f"(r.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return r;
+}
+// 4th-order central differences 8 (f[1] - f[-1]) - (f[2] - f[-2]) at nodes 0
+// and 1 of a line of six values f[-2 .. 3], for two lines at once, combined
+// with the CIC weights w0 (node 0) and w1 (node 1)
+__device__ __forceinline__ float2 fd4_cic_pair(const float2* r, float w0, float w1) {
+    const float2 e8 = pk2(8.0f);
+    const float2 g0 = pfma(e8, psub(r[3], r[1]), psub(r[0], r[4]));
+    const float2 g1 = pfma(e8, psub(r[4], r[2]), psub(r[1], r[5]));
+    return pfma(pk2(w1), g1, pmul(pk2(w0), g0));
+}
+
+template <int NB> struct CodeType { using T = int8_t; };
+template <> struct CodeType<2> { using T = int16_t; };
+
+// The three axis rows of a [3][Np] code array as separate pointers, so a
+// particle's codes are addressed by its 32-bit index alone.
+template <int NB>
+struct CodeRows {
+    using T = typename CodeType<NB>::T;
+    T* r[3];
+    __device__ __forceinline__ CodeRows(const void* base, int64_t np) {
+        r[0] = reinterpret_cast<T*>(const_cast<void*>(base));
+        r[1] = r[0] + np;
+        r[2] = r[1] + np;
+    }
+    __device__ __forceinline__ int get(int d, unsigned i) const { return (int)r[d][i]; }
+    // velocity code clamped to [-lim, lim] (the encoder never writes anything
+    // else; the clamp keeps table reads in bounds regardless)
+    __device__ __forceinline__ int get_nu(int d, unsigned i, int lim) const { return max(-lim, min(lim, (int)r[d][i])); }
+    __device__ __forceinline__ void put(int d, unsigned i, int v) const { r[d][i] = (T)v; }
+};
 
 template <int NB>
 __device__ __forceinline__ int load_code(const void* base, int64_t idx) {

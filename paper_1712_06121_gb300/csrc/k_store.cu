@@ -31,6 +31,14 @@ __device__ __forceinline__ int upper_cell(const unsigned* off, int ncell, unsign
     return lo;
 }
 
+// brick of a CTA launched on the (nb, nb, nb) grid: its coordinates and storage rank
+__device__ __forceinline__ int grid_brick(const Geo& g, int* bx, int* by, int* bz) {
+    *bx = blockIdx.x;
+    *by = blockIdx.y;
+    *bz = blockIdx.z;
+    return (int)blockIdx.x + g.nb * ((int)blockIdx.y + g.nb * (int)blockIdx.z);
+}
+
 __device__ __forceinline__ void brick_coords(const Geo& g, int brick, int* bx, int* by, int* bz) {
     *bx = brick % g.nb;
     *by = (brick / g.nb) % g.nb;
@@ -300,27 +308,37 @@ __device__ __forceinline__ float node_value(unsigned lo, unsigned hi) {
 // fit look their cell up in it, larger ones (crowded late epochs) search
 constexpr int DEP_QCAP = 2048;
 
+// words of the deposit's node sums: the padded 32-bit tile of the common
+// case, (F + 8) x (F + 2)^2 words, or F^3 {lo, hi} pairs, whichever is larger
+__host__ __device__ __forceinline__ int dep_acc_words(int F) {
+    const int fast = (F + 8) * (F + 2) * (F + 2);
+    return fast > 2 * F * F * F ? fast : 2 * F * F * F;
+}
+
 template <int NX, int FC>
 __global__ void __launch_bounds__(T_BRICK) k_deposit(Geo g, StoreDev s, float* __restrict__ mesh, float fscale) {
     extern __shared__ unsigned long long dep_smem[];
     // FC > 0: the brick side in fine cells is the compile-time FC, else g.F
     const int lF = FC == 16 ? 4 : FC == 8 ? 3 : FC == 4 ? 2 : g.lF, F = 1 << lF, F3 = 1 << (3 * lF);
     const int E = g.B + 1, E3 = E * E * E;
-    // node sums: [F3] 32-bit words when no sum can exceed 32 bits ("small",
-    // block-uniform), else [F3] {lo, hi} pairs
+    // node sums (block-uniform choice): when no sum can exceed 32 bits
+    // ("small"), a padded tile of 32-bit words covering x in [-4, F + 4) and
+    // y, z in [-1, F], so every corner of every contributing particle lies
+    // inside it (no range checks) and rows start on 16-byte boundaries; else
+    // [F3] {lo, hi} pairs over the brick's own nodes
     unsigned* acc = reinterpret_cast<unsigned*>(dep_smem);
-    unsigned* cstart = acc + 2 * F3;                                 // [E3]
+    unsigned* cstart = acc + dep_acc_words(F);                       // [E3]
     unsigned* cpref = cstart + E3;                                   // [E3 + 1]
     int* cpack = reinterpret_cast<int*>(cpref + E3 + 1);             // [E3] packed cell offsets
     unsigned char* qcell = reinterpret_cast<unsigned char*>(cpack + E3);   // [DEP_QCAP] cell of each slot
     int bx, by, bz;
-    brick_coords(g, blockIdx.x, &bx, &by, &bz);
+    grid_brick(g, &bx, &by, &bz);
     const int c0[3] = {bx * g.B, by * g.B, bz * g.B};
     for (int t = threadIdx.x; t < E3; t += blockDim.x) {
         int ec[3];
         split3(t, E, div_magic(E), ec);
         const int lx = ec[0] - 1, ly = ec[1] - 1, lz = ec[2] - 1;
-        const int L = cell_rank(g, wrapi(c0[0] + lx, g.Nc), wrapi(c0[1] + ly, g.Nc), wrapi(c0[2] + lz, g.Nc));
+        const int L = cell_rank(g, wrap1(c0[0] + lx, g.Nc), wrap1(c0[1] + ly, g.Nc), wrap1(c0[2] + lz, g.Nc));
         const unsigned a = s.offsets[L];
         cstart[t] = a;
         cpref[t + 1] = s.offsets[L + 1] - a;
@@ -350,12 +368,62 @@ __global__ void __launch_bounds__(T_BRICK) k_deposit(Geo g, StoreDev s, float* _
     // when fewer than 2^(32 - 3 s) particles feed the brick
     const bool small = 3 * sb < 32 && total < (1u << (32 - 3 * sb));
     const int ws = small ? 0 : 1;                                   // log2 words per node
-    for (int t = threadIdx.x; t < (F3 << ws) / 4; t += blockDim.x)  // F3 is a multiple of 64
-        reinterpret_cast<uint4*>(acc)[t] = make_uint4(0u, 0u, 0u, 0u);
     const bool table = total <= (unsigned)DEP_QCAP && E3 <= 256;    // block-uniform
     if (table)
         for (int t = threadIdx.x; t < E3; t += blockDim.x)
             for (unsigned q = cpref[t], q1 = min(cpref[t + 1], total); q < q1; ++q) qcell[q] = (unsigned char)t;
+    const int ox = c0[0] * g.R, oy = c0[1] * g.R, oz = c0[2] * g.R;
+    if (NX == 1 && small && table) {
+        // the common case: padded 32-bit tile, node (x, y, z) of the brick at
+        // (x + 4) + DX ((y + 1) + DY (z + 1)); a particle's 8 corners at fixed
+        // offsets from its base node, no range checks
+        const int DX = F + 8, DY = F + 2, DXY = DX * DY;
+        for (int t = threadIdx.x; t < DXY * DY / 4; t += blockDim.x)       // DX is a multiple of 4
+            reinterpret_cast<uint4*>(acc)[t] = make_uint4(0u, 0u, 0u, 0u);
+        __syncthreads();
+        const int8_t* cx = reinterpret_cast<const int8_t*>(s.chi);
+        const int8_t* cy = cx + g.Np;
+        const int8_t* cz = cy + g.Np;
+        const int shift = sb;
+        for (unsigned q = threadIdx.x; q < total; q += blockDim.x) {
+            const int t = qcell[q];
+            const unsigned i = cstart[t] + (q - cpref[t]);
+            if (i >= (unsigned)g.Np) continue;
+            const int pk = cpack[t];
+            // Q = 2 (chi + 128) + 1: fine cell (Q >> sb) inside the coarse cell, weight Q & wmask
+            const int Qx = 2 * (int)cx[i] + 257, Qy = 2 * (int)cy[i] + 257, Qz = 2 * (int)cz[i] + 257;
+            const int nx = ((pk & 255) - 1) * g.R + (Qx >> shift);
+            const int ny = (((pk >> 8) & 255) - 1) * g.R + (Qy >> shift);
+            const int nz = ((pk >> 16) - 1) * g.R + (Qz >> shift);
+            // a particle of the layer below more than one fine cell from the brick feeds none of its nodes
+            if (min(nx, min(ny, nz)) < -1) continue;
+            const unsigned wxn = Qx & wmask, wxm = wone - wxn;
+            const unsigned wyn = Qy & wmask, wym = wone - wyn;
+            const unsigned wzn = Qz & wmask, wzm = wone - wzn;
+            const unsigned w00 = wym * wzm, w10 = wyn * wzm, w01 = wym * wzn, w11 = wyn * wzn;
+            unsigned* a = acc + (nx + 4) + DX * ((ny + 1) + DY * (nz + 1));
+            atomicAdd(a, wxm * w00);
+            atomicAdd(a + 1, wxn * w00);
+            atomicAdd(a + DX, wxm * w10);
+            atomicAdd(a + DX + 1, wxn * w10);
+            atomicAdd(a + DXY, wxm * w01);
+            atomicAdd(a + DXY + 1, wxn * w01);
+            atomicAdd(a + DXY + DX, wxm * w11);
+            atomicAdd(a + DXY + DX + 1, wxn * w11);
+        }
+        __syncthreads();
+        for (int t4 = threadIdx.x; t4 < F3 / 4; t4 += blockDim.x) {
+            const int t = 4 * t4;
+            const int x = t & (F - 1), y = (t >> lF) & (F - 1), z = t >> (2 * lF);
+            const uint4 v = *reinterpret_cast<const uint4*>(&acc[(x + 4) + DX * ((y + 1) + DY * (z + 1))]);
+            *reinterpret_cast<float4*>(&mesh[((int64_t)(oz + z) * g.N + (oy + y)) * g.S + ox + x]) =
+                make_float4(u32_to_float_rn(v.x) * fscale, u32_to_float_rn(v.y) * fscale,
+                            u32_to_float_rn(v.z) * fscale, u32_to_float_rn(v.w) * fscale);
+        }
+        return;
+    }
+    for (int t = threadIdx.x; t < (F3 << ws) / 4; t += blockDim.x)  // F3 is a multiple of 64
+        reinterpret_cast<uint4*>(acc)[t] = make_uint4(0u, 0u, 0u, 0u);
     __syncthreads();
     for (unsigned q = threadIdx.x; q < total; q += blockDim.x) {
         const int t = table ? (int)qcell[q] : upper_cell(cpref, E3, q);
@@ -410,7 +478,6 @@ __global__ void __launch_bounds__(T_BRICK) k_deposit(Geo g, StoreDev s, float* _
     __syncthreads();
     // four consecutive x nodes per thread: one or two 16-byte shared loads,
     // one 16-byte store (F and the row stride S are multiples of 4)
-    const int ox = c0[0] * g.R, oy = c0[1] * g.R, oz = c0[2] * g.R;
     for (int t4 = threadIdx.x; t4 < F3 / 4; t4 += blockDim.x) {
         const int t = 4 * t4;
         const int x = t & (F - 1), y = (t >> lF) & (F - 1), z = t >> (2 * lF);
@@ -455,7 +522,7 @@ __global__ void __launch_bounds__(T_BRICK, 4) k_passA(Geo g, StoreDev s, const f
     const unsigned mBh = div_magic(Bh);
     const int lim = g.nulim;
     int bx, by, bz;
-    brick_coords(g, blockIdx.x, &bx, &by, &bz);
+    const int brick = grid_brick(g, &bx, &by, &bz);
     const int ox = bx * F - 4, oy = by * F - 2, oz = bz * F - 2;      // tile origin
     long long* vs = reinterpret_cast<long long*>(pa_smem);                 // [3][H3]
     const unsigned sbase = smem_addr(pa_smem);
@@ -487,7 +554,7 @@ __global__ void __launch_bounds__(T_BRICK, 4) k_passA(Geo g, StoreDev s, const f
         thr = sthr;
         key0 = __float_as_int(cur.est[2]);
     }
-    const int L0 = blockIdx.x * nbc;
+    const int L0 = brick * nbc;
     for (int t = threadIdx.x; t < 3 * nbc; t += blockDim.x)
         cp_async4(&svc[t], &s.vc[(int64_t)(t >> (3 * g.lB)) * g.Ncc + L0 + (t & (nbc - 1))]);
     for (int c = threadIdx.x; c <= nbc; c += blockDim.x) sm_off[c] = s.offsets[L0 + c];
@@ -496,6 +563,23 @@ __global__ void __launch_bounds__(T_BRICK, 4) k_passA(Geo g, StoreDev s, const f
         vs[t] = 0;
         vs[H3 + t] = 0;
         vs[2 * H3 + t] = 0;
+    }
+    // per axis d and halo coordinate e in [0, Bh): the coarse cell's home
+    // brick coordinate (bits 0-7), its coordinate in that brick (8-11), this
+    // brick's rank among the cell's candidate bricks (12-15), the number of
+    // candidates (16-19) and of candidate slots before the cell (20-23); the
+    // flattened slot of a halo cell combines the three axes (flat_slot)
+    __shared__ unsigned axis_desc[3 * 8];
+    if (threadIdx.x < 3 * Bh) {
+        const int d = threadIdx.x / Bh, ee = threadIdx.x - d * Bh;
+        const int me = d == 0 ? bx : d == 1 ? by : bz;
+        const int c = wrap1(me * g.B - 1 + ee, g.Nc);
+        const int lx = c & (g.B - 1), hbc = c >> g.lB;
+        const int lo = lx == 0 ? wrap1(hbc - 1, g.nb) : -1;
+        const int hi = lx == g.B - 1 ? wrap1(hbc + 1, g.nb) : -1;
+        const int r = (hbc < me) + (lo >= 0 && lo < me) + (hi >= 0 && hi < me);
+        axis_desc[threadIdx.x] = (unsigned)hbc | ((unsigned)lx << 8) | ((unsigned)r << 12) |
+                                 ((unsigned)ncand(lx, g.B) << 16) | ((unsigned)ncand_before(lx) << 20);
     }
     if (!use_tma) {
         // rows of TX = F + 8 nodes start on a 16-byte boundary: 4-node chunks;
@@ -522,13 +606,15 @@ __global__ void __launch_bounds__(T_BRICK, 4) k_passA(Geo g, StoreDev s, const f
     // while the tile is in flight
     const unsigned q1 = min(s.offsets[L0 + nbc], (unsigned)g.Np);
     unsigned i = min(s.offsets[L0], q1) + threadIdx.x;
-    if (threadIdx.x == 0 && q1 - (i - threadIdx.x) > (unsigned)PB_BIG) w.big[1 + atomicAdd(w.big, 1)] = blockIdx.x;
+    if (threadIdx.x == 0 && q1 - (i - threadIdx.x) > (unsigned)PB_BIG) w.big[1 + atomicAdd(w.big, 1)] = brick;
+    const CodeRows<NX> chi_r(s.chi, g.Np);
+    const CodeRows<NV> nu_r(s.nu, g.Np);
     int nchi[3] = {0, 0, 0}, nnu[3] = {0, 0, 0};
     if (i < q1) {
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
-            nchi[d] = load_code<NX>(s.chi, d * g.Np + i);
-            nnu[d] = load_nu<NV>(s.nu, d * g.Np + i, lim);
+            nchi[d] = chi_r.get(d, i);
+            nnu[d] = nu_r.get_nu(d, i, lim);
         }
     }
     cp_async_wait_all();
@@ -557,105 +643,88 @@ __global__ void __launch_bounds__(T_BRICK, 4) k_passA(Geo g, StoreDev s, const f
     int mig = 0;
     bool migbad = false;
     const int TT = T * TS;   // z stride of the tile
+    const int lB = g.lB, bm = g.B - 1;
     for (; i < q1; i += blockDim.x) {
         // this round's codes; the next round's are requested now
         const int cchi[3] = {nchi[0], nchi[1], nchi[2]}, cnu[3] = {nnu[0], nnu[1], nnu[2]};
         if (i + blockDim.x < q1) {
 #pragma unroll
             for (int d = 0; d < 3; ++d) {
-                nchi[d] = load_code<NX>(s.chi, d * g.Np + i + blockDim.x);
-                nnu[d] = load_nu<NV>(s.nu, d * g.Np + i + blockDim.x, lim);
+                nchi[d] = chi_r.get(d, i + blockDim.x);
+                nnu[d] = nu_r.get_nu(d, i + blockDim.x, lim);
             }
         }
-        int lc = table ? (int)qcell[i - q0] : upper_cell(sm_off, nbc, i);
-        int l[3] = {lc & (g.B - 1), (lc >> g.lB) & (g.B - 1), lc >> (2 * g.lB)};
+        const int lc = table ? (int)qcell[i - q0] : upper_cell(sm_off, nbc, i);
+        const int l[3] = {lc & bm, (lc >> lB) & bm, lc >> (2 * lB)};
         int Q[3], n[3];
-        float wv[3];
+        float w1[3], w0[3];
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
             Q[d] = 2 * (cchi[d] + half) + 1;
             n[d] = (d == 0 ? 4 : 2) + (l[d] << g.r) + (Q[d] >> sb);
-            wv[d] = (float)(Q[d] & wmask) * winv;
+            w1[d] = u16_to_float((unsigned)(Q[d] & wmask)) * winv;       // exact (< 2^16)
+            w0[d] = 1.0f - w1[d];
         }
-        // CIC gather of the FD4 gradient: per axis, 4 lines of 6 nodes, read
-        // as 28 pairs of x-adjacent nodes {o, o + 1}.  A particle with odd
-        // n_y / 2 reads each pair as {o + 1, o} and swaps it back: near a
-        // uniform lattice (two fine cells per particle spacing) every node
-        // index is even, so unswapped a warp's loads would fall on the 16 even
-        // banks only; the swap spreads them over all 32.
+        // CIC gather of the FD4 gradient (56 nodes, read as 28 pairs of
+        // x-adjacent nodes {o, o + 1}).  Near a uniform lattice every node
+        // index is even, so a warp's loads would use the 16 even banks only; a
+        // particle with odd n_y / 2 reads each pair in the other order, which
+        // spreads a warp's loads over all 32 banks.  Columns along y and z
+        // keep the swapped order and take the matching x weights (ca, cb);
+        // rows along x are put back in order.  Two lines at a time in packed
+        // FP32 pairs.
         const int base = (n[2] * T + n[1]) * TS + n[0];
         const int sh = (n[1] >> 1) & 1;
         const float* pa = tile + base + sh;
         const float* pb = tile + base + 1 - sh;
-        auto pair = [&](int o, float& lo, float& hi) {
-            const float u = pa[o], v = pb[o];
-            lo = sh ? v : u;
-            hi = sh ? u : v;
-        };
-        float gx = 0.0f, gy = 0.0f, gz = 0.0f;
+        const float ca = sh ? w1[0] : w0[0], cb = sh ? w0[0] : w1[0];   // x weights of the pa, pb values
+        float2 gy2 = make_float2(0.0f, 0.0f), gz2 = make_float2(0.0f, 0.0f), gx2 = make_float2(0.0f, 0.0f);
 #pragma unroll
-        for (int a = 0; a < 2; ++a) {
+        for (int b = 0; b < 2; ++b) {
+            float2 r[6];
 #pragma unroll
-            for (int b = 0; b < 2; ++b) {
-                float r[6];                            // r[j]: node j - 2 of the line
-                {   // x rows at (y + a, z + b)
-                    const int o = a * TS + b * TT;
-                    pair(o - 2, r[0], r[1]);
-                    pair(o, r[2], r[3]);
-                    pair(o + 2, r[4], r[5]);
-                    float g0 = 8.0f * (r[3] - r[1]) - (r[4] - r[0]);
-                    float g1 = 8.0f * (r[4] - r[2]) - (r[5] - r[1]);
-                    float wyz = (a ? wv[1] : 1.0f - wv[1]) * (b ? wv[2] : 1.0f - wv[2]);
-                    gx += wyz * ((1.0f - wv[0]) * g0 + wv[0] * g1);
-                }
-                {   // y columns at (x + a, z + b)
+            for (int k = 0; k < 6; ++k) r[k] = make_float2(pa[b * TT + (k - 2) * TS], pb[b * TT + (k - 2) * TS]);
+            gy2 = pfma(pk2(b ? w1[2] : w0[2]), fd4_cic_pair(r, w0[1], w1[1]), gy2);   // y columns at z + b
 #pragma unroll
-                    for (int k = 0; k < 6; ++k) {
-                        float lo, hi;
-                        pair(b * TT + (k - 2) * TS, lo, hi);
-                        r[k] = a ? hi : lo;
-                    }
-                    float g0 = 8.0f * (r[3] - r[1]) - (r[4] - r[0]);
-                    float g1 = 8.0f * (r[4] - r[2]) - (r[5] - r[1]);
-                    float wxz = (a ? wv[0] : 1.0f - wv[0]) * (b ? wv[2] : 1.0f - wv[2]);
-                    gy += wxz * ((1.0f - wv[1]) * g0 + wv[1] * g1);
-                }
-                {   // z columns at (x + a, y + b)
+            for (int k = 0; k < 6; ++k) r[k] = make_float2(pa[b * TS + (k - 2) * TT], pb[b * TS + (k - 2) * TT]);
+            gz2 = pfma(pk2(b ? w1[1] : w0[1]), fd4_cic_pair(r, w0[2], w1[2]), gz2);   // z columns at y + b
+            // x rows at (y + a, z + b), a = 0, 1 in the two lanes, in natural order
 #pragma unroll
-                    for (int k = 0; k < 6; ++k) {
-                        float lo, hi;
-                        pair(b * TS + (k - 2) * TT, lo, hi);
-                        r[k] = a ? hi : lo;
-                    }
-                    float g0 = 8.0f * (r[3] - r[1]) - (r[4] - r[0]);
-                    float g1 = 8.0f * (r[4] - r[2]) - (r[5] - r[1]);
-                    float wxy = (a ? wv[0] : 1.0f - wv[0]) * (b ? wv[1] : 1.0f - wv[1]);
-                    gz += wxy * ((1.0f - wv[2]) * g0 + wv[2] * g1);
+            for (int k = 0; k < 6; k += 2) {
+#pragma unroll
+                for (int a = 0; a < 2; ++a) {
+                    const int o = a * TS + b * TT + (k - 2);
+                    const float u = pa[o], v = pb[o];
+                    (a ? r[k].y : r[k].x) = sh ? v : u;
+                    (a ? r[k + 1].y : r[k + 1].x) = sh ? u : v;
                 }
             }
+            gx2 = pfma(pmul(make_float2(w0[1], w1[1]), pk2(b ? w1[2] : w0[2])), fd4_cic_pair(r, w0[0], w1[0]), gx2);
         }
         const float fsc = -1.0f / 12.0f;
-        const float force[3] = {gx * fsc, gy * fsc, gz * fsc};
+        const float force[3] = {(gx2.x + gx2.y) * fsc, __fmaf_rn(ca, gy2.x, cb * gy2.y) * fsc,
+                                __fmaf_rn(ca, gz2.x, cb * gz2.y) * fsc};
+        // kick (update_vp): the code is decided on v - v_c + F K = offset + F K,
+        // re-encoded against the same v_c; then the drift of the in-cell
+        // offset Q / 2^(8n+1) by the decoded momentum, rounded once
         int e[3];
         float pv[3], un[3];
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
-            const float vcd = svc[(d << (3 * g.lB)) + lc];
-            const int nu = cnu[d];
-            float v = vcd + dec[nu + lim];
-            float p1 = __fmaf_rn(force[d], kick, v);
-            float dd = p1 - vcd;
+            const float vcd = svc[(d << (3 * lB)) + lc];
+            const float dd = __fmaf_rn(force[d], kick, dec[cnu[d] + lim]);
             const int nu1 = NV == 1 ? nu_from_table(dd, thr, stab, key0, lim)
                                     : nu_from_thresholds(dd, thr, lim, nu_estimate(dd, e0, e1));
-            store_code<NV>(s.nu, d * g.Np + i, nu1);
-            float p2 = vcd + dec[nu1 + lim];
-            float r2 = p2 - vcd;
-            sacc = __fmaf_rn(r2, r2, sacc);
-            int bin = drift_bin(Q[d], p2, dc, inv2q, two8n, &un[d]);
-            int sh = bin >> nbits;
-            if (sh < -1 || sh > 1) { migbad = true; sh = max(-1, min(1, sh)); }
-            mig = max(mig, abs(sh));
-            e[d] = l[d] + sh + 1;
+            nu_r.put(d, i, nu1);
+            const float off1 = dec[nu1 + lim];
+            const float p2 = vcd + off1;
+            sacc = __fmaf_rn(off1, off1, sacc);
+            un[d] = __fmaf_rn(p2, dc, u16_to_float((unsigned)Q[d]) * inv2q);
+            const int sh1 = (int)floorf(un[d] * two8n) >> nbits;
+            const int shc = max(-1, min(1, sh1));
+            migbad |= sh1 != shc;
+            mig |= shc & 1;                        // 1 if the particle changes cell along d
+            e[d] = l[d] + shc + 1;
             pv[d] = p2;
         }
         const int ei = e[0] + Bh * (e[1] + Bh * e[2]);
@@ -677,15 +746,22 @@ __global__ void __launch_bounds__(T_BRICK, 4) k_passA(Geo g, StoreDev s, const f
     }
     if (migbad) atomicOr(w.flags, ERR_MIGRATION);
     __syncthreads();
-    const int bc[3] = {bx, by, bz};
+    // each halo cell's slot in the flattened (cell, brick) order and its cell
+    // rank, from the per-axis descriptions staged before the particle loop
+    const int S1 = Bh, S2 = Bh * Bh;
     for (int t = threadIdx.x; t < H3; t += blockDim.x) {
         const unsigned h = hist[t];
-        int e[3];
-        split3(t, Bh, mBh, e);
-        w.ghost[flat_slot(g, bc, e)] = h;                 // every slot has exactly one writer
+        int ec[3];
+        split3(t, Bh, mBh, ec);
+        const unsigned ax = axis_desc[ec[0]], ay = axis_desc[Bh + ec[1]], az = axis_desc[2 * Bh + ec[2]];
+        const int hb = (int)(ax & 255u) + g.nb * ((int)(ay & 255u) + g.nb * (int)(az & 255u));
+        const int nc0 = (ax >> 16) & 15, nc1 = (ay >> 16) & 15, nc2 = (az >> 16) & 15;
+        const int pre = (int)((az >> 20) & 15) * S2 + nc2 * ((int)((ay >> 20) & 15) * S1 + nc1 * (int)((ax >> 20) & 15));
+        const int rank = ((int)((az >> 12) & 15) * nc1 + (int)((ay >> 12) & 15)) * nc0 + (int)((ax >> 12) & 15);
+        w.ghost[(int64_t)hb * H3 + pre + rank] = h;          // every slot has exactly one writer
         if (h) {
-            const int L = cell_rank(g, wrap1(bx * g.B - 1 + e[0], g.Nc), wrap1(by * g.B - 1 + e[1], g.Nc),
-                                    wrap1(bz * g.B - 1 + e[2], g.Nc));
+            const int L = (hb << (3 * lB)) + (int)((ax >> 8) & 15) + ((int)((ay >> 8) & 15) << lB) +
+                          ((int)((az >> 8) & 15) << (2 * lB));
 #pragma unroll
             for (int d = 0; d < 3; ++d)
                 atomicAdd(reinterpret_cast<unsigned long long*>(&w.vsum_new[(int64_t)d * g.Ncc + L]),
@@ -694,7 +770,7 @@ __global__ void __launch_bounds__(T_BRICK, 4) k_passA(Geo g, StoreDev s, const f
     }
     __shared__ float red[T_BRICK / 32];
     const float tot = block_sum_float(sacc, red);
-    if (threadIdx.x == 0) w.part[blockIdx.x] = tot;
+    if (threadIdx.x == 0) w.part[brick] = tot;
     // block max of the migration
     __shared__ int mmax;
     if (threadIdx.x == 0) mmax = 0;
@@ -755,6 +831,8 @@ template <int NX, int NV>
 struct PassB {
     Geo g;
     const StoreDev& sn;
+    CodeRows<NX> chi_n;
+    CodeRows<NV> nu_n;
     const float* dec;
     const float* thr;
     const unsigned char* stab;
@@ -794,11 +872,10 @@ struct PassB {
         }
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
-            store_code<NX>(sn.chi, d * g.Np + pos, q.chi[d]);
+            chi_n.put(d, pos, q.chi[d]);
             const float dd = q.pv[d] - svn[d * H3 + q.ei];
-            store_code<NV>(sn.nu, d * g.Np + pos,
-                           NV == 1 ? nu_from_table(dd, thr, stab, key0, lim)
-                                   : nu_from_thresholds(dd, thr, lim, nu_estimate(dd, e0, e1)));
+            nu_n.put(d, pos, NV == 1 ? nu_from_table(dd, thr, stab, key0, lim)
+                                     : nu_from_thresholds(dd, thr, lim, nu_estimate(dd, e0, e1)));
         }
         if (sn.id) sn.id[pos] = cid;
     }
@@ -845,7 +922,10 @@ __global__ void __launch_bounds__(PB_WARPS * 32, 5) k_passB(Geo g, StoreDev so, 
     float* sthr = sdec + (NV == 1 ? 2 * lim + 1 : 0);                       // NV == 1: [lim + 2]
     unsigned char* stab = reinterpret_cast<unsigned char*>(sthr + (NV == 1 ? lim + 2 : 0));   // NV == 1: [VT_N]
     unsigned* wbase = reinterpret_cast<unsigned*>(stab + (NV == 1 ? VT_N : 0));
-    PassB<NX, NV> pb{g, sn, cur.dec, next.thr, stab, 0, lim, dc, next.est[0], next.est[1]};
+    PassB<NX, NV> pb{g, sn, CodeRows<NX>(sn.chi, g.Np), CodeRows<NV>(sn.nu, g.Np), cur.dec, next.thr, stab, 0, lim,
+                     dc, next.est[0], next.est[1]};
+    const CodeRows<NX> chi_o(so.chi, g.Np);
+    const CodeRows<NV> nu_o(so.nu, g.Np);
     if (NV == 1) {
         for (int t = threadIdx.x; t < 2 * lim + 1; t += blockDim.x) sdec[t] = cur.dec[t];
         for (int t = threadIdx.x; t < lim + 2; t += blockDim.x) sthr[t] = next.thr[t];
@@ -881,8 +961,8 @@ __global__ void __launch_bounds__(PB_WARPS * 32, 5) k_passB(Geo g, StoreDev so, 
                     int cchi[3], cnu[3];
 #pragma unroll
                     for (int d = 0; d < 3; ++d) {
-                        cchi[d] = load_code<NX>(so.chi, d * g.Np + i);
-                        cnu[d] = load_nu<NV>(so.nu, d * g.Np + i, lim);
+                        cchi[d] = chi_o.get(d, i);
+                        cnu[d] = nu_o.get_nu(d, i, lim);
                     }
                     if (sn.id) cid = so.id[i];
                     q = pb.move(upper_cell(sm_off, nbc, i), svc, cchi, cnu);
@@ -934,8 +1014,8 @@ __global__ void __launch_bounds__(PB_WARPS * 32, 5) k_passB(Geo g, StoreDev so, 
     if (p0 + lane < p1) {
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
-            nchi[d] = load_code<NX>(so.chi, d * g.Np + p0 + lane);
-            nnu[d] = load_nu<NV>(so.nu, d * g.Np + p0 + lane, lim);
+            nchi[d] = chi_o.get(d, p0 + lane);
+            nnu[d] = nu_o.get_nu(d, p0 + lane, lim);
         }
         if (sn.id) nid = so.id[p0 + lane];
     }
@@ -951,8 +1031,8 @@ __global__ void __launch_bounds__(PB_WARPS * 32, 5) k_passB(Geo g, StoreDev so, 
         if (i + 32 < p1) {
 #pragma unroll
             for (int d = 0; d < 3; ++d) {
-                nchi[d] = load_code<NX>(so.chi, d * g.Np + i + 32);
-                nnu[d] = load_nu<NV>(so.nu, d * g.Np + i + 32, lim);
+                nchi[d] = chi_o.get(d, i + 32);
+                nnu[d] = nu_o.get_nu(d, i + 32, lim);
             }
             if (sn.id) nid = so.id[i + 32];
         }
@@ -1011,10 +1091,11 @@ struct Disp {
     static void passA(const Geo& g, const StoreDev& s, const float* phig, const CUtensorMap& tmap, int use_tma,
                       const CodecDev& cur, float kick, float dc, const StepScratch& w, const DriftDebug& dbg,
                       size_t sm, cudaStream_t st) {
+        const dim3 grid(g.nb, g.nb, g.nb);
         if (g.F == 16)
-            k_passA<NX, NV, 16><<<g.nbricks, T_BRICK, sm, st>>>(g, s, phig, tmap, use_tma, cur, kick, dc, w, dbg);
+            k_passA<NX, NV, 16><<<grid, T_BRICK, sm, st>>>(g, s, phig, tmap, use_tma, cur, kick, dc, w, dbg);
         else
-            k_passA<NX, NV, 0><<<g.nbricks, T_BRICK, sm, st>>>(g, s, phig, tmap, use_tma, cur, kick, dc, w, dbg);
+            k_passA<NX, NV, 0><<<grid, T_BRICK, sm, st>>>(g, s, phig, tmap, use_tma, cur, kick, dc, w, dbg);
     }
     static void passB(const Geo& g, const StoreDev& so, const StoreDev& sn, const CodecDev& cur,
                       const CodecDev& next, float dc, const unsigned* ghost, const float* vcn, unsigned* flags,
@@ -1099,21 +1180,22 @@ void launch_decode(const Geo& g, const StoreDev& s, const float* dec, float* pos
 }
 
 static size_t deposit_smem(const Geo& g) {
-    const int F3 = g.F * g.F * g.F, E = g.B + 1, E3 = E * E * E;
-    return (size_t)F3 * 8 + (size_t)(3 * E3 + 1) * 4 + DEP_QCAP;
+    const int E = g.B + 1, E3 = E * E * E;
+    return (size_t)dep_acc_words(g.F) * 4 + (size_t)(3 * E3 + 1) * 4 + DEP_QCAP;
 }
 
 void launch_deposit(const Geo& g, const StoreDev& s, float* mesh, double scale, cudaStream_t st) {
     size_t sm = deposit_smem(g);
     const bool f16 = g.F == 16;
+    const dim3 grid(g.nb, g.nb, g.nb);
     if (g.nchi == 1) {
         set_smem_attrs<1, 1>(); set_smem_attrs<1, 2>();
-        if (f16) k_deposit<1, 16><<<g.nbricks, T_BRICK, sm, st>>>(g, s, mesh, (float)scale);
-        else k_deposit<1, 0><<<g.nbricks, T_BRICK, sm, st>>>(g, s, mesh, (float)scale);
+        if (f16) k_deposit<1, 16><<<grid, T_BRICK, sm, st>>>(g, s, mesh, (float)scale);
+        else k_deposit<1, 0><<<grid, T_BRICK, sm, st>>>(g, s, mesh, (float)scale);
     } else {
         set_smem_attrs<2, 1>(); set_smem_attrs<2, 2>();
-        if (f16) k_deposit<2, 16><<<g.nbricks, T_BRICK, sm, st>>>(g, s, mesh, (float)scale);
-        else k_deposit<2, 0><<<g.nbricks, T_BRICK, sm, st>>>(g, s, mesh, (float)scale);
+        if (f16) k_deposit<2, 16><<<grid, T_BRICK, sm, st>>>(g, s, mesh, (float)scale);
+        else k_deposit<2, 0><<<grid, T_BRICK, sm, st>>>(g, s, mesh, (float)scale);
     }
 }
 
