@@ -331,34 +331,40 @@ __global__ void __launch_bounds__(T_BRICK) k_deposit(Geo g, StoreDev s, float* _
     unsigned* cpref = cstart + E3;                                   // [E3 + 1]
     int* cpack = reinterpret_cast<int*>(cpref + E3 + 1);             // [E3] packed cell offsets
     unsigned char* qcell = reinterpret_cast<unsigned char*>(cpack + E3);   // [DEP_QCAP] cell of each slot
+    __shared__ unsigned wsum[T_BRICK / 32];
     int bx, by, bz;
     grid_brick(g, &bx, &by, &bz);
     const int c0[3] = {bx * g.B, by * g.B, bz * g.B};
-    for (int t = threadIdx.x; t < E3; t += blockDim.x) {
+    // the cells of the brick and of its one-cell layer below (E^3 <= 125 <=
+    // one per thread), their particle counts scanned across the block
+    unsigned cnt = 0;
+    const int t = threadIdx.x;
+    if (t < E3) {
         int ec[3];
         split3(t, E, div_magic(E), ec);
         const int lx = ec[0] - 1, ly = ec[1] - 1, lz = ec[2] - 1;
         const int L = cell_rank(g, wrap1(c0[0] + lx, g.Nc), wrap1(c0[1] + ly, g.Nc), wrap1(c0[2] + lz, g.Nc));
         const unsigned a = s.offsets[L];
         cstart[t] = a;
-        cpref[t + 1] = s.offsets[L + 1] - a;
+        cnt = s.offsets[L + 1] - a;
         cpack[t] = (lx + 1) | ((ly + 1) << 8) | ((lz + 1) << 16);
     }
-    __syncthreads();
-    if (threadIdx.x < 32) {   // inclusive scan of the E3 counts by warp 0, 32 at a time
-        const int lane = threadIdx.x;
-        unsigned carry = 0;
-        if (lane == 0) cpref[0] = 0;
-        for (int b = 0; b < E3; b += 32) {
-            unsigned v = (b + lane < E3) ? cpref[b + lane + 1] : 0u;
+    // node sums cleared while the offsets are in flight (both layouts)
+    for (int u = threadIdx.x; u < dep_acc_words(F) / 4; u += blockDim.x)
+        reinterpret_cast<uint4*>(acc)[u] = make_uint4(0u, 0u, 0u, 0u);
+    {
+        const int lane = t & 31, wp = t >> 5;
+        unsigned v = cnt;
 #pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const unsigned u = __shfl_up_sync(0xffffffffu, v, o);
-                if (lane >= o) v += u;
-            }
-            if (b + lane < E3) cpref[b + lane + 1] = carry + v;
-            carry += __shfl_sync(0xffffffffu, v, 31);
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned u = __shfl_up_sync(0xffffffffu, v, o);
+            if (lane >= o) v += u;
         }
+        if (lane == 31) wsum[wp] = v;
+        __syncthreads();
+        for (int k = 0; k < wp; ++k) v += wsum[k];
+        if (t < E3) cpref[t + 1] = v;
+        if (t == 0) cpref[0] = 0;
     }
     __syncthreads();
     const int nbits = 8 * NX, half = 1 << (nbits - 1);
@@ -378,20 +384,33 @@ __global__ void __launch_bounds__(T_BRICK) k_deposit(Geo g, StoreDev s, float* _
         // (x + 4) + DX ((y + 1) + DY (z + 1)); a particle's 8 corners at fixed
         // offsets from its base node, no range checks
         const int DX = F + 8, DY = F + 2, DXY = DX * DY;
-        for (int t = threadIdx.x; t < DXY * DY / 4; t += blockDim.x)       // DX is a multiple of 4
-            reinterpret_cast<uint4*>(acc)[t] = make_uint4(0u, 0u, 0u, 0u);
-        __syncthreads();
+        __syncthreads();                                                    // cell table complete
         const int8_t* cx = reinterpret_cast<const int8_t*>(s.chi);
         const int8_t* cy = cx + g.Np;
         const int8_t* cz = cy + g.Np;
         const int shift = sb;
+        // the next round's cell and codes are requested before this round's atomics
+        int tn = 0, xn = 0, yn = 0, zn = 0;
+        bool okn = false;
+        auto fetch = [&](unsigned qq) {
+            tn = qcell[qq];
+            const unsigned ii = cstart[tn] + (qq - cpref[tn]);
+            okn = ii < (unsigned)g.Np;
+            if (okn) {
+                xn = cx[ii];
+                yn = cy[ii];
+                zn = cz[ii];
+            }
+        };
+        if (threadIdx.x < total) fetch(threadIdx.x);
         for (unsigned q = threadIdx.x; q < total; q += blockDim.x) {
-            const int t = qcell[q];
-            const unsigned i = cstart[t] + (q - cpref[t]);
-            if (i >= (unsigned)g.Np) continue;
-            const int pk = cpack[t];
+            const int tc = tn, chx = xn, chy = yn, chz = zn;
+            const bool ok = okn;
+            if (q + blockDim.x < total) fetch(q + blockDim.x);
+            if (!ok) continue;
+            const int pk = cpack[tc];
             // Q = 2 (chi + 128) + 1: fine cell (Q >> sb) inside the coarse cell, weight Q & wmask
-            const int Qx = 2 * (int)cx[i] + 257, Qy = 2 * (int)cy[i] + 257, Qz = 2 * (int)cz[i] + 257;
+            const int Qx = 2 * chx + 257, Qy = 2 * chy + 257, Qz = 2 * chz + 257;
             const int nx = ((pk & 255) - 1) * g.R + (Qx >> shift);
             const int ny = (((pk >> 8) & 255) - 1) * g.R + (Qy >> shift);
             const int nz = ((pk >> 16) - 1) * g.R + (Qz >> shift);
@@ -412,18 +431,27 @@ __global__ void __launch_bounds__(T_BRICK) k_deposit(Geo g, StoreDev s, float* _
             atomicAdd(a + DXY + DX + 1, wxn * w11);
         }
         __syncthreads();
+        // the brick's rows (32-bit offsets: N^2 S < 2^31 for N <= 1024)
+        float* mbase = mesh + ((int64_t)oz * g.N + oy) * g.S + ox;
         for (int t4 = threadIdx.x; t4 < F3 / 4; t4 += blockDim.x) {
             const int t = 4 * t4;
             const int x = t & (F - 1), y = (t >> lF) & (F - 1), z = t >> (2 * lF);
             const uint4 v = *reinterpret_cast<const uint4*>(&acc[(x + 4) + DX * ((y + 1) + DY * (z + 1))]);
-            *reinterpret_cast<float4*>(&mesh[((int64_t)(oz + z) * g.N + (oy + y)) * g.S + ox + x]) =
-                make_float4(u32_to_float_rn(v.x) * fscale, u32_to_float_rn(v.y) * fscale,
-                            u32_to_float_rn(v.z) * fscale, u32_to_float_rn(v.w) * fscale);
+            float4 f;
+            if (max(max(v.x, v.y), max(v.z, v.w)) < (1u << 23)) {     // exact: 2^23 + u is a float
+                f = make_float4(__uint_as_float(0x4B000000u | v.x) - 8388608.0f,
+                                __uint_as_float(0x4B000000u | v.y) - 8388608.0f,
+                                __uint_as_float(0x4B000000u | v.z) - 8388608.0f,
+                                __uint_as_float(0x4B000000u | v.w) - 8388608.0f);
+            } else {
+                f = make_float4(u32_to_float_rn(v.x), u32_to_float_rn(v.y), u32_to_float_rn(v.z),
+                                u32_to_float_rn(v.w));
+            }
+            *reinterpret_cast<float4*>(mbase + (unsigned)((z * g.N + y) * g.S + x)) =
+                make_float4(f.x * fscale, f.y * fscale, f.z * fscale, f.w * fscale);
         }
         return;
     }
-    for (int t = threadIdx.x; t < (F3 << ws) / 4; t += blockDim.x)  // F3 is a multiple of 64
-        reinterpret_cast<uint4*>(acc)[t] = make_uint4(0u, 0u, 0u, 0u);
     __syncthreads();
     for (unsigned q = threadIdx.x; q < total; q += blockDim.x) {
         const int t = table ? (int)qcell[q] : upper_cell(cpref, E3, q);
