@@ -72,7 +72,11 @@ typedef struct {
                               4 together with v_bytes = 4: uncompressed FP32
                               particles (see "Uncompressed store" below)       */
     int32_t v_bytes;       /* n_nu in {1, 2}: velocity code width (Eq. nu)      */
-    int32_t id_bytes;      /* 0 (no particle IDs) or 4 (uint32 I_P)             */
+    int32_t id_bytes;      /* n_I: 0 (no particle IDs), 1, 2 or 4 bytes of I_P
+                              per particle (Section 2.1: a PID array tells
+                              particle types apart -- 1 byte holds eight kinds
+                              as bits, or 256 type numbers -- or every
+                              particle); the uncompressed store: 0 or 4      */
     int32_t gradient;      /* CUBE_GRAD_FD4: 4th-order finite-difference force  */
     int32_t deconv_power;  /* the Green's function is divided by W_CIC(k)^p,
                               p in {0, 1, 2}; 2 compensates deposit and gather  */
@@ -122,6 +126,8 @@ cube_status cube_destroy(cube_ctx* ctx);
    pos   [3][N_p] float, fine-cell coordinates (wrapped periodically);
    vel   [3][N_p] float, momenta p;
    id    [N_p] uint32 particle IDs, or NULL for 0..N_p-1 (ignored if id_bytes=0);
+         the low id_bytes bytes of each are stored (cube_decode returns them
+         zero-extended);
    a     scale factor of both positions and momenta;
    sigma per-dimension velocity-code scale sigma_Delta/sqrt(3) of Eqs. nu, v
          (Eq. vdelta gives it at the ICs); <= 0 measures it from the particles
@@ -379,7 +385,7 @@ cube_status cube_counts_to_offsets_noalloc(const uint32_t* counts, int64_t n_cel
    {"CUBECKP1", n_fine, ratio, n_particles, x_bytes, v_bytes, id_bytes,
    brick, a, a_p, sigma}, then 16-byte aligned sections: counts u32[N_c^3],
    v_c f32[3][N_c^3], chi [3][N] and nu [3][N] codes of x_bytes / v_bytes,
-   ids u32[N] when id_bytes = 4.  The uncompressed store (x_bytes = 4)
+   ids (id_bytes bytes each) [N] when id_bytes > 0.  The uncompressed store (x_bytes = 4)
    stores positions f32[3][N] and momenta f32[3][N] instead of the first four
    sections.  12 bytes per particle for x1v1 with ids (6 of codes, 4 of
    ids, 2 of coarse fields at 8 particles per coarse cell), against 28 for
@@ -423,7 +429,7 @@ cube_status cube_counts_unpack(const uint8_t* bytes, int64_t n_cells, const uint
    sizing runs and comparing layouts.  Host only, no device. */
 typedef struct {
     int32_t x_bytes, v_bytes;     /* n_chi, n_nu in {1, 2}                          */
-    int32_t id_bytes;             /* n_I in {0, 4}                                  */
+    int32_t id_bytes;             /* n_I in {0, 1, 2, 4}                            */
     int32_t ratio;                /* R: fine cells per coarse cell, >= 1            */
     int32_t coarse_per_image;     /* N_c / M_g: coarse cells per image side, >= 1   */
     int32_t buffer;               /* N_b: buffer depth in coarse cells, >= 0        */
@@ -473,6 +479,67 @@ cube_status cube_memory_model(const cube_memory_config* cfg, cube_memory_layout*
 cube_status cube_autotune_brick(const cube_params* params, const float* pos, const float* vel, double a,
                                 double sigma, int32_t n_steps, void* cuda_stream, int32_t* best_brick,
                                 double* ms_per_step);
+
+/* ---------------------------------------------------------------- batches: many simulations per launch */
+
+/* A batch steps several simulations ("members") of the same geometry with one
+   launch per kernel of the step: the members share n_fine, ratio,
+   n_particles, the code and id widths, the brick, omega_m, omega_l, gradient
+   and deconv_power; only the box may differ.  Every member's state and work
+   buffers lie in one device slab at a fixed stride, and each kernel takes the
+   member as one more grid dimension, with that member's epochs, kick and
+   drift factors from a small per-member table.  This is the paper's
+   observation that a step's result does not depend on how the volume is
+   tiled (Section 3), applied across simulations: a member's results are
+   bit-identical to the same simulation stepped alone.
+
+   Each member is a full cube_ctx (cube_batch_member): encode, decode, P(k),
+   statistics, checkpoints and single steps through the ordinary calls, on the
+   batch's stream.  Do not cube_destroy a member: cube_batch_destroy frees
+   them.  Calls are stream-ordered on the batch's stream; the batch must not be
+   used by two threads at once. */
+typedef struct cube_batch cube_batch;
+
+/* params: [members] parameter sets (they must agree on everything but the
+   box; compressed stores only), members in [1, 4096].  Allocates one slab of
+   members x (state + work bytes of one member, cube_server_sizes).
+   Errors: CUBE_E_ARG, CUBE_E_NOMEM, CUBE_E_CUDA. */
+cube_status cube_batch_create(const cube_params* params, int32_t members, void* cuda_stream, cube_batch** out);
+
+/* Waits for the batch's stream, then frees the members and the slab. */
+cube_status cube_batch_destroy(cube_batch* batch);
+
+/* The context of member i (owned by the batch).  Errors: CUBE_E_ARG. */
+cube_status cube_batch_member(cube_batch* batch, int32_t i, cube_ctx** out);
+
+/* One KD step of every member i with a_to[i] > a_from[i] (a_from[i] must
+   equal the member's epoch); members with a_to[i] <= a_from[i] sit the step
+   out.  Members stepped together must have taken the same number of steps
+   since they were encoded (a member that sat a step out continues alone with
+   cube_pm_step).  Host arrays [members].  Enqueues 15 kernel launches for
+   the whole batch (a context stepped alone launches the same kernels once
+   per step).  Errors: CUBE_E_ARG, CUBE_E_STATE; device errors are latched in
+   each member's flags (cube_stats_get). */
+cube_status cube_batch_step(cube_batch* batch, const double* a_from, const double* a_to);
+
+/* For every member i with a_max[i] above its epoch: the largest a_to[i] <=
+   a_max[i] that keeps the member's fastest particle within `cells` coarse
+   cells (cube_next_epoch), from one read-back of all members' largest
+   momentum; a_to[i] = the member's epoch otherwise.  Synchronises.
+   Errors: CUBE_E_ARG (cells not in (0, 1], or a member cannot step), CUBE_E_STATE. */
+cube_status cube_batch_next_epochs(cube_batch* batch, const double* a_max, double cells, double* a_to);
+
+/* The same in two halves, so the host need not wait: _enqueue queues every
+   member's largest-momentum reduction and its copy into pinned memory behind
+   the batch's work so far; _poll returns at once, with *ready 0 while the copy
+   is in flight, else *ready 1 and a_to as cube_batch_next_epochs gives it.
+   Errors: CUBE_E_ARG, CUBE_E_STATE (poll without an enqueue). */
+cube_status cube_batch_epochs_enqueue(cube_batch* batch);
+cube_status cube_batch_epochs_poll(cube_batch* batch, const double* a_max, double cells, double* a_to,
+                                   int32_t* ready);
+
+/* Kernels cube_batch_step has launched for this batch (all members). */
+cube_status cube_batch_launches(cube_batch* batch, int64_t* launches);
 
 /* ---------------------------------------------------------------- serving: many simulations on one GPU */
 
@@ -570,6 +637,15 @@ cube_status cube_server_release(cube_server* srv, int64_t ticket);
 
 /* Device bytes held now: resident states plus work areas. */
 cube_status cube_server_bytes(cube_server* srv, int64_t* bytes_in_use);
+
+/* Admission order: CUBE_ADMIT_FIFO (default) admits queued requests in
+   arrival order; CUBE_ADMIT_SHORTEST admits the queued request with the least
+   remaining work (particles x scheduled steps; ties in arrival order) first,
+   which shortens short requests' latency at the expense of long ones.  In
+   both, the request chosen next waits for memory and nothing overtakes it.
+   Applies from the next admission.  Errors: CUBE_E_ARG. */
+enum { CUBE_ADMIT_FIFO = 0, CUBE_ADMIT_SHORTEST = 1 };
+cube_status cube_server_set_policy(cube_server* srv, int32_t policy);
 
 /* Test hook for the admission path: the next n allocations of a larger
    stream work area report "out of memory" without calling CUDA.  When a

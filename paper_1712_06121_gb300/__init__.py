@@ -135,6 +135,15 @@ _sigs = {
     "cube_server_release": ([_P, ctypes.c_int64], ctypes.c_int),
     "cube_server_bytes": ([_P, ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
     "cube_server_inject_alloc_failures": ([_P, ctypes.c_int32], ctypes.c_int),
+    "cube_server_set_policy": ([_P, ctypes.c_int32], ctypes.c_int),
+    "cube_batch_create": ([ctypes.POINTER(cube_params), ctypes.c_int32, _P, ctypes.POINTER(_P)], ctypes.c_int),
+    "cube_batch_destroy": ([_P], ctypes.c_int),
+    "cube_batch_member": ([_P, ctypes.c_int32, ctypes.POINTER(_P)], ctypes.c_int),
+    "cube_batch_step": ([_P, _P, _P], ctypes.c_int),
+    "cube_batch_next_epochs": ([_P, _P, ctypes.c_double, _P], ctypes.c_int),
+    "cube_batch_launches": ([_P, ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
+    "cube_batch_epochs_enqueue": ([_P], ctypes.c_int),
+    "cube_batch_epochs_poll": ([_P, _P, ctypes.c_double, _P, ctypes.POINTER(ctypes.c_int32)], ctypes.c_int),
 }
 for _name, (_args, _res) in _sigs.items():
     _f = getattr(_lib, _name)
@@ -440,6 +449,68 @@ def cube_server_bytes(srv):
     return v.value
 
 
+CUBE_ADMIT_FIFO, CUBE_ADMIT_SHORTEST = 0, 1
+
+
+def cube_server_set_policy(srv, policy):
+    _check(_lib.cube_server_set_policy(srv, int(policy)))
+
+
 def cube_server_inject_alloc_failures(srv, n):
     _check(_lib.cube_server_inject_alloc_failures(srv, int(n)))
 
+
+# ---------------------------------------------------------------- batches
+def cube_batch_create(params_list, stream=None):
+    """A batch of same-geometry simulations (list of cube_params); returns its handle."""
+    if stream is not None and hasattr(stream, "cuda_stream"):
+        stream = stream.cuda_stream
+    arr = (cube_params * len(params_list))(*params_list)
+    b = _P()
+    _check(_lib.cube_batch_create(arr, len(params_list), stream, ctypes.byref(b)))
+    return b
+
+
+def cube_batch_destroy(batch):
+    _check(_lib.cube_batch_destroy(batch))
+
+
+def cube_batch_member(batch, i):
+    c = _P()
+    _check(_lib.cube_batch_member(batch, int(i), ctypes.byref(c)))
+    return c
+
+
+def cube_batch_step(batch, a_from, a_to):
+    import numpy as np
+    af = np.ascontiguousarray(a_from, dtype=np.float64)
+    at = np.ascontiguousarray(a_to, dtype=np.float64)
+    _check(_lib.cube_batch_step(batch, af.ctypes.data, at.ctypes.data))
+
+
+def cube_batch_next_epochs(batch, a_max, cells=0.5):
+    import numpy as np
+    am = np.ascontiguousarray(a_max, dtype=np.float64)
+    out = np.empty_like(am)
+    _check(_lib.cube_batch_next_epochs(batch, am.ctypes.data, float(cells), out.ctypes.data))
+    return out
+
+
+def cube_batch_launches(batch):
+    v = ctypes.c_int64()
+    _check(_lib.cube_batch_launches(batch, ctypes.byref(v)))
+    return v.value
+
+
+def cube_batch_epochs_enqueue(batch):
+    _check(_lib.cube_batch_epochs_enqueue(batch))
+
+
+def cube_batch_epochs_poll(batch, a_max, cells=0.5):
+    """None while the read-back is in flight, else the members' next epochs."""
+    import numpy as np
+    am = np.ascontiguousarray(a_max, dtype=np.float64)
+    out = np.empty_like(am)
+    ready = ctypes.c_int32()
+    _check(_lib.cube_batch_epochs_poll(batch, am.ctypes.data, float(cells), out.ctypes.data, ctypes.byref(ready)))
+    return out if ready.value else None

@@ -184,6 +184,7 @@ struct cube_ctx {
     void* stage_ws = nullptr;           // host-staging region of the work slab
     size_t stage_ws_bytes = 0;
     bool served = false;
+    bool member = false;                // a batch member: its slab belongs to the batch
     // drifted-state export
     bool keep = false;
     int* dbg_cell = nullptr;
@@ -227,7 +228,7 @@ size_t state_layout(cube_ctx* c, char* base) {
         if (k == 0 || !c->raw) {         // the uncompressed store is updated in place
             carve(base, off, c->chi[k], 3 * Np * g.nchi);
             carve(base, off, c->nu[k], 3 * Np * g.nnu);
-            if (c->P.id_bytes) carve(base, off, c->id[k], Np * 4);
+            if (c->P.id_bytes) carve(base, off, c->id[k], Np * (size_t)c->P.id_bytes);
         }
         carve(base, off, c->codec[k].dec, (size_t)(2 * g.nulim + 1) * 4);
         carve(base, off, c->codec[k].thr, (size_t)(g.nulim + 2) * 4);
@@ -311,8 +312,7 @@ cube_status latched(cube_ctx* c) {
 // N + 8, N + 5, N + 5) whose box is pass A's tile ((F + 8) x (F + 5) x (F + 5)).
 // The encoder comes from the driver through the runtime; any failure leaves
 // pass A on its cp.async path.
-bool encode_phig_map(cube_ctx* c) {
-    const Geo& g = c->g;
+bool encode_phig_map(const Geo& g, float* phig, int members, size_t stride, CUtensorMap* out) {
     PFN_cuTensorMapEncodeTiled_v12000 enc = nullptr;
     cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
     if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", (void**)&enc, 12000, cudaEnableDefault, &q) !=
@@ -321,15 +321,21 @@ bool encode_phig_map(cube_ctx* c) {
         cudaGetLastError();
         return false;
     }
-    const cuuint64_t dims[3] = {(cuuint64_t)phig_nx(g.N), (cuuint64_t)phig_ny(g.N), (cuuint64_t)phig_ny(g.N)};
-    const cuuint64_t strides[2] = {(cuuint64_t)phig_nx(g.N) * 4, (cuuint64_t)phig_nx(g.N) * phig_ny(g.N) * 4};
-    const cuuint32_t box[3] = {(cuuint32_t)(g.F + 8), (cuuint32_t)(g.F + 5), (cuuint32_t)(g.F + 5)};
-    const cuuint32_t unit[3] = {1, 1, 1};
-    const CUresult r = enc(&c->phig_map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, c->phig, dims, strides, box, unit,
+    const cuuint64_t plane = (cuuint64_t)phig_nx(g.N) * phig_ny(g.N) * 4;
+    // 4-D: x, y, z and the member of a batch (one member: any stride that is a multiple of 16)
+    const cuuint64_t dims[4] = {(cuuint64_t)phig_nx(g.N), (cuuint64_t)phig_ny(g.N), (cuuint64_t)phig_ny(g.N),
+                                (cuuint64_t)members};
+    const cuuint64_t strides[3] = {(cuuint64_t)phig_nx(g.N) * 4, plane,
+                                   members > 1 ? (cuuint64_t)stride : plane * phig_ny(g.N)};
+    const cuuint32_t box[4] = {(cuuint32_t)(g.F + 8), (cuuint32_t)(g.F + 5), (cuuint32_t)(g.F + 5), 1};
+    const cuuint32_t unit[4] = {1, 1, 1, 1};
+    const CUresult r = enc(out, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, phig, dims, strides, box, unit,
                            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS;
 }
+
+bool encode_phig_map(cube_ctx* c) { return encode_phig_map(c->g, c->phig, 1, 0, &c->phig_map); }
 
 // geometry and flags of a context from validated parameters (brick side B)
 void init_geo(cube_ctx* c, const cube_params* params, int B) {
@@ -353,6 +359,7 @@ void init_geo(cube_ctx* c, const cube_params* params, int B) {
     g.nbricks = g.nb * g.nb * g.nb;
     g.Np = params->n_particles;
     g.nulim = c->raw ? 127 : (1 << (8 * g.nnu - 1)) - 1;   // (no codec tables are used uncompressed)
+    g.nid = params->id_bytes;
     g.lB = 0;
     while ((1 << g.lB) < g.B) ++g.lB;
     g.lF = 0;
@@ -374,7 +381,10 @@ cube_status check_params(const cube_params* p, int* brick) {
     const bool raw = p->x_bytes == 4 && p->v_bytes == 4;
     if (!raw && ((p->x_bytes != 1 && p->x_bytes != 2) || (p->v_bytes != 1 && p->v_bytes != 2)))
         return fail(CUBE_E_ARG, "x_bytes and v_bytes must be 1 or 2 (codes), or both 4 (uncompressed FP32)");
-    if (p->id_bytes != 0 && p->id_bytes != 4) return fail(CUBE_E_ARG, "id_bytes must be 0 or 4");
+    if (p->id_bytes != 0 && p->id_bytes != 1 && p->id_bytes != 2 && p->id_bytes != 4)
+        return fail(CUBE_E_ARG, "id_bytes must be 0, 1, 2 or 4");
+    if (raw && p->id_bytes != 0 && p->id_bytes != 4)
+        return fail(CUBE_E_ARG, "the uncompressed store keeps 4-byte particle IDs (id_bytes 0 or 4)");
     if (p->gradient != CUBE_GRAD_FD4) return fail(CUBE_E_ARG, "only CUBE_GRAD_FD4 is implemented");
     if (p->deconv_power < 0 || p->deconv_power > 2) return fail(CUBE_E_ARG, "deconv_power must be 0, 1 or 2");
     if (!(p->box > 0.0) || !(p->omega_m > 0.0) || !(p->omega_l >= 0.0)) return fail(CUBE_E_ARG, "box, omega_m must be > 0");
@@ -400,7 +410,9 @@ const char* cube_last_error(void) { return g_err.c_str(); }
 
 cube_status cube_destroy(cube_ctx* c) {
     if (!c) return CUBE_OK;
-    if (c->served) {                     // stream-ordered: no device-wide synchronisation
+    if (c->member) {                     // the batch frees the slab
+        cudaStreamSynchronize(c->st);
+    } else if (c->served) {              // stream-ordered: no device-wide synchronisation
         if (c->state_slab) cudaFreeAsync(c->state_slab, c->st);
     } else {
         cudaStreamSynchronize(c->st);
@@ -419,7 +431,10 @@ cube_status cube_destroy(cube_ctx* c) {
     return CUBE_OK;
 }
 
-static cube_status create_ctx(const cube_params* params, void* cuda_stream, bool served, cube_ctx** out) {
+// member_base: a batch member's device slab (state, then work at the next
+// 256-byte boundary), allocated by the batch; null: the context allocates
+static cube_status create_ctx(const cube_params* params, void* cuda_stream, bool served, cube_ctx** out,
+                              char* member_base = nullptr) {
     if (!out) return fail(CUBE_E_ARG, "out is NULL");
     *out = nullptr;
     int B = 0;
@@ -442,16 +457,23 @@ static cube_status create_ctx(const cube_params* params, void* cuda_stream, bool
     };
     c->state_size = state_layout(c, nullptr);
     c->work_size = work_layout(c, nullptr);
-    {
-        cudaError_t e = c->served ? cudaMallocAsync((void**)&c->state_slab, c->state_size, c->st)
-                                  : cudaMalloc((void**)&c->state_slab, c->state_size);
-        if (e == cudaSuccess && !c->served) e = cudaMalloc((void**)&c->work_slab, c->work_size);
-        if (e != cudaSuccess) return bad(e, "device memory");
-    }
-    state_layout(c, c->state_slab);
-    if (!c->served) {
-        c->work_base = c->work_slab;
+    if (member_base) {
+        c->member = true;
+        state_layout(c, member_base);
+        c->work_base = member_base + ((c->state_size + 255) & ~(size_t)255);
         work_layout(c, c->work_base);
+    } else {
+        {
+            cudaError_t e = c->served ? cudaMallocAsync((void**)&c->state_slab, c->state_size, c->st)
+                                      : cudaMalloc((void**)&c->state_slab, c->state_size);
+            if (e == cudaSuccess && !c->served) e = cudaMalloc((void**)&c->work_slab, c->work_size);
+            if (e != cudaSuccess) return bad(e, "device memory");
+        }
+        state_layout(c, c->state_slab);
+        if (!c->served) {
+            c->work_base = c->work_slab;
+            work_layout(c, c->work_base);
+        }
     }
     FftPlan& f = c->fft;
     // host tables (FP64 libm), uploaded once (stream-ordered: pageable sources are
@@ -560,6 +582,7 @@ static cube_status encode_impl(cube_ctx* c, const float* pos, const float* vel, 
     if (hpos) { CK(cudaMemcpyAsync(sp, pos, 12 * Np, cudaMemcpyHostToDevice, c->st)); dpos = (const float*)sp; sp += 12 * Np; }
     if (hvel) { CK(cudaMemcpyAsync(sp, vel, 12 * Np, cudaMemcpyHostToDevice, c->st)); dvel = (const float*)sp; sp += 12 * Np; }
     if (hid) { CK(cudaMemcpyAsync(sp, id, 4 * Np, cudaMemcpyHostToDevice, c->st)); did = (const unsigned*)sp; }
+    c->cur = 0;                          // a fresh store always starts in buffer 0 (batch members stay in step)
     const int k = c->cur;
     CK(cudaMemsetAsync(c->flags, 0, 4, c->st));
     CK(cudaMemsetAsync(c->counts[k], 0, (size_t)g.Ncc * 4, c->st));
@@ -949,7 +972,7 @@ size_t ckpt_layout(const Geo& g, bool raw, int id_bytes, size_t sec[5]) {
     const size_t N = (size_t)g.Np, Ncc = (size_t)g.Ncc;
     size_t off = sizeof(CkptHeader);
     const size_t sz[5] = {raw ? 12 * N : 4 * Ncc, raw ? 12 * N : 12 * Ncc, raw ? 0 : 3 * N * g.nchi,
-                          raw ? 0 : 3 * N * g.nnu, id_bytes ? 4 * N : 0};
+                          raw ? 0 : 3 * N * g.nnu, (size_t)id_bytes * N};
     for (int i = 0; i < 5; ++i) {
         sec[i] = off;
         off = align16(off + sz[i]);
@@ -1004,7 +1027,7 @@ cube_status cube_checkpoint_save(cube_ctx* c, void* buf) {
         CK(cudaMemcpyAsync(b + sec[2], c->chi[k], 3 * N * g.nchi, cudaMemcpyDefault, c->st));
         CK(cudaMemcpyAsync(b + sec[3], c->nu[k], 3 * N * g.nnu, cudaMemcpyDefault, c->st));
     }
-    if (c->P.id_bytes) CK(cudaMemcpyAsync(b + sec[4], c->id[k], 4 * N, cudaMemcpyDefault, c->st));
+    if (c->P.id_bytes) CK(cudaMemcpyAsync(b + sec[4], c->id[k], (size_t)c->P.id_bytes * N, cudaMemcpyDefault, c->st));
     return latched(c);
 }
 
@@ -1024,6 +1047,7 @@ cube_status cube_checkpoint_load(cube_ctx* c, const void* buf) {
     ckpt_layout(g, c->raw, c->P.id_bytes, sec);
     const char* b = (const char*)buf;
     const size_t N = (size_t)g.Np, Ncc = (size_t)g.Ncc;
+    c->cur = 0;                          // a loaded store starts in buffer 0, as an encoded one
     const int k = c->cur;
     c->encoded = false;                  // until the whole store is in place
     if (c->raw) {
@@ -1040,7 +1064,7 @@ cube_status cube_checkpoint_load(cube_ctx* c, const void* buf) {
         launch_codec_tables(g.nulim, c->tanv, c->tanh_, c->codec[k], c->st);
         c->launches += 4 + 1;
     }
-    if (c->P.id_bytes) CK(cudaMemcpyAsync(c->id[k], b + sec[4], 4 * N, cudaMemcpyDefault, c->st));
+    if (c->P.id_bytes) CK(cudaMemcpyAsync(c->id[k], b + sec[4], (size_t)c->P.id_bytes * N, cudaMemcpyDefault, c->st));
     CK(cudaMemsetAsync(c->flags, 0, 4, c->st));
     CK(cudaMemsetAsync(c->maxmig, 0, 4, c->st));
     // the counts must add up to N_p in 64 bits, none above N_p (a sum that
@@ -1231,6 +1255,240 @@ cube_status cube_profile_read(cube_ctx* c, double* ms, int32_t* kernels, int32_t
 
 const char* cube_phase_name(int32_t phase) {
     return (phase >= 0 && phase < CUBE_PHASES) ? kPhaseNames[phase] : "";
+}
+
+// ---------------------------------------------------------------- batches
+// Simulations with the same geometry (mesh, particle count, codes, brick,
+// cosmology and deconvolution; only the box may differ) stepped together:
+// every member lives in one slab at a fixed stride, so each kernel of the
+// step is launched once for all members (an extra grid dimension), with the
+// members' own epochs, kick and drift factors from a per-member table.
+struct cube_batch {
+    std::vector<cube_ctx*> m;
+    char* slab = nullptr;
+    size_t stride = 0;
+    cudaStream_t st = nullptr;
+    CUtensorMap map{};                  // 4-D map (x, y, z, member) of the members' ghosted Phi
+    bool tma = false;
+    MemberStep* ms_dev = nullptr;       // [members]
+    MemberStep* ms_host = nullptr;      // pinned [members]
+    unsigned* vmax_host = nullptr;      // pinned [members]: largest |p| per member (float bits)
+    cudaEvent_t ms_copied = nullptr;    // the last table upload has been read
+    cudaEvent_t vmax_ready = nullptr;   // the maxima read-back has arrived
+    bool vmax_pending = false;
+    int64_t launches = 0;
+};
+
+cube_status cube_batch_destroy(cube_batch* b) {
+    if (!b) return CUBE_OK;
+    if (b->st) cudaStreamSynchronize(b->st);
+    for (cube_ctx* c : b->m) cube_destroy(c);
+    if (b->slab) cudaFree(b->slab);
+    if (b->ms_dev) cudaFree(b->ms_dev);
+    if (b->ms_host) cudaFreeHost(b->ms_host);
+    if (b->vmax_host) cudaFreeHost(b->vmax_host);
+    if (b->ms_copied) cudaEventDestroy(b->ms_copied);
+    if (b->vmax_ready) cudaEventDestroy(b->vmax_ready);
+    delete b;
+    return CUBE_OK;
+}
+
+cube_status cube_batch_create(const cube_params* params, int32_t members, void* cuda_stream, cube_batch** out) {
+    if (!out || !params) return fail(CUBE_E_ARG, "NULL argument");
+    *out = nullptr;
+    if (members < 1 || members > 4096) return fail(CUBE_E_ARG, "members must be in [1, 4096]");
+    int B0 = 0;
+    cube_status s = check_params(&params[0], &B0);
+    if (s != CUBE_OK) return s;
+    if (params[0].x_bytes == 4) return fail(CUBE_E_ARG, "batches hold compressed stores (x_bytes 1 or 2)");
+    for (int i = 1; i < members; ++i) {
+        const cube_params &p = params[i], &q = params[0];
+        int B = 0;
+        if ((s = check_params(&p, &B)) != CUBE_OK) return s;
+        if (p.n_fine != q.n_fine || p.ratio != q.ratio || p.n_particles != q.n_particles || p.x_bytes != q.x_bytes ||
+            p.v_bytes != q.v_bytes || p.id_bytes != q.id_bytes || p.omega_m != q.omega_m || p.omega_l != q.omega_l ||
+            p.gradient != q.gradient || p.deconv_power != q.deconv_power || B != B0)
+            return fail(CUBE_E_ARG, "batch members must share everything but the box");
+    }
+    cube_batch* b = new cube_batch();
+    b->st = (cudaStream_t)cuda_stream;
+    auto bad = [&](cudaError_t e, const char* what) -> cube_status {
+        cube_batch_destroy(b);
+        return fail(e == cudaErrorMemoryAllocation ? CUBE_E_NOMEM : CUBE_E_CUDA,
+                    std::string(what) + ": " + cudaGetErrorString(e));
+    };
+    {
+        cube_ctx probe;
+        init_geo(&probe, &params[0], B0);
+        const size_t st_sz = state_layout(&probe, nullptr), wk_sz = work_layout(&probe, nullptr);
+        b->stride = ((st_sz + 255) & ~(size_t)255) + ((wk_sz + 255) & ~(size_t)255);
+    }
+    cudaError_t e = cudaMalloc((void**)&b->slab, b->stride * (size_t)members);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&b->ms_dev, sizeof(MemberStep) * members);
+    if (e == cudaSuccess) e = cudaMallocHost((void**)&b->ms_host, sizeof(MemberStep) * members);
+    if (e == cudaSuccess) e = cudaMallocHost((void**)&b->vmax_host, sizeof(unsigned) * members);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ms_copied, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->vmax_ready, cudaEventDisableTiming);
+    if (e != cudaSuccess) return bad(e, "device memory");
+    for (int i = 0; i < members; ++i) {
+        cube_ctx* c = nullptr;
+        s = create_ctx(&params[i], cuda_stream, false, &c, b->slab + (size_t)i * b->stride);
+        if (s != CUBE_OK) {
+            const std::string msg = g_err;
+            cube_batch_destroy(b);
+            return fail(s, msg);
+        }
+        b->m.push_back(c);
+    }
+    b->tma = encode_phig_map(b->m[0]->g, b->m[0]->phig, members, b->stride, &b->map);
+    *out = b;
+    return CUBE_OK;
+}
+
+cube_status cube_batch_member(cube_batch* b, int32_t i, cube_ctx** out) {
+    if (!b || !out) return fail(CUBE_E_ARG, "NULL argument");
+    if (i < 0 || i >= (int)b->m.size()) return fail(CUBE_E_ARG, "member index out of range");
+    *out = b->m[i];
+    return CUBE_OK;
+}
+
+// every member's largest |p| into pinned memory (one copy: they lie one stride
+// apart), enqueued, with an event marking its arrival
+static cube_status batch_vmax_enqueue(cube_batch* b) {
+    const int K = (int)b->m.size();
+    for (int i = 0; i < K; ++i) {
+        cube_ctx* c = b->m[i];
+        if (!c->encoded) return fail(CUBE_E_STATE, "a member has no store: call cube_encode first");
+        launch_max_speed(c->g, c->store(c->cur), c->codec[c->cur].dec, c->vmax, b->st);
+        c->launches += 1;
+    }
+    CK(cudaMemcpy2DAsync(b->vmax_host, sizeof(unsigned), b->m[0]->vmax, b->stride, sizeof(unsigned), K,
+                         cudaMemcpyDeviceToHost, b->st));
+    CK(cudaEventRecord(b->vmax_ready, b->st));
+    b->vmax_pending = true;
+    return CUBE_OK;
+}
+
+// the epochs from the read-back maxima (bisection on the host, as cube_next_epoch)
+static cube_status batch_epochs(cube_batch* b, const double* a_max, double cells, double* a_to) {
+    const int K = (int)b->m.size();
+    for (int i = 0; i < K; ++i) {
+        cube_ctx* c = b->m[i];
+        if (!(a_max[i] > c->a)) {
+            a_to[i] = c->a;
+            continue;
+        }
+        float p;
+        std::memcpy(&p, &b->vmax_host[i], 4);
+        a_to[i] = epoch_limit(c, (double)p, a_max[i], cells);
+        if (!(a_to[i] > c->a)) return fail(CUBE_E_ARG, "no step keeps a member's fastest particle within the limit");
+    }
+    return CUBE_OK;
+}
+
+cube_status cube_batch_next_epochs(cube_batch* b, const double* a_max, double cells, double* a_to) {
+    if (!b || !a_max || !a_to) return fail(CUBE_E_ARG, "NULL argument");
+    if (!(cells > 0.0 && cells <= 1.0)) return fail(CUBE_E_ARG, "cells must be in (0, 1]");
+    cube_status s = batch_vmax_enqueue(b);
+    if (s != CUBE_OK) return s;
+    CK(cudaEventSynchronize(b->vmax_ready));
+    b->vmax_pending = false;
+    return batch_epochs(b, a_max, cells, a_to);
+}
+
+cube_status cube_batch_epochs_enqueue(cube_batch* b) {
+    if (!b) return fail(CUBE_E_ARG, "NULL argument");
+    return batch_vmax_enqueue(b);
+}
+
+cube_status cube_batch_epochs_poll(cube_batch* b, const double* a_max, double cells, double* a_to, int32_t* ready) {
+    if (!b || !a_max || !a_to || !ready) return fail(CUBE_E_ARG, "NULL argument");
+    if (!(cells > 0.0 && cells <= 1.0)) return fail(CUBE_E_ARG, "cells must be in (0, 1]");
+    *ready = 0;
+    if (!b->vmax_pending) return fail(CUBE_E_STATE, "no read-back enqueued: call cube_batch_epochs_enqueue first");
+    const cudaError_t q = cudaEventQuery(b->vmax_ready);
+    if (q == cudaErrorNotReady) return CUBE_OK;
+    if (q != cudaSuccess) return fail(CUBE_E_CUDA, cudaGetErrorString(q));
+    b->vmax_pending = false;
+    *ready = 1;
+    return batch_epochs(b, a_max, cells, a_to);
+}
+
+cube_status cube_batch_step(cube_batch* b, const double* a_from, const double* a_to) {
+    if (!b || !a_from || !a_to) return fail(CUBE_E_ARG, "NULL argument");
+    const int K = (int)b->m.size();
+    int cur = -1, nact = 0;
+    for (int i = 0; i < K; ++i) {
+        cube_ctx* c = b->m[i];
+        if (!(a_to[i] > a_from[i])) continue;                       // sits this step out
+        if (!c->encoded) return fail(CUBE_E_STATE, "a member has no store: call cube_encode first");
+        if (std::fabs(a_from[i] - c->a) > 1e-12 * std::max(1.0, std::fabs(a_from[i])))
+            return fail(CUBE_E_STATE, "a member's a_from differs from its store's epoch");
+        if (cur >= 0 && c->cur != cur)
+            return fail(CUBE_E_STATE, "members stepped together must have taken the same number of steps "
+                                      "(a member that sat a step out continues with cube_pm_step)");
+        cur = c->cur;
+        ++nact;
+    }
+    if (!nact) return CUBE_OK;
+    CK(cudaEventSynchronize(b->ms_copied));                         // the previous table has been read
+    for (int i = 0; i < K; ++i) {
+        cube_ctx* c = b->m[i];
+        MemberStep& ms = b->ms_host[i];
+        ms = MemberStep{0.0f, 0.0f, 1.0, 0, 0};
+        if (!(a_to[i] > a_from[i])) continue;
+        const double a_mid = 0.5 * (a_from[i] + a_to[i]);
+        ms.kick = (float)c->cosmo.kick(c->a_p, a_mid);
+        ms.dc = (float)(c->cosmo.drift(a_from[i], a_to[i]) / c->g.R);
+        ms.ratio = c->cosmo.g(a_to[i]) / c->cosmo.g(a_from[i]);
+        ms.active = 1;
+    }
+    CK(cudaMemcpyAsync(b->ms_dev, b->ms_host, sizeof(MemberStep) * K, cudaMemcpyHostToDevice, b->st));
+    CK(cudaEventRecord(b->ms_copied, b->st));
+    cube_ctx* c0 = b->m[0];
+    const Geo& g = c0->g;
+    const int k = cur, kn = 1 - cur;
+    const Batch bt{K, b->stride, b->ms_dev};
+    launch_batch_clear(g, c0->vsum, c0->maxmig, b->st, bt);
+    launch_deposit(g, c0->store(k), c0->mesh, particle_mass(g) * std::ldexp(1.0, -3 * g.sbits), b->st, bt);
+    fft_x_r2c(c0->fft, c0->mesh, g.S, b->st, bt);
+    fft_y(c0->fft, c0->mesh, g.S, false, b->st, bt);
+    const float g0 = (float)(-1.5 * c0->P.omega_m / std::pow((double)g.N, 3));
+    fft_z(c0->fft, c0->mesh, g.S, g0, true, b->st, bt);
+    fft_y(c0->fft, c0->mesh, g.S, true, b->st, bt);
+    fft_x_c2r(c0->fft, c0->mesh, g.S, c0->phig, b->st, bt);
+    StepScratch w{c0->counts[kn], c0->vsum, c0->ghost, c0->part, c0->flags, c0->maxmig, c0->maxmig + 1};
+    const DriftDebug nodbg{nullptr, nullptr, nullptr, nullptr};
+    launch_passA(g, c0->store(k), c0->phig, b->tma ? &b->map : nullptr, c0->codec[k], 0.0f, 0.0f, w, nodbg, b->st,
+                 bt);
+    launch_sigma_finalize(c0->part, g.nbricks, 3.0 * (double)g.Np, 1.0, 0.0, c0->codec[kn].sigma, b->st, bt);
+    launch_codec_tables(g.nulim, c0->tanv, c0->tanh_, c0->codec[kn], b->st, bt);
+    exclusive_scan(c0->ghost, c0->ghost, (int64_t)g.nbricks * (g.Bh * g.Bh * g.Bh), c0->scan_tmp, b->st, bt);
+    launch_cells(g, w, c0->offsets[kn], c0->vc[kn], b->st, bt);
+    launch_passB(g, c0->store(k), c0->store(kn), c0->codec[k], c0->codec[kn], 0.0f, w, b->st, bt);
+    b->launches += 1 + 1 + 5 + 1 + 2 + 4 + 1 + 1;
+    CK(cudaGetLastError());
+    for (int i = 0; i < K; ++i) {
+        cube_ctx* c = b->m[i];
+        if (!(a_to[i] > a_from[i])) {
+            if (g.N > 256) c->phig_valid = false;   // large meshes' sweeps run member by member, over it too
+            continue;
+        }
+        c->cur = kn;
+        c->a_p = 0.5 * (a_from[i] + a_to[i]);
+        c->a = a_to[i];
+        c->steps += 1;
+        c->phig_valid = true;
+        c->dbg_valid = false;
+        c->timed = false;
+    }
+    return CUBE_OK;
+}
+
+cube_status cube_batch_launches(cube_batch* b, int64_t* launches) {
+    if (!b || !launches) return fail(CUBE_E_ARG, "NULL argument");
+    *launches = b->launches;
+    return CUBE_OK;
 }
 
 }  // extern "C"

@@ -83,6 +83,16 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const void* tmap, int x, 
         : "memory");
 }
 
+// 4-D tiled TMA load (x, y, z, member) of the tensor map's box, completing on `bar`
+__device__ __forceinline__ void tma_load_4d(void* dst, const void* tmap, int x, int y, int z, int w,
+                                            unsigned long long* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
+        "[%6];" ::"r"(smem_addr(dst)),
+        "l"(tmap), "r"(x), "r"(y), "r"(z), "r"(w), "r"(smem_addr(bar))
+        : "memory");
+}
+
 // floor(t / d) for 0 <= t < 4096 and 2 <= d <= 8 as (t * ceil(2^16 / d)) >> 16
 // (checked exhaustively over that range); m = div_magic(d)
 __host__ __device__ __forceinline__ unsigned div_magic(int d) { return (65536u + (unsigned)d - 1u) / (unsigned)d; }
@@ -111,6 +121,7 @@ struct Geo {
     int nbricks;  // nb^3
     int64_t Np;
     int nulim;    // 2^(8 nnu - 1) - 1: largest |nu|
+    int nid;      // bytes per particle ID (n_I: 0, 1, 2 or 4)
     int lB, lF;   // log2(B), log2(F): brick and fine-tile sides are powers of two
     int nsm;      // SMs of the device (grid sizing)
 };
@@ -262,6 +273,18 @@ __device__ __forceinline__ float2 fd4_cic_pair(const float2* r, float w0, float 
     const float2 g0 = pfma(e8, psub(r[3], r[1]), psub(r[0], r[4]));
     const float2 g1 = pfma(e8, psub(r[4], r[2]), psub(r[1], r[5]));
     return pfma(pk2(w1), g1, pmul(pk2(w0), g0));
+}
+
+// particle ID i of an n-byte ID array (n = 1, 2 or 4), zero-extended
+__device__ __forceinline__ unsigned load_pid(const void* p, unsigned i, int n) {
+    return n == 1 ? (unsigned)reinterpret_cast<const uint8_t*>(p)[i]
+                  : n == 2 ? (unsigned)reinterpret_cast<const uint16_t*>(p)[i] : reinterpret_cast<const unsigned*>(p)[i];
+}
+// store the low n bytes of v as particle ID i
+__device__ __forceinline__ void store_pid(void* p, unsigned i, int n, unsigned v) {
+    if (n == 1) reinterpret_cast<uint8_t*>(p)[i] = (uint8_t)v;
+    else if (n == 2) reinterpret_cast<uint16_t*>(p)[i] = (uint16_t)v;
+    else reinterpret_cast<unsigned*>(p)[i] = v;
 }
 
 template <int NB> struct CodeType { using T = int8_t; };

@@ -506,9 +506,14 @@ __device__ __forceinline__ void xpass_store(const float2* buf, const float2* tw,
 
 // r2c: the N reals of a row as N/2 complex z[k] = x[2k] + i x[2k+1], an
 // N/2-point FFT Z, then X[k] = (Z[k] + Z*[h-k])/2 - i W^k (Z[k] - Z*[h-k])/2
-template <int N>
-__global__ void __launch_bounds__(XFFT_T) k_fft_x_r2c(float* mesh, int S, const float2* __restrict__ tw) {
+template <int N, bool BAT>
+__global__ void __launch_bounds__(XFFT_T) k_fft_x_r2c(float* mesh, int S, const float2* __restrict__ tw, Batch bt) {
     extern __shared__ float2 fsm[];
+    if constexpr (BAT) {                                     // member blockIdx.y of a batch
+        const int m = blockIdx.y;
+        if (bt.ms && !bt.ms[m].active) return;
+        mesh = moved(mesh, m * bt.stride);
+    }
     constexpr int h = N / 2;
     float2* stw = fsm;               // [N]
     float2* buf = fsm + N;           // [h][NC]
@@ -540,10 +545,16 @@ __global__ void __launch_bounds__(XFFT_T) k_fft_x_r2c(float* mesh, int S, const 
 
 // c2r: the packing above inverted inside the first pass, the N/2-point
 // inverse FFT, and the last pass writing the row's N reals
-template <int N>
+template <int N, bool BAT>
 __global__ void __launch_bounds__(XFFT_T) k_fft_x_c2r(const float* mesh, int S, const float2* __restrict__ tw,
-                                                     float* __restrict__ phig) {
+                                                     float* __restrict__ phig, Batch bt) {
     extern __shared__ float2 fsm[];
+    if constexpr (BAT) {                                     // member blockIdx.y of a batch
+        const int m = blockIdx.y;
+        if (bt.ms && !bt.ms[m].active) return;
+        mesh = moved(mesh, m * bt.stride);
+        phig = moved(phig, m * bt.stride);
+    }
     constexpr int h = N / 2;
     float2* stw = fsm;               // [N]
     float2* buf = fsm + N;           // [h][NC]
@@ -566,9 +577,15 @@ __global__ void __launch_bounds__(XFFT_T) k_fft_x_c2r(const float* mesh, int S, 
 template <int N>
 constexpr int ntile_x() { return (N / 2 + NC - 1) / NC; }
 
-template <int N, bool INV>
-__global__ void __launch_bounds__(FFT_T, N <= 512 ? 2 : 1) k_fft_y(float* mesh, int S, const float2* __restrict__ tw) {
+template <int N, bool INV, bool BAT>
+__global__ void __launch_bounds__(FFT_T, N <= 512 ? 2 : 1) k_fft_y(float* mesh, int S, const float2* __restrict__ tw,
+                                                                    Batch bt) {
     extern __shared__ float2 fsm[];
+    if constexpr (BAT) {                                     // member blockIdx.z of a batch
+        const int m = blockIdx.z;
+        if (bt.ms && !bt.ms[m].active) return;
+        mesh = moved(mesh, m * bt.stride);
+    }
     constexpr int h = N / 2;
     float2* stw = fsm;
     float2* buf = fsm + N;
@@ -618,10 +635,16 @@ struct GreenPost {
 };
 
 // One tile of 16 consecutive kx (0 .. N/2) at one ky.
-template <int N, int MODE>   // 0: forward only, 1: forward, Green, inverse
+template <int N, int MODE, bool BAT>   // MODE 0: forward only, 1: forward, Green, inverse
 __global__ void __launch_bounds__(FFT_T, N <= 512 ? 2 : 1) k_fft_z(float* mesh, int S, const float2* __restrict__ tw,
-                                                 const float* __restrict__ k2, const float* __restrict__ wdec, float g0) {
+                                                 const float* __restrict__ k2, const float* __restrict__ wdec, float g0,
+                                                 Batch bt) {
     extern __shared__ float2 fsm[];
+    if constexpr (BAT) {                                     // member blockIdx.z of a batch
+        const int m = blockIdx.z;
+        if (bt.ms && !bt.ms[m].active) return;
+        mesh = moved(mesh, m * bt.stride);
+    }
     constexpr int ncol = N / 2 + 1;
     float2* stw = fsm;
     float2* buf = fsm + N;
@@ -743,37 +766,97 @@ size_t tile_smem(int N, int n) { return (size_t)(N + n * NC + NC) * sizeof(float
 
 template <int N>
 struct Sweeps {
+    template <bool BAT>
+    static void attrs_for() {
+        if constexpr (BAT && !(N <= 256)) return;
+        else {
+        const int big = (int)tile_smem(N, N), half = (int)tile_smem(N, N / 2);
+        cudaFuncSetAttribute(k_fft_x_r2c<N, BAT>, cudaFuncAttributeMaxDynamicSharedMemorySize, half);
+        cudaFuncSetAttribute(k_fft_x_c2r<N, BAT>, cudaFuncAttributeMaxDynamicSharedMemorySize, half);
+        cudaFuncSetAttribute(k_fft_y<N, false, BAT>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+        cudaFuncSetAttribute(k_fft_y<N, true, BAT>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+        cudaFuncSetAttribute(k_fft_z<N, 0, BAT>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+        cudaFuncSetAttribute(k_fft_z<N, 1, BAT>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+        }
+    }
+    // instances with a member dimension exist for the small meshes, where a
+    // step is launch-bound; a batch of larger meshes is launched member by member
+    static constexpr bool kBatchable = N <= 256;
     static void attrs() {
         static bool done = false;
         if (done) return;
-        const int big = (int)tile_smem(N, N), half = (int)tile_smem(N, N / 2);
-        cudaFuncSetAttribute(k_fft_x_r2c<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, half);
-        cudaFuncSetAttribute(k_fft_x_c2r<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, half);
-        cudaFuncSetAttribute(k_fft_y<N, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-        cudaFuncSetAttribute(k_fft_y<N, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-        cudaFuncSetAttribute(k_fft_z<N, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-        cudaFuncSetAttribute(k_fft_z<N, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+        attrs_for<false>();
+        if constexpr (kBatchable) attrs_for<true>();
         done = true;
     }
-    static void x_r2c(const FftPlan& p, float* mesh, int S, cudaStream_t st) {
-        attrs();
-        k_fft_x_r2c<N><<<(N * N) / NC, XFFT_T, tile_smem(N, N / 2), st>>>(mesh, S, p.tw);
+    // a batch (several members or a per-member table) takes the instances with a member dimension
+    static bool batched(const Batch& bt) { return bt.members > 1 || bt.ms != nullptr; }
+    // member by member: every member, stepped or not (a member that sits the
+    // step out only has its scratch mesh and potential rewritten)
+    template <class Fn>
+    static void per_member(const Batch& bt, Fn fn) {
+        for (int m = 0; m < bt.members; ++m) fn((size_t)m * bt.stride);
     }
-    static void y(const FftPlan& p, float* mesh, int S, bool inv, cudaStream_t st) {
+    static void x_r2c(const FftPlan& p, float* mesh, int S, cudaStream_t st, const Batch& bt) {
         attrs();
-        dim3 gy(ntile_x<N>(), N);
-        if (inv) k_fft_y<N, true><<<gy, FFT_T, tile_smem(N, N), st>>>(mesh, S, p.tw);
-        else k_fft_y<N, false><<<gy, FFT_T, tile_smem(N, N), st>>>(mesh, S, p.tw);
+        if constexpr (kBatchable) {
+            if (batched(bt)) {
+                k_fft_x_r2c<N, true><<<dim3((N * N) / NC, bt.members), XFFT_T, tile_smem(N, N / 2), st>>>(mesh, S,
+                                                                                                         p.tw, bt);
+                return;
+            }
+        }
+        per_member(bt, [&](size_t o) {
+            k_fft_x_r2c<N, false><<<(N * N) / NC, XFFT_T, tile_smem(N, N / 2), st>>>(moved(mesh, o), S, p.tw, kSingle);
+        });
     }
-    static void z(const FftPlan& p, float* mesh, int S, float g0, bool green, cudaStream_t st) {
+    static void y(const FftPlan& p, float* mesh, int S, bool inv, cudaStream_t st, const Batch& bt) {
         attrs();
+        const size_t sm = tile_smem(N, N);
+        if constexpr (kBatchable) {
+            if (batched(bt)) {
+                const dim3 gy(ntile_x<N>(), N, bt.members);
+                if (inv) k_fft_y<N, true, true><<<gy, FFT_T, sm, st>>>(mesh, S, p.tw, bt);
+                else k_fft_y<N, false, true><<<gy, FFT_T, sm, st>>>(mesh, S, p.tw, bt);
+                return;
+            }
+        }
+        const dim3 gy(ntile_x<N>(), N);
+        per_member(bt, [&](size_t o) {
+            if (inv) k_fft_y<N, true, false><<<gy, FFT_T, sm, st>>>(moved(mesh, o), S, p.tw, kSingle);
+            else k_fft_y<N, false, false><<<gy, FFT_T, sm, st>>>(moved(mesh, o), S, p.tw, kSingle);
+        });
+    }
+    static void z(const FftPlan& p, float* mesh, int S, float g0, bool green, cudaStream_t st, const Batch& bt) {
+        attrs();
+        const size_t sm = tile_smem(N, N);
+        if constexpr (kBatchable) {
+            if (batched(bt)) {
+                const dim3 gz((N / 2 + NC) / NC, N, bt.members);
+                if (green) k_fft_z<N, 1, true><<<gz, FFT_T, sm, st>>>(mesh, S, p.tw, p.k2, p.wdec, g0, bt);
+                else k_fft_z<N, 0, true><<<gz, FFT_T, sm, st>>>(mesh, S, p.tw, p.k2, p.wdec, g0, bt);
+                return;
+            }
+        }
         const dim3 gz((N / 2 + NC) / NC, N);
-        if (green) k_fft_z<N, 1><<<gz, FFT_T, tile_smem(N, N), st>>>(mesh, S, p.tw, p.k2, p.wdec, g0);
-        else k_fft_z<N, 0><<<gz, FFT_T, tile_smem(N, N), st>>>(mesh, S, p.tw, p.k2, p.wdec, g0);
+        per_member(bt, [&](size_t o) {
+            if (green) k_fft_z<N, 1, false><<<gz, FFT_T, sm, st>>>(moved(mesh, o), S, p.tw, p.k2, p.wdec, g0, kSingle);
+            else k_fft_z<N, 0, false><<<gz, FFT_T, sm, st>>>(moved(mesh, o), S, p.tw, p.k2, p.wdec, g0, kSingle);
+        });
     }
-    static void x_c2r(const FftPlan& p, float* mesh, int S, float* phig, cudaStream_t st) {
+    static void x_c2r(const FftPlan& p, float* mesh, int S, float* phig, cudaStream_t st, const Batch& bt) {
         attrs();
-        k_fft_x_c2r<N><<<(N * N) / NC, XFFT_T, tile_smem(N, N / 2), st>>>(mesh, S, p.tw, phig);
+        if constexpr (kBatchable) {
+            if (batched(bt)) {
+                k_fft_x_c2r<N, true><<<dim3((N * N) / NC, bt.members), XFFT_T, tile_smem(N, N / 2), st>>>(mesh, S,
+                                                                                                         p.tw, phig, bt);
+                return;
+            }
+        }
+        per_member(bt, [&](size_t o) {
+            k_fft_x_c2r<N, false><<<(N * N) / NC, XFFT_T, tile_smem(N, N / 2), st>>>(moved(mesh, o), S, p.tw,
+                                                                                     moved(phig, o), kSingle);
+        });
     }
 };
 
@@ -798,26 +881,26 @@ bool fft_size_supported(int N) {
         default: break;                                  \
     }
 
-void fft_x_r2c(const FftPlan& p, float* mesh, int S, cudaStream_t st) {
-#define DCASE(n) case n: Sweeps<n>::x_r2c(p, mesh, S, st); break;
+void fft_x_r2c(const FftPlan& p, float* mesh, int S, cudaStream_t st, const Batch& bt) {
+#define DCASE(n) case n: Sweeps<n>::x_r2c(p, mesh, S, st, bt); break;
     DISPATCH()
 #undef DCASE
 }
 
-void fft_y(const FftPlan& p, float* mesh, int S, bool inverse, cudaStream_t st) {
-#define DCASE(n) case n: Sweeps<n>::y(p, mesh, S, inverse, st); break;
+void fft_y(const FftPlan& p, float* mesh, int S, bool inverse, cudaStream_t st, const Batch& bt) {
+#define DCASE(n) case n: Sweeps<n>::y(p, mesh, S, inverse, st, bt); break;
     DISPATCH()
 #undef DCASE
 }
 
-void fft_z(const FftPlan& p, float* mesh, int S, float g0, bool green, cudaStream_t st) {
-#define DCASE(n) case n: Sweeps<n>::z(p, mesh, S, g0, green, st); break;
+void fft_z(const FftPlan& p, float* mesh, int S, float g0, bool green, cudaStream_t st, const Batch& bt) {
+#define DCASE(n) case n: Sweeps<n>::z(p, mesh, S, g0, green, st, bt); break;
     DISPATCH()
 #undef DCASE
 }
 
-void fft_x_c2r(const FftPlan& p, float* mesh, int S, float* phig, cudaStream_t st) {
-#define DCASE(n) case n: Sweeps<n>::x_c2r(p, mesh, S, phig, st); break;
+void fft_x_c2r(const FftPlan& p, float* mesh, int S, float* phig, cudaStream_t st, const Batch& bt) {
+#define DCASE(n) case n: Sweeps<n>::x_c2r(p, mesh, S, phig, st, bt); break;
     DISPATCH()
 #undef DCASE
 }

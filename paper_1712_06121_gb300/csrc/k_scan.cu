@@ -52,8 +52,14 @@ __device__ __forceinline__ void load4(const unsigned* __restrict__ in, int64_t b
     }
 }
 
-__global__ void k_scan_reduce(const unsigned* __restrict__ in, int64_t n, unsigned* __restrict__ bsum, bool vec) {
+// (member blockIdx.y of a batch: its arrays are `stride` bytes further on)
+__global__ void k_scan_reduce(const unsigned* __restrict__ in, int64_t n, unsigned* __restrict__ bsum, bool vec,
+                              Batch bt) {
     __shared__ unsigned sw[32];
+    const int m = blockIdx.y;
+    if (bt.ms && !bt.ms[m].active) return;
+    in = moved(in, m * bt.stride);
+    bsum = moved(bsum, m * bt.stride);
     unsigned v[SCAN_ITEMS];
     load4(in, (int64_t)blockIdx.x * SCAN_TILE + (int64_t)threadIdx.x * SCAN_ITEMS, n, vec, v);
     const unsigned s = v[0] + v[1] + v[2] + v[3];
@@ -63,8 +69,12 @@ __global__ void k_scan_reduce(const unsigned* __restrict__ in, int64_t n, unsign
 }
 
 // exclusive scan of the block sums in place (single block, any count)
-__global__ void k_scan_bsums(unsigned* bsum, int nb, unsigned* total_out) {
+__global__ void k_scan_bsums(unsigned* bsum, int nb, unsigned* total_out, Batch bt) {
     __shared__ unsigned sw[32];
+    const int m = blockIdx.x;
+    if (bt.ms && !bt.ms[m].active) return;
+    bsum = moved(bsum, m * bt.stride);
+    total_out = moved(total_out, m * bt.stride);
     unsigned carry = 0;
     for (int base = 0; base < nb; base += SCAN_T) {
         int i = base + threadIdx.x;
@@ -78,8 +88,13 @@ __global__ void k_scan_bsums(unsigned* bsum, int nb, unsigned* total_out) {
 }
 
 __global__ void k_scan_down(const unsigned* in, int64_t n, const unsigned* __restrict__ bsum, unsigned* out,
-                            bool vec) {
+                            bool vec, Batch bt) {
     __shared__ unsigned sw[32];
+    const int m = blockIdx.y;
+    if (bt.ms && !bt.ms[m].active) return;
+    in = moved(in, m * bt.stride);
+    bsum = moved(bsum, m * bt.stride);
+    out = moved(out, m * bt.stride);
     const int64_t base = (int64_t)blockIdx.x * SCAN_TILE + (int64_t)threadIdx.x * SCAN_ITEMS;
     unsigned v[SCAN_ITEMS];
     load4(in, base, n, vec, v);
@@ -99,7 +114,11 @@ __global__ void k_scan_down(const unsigned* in, int64_t n, const unsigned* __res
     }
 }
 
-__global__ void k_write_total(unsigned* out, int64_t n, const unsigned* total) { out[n] = *total; }
+__global__ void k_write_total(unsigned* out, int64_t n, const unsigned* total, Batch bt) {
+    const int m = blockIdx.x;
+    if (bt.ms && !bt.ms[m].active) return;
+    moved(out, m * bt.stride)[n] = *moved(total, m * bt.stride);
+}
 
 // 64-bit sum and maximum of n 32-bit counts: out2[0] += sum, out2[1] = max(out2[1], max)
 __global__ void k_count_totals(const unsigned* __restrict__ c, int64_t n, unsigned long long* out2) {
@@ -166,15 +185,16 @@ __global__ void __launch_bounds__(RX_T) k_radix_scatter(const unsigned* __restri
 
 int scan_tmp_words(int64_t n) { return (int)((n + SCAN_TILE - 1) / SCAN_TILE) + 1; }
 
-void exclusive_scan(const unsigned* in, unsigned* out, int64_t n, unsigned* tmp, cudaStream_t st) {
+void exclusive_scan(const unsigned* in, unsigned* out, int64_t n, unsigned* tmp, cudaStream_t st, const Batch& bt) {
     int nb = (int)((n + SCAN_TILE - 1) / SCAN_TILE);
     if (nb == 0) nb = 1;
     unsigned* total = tmp + nb;
+    // (members are whole multiples of 256 bytes apart: the same alignment)
     const bool vec = ((reinterpret_cast<uintptr_t>(in) | reinterpret_cast<uintptr_t>(out)) & 15) == 0;
-    k_scan_reduce<<<nb, SCAN_T, 0, st>>>(in, n, tmp, vec);
-    k_scan_bsums<<<1, SCAN_T, 0, st>>>(tmp, nb, total);
-    k_scan_down<<<nb, SCAN_T, 0, st>>>(in, n, tmp, out, vec);
-    k_write_total<<<1, 1, 0, st>>>(out, n, total);
+    k_scan_reduce<<<dim3(nb, bt.members), SCAN_T, 0, st>>>(in, n, tmp, vec, bt);
+    k_scan_bsums<<<bt.members, SCAN_T, 0, st>>>(tmp, nb, total, bt);
+    k_scan_down<<<dim3(nb, bt.members), SCAN_T, 0, st>>>(in, n, tmp, out, vec, bt);
+    k_write_total<<<bt.members, 1, 0, st>>>(out, n, total, bt);
 }
 
 void count_totals(const unsigned* counts, int64_t n, unsigned long long* out2, cudaStream_t st) {

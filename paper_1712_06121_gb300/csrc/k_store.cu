@@ -18,7 +18,6 @@ namespace cube {
 namespace {
 
 constexpr int T_BRICK = 256;                 // threads of the per-brick kernels
-constexpr int W_BRICK = T_BRICK / 32;
 constexpr double PI_D = 3.141592653589793;   // nearest double to pi
 
 __device__ __forceinline__ int upper_cell(const unsigned* off, int ncell, unsigned i) {
@@ -31,12 +30,15 @@ __device__ __forceinline__ int upper_cell(const unsigned* off, int ncell, unsign
     return lo;
 }
 
-// brick of a CTA launched on the (nb, nb, nb) grid: its coordinates and storage rank
-__device__ __forceinline__ int grid_brick(const Geo& g, int* bx, int* by, int* bz) {
+// brick of a CTA launched on the (nb, nb, nb x members) grid: its
+// coordinates and storage rank; *m the member of a batch
+template <bool BAT>
+__device__ __forceinline__ int grid_brick(const Geo& g, int* bx, int* by, int* bz, int* m) {
+    *m = BAT ? (int)blockIdx.z / g.nb : 0;
     *bx = blockIdx.x;
     *by = blockIdx.y;
-    *bz = blockIdx.z;
-    return (int)blockIdx.x + g.nb * ((int)blockIdx.y + g.nb * (int)blockIdx.z);
+    *bz = (int)blockIdx.z - *m * g.nb;
+    return *bx + g.nb * (*by + g.nb * *bz);
 }
 
 __device__ __forceinline__ void brick_coords(const Geo& g, int brick, int* bx, int* by, int* bz) {
@@ -143,8 +145,15 @@ __global__ void k_encode_sigma(Geo g, const float* __restrict__ vel, const unsig
 }
 
 __global__ void k_sigma_finalize(const float* __restrict__ part, int nparts, double count, double ratio,
-                                 double fixed, double* sigma_out) {
+                                 double fixed, double* sigma_out, Batch bt) {
     __shared__ double sh[32];
+    const int m = blockIdx.x;                                // member of a batch
+    if (bt.ms) {
+        if (!bt.ms[m].active) return;
+        ratio = bt.ms[m].ratio;
+    }
+    part = moved(part, m * bt.stride);
+    sigma_out = moved(sigma_out, m * bt.stride);
     // strided FP32 sums per thread (coalesced loads, fixed order), then a fixed tree in FP64
     float acc = 0.0f;
 #pragma unroll 8
@@ -201,8 +210,12 @@ __device__ void codec_tables_body(int lim, const double* __restrict__ tanv, cons
 
 __global__ void k_codec_tables(int lim, const double* __restrict__ tanv, const double* __restrict__ tanh_,
                                const double* __restrict__ sigma, float* __restrict__ dec, float* __restrict__ thr,
-                               float* __restrict__ est, unsigned char* __restrict__ vtab) {
-    codec_tables_body(lim, tanv, tanh_, *sigma, dec, thr, est, vtab);
+                               float* __restrict__ est, unsigned char* __restrict__ vtab, Batch bt) {
+    const int m = blockIdx.y;                                // member of a batch
+    if (bt.ms && !bt.ms[m].active) return;
+    const size_t o = m * bt.stride;
+    codec_tables_body(lim, moved(tanv, o), moved(tanh_, o), *moved(sigma, o), moved(dec, o), moved(thr, o),
+                      moved(est, o), moved(vtab, o));
 }
 
 template <int NX, int NV>
@@ -234,7 +247,7 @@ __global__ void k_encode_scatter(Geo g, const float* __restrict__ pos, const flo
         int nu = nu_from_thresholds(dd, thr, g.nulim, nu_estimate(dd, e0, e1));
         store_code<NV>(s.nu, d * g.Np + j, nu);
     }
-    if (s.id) s.id[j] = id_in ? id_in[i] : (unsigned)i;
+    if (s.id) store_pid(s.id, (unsigned)j, g.nid, id_in ? id_in[i] : (unsigned)i);
 }
 
 // ------------------------------------------------------------------ decode
@@ -265,7 +278,7 @@ __global__ void __launch_bounds__(T_BRICK) k_decode(Geo g, StoreDev s, const flo
             int nu = load_nu<NV>(s.nu, d * g.Np + i, g.nulim);
             vel[d * g.Np + i] = s.vc[(int64_t)d * g.Ncc + L0 + lc] + dec[nu + g.nulim];
         }
-        if (id) id[i] = s.id ? s.id[i] : i;
+        if (id) id[i] = s.id ? load_pid(s.id, i, g.nid) : i;
     }
 }
 
@@ -315,8 +328,9 @@ __host__ __device__ __forceinline__ int dep_acc_words(int F) {
     return fast > 2 * F * F * F ? fast : 2 * F * F * F;
 }
 
-template <int NX, int FC>
-__global__ void __launch_bounds__(T_BRICK) k_deposit(Geo g, StoreDev s, float* __restrict__ mesh, float fscale) {
+template <int NX, int FC, bool BAT>
+__global__ void __launch_bounds__(T_BRICK) k_deposit(Geo g, StoreDev s, float* __restrict__ mesh, float fscale,
+                                                     Batch bt) {
     extern __shared__ unsigned long long dep_smem[];
     // FC > 0: the brick side in fine cells is the compile-time FC, else g.F
     const int lF = FC == 16 ? 4 : FC == 8 ? 3 : FC == 4 ? 2 : g.lF, F = 1 << lF, F3 = 1 << (3 * lF);
@@ -332,8 +346,13 @@ __global__ void __launch_bounds__(T_BRICK) k_deposit(Geo g, StoreDev s, float* _
     int* cpack = reinterpret_cast<int*>(cpref + E3 + 1);             // [E3] packed cell offsets
     unsigned char* qcell = reinterpret_cast<unsigned char*>(cpack + E3);   // [DEP_QCAP] cell of each slot
     __shared__ unsigned wsum[T_BRICK / 32];
-    int bx, by, bz;
-    grid_brick(g, &bx, &by, &bz);
+    int bx, by, bz, m;
+    grid_brick<BAT>(g, &bx, &by, &bz, &m);
+    if constexpr (BAT) {                                     // member m of a batch
+        if (bt.ms && !bt.ms[m].active) return;
+        s = moved(s, m * bt.stride);
+        mesh = moved(mesh, m * bt.stride);
+    }
     const int c0[3] = {bx * g.B, by * g.B, bz * g.B};
     // the cells of the brick and of its one-cell layer below (E^3 <= 125 <=
     // one per thread), their particle counts scanned across the block
@@ -533,11 +552,11 @@ constexpr int PB_BIG = 1024;
 // ([o - 2, o + F + 3) per axis, periodic), brick offsets, the histogram of
 // destination cells over the brick and its one-cell halo (Bh^3 cells) with
 // fixed-point momentum sums, and (1-byte velocities) the codec tables.
-template <int NX, int NV, int FC>
+template <int NX, int NV, int FC, bool BAT>
 __global__ void __launch_bounds__(T_BRICK, 4) k_passA(Geo g, StoreDev s, const float* __restrict__ phig,
                                                       const __grid_constant__ CUtensorMap tmap, int use_tma,
                                                       CodecDev cur, float kick, float dc, StepScratch w,
-                                                      DriftDebug dbg) {
+                                                      DriftDebug dbg, Batch bt) {
     extern __shared__ unsigned char pa_smem[];
     __shared__ __align__(8) unsigned long long tile_bar;
     // Phi tile: T x T rows (y, z: [o - 2, o + F + 3)) of TX = F + 8 nodes
@@ -549,8 +568,20 @@ __global__ void __launch_bounds__(T_BRICK, 4) k_passA(Geo g, StoreDev s, const f
     const int nbc = g.B * g.B * g.B, Bh = g.Bh, H3 = Bh * Bh * Bh;
     const unsigned mBh = div_magic(Bh);
     const int lim = g.nulim;
-    int bx, by, bz;
-    const int brick = grid_brick(g, &bx, &by, &bz);
+    int bx, by, bz, m;
+    const int brick = grid_brick<BAT>(g, &bx, &by, &bz, &m);
+    if constexpr (BAT) {                                     // member m of a batch
+        if (bt.ms) {
+            if (!bt.ms[m].active) return;
+            kick = bt.ms[m].kick;
+            dc = bt.ms[m].dc;
+        }
+        const size_t o = m * bt.stride;
+        s = moved(s, o);
+        phig = moved(phig, o);
+        cur = moved(cur, o);
+        w = moved(w, o);
+    }
     const int ox = bx * F - 4, oy = by * F - 2, oz = bz * F - 2;      // tile origin
     long long* vs = reinterpret_cast<long long*>(pa_smem);                 // [3][H3]
     const unsigned sbase = smem_addr(pa_smem);
@@ -560,7 +591,7 @@ __global__ void __launch_bounds__(T_BRICK, 4) k_passA(Geo g, StoreDev s, const f
         __syncthreads();
         if (threadIdx.x == 0) {
             mbar_expect_tx(&tile_bar, (unsigned)T3 * 4u);
-            tma_load_3d(tile, &tmap, ox + PHIG_X0, oy + PHIG_Y0, oz + PHIG_Y0, &tile_bar);
+            tma_load_4d(tile, &tmap, ox + PHIG_X0, oy + PHIG_Y0, oz + PHIG_Y0, m, &tile_bar);
         }
     }
     unsigned* hist = reinterpret_cast<unsigned*>(tile + T3);                // [H3]
@@ -812,9 +843,17 @@ __global__ void __launch_bounds__(T_BRICK, 4) k_passA(Geo g, StoreDev s, const f
 // After the exclusive scan of the flattened histograms, a cell's first slot
 // holds offset*[c] and its slots span counts*[c] particles.  Also
 // v_c* = mean momentum of the cell's new particles (fixed point).
-__global__ void k_cells(Geo g, StepScratch w, unsigned* __restrict__ off_new, float* __restrict__ vc_new) {
+template <bool BAT>
+__global__ void k_cells(Geo g, StepScratch w, unsigned* __restrict__ off_new, float* __restrict__ vc_new, Batch bt) {
     const int L = blockIdx.x * blockDim.x + threadIdx.x;
     if (L >= g.Ncc) return;
+    if constexpr (BAT) {                                     // member blockIdx.y of a batch
+        const int m = blockIdx.y;
+        if (bt.ms && !bt.ms[m].active) return;
+        w = moved(w, m * bt.stride);
+        off_new = moved(off_new, m * bt.stride);
+        vc_new = moved(vc_new, m * bt.stride);
+    }
     const int nbc = g.B * g.B * g.B;
     const int hb = L / nbc, lc = L - hb * nbc;
     const int l[3] = {lc % g.B, (lc / g.B) % g.B, lc / (g.B * g.B)};
@@ -905,7 +944,7 @@ struct PassB {
             nu_n.put(d, pos, NV == 1 ? nu_from_table(dd, thr, stab, key0, lim)
                                      : nu_from_thresholds(dd, thr, lim, nu_estimate(dd, e0, e1)));
         }
-        if (sn.id) sn.id[pos] = cid;
+        if (sn.id) store_pid(sn.id, pos, g.nid, cid);
     }
 };
 
@@ -934,15 +973,31 @@ __device__ __forceinline__ void passB_stage(const Geo& g, const StoreDev& so, co
     }
 }
 
-template <int NX, int NV>
+template <int NX, int NV, bool BAT>
 __global__ void __launch_bounds__(PB_WARPS * 32, 5) k_passB(Geo g, StoreDev so, StoreDev sn, CodecDev cur, CodecDev next,
                                                         float dc, const unsigned* __restrict__ ghost,
                                                         const float* __restrict__ vc_new, unsigned* flags,
-                                                        const int* __restrict__ big, int nbig_ctas) {
+                                                        const int* __restrict__ big, int nbig_ctas, Batch bt) {
     extern __shared__ unsigned pb_smem[];
     const int nbc = g.B * g.B * g.B, H3 = g.Bh * g.Bh * g.Bh;
     const int lim = g.nulim;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if constexpr (BAT) {                                     // member blockIdx.y of a batch
+        const int m = blockIdx.y;
+        if (bt.ms) {
+            if (!bt.ms[m].active) return;
+            dc = bt.ms[m].dc;
+        }
+        const size_t o = m * bt.stride;
+        so = moved(so, o);
+        sn = moved(sn, o);
+        cur = moved(cur, o);
+        next = moved(next, o);
+        ghost = moved(ghost, o);
+        vc_new = moved(vc_new, o);
+        flags = moved(flags, o);
+        big = moved(big, o);
+    }
     const bool big_cta = (int)blockIdx.x < nbig_ctas;
     const int nbig = big_cta ? big[0] : 0;
     if (big_cta && (int)blockIdx.x >= nbig) return;          // no crowded brick left for this CTA
@@ -992,7 +1047,7 @@ __global__ void __launch_bounds__(PB_WARPS * 32, 5) k_passB(Geo g, StoreDev so, 
                         cchi[d] = chi_o.get(d, i);
                         cnu[d] = nu_o.get_nu(d, i, lim);
                     }
-                    if (sn.id) cid = so.id[i];
+                    if (sn.id) cid = load_pid(so.id, i, g.nid);
                     q = pb.move(upper_cell(sm_off, nbc, i), svc, cchi, cnu);
                     peers = __match_any_sync(am, q.ei);
                     leader = __ffs(peers) - 1;
@@ -1045,7 +1100,7 @@ __global__ void __launch_bounds__(PB_WARPS * 32, 5) k_passB(Geo g, StoreDev so, 
             nchi[d] = chi_o.get(d, p0 + lane);
             nnu[d] = nu_o.get_nu(d, p0 + lane, lim);
         }
-        if (sn.id) nid = so.id[p0 + lane];
+        if (sn.id) nid = load_pid(so.id, p0 + lane, g.nid);
     }
     passB_stage(g, so, ghost, vc_new, brick, lane, 32, sm_off, run, svc, svn);
     __syncwarp();
@@ -1062,7 +1117,7 @@ __global__ void __launch_bounds__(PB_WARPS * 32, 5) k_passB(Geo g, StoreDev so, 
                 nchi[d] = chi_o.get(d, i + 32);
                 nnu[d] = nu_o.get_nu(d, i + 32, lim);
             }
-            if (sn.id) nid = so.id[i + 32];
+            if (sn.id) nid = load_pid(so.id, i + 32, g.nid);
         }
         if (act) {
             const PbParticle q = pb.move(upper_cell(sm_off, nbc, i), svc, cchi, cnu);
@@ -1118,20 +1173,29 @@ template <int NX, int NV>
 struct Disp {
     static void passA(const Geo& g, const StoreDev& s, const float* phig, const CUtensorMap& tmap, int use_tma,
                       const CodecDev& cur, float kick, float dc, const StepScratch& w, const DriftDebug& dbg,
-                      size_t sm, cudaStream_t st) {
-        const dim3 grid(g.nb, g.nb, g.nb);
-        if (g.F == 16)
-            k_passA<NX, NV, 16><<<grid, T_BRICK, sm, st>>>(g, s, phig, tmap, use_tma, cur, kick, dc, w, dbg);
-        else
-            k_passA<NX, NV, 0><<<grid, T_BRICK, sm, st>>>(g, s, phig, tmap, use_tma, cur, kick, dc, w, dbg);
+                      size_t sm, cudaStream_t st, const Batch& bt) {
+        const dim3 grid(g.nb, g.nb, g.nb * bt.members);
+        const bool bat = bt.members > 1 || bt.ms;
+        if (g.F == 16) {
+            if (bat) k_passA<NX, NV, 16, true><<<grid, T_BRICK, sm, st>>>(g, s, phig, tmap, use_tma, cur, kick, dc, w, dbg, bt);
+            else k_passA<NX, NV, 16, false><<<grid, T_BRICK, sm, st>>>(g, s, phig, tmap, use_tma, cur, kick, dc, w, dbg, bt);
+        } else {
+            if (bat) k_passA<NX, NV, 0, true><<<grid, T_BRICK, sm, st>>>(g, s, phig, tmap, use_tma, cur, kick, dc, w, dbg, bt);
+            else k_passA<NX, NV, 0, false><<<grid, T_BRICK, sm, st>>>(g, s, phig, tmap, use_tma, cur, kick, dc, w, dbg, bt);
+        }
     }
     static void passB(const Geo& g, const StoreDev& so, const StoreDev& sn, const CodecDev& cur,
                       const CodecDev& next, float dc, const unsigned* ghost, const float* vcn, unsigned* flags,
-                      const int* big, size_t sm, cudaStream_t st) {
+                      const int* big, size_t sm, cudaStream_t st, const Batch& bt) {
         // CTAs for crowded bricks first (at most Np / (PB_BIG + 1) of them exist)
         const int nbig_ctas = (int)std::min<int64_t>(2 * g.nsm, g.Np / (PB_BIG + 1));
         const int grid = nbig_ctas + (g.nbricks + PB_WARPS - 1) / PB_WARPS;
-        k_passB<NX, NV><<<grid, PB_WARPS * 32, sm, st>>>(g, so, sn, cur, next, dc, ghost, vcn, flags, big, nbig_ctas);
+        if (bt.members > 1 || bt.ms)
+            k_passB<NX, NV, true><<<dim3(grid, bt.members), PB_WARPS * 32, sm, st>>>(g, so, sn, cur, next, dc, ghost,
+                                                                                   vcn, flags, big, nbig_ctas, bt);
+        else
+            k_passB<NX, NV, false><<<grid, PB_WARPS * 32, sm, st>>>(g, so, sn, cur, next, dc, ghost, vcn, flags, big,
+                                                                    nbig_ctas, bt);
     }
 };
 
@@ -1139,17 +1203,40 @@ template <int NX, int NV>
 void set_smem_attrs() {
     static bool done = false;
     if (done) return;
-    cudaFuncSetAttribute(k_passA<NX, NV, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    cudaFuncSetAttribute(k_passA<NX, NV, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    cudaFuncSetAttribute(k_passB<NX, NV>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    cudaFuncSetAttribute(k_deposit<NX, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    cudaFuncSetAttribute(k_deposit<NX, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    const int lim = 200 * 1024;
+    cudaFuncSetAttribute(k_passA<NX, NV, 0, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+    cudaFuncSetAttribute(k_passA<NX, NV, 16, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+    cudaFuncSetAttribute(k_passA<NX, NV, 0, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+    cudaFuncSetAttribute(k_passA<NX, NV, 16, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+    cudaFuncSetAttribute(k_passB<NX, NV, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+    cudaFuncSetAttribute(k_passB<NX, NV, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+    cudaFuncSetAttribute(k_deposit<NX, 0, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+    cudaFuncSetAttribute(k_deposit<NX, 16, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+    cudaFuncSetAttribute(k_deposit<NX, 0, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+    cudaFuncSetAttribute(k_deposit<NX, 16, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
     done = true;
+}
+
+// the step's cleared scratch of every stepped member of a batch: the
+// fixed-point momentum sums [3][Ncc] and the migration / crowded-brick words
+__global__ void k_batch_clear(int64_t n64, long long* __restrict__ vsum, int* __restrict__ mig, Batch bt) {
+    const int m = blockIdx.y;
+    if (bt.ms && !bt.ms[m].active) return;
+    vsum = moved(vsum, m * bt.stride);
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n64; t += (int64_t)gridDim.x * blockDim.x)
+        vsum[t] = 0;
+    if (blockIdx.x == 0 && threadIdx.x < 2) moved(mig, m * bt.stride)[threadIdx.x] = 0;
 }
 
 }  // namespace
 
 // ------------------------------------------------------------------ launchers
+void launch_batch_clear(const Geo& g, long long* vsum, int* maxmig, cudaStream_t st, const Batch& bt) {
+    const int64_t n = 3 * (int64_t)g.Ncc;
+    k_batch_clear<<<dim3((unsigned)std::min<int64_t>(1024, (n + 255) / 256), bt.members), 256, 0, st>>>(n, vsum,
+                                                                                                     maxmig, bt);
+}
+
 static inline int nblk(int64_t n, int t) { return (int)((n + t - 1) / t); }
 
 void launch_encode_keys(const Geo& g, const float* pos, const float* vel, unsigned* key, unsigned* val,
@@ -1170,15 +1257,16 @@ void launch_encode_sigma(const Geo& g, const float* vel, const unsigned* key, co
 }
 
 void launch_sigma_finalize(const float* part, int nparts, double count, double ratio, double fixed,
-                           double* sigma_out, cudaStream_t st) {
-    k_sigma_finalize<<<1, 1024, 0, st>>>(part, nparts, count, ratio, fixed, sigma_out);
+                           double* sigma_out, cudaStream_t st, const Batch& bt) {
+    k_sigma_finalize<<<bt.members, 1024, 0, st>>>(part, nparts, count, ratio, fixed, sigma_out, bt);
 }
 
-void launch_codec_tables(int nulim, const double* tanv, const double* tanh_, const CodecDev& c, cudaStream_t st) {
+void launch_codec_tables(int nulim, const double* tanv, const double* tanh_, const CodecDev& c, cudaStream_t st,
+                         const Batch& bt) {
     // 1-byte codes (nulim 127) fit one block, which also builds the bucket table
     const bool one = nulim + 2 <= 256;
-    k_codec_tables<<<nblk(nulim + 2, 256), 256, 0, st>>>(nulim, tanv, tanh_, c.sigma, c.dec, c.thr, c.est,
-                                                        one ? c.vtab : nullptr);
+    k_codec_tables<<<dim3(nblk(nulim + 2, 256), bt.members), 256, 0, st>>>(nulim, tanv, tanh_, c.sigma, c.dec, c.thr,
+                                                                          c.est, one ? c.vtab : nullptr, bt);
 }
 
 void launch_encode_scatter(const Geo& g, const float* pos, const float* vel, const unsigned* id_in,
@@ -1212,18 +1300,29 @@ static size_t deposit_smem(const Geo& g) {
     return (size_t)dep_acc_words(g.F) * 4 + (size_t)(3 * E3 + 1) * 4 + DEP_QCAP;
 }
 
-void launch_deposit(const Geo& g, const StoreDev& s, float* mesh, double scale, cudaStream_t st) {
+void launch_deposit(const Geo& g, const StoreDev& s, float* mesh, double scale, cudaStream_t st, const Batch& bt) {
     size_t sm = deposit_smem(g);
-    const bool f16 = g.F == 16;
-    const dim3 grid(g.nb, g.nb, g.nb);
+    const bool f16 = g.F == 16, bat = bt.members > 1 || bt.ms;
+    const dim3 grid(g.nb, g.nb, g.nb * bt.members);
+    const float fs = (float)scale;
     if (g.nchi == 1) {
         set_smem_attrs<1, 1>(); set_smem_attrs<1, 2>();
-        if (f16) k_deposit<1, 16><<<grid, T_BRICK, sm, st>>>(g, s, mesh, (float)scale);
-        else k_deposit<1, 0><<<grid, T_BRICK, sm, st>>>(g, s, mesh, (float)scale);
+        if (f16) {
+            if (bat) k_deposit<1, 16, true><<<grid, T_BRICK, sm, st>>>(g, s, mesh, fs, bt);
+            else k_deposit<1, 16, false><<<grid, T_BRICK, sm, st>>>(g, s, mesh, fs, bt);
+        } else {
+            if (bat) k_deposit<1, 0, true><<<grid, T_BRICK, sm, st>>>(g, s, mesh, fs, bt);
+            else k_deposit<1, 0, false><<<grid, T_BRICK, sm, st>>>(g, s, mesh, fs, bt);
+        }
     } else {
         set_smem_attrs<2, 1>(); set_smem_attrs<2, 2>();
-        if (f16) k_deposit<2, 16><<<grid, T_BRICK, sm, st>>>(g, s, mesh, (float)scale);
-        else k_deposit<2, 0><<<grid, T_BRICK, sm, st>>>(g, s, mesh, (float)scale);
+        if (f16) {
+            if (bat) k_deposit<2, 16, true><<<grid, T_BRICK, sm, st>>>(g, s, mesh, fs, bt);
+            else k_deposit<2, 16, false><<<grid, T_BRICK, sm, st>>>(g, s, mesh, fs, bt);
+        } else {
+            if (bat) k_deposit<2, 0, true><<<grid, T_BRICK, sm, st>>>(g, s, mesh, fs, bt);
+            else k_deposit<2, 0, false><<<grid, T_BRICK, sm, st>>>(g, s, mesh, fs, bt);
+        }
     }
 }
 
@@ -1237,19 +1336,22 @@ static size_t passA_smem(const Geo& g) {
 }
 
 void launch_passA(const Geo& g, const StoreDev& s, const float* phig, const CUtensorMap* tmap, const CodecDev& cur,
-                  float kick, float dc, const StepScratch& w, const DriftDebug& dbg, cudaStream_t st) {
+                  float kick, float dc, const StepScratch& w, const DriftDebug& dbg, cudaStream_t st,
+                  const Batch& bt) {
     size_t sm = passA_smem(g);
     static const CUtensorMap none{};
     const CUtensorMap& tm = tmap ? *tmap : none;
     const int use = tmap != nullptr;
-    if (g.nchi == 1 && g.nnu == 1) { set_smem_attrs<1, 1>(); Disp<1, 1>::passA(g, s, phig, tm, use, cur, kick, dc, w, dbg, sm, st); }
-    else if (g.nchi == 1) { set_smem_attrs<1, 2>(); Disp<1, 2>::passA(g, s, phig, tm, use, cur, kick, dc, w, dbg, sm, st); }
-    else if (g.nnu == 1) { set_smem_attrs<2, 1>(); Disp<2, 1>::passA(g, s, phig, tm, use, cur, kick, dc, w, dbg, sm, st); }
-    else { set_smem_attrs<2, 2>(); Disp<2, 2>::passA(g, s, phig, tm, use, cur, kick, dc, w, dbg, sm, st); }
+    if (g.nchi == 1 && g.nnu == 1) { set_smem_attrs<1, 1>(); Disp<1, 1>::passA(g, s, phig, tm, use, cur, kick, dc, w, dbg, sm, st, bt); }
+    else if (g.nchi == 1) { set_smem_attrs<1, 2>(); Disp<1, 2>::passA(g, s, phig, tm, use, cur, kick, dc, w, dbg, sm, st, bt); }
+    else if (g.nnu == 1) { set_smem_attrs<2, 1>(); Disp<2, 1>::passA(g, s, phig, tm, use, cur, kick, dc, w, dbg, sm, st, bt); }
+    else { set_smem_attrs<2, 2>(); Disp<2, 2>::passA(g, s, phig, tm, use, cur, kick, dc, w, dbg, sm, st, bt); }
 }
 
-void launch_cells(const Geo& g, const StepScratch& w, unsigned* off_new, float* vc_new, cudaStream_t st) {
-    k_cells<<<nblk(g.Ncc, 256), 256, 0, st>>>(g, w, off_new, vc_new);
+void launch_cells(const Geo& g, const StepScratch& w, unsigned* off_new, float* vc_new, cudaStream_t st,
+                  const Batch& bt) {
+    if (bt.members > 1 || bt.ms) k_cells<true><<<dim3(nblk(g.Ncc, 256), bt.members), 256, 0, st>>>(g, w, off_new, vc_new, bt);
+    else k_cells<false><<<nblk(g.Ncc, 256), 256, 0, st>>>(g, w, off_new, vc_new, bt);
 }
 
 static size_t passB_smem(const Geo& g) {
@@ -1260,13 +1362,13 @@ static size_t passB_smem(const Geo& g) {
 }
 
 void launch_passB(const Geo& g, const StoreDev& so, const StoreDev& sn, const CodecDev& cur, const CodecDev& next,
-                  float dc, const StepScratch& w, cudaStream_t st) {
+                  float dc, const StepScratch& w, cudaStream_t st, const Batch& bt) {
     size_t sm = passB_smem(g);
     const float* vcn = sn.vc;
-    if (g.nchi == 1 && g.nnu == 1) { set_smem_attrs<1, 1>(); Disp<1, 1>::passB(g, so, sn, cur, next, dc, w.ghost, vcn, w.flags, w.big, sm, st); }
-    else if (g.nchi == 1) { set_smem_attrs<1, 2>(); Disp<1, 2>::passB(g, so, sn, cur, next, dc, w.ghost, vcn, w.flags, w.big, sm, st); }
-    else if (g.nnu == 1) { set_smem_attrs<2, 1>(); Disp<2, 1>::passB(g, so, sn, cur, next, dc, w.ghost, vcn, w.flags, w.big, sm, st); }
-    else { set_smem_attrs<2, 2>(); Disp<2, 2>::passB(g, so, sn, cur, next, dc, w.ghost, vcn, w.flags, w.big, sm, st); }
+    if (g.nchi == 1 && g.nnu == 1) { set_smem_attrs<1, 1>(); Disp<1, 1>::passB(g, so, sn, cur, next, dc, w.ghost, vcn, w.flags, w.big, sm, st, bt); }
+    else if (g.nchi == 1) { set_smem_attrs<1, 2>(); Disp<1, 2>::passB(g, so, sn, cur, next, dc, w.ghost, vcn, w.flags, w.big, sm, st, bt); }
+    else if (g.nnu == 1) { set_smem_attrs<2, 1>(); Disp<2, 1>::passB(g, so, sn, cur, next, dc, w.ghost, vcn, w.flags, w.big, sm, st, bt); }
+    else { set_smem_attrs<2, 2>(); Disp<2, 2>::passB(g, so, sn, cur, next, dc, w.ghost, vcn, w.flags, w.big, sm, st, bt); }
 }
 
 void launch_store_sums(const Geo& g, const StoreDev& s, const float* dec, long long* out4, cudaStream_t st) {

@@ -2,6 +2,7 @@
 #pragma once
 
 #include <string>
+#include <type_traits>
 
 #include <cuda.h>
 
@@ -44,12 +45,36 @@ __device__ __forceinline__ int stable_round_rank(int digit, bool active, unsigne
     return pos;
 }
 
+// ------------------------------------------------------------ batches
+// A batched launch steps several members (simulations with the same
+// geometry) at once: member m's device buffers are member 0's plus m * stride
+// bytes, so every kernel of the step takes one extra grid dimension over the
+// members and moves its pointers by m * stride.  A single context is the
+// batch of one (members 1, stride 0, no per-member table).
+struct MemberStep {
+    float kick, dc;     // the step's kick factor and drift per coarse cell
+    double ratio;       // momentum growth ratio of the codec-scale update
+    int active;         // 0: the member is not stepped (its kernels return at once)
+    int pad;
+};
+struct Batch {
+    int members;
+    size_t stride;               // bytes between consecutive members' buffers
+    const MemberStep* ms;        // [members] (device) or null
+};
+template <class T>
+__host__ __device__ __forceinline__ T* moved(T* p, size_t off) {
+    return p ? reinterpret_cast<T*>(reinterpret_cast<char*>(const_cast<typename std::remove_const<T>::type*>(p)) + off)
+             : p;
+}
+
 // ------------------------------------------------------------ cube_api.cu
 void set_last_error(const std::string& msg);     // message for cube_last_error()
 
 // ------------------------------------------------------------ k_scan.cu
 int scan_tmp_words(int64_t n);
-void exclusive_scan(const unsigned* in, unsigned* out, int64_t n, unsigned* tmp, cudaStream_t st);
+void exclusive_scan(const unsigned* in, unsigned* out, int64_t n, unsigned* tmp, cudaStream_t st,
+                    const Batch& bt = Batch{1, 0, nullptr});
 // out2[0] = 64-bit sum, out2[1] = maximum of n counts
 void count_totals(const unsigned* counts, int64_t n, unsigned long long* out2, cudaStream_t st);
 int64_t radix_tmp_words(int64_t n);
@@ -62,7 +87,7 @@ struct StoreDev {
     float* vc;          // [3][Ncc]
     void* chi;          // [3][Np]
     void* nu;           // [3][Np]
-    unsigned* id;       // [Np] or null
+    void* id;           // [Np] particle IDs of Geo::nid bytes (1, 2 or 4), or null
 };
 
 struct CodecDev {
@@ -92,6 +117,21 @@ struct StepScratch {
                             // particles, then their indices (listed by pass A)
 };
 
+// the same buffers of the member `off` bytes further on
+__host__ __device__ __forceinline__ StoreDev moved(const StoreDev& s, size_t off) {
+    return StoreDev{moved(s.counts, off), moved(s.offsets, off), moved(s.vc, off), moved(s.chi, off),
+                    moved(s.nu, off), moved(s.id, off)};
+}
+__host__ __device__ __forceinline__ CodecDev moved(const CodecDev& c, size_t off) {
+    return CodecDev{moved(c.dec, off), moved(c.thr, off), moved(c.est, off), moved(c.vtab, off), moved(c.sigma, off)};
+}
+__host__ __device__ __forceinline__ StepScratch moved(const StepScratch& w, size_t off) {
+    return StepScratch{moved(w.counts_new, off), moved(w.vsum_new, off), moved(w.ghost, off), moved(w.part, off),
+                       moved(w.flags, off), moved(w.maxmig, off), moved(w.big, off)};
+}
+// a batch of one: a single context's launch
+constexpr Batch kSingle{1, 0, nullptr};
+
 void launch_encode_keys(const Geo& g, const float* pos, const float* vel, unsigned* key, unsigned* val,
                         unsigned* counts, long long* vsum, unsigned* flags, cudaStream_t st);
 void launch_vc_finalize(const Geo& g, const unsigned* counts, const long long* vsum, float* vc, cudaStream_t st);
@@ -99,20 +139,28 @@ int encode_sigma_blocks(const Geo& g);
 void launch_encode_sigma(const Geo& g, const float* vel, const unsigned* key_sorted_or_raw, const float* vc,
                          float* part, cudaStream_t st);
 void launch_sigma_finalize(const float* part, int nparts, double count, double ratio, double fixed,
-                           double* sigma_out, cudaStream_t st);
-void launch_codec_tables(int nulim, const double* tanv, const double* tanh, const CodecDev& c, cudaStream_t st);
+                           double* sigma_out, cudaStream_t st, const Batch& bt = Batch{1, 0, nullptr});
+void launch_codec_tables(int nulim, const double* tanv, const double* tanh, const CodecDev& c, cudaStream_t st,
+                         const Batch& bt = Batch{1, 0, nullptr});
 void launch_encode_scatter(const Geo& g, const float* pos, const float* vel, const unsigned* id_in,
                            const unsigned* key_sorted, const unsigned* perm, const float* vc, const CodecDev& c,
                            StoreDev s, cudaStream_t st);
 void launch_decode(const Geo& g, const StoreDev& s, const float* dec, float* pos, float* vel, unsigned* id,
                    cudaStream_t st);
-void launch_deposit(const Geo& g, const StoreDev& s, float* mesh, double scale, cudaStream_t st);
+void launch_deposit(const Geo& g, const StoreDev& s, float* mesh, double scale, cudaStream_t st,
+                    const Batch& bt = Batch{1, 0, nullptr});
 // phig: ghosted Phi; tmap: TMA map of phig with the brick's tile as its box, or NULL (cp.async loads)
+// (tmap: a 4-D map over (x, y, z, member) of the members' ghosted Phi)
 void launch_passA(const Geo& g, const StoreDev& s, const float* phig, const CUtensorMap* tmap, const CodecDev& cur,
-                  float kick, float dc, const StepScratch& w, const DriftDebug& dbg, cudaStream_t st);
-void launch_cells(const Geo& g, const StepScratch& w, unsigned* off_new, float* vc_new, cudaStream_t st);
+                  float kick, float dc, const StepScratch& w, const DriftDebug& dbg, cudaStream_t st,
+                  const Batch& bt = Batch{1, 0, nullptr});
+// a batch step's cleared scratch (momentum sums, migration words) of its stepped members
+void launch_batch_clear(const Geo& g, long long* vsum, int* maxmig, cudaStream_t st, const Batch& bt);
+void launch_cells(const Geo& g, const StepScratch& w, unsigned* off_new, float* vc_new, cudaStream_t st,
+                  const Batch& bt = Batch{1, 0, nullptr});
 void launch_passB(const Geo& g, const StoreDev& s_old, const StoreDev& s_new, const CodecDev& cur,
-                  const CodecDev& next, float dc, const StepScratch& w, cudaStream_t st);
+                  const CodecDev& next, float dc, const StepScratch& w, cudaStream_t st,
+                  const Batch& bt = Batch{1, 0, nullptr});
 // sums over the current store: out[0..2] momentum of the decoded particles in
 // 2^-24 fixed point, out[3] the particle count (sum of the cell counts)
 void launch_store_sums(const Geo& g, const StoreDev& s, const float* dec, long long* out4, cudaStream_t st);
@@ -138,10 +186,14 @@ struct FftPlan {
 };
 
 bool fft_size_supported(int N);                                                    // compiled mesh sizes
-void fft_x_r2c(const FftPlan& p, float* mesh, int S, cudaStream_t st);                 // rows: r2c
-void fft_y(const FftPlan& p, float* mesh, int S, bool inverse, cudaStream_t st);        // y columns
-void fft_z(const FftPlan& p, float* mesh, int S, float g0, bool green, cudaStream_t st); // z (+ Green, inverse)
-void fft_x_c2r(const FftPlan& p, float* mesh, int S, float* phig, cudaStream_t st);     // rows: c2r into ghosted Phi
+void fft_x_r2c(const FftPlan& p, float* mesh, int S, cudaStream_t st,
+               const Batch& bt = Batch{1, 0, nullptr});                                      // rows: r2c
+void fft_y(const FftPlan& p, float* mesh, int S, bool inverse, cudaStream_t st,
+           const Batch& bt = Batch{1, 0, nullptr});                                          // y columns
+void fft_z(const FftPlan& p, float* mesh, int S, float g0, bool green, cudaStream_t st,
+           const Batch& bt = Batch{1, 0, nullptr});                                          // z (+ Green, inverse)
+void fft_x_c2r(const FftPlan& p, float* mesh, int S, float* phig, cudaStream_t st,
+               const Batch& bt = Batch{1, 0, nullptr});                                      // rows: c2r into ghosted Phi
 int pk_blocks(int N);
 void launch_pk_bin(const FftPlan& p, const float* mesh, int S, int nbins, double pfac, double kfund,
                    double* part, cudaStream_t st);

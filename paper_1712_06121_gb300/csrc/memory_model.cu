@@ -27,7 +27,8 @@ extern "C" cube_status cube_memory_model(const cube_memory_config* cfg, cube_mem
     const cube_memory_config& c = *cfg;
     if (c.x_bytes < 1 || c.x_bytes > 2 || c.v_bytes < 1 || c.v_bytes > 2)
         return served_fail(CUBE_E_ARG, "x_bytes and v_bytes must be 1 or 2");
-    if (c.id_bytes != 0 && c.id_bytes != 4) return served_fail(CUBE_E_ARG, "id_bytes must be 0 or 4");
+    if (c.id_bytes != 0 && c.id_bytes != 1 && c.id_bytes != 2 && c.id_bytes != 4)
+        return served_fail(CUBE_E_ARG, "id_bytes must be 0, 1, 2 or 4");
     if (c.ratio < 1 || c.coarse_per_image < 1 || c.tiles < 1 || c.buffer < 0)
         return served_fail(CUBE_E_ARG, "ratio, coarse_per_image, tiles must be >= 1 and buffer >= 0");
     if (c.coarse_per_image % c.tiles != 0) return served_fail(CUBE_E_ARG, "tiles must divide coarse_per_image");

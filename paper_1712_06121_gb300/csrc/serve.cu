@@ -95,6 +95,7 @@ struct cube_server {
     std::vector<cudaEvent_t> spare;       // recycled step events
     int64_t next_ticket = 1;
     int inject_alloc_failures = 0;        // test hook: work-area allocations to refuse
+    int policy = CUBE_ADMIT_FIFO;         // which queued request is admitted next
     std::chrono::steady_clock::time_point t0;
 
     double now() const { return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count(); }
@@ -206,9 +207,21 @@ finish:
     return CUBE_OK;
 }
 
+// remaining work of a queued request: particles x scheduled steps
+double request_work(const Request* r) {
+    return (double)r->prm.n_particles * (double)(r->epochs.size() - 1);
+}
+
 cube_status admit(cube_server* s) {
     while (!s->queue.empty() && (int)s->running.size() < s->max_running) {
-        Request* r = s->queue.front();
+        // FIFO: the oldest request; shortest first: the least remaining work
+        // (ties: the oldest).  The chosen request waits for memory; nothing
+        // behind it overtakes it.
+        auto pick = s->queue.begin();
+        if (s->policy == CUBE_ADMIT_SHORTEST)
+            for (auto it = s->queue.begin(); it != s->queue.end(); ++it)
+                if (request_work(*it) < request_work(*pick)) pick = it;
+        Request* r = *pick;
         // the stream with the fewest running requests whose work area fits
         // the request (or can grow within the budget); ties: no growth, then
         // the lowest index
@@ -235,7 +248,7 @@ cube_status admit(cube_server* s) {
             else e = cudaMallocAsync((void**)&fresh, r->work_bytes, sl.st);
             if (e != cudaSuccess) {
                 cudaGetLastError();
-                s->queue.pop_front();
+                s->queue.erase(pick);
                 if (e != cudaErrorMemoryAllocation) {
                     fail_request(s, r, CUBE_E_CUDA);
                     return served_fail(CUBE_E_CUDA, cudaGetErrorString(e));
@@ -248,7 +261,7 @@ cube_status admit(cube_server* s) {
             sl.work = fresh;
             sl.bytes = r->work_bytes;
         }
-        s->queue.pop_front();
+        s->queue.erase(pick);
         r->slot = k;
         r->t_admit = s->now();
         cube_status st = served_create(&r->prm, sl.st, &r->ctx);
@@ -464,6 +477,13 @@ cube_status cube_server_release(cube_server* s, int64_t ticket) {
     if (r->pk) cudaFreeHost(r->pk);
     s->reqs.erase(ticket);
     delete r;
+    return CUBE_OK;
+}
+
+cube_status cube_server_set_policy(cube_server* s, int32_t policy) {
+    if (!s || (policy != CUBE_ADMIT_FIFO && policy != CUBE_ADMIT_SHORTEST))
+        return served_fail(CUBE_E_ARG, "server is NULL or the policy is unknown");
+    s->policy = policy;
     return CUBE_OK;
 }
 

@@ -27,7 +27,8 @@ def read_store(cube, ctx):
         vc=device_view(st.vc, (3, ncc), "<f4").cpu().numpy(),
         chi=device_view(st.chi, (3, n), ct).cpu().numpy().astype(np.int64),
         nu=device_view(st.nu, (3, n), vt).cpu().numpy().astype(np.int64),
-        ids=device_view(st.id, (n,), "<u4").cpu().numpy() if st.id else None,
+        ids=(device_view(st.id, (n,), {1: "|u1", 2: "<u2", 4: "<u4"}[st.id_bytes]).cpu().numpy().astype(np.uint32)
+             if st.id else None),
         sigma=st.sigma, a=st.a, a_p=st.a_p, brick=st.brick, n_coarse=st.n_coarse)
     torch.cuda.synchronize()
     return out

@@ -27,11 +27,12 @@ def cube():
     return c
 
 
-def _setup(cube, xb, vb, nps=32):
+def _setup(cube, xb, vb, nps=32, id_bytes=4):
     w = synth.WORKLOADS["pm64"]
     ic = synth.make_ics(w, n_part_side=nps, n_fine=2 * nps)
     om, ol, _ = w.omega()
-    prm = cube.make_params(2 * nps, nps ** 3, x_bytes=xb, v_bytes=vb, box=w.box, omega_m=om, omega_l=ol)
+    prm = cube.make_params(2 * nps, nps ** 3, x_bytes=xb, v_bytes=vb, box=w.box, omega_m=om, omega_l=ol,
+                           id_bytes=id_bytes)
     return w, ic, prm
 
 
@@ -41,9 +42,9 @@ def _decode(cube, ctx, n):
     return out
 
 
-@pytest.mark.parametrize("xb,vb", [(1, 1), (2, 2), (1, 2), (4, 4)])
-def test_checkpoint_round_trip_and_continuation(cube, xb, vb):
-    w, ic, prm = _setup(cube, xb, vb)
+@pytest.mark.parametrize("xb,vb,idb", [(1, 1, 4), (2, 2, 4), (1, 2, 4), (4, 4, 4), (1, 1, 1), (2, 1, 2)])
+def test_checkpoint_round_trip_and_continuation(cube, xb, vb, idb):
+    w, ic, prm = _setup(cube, xb, vb, id_bytes=idb)
     n = 32 ** 3
     sched = synth.uniform_schedule(w.a_init, 0.08, 6)
     a = cube.cube_create(prm, torch.cuda.current_stream())

@@ -548,3 +548,37 @@ def test_runs_are_deterministic_and_brick_invariant(cube):
     for brick in (1, 2):
         c = _run_decoded(cube, ic, w, 32, 64, brick)
         assert np.array_equal(a[0], c[0]) and np.array_equal(a[1], c[1])
+
+
+@pytest.mark.parametrize("id_bytes", [1, 2])
+def test_narrow_particle_ids_follow_their_particles(cube, id_bytes):
+    """Section 2.1's PID array I_P with n_I = 1 or 2 bytes per particle (for
+    instance particle types): the low n_I bytes of each ID travel with their
+    particle through encode and three re-sorts exactly as the 4-byte IDs do,
+    and the particles themselves are those of the 4-byte run."""
+    w, ic = _ics(32, 64)
+    n = 32 ** 3
+    ids = np.random.default_rng(5).integers(0, 2 ** 32, n, dtype=np.uint64).astype(np.uint32)
+    out = {}
+    for nb in (4, id_bytes):
+        om, ol, _ = w.omega()
+        prm = cube.make_params(64, n, x_bytes=1, v_bytes=2, id_bytes=nb, box=w.box, omega_m=om, omega_l=ol)
+        ctx = cube.cube_create(prm, torch.cuda.current_stream())
+        try:
+            cube.cube_encode(ctx, ic.pos, ic.vel, ids, w.a_init, ic.sigma_1d)
+            sched = synth.uniform_schedule(w.a_init, 0.05, 3)
+            for i in range(3):
+                cube.cube_pm_step(ctx, sched[i], sched[i + 1])
+            g = read_store(cube, ctx)
+            pos, vel, got = np.empty((3, n), np.float32), np.empty((3, n), np.float32), np.empty(n, np.uint32)
+            cube.cube_decode(ctx, pos, vel, got)
+            out[nb] = (g, pos, vel, got)
+        finally:
+            cube.cube_destroy(ctx)
+    mask = np.uint32((1 << (8 * id_bytes)) - 1)
+    wide, narrow = out[4], out[id_bytes]
+    for k in ("counts", "chi", "nu", "vc"):
+        assert np.array_equal(wide[0][k], narrow[0][k])
+    assert np.array_equal(wide[1], narrow[1]) and np.array_equal(wide[2], narrow[2])
+    assert np.array_equal(wide[3] & mask, narrow[3])
+    assert np.array_equal(narrow[0]["ids"], narrow[3])

@@ -307,3 +307,50 @@ def test_a_work_area_that_cannot_grow_fails_only_the_new_request(cube):
         assert cube.cube_server_bytes(srv) == b_wb
     finally:
         cube.cube_server_destroy(srv)
+
+
+def test_shortest_work_first_admission(cube):
+    """CUBE_ADMIT_SHORTEST: with one request running at a time, queued
+    requests are admitted in increasing particles x steps (ties in arrival
+    order); CUBE_ADMIT_FIFO admits them in arrival order.  Results do not
+    depend on the order."""
+    mix = _mix()[:5]
+    ics = [synth.make_ics(w) for w in mix]
+    work = [w.n_particles * w.n_steps for w in mix]
+    results = {}
+    for policy in (cube.CUBE_ADMIT_FIFO, cube.CUBE_ADMIT_SHORTEST):
+        srv = cube.cube_server_create(8 << 30, n_streams=1, max_running=1)
+        try:
+            cube.cube_server_set_policy(srv, policy)
+            keep, tickets = [], []
+            for w, ic in zip(mix, ics):
+                host = (_pinned(ic.pos), _pinned(ic.vel), _pinned(ic.ids.view(np.int32)))
+                keep.append(host)
+                sch = synth.uniform_schedule(w.a_init, w.a_final, w.n_steps)
+                tickets.append(cube.cube_server_submit(srv, _params(cube, w), *host, ic.sigma_1d, sch, 4))
+            cube.cube_server_drain(srv)
+            infos = [cube.cube_server_info(srv, t) for t in tickets]
+            assert all(i.state == cube.CUBE_REQ_DONE for i in infos)
+            order = list(np.argsort([i.t_admit for i in infos], kind="stable"))
+            outs = []
+            for w, t in zip(mix, tickets):
+                n = w.n_particles
+                pos, vel, ids = np.empty((3, n), np.float32), np.empty((3, n), np.float32), np.empty(n, np.uint32)
+                cube.cube_server_decode(srv, t, pos, vel, ids)
+                outs.append((pos, vel, ids))
+            results[policy] = outs
+        finally:
+            cube.cube_server_destroy(srv)
+        if policy == cube.CUBE_ADMIT_FIFO:
+            assert order == list(range(len(mix)))
+        else:
+            assert order == sorted(range(len(mix)), key=lambda i: (work[i], i))
+    for a, b in zip(results[cube.CUBE_ADMIT_FIFO], results[cube.CUBE_ADMIT_SHORTEST]):
+        for x, y in zip(a, b):
+            assert np.array_equal(x, y)
+    with pytest.raises(cube.CubeError):
+        srv = cube.cube_server_create(1 << 30, n_streams=1, max_running=1)
+        try:
+            cube.cube_server_set_policy(srv, 7)
+        finally:
+            cube.cube_server_destroy(srv)

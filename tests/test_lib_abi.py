@@ -41,7 +41,7 @@ def test_binding_has_the_same_names(lib):
 
 @pytest.mark.parametrize("field,value", [("n_fine", 100), ("n_fine", 2048), ("ratio", 3), ("x_bytes", 3),
                                          ("x_bytes", 4),
-                                         ("v_bytes", 0), ("id_bytes", 2), ("deconv_power", 5), ("brick", 3),
+                                         ("v_bytes", 0), ("id_bytes", 3), ("deconv_power", 5), ("brick", 3),
                                          ("n_particles", 0), ("gradient", 7)])
 def test_invalid_params_are_rejected_before_any_device_call(lib, field, value):
     import paper_1712_06121_gb300 as cube

@@ -99,7 +99,7 @@ def test_three_tiles_per_side_minimise_the_table_configuration(cube):
     assert min(totals, key=totals.get) == 3
 
 
-@pytest.mark.parametrize("field,value", [("x_bytes", 3), ("v_bytes", 0), ("id_bytes", 2), ("ratio", 0),
+@pytest.mark.parametrize("field,value", [("x_bytes", 3), ("v_bytes", 0), ("id_bytes", 3), ("ratio", 0),
                                          ("coarse_per_image", 0), ("buffer", -1), ("tiles", 5),
                                          ("eps_image", -0.1), ("particles_per_image", 0.0)])
 def test_bad_configurations_are_refused(cube, field, value):
@@ -108,7 +108,7 @@ def test_bad_configurations_are_refused(cube, field, value):
     assert e.value.status == cube.CUBE_E_ARG
 
 
-@pytest.mark.parametrize("nps,xb,vb,idb", [(256, 1, 1, 4), (128, 1, 2, 0), (64, 2, 2, 4)])
+@pytest.mark.parametrize("nps,xb,vb,idb", [(256, 1, 1, 4), (128, 1, 2, 0), (64, 2, 2, 4), (128, 1, 1, 1), (64, 1, 2, 2)])
 def test_resident_state_is_the_models_single_image_particle_arrays(cube, nps, xb, vb, idb):
     """One GPU holds the whole periodic box: one image, no buffer, the
     re-sorted store full size (N_b = 0, M_t = 1, no margins).  There the

@@ -73,7 +73,7 @@ def test_server_argument_checks(cube):
     assert cube._lib.cube_server_release(None, 1) == cube.CUBE_E_ARG
 
 
-@pytest.mark.parametrize("nps,xb,vb,ids", [(256, 1, 1, 4), (64, 2, 2, 0), (48, 4, 4, 4)])
+@pytest.mark.parametrize("nps,xb,vb,ids", [(256, 1, 1, 4), (64, 2, 2, 0), (48, 4, 4, 4), (64, 1, 1, 1), (32, 1, 2, 2)])
 def test_checkpoint_size_follows_the_documented_layout(cube, nps, xb, vb, ids):
     """64-byte header, then counts, v_c, chi, nu, ids, each 16-byte aligned
     (uncompressed: positions and momenta as floats)."""
@@ -83,6 +83,6 @@ def test_checkpoint_size_follows_the_documented_layout(cube, nps, xb, vb, ids):
     if xb == 4:
         want = 64 + a16(12 * n) + a16(12 * n) + a16(4 * n if ids else 0)
     else:
-        want = 64 + a16(4 * ncc) + a16(12 * ncc) + a16(3 * n * xb) + a16(3 * n * vb) + a16(4 * n if ids else 0)
+        want = 64 + a16(4 * ncc) + a16(12 * ncc) + a16(3 * n * xb) + a16(3 * n * vb) + a16(ids * n)
     got = cube.cube_checkpoint_size(cube.make_params(nf, n, x_bytes=xb, v_bytes=vb, id_bytes=ids))
     assert got == want
