@@ -200,11 +200,19 @@ __device__ __forceinline__ float vel_unfix_mean(long long s, unsigned n) {
 // tan(pi (k - 1/2) / M) / s, thr[lim + 1] = +inf, so |d| >= thr[k]  <=>  the
 // nearest integer of (M/pi) atan(|d| s) is >= k (halves away from zero).
 // `est` is any starting guess; the result does not depend on it.
+// The two thresholds around the guess are requested together, so a guess
+// within one code costs one memory round trip.
 __device__ __forceinline__ int nu_from_thresholds(float d, const float* __restrict__ thr, int lim, int est) {
     float a = fabsf(d);
     int k = min(max(est, 0), lim);
-    while (k < lim && a >= thr[k + 1]) ++k;
-    while (k > 0 && a < thr[k]) --k;
+    const float lo = thr[k], hi = thr[k + 1];            // thr[lim + 1] = +inf
+    if (a >= hi) {
+        ++k;
+        while (k < lim && a >= thr[k + 1]) ++k;
+    } else if (a < lo) {
+        --k;
+        while (k > 0 && a < thr[k]) --k;
+    }
     return d < 0.0f ? -k : k;
 }
 

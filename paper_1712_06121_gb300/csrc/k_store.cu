@@ -786,6 +786,7 @@ __global__ void __launch_bounds__(T_BRICK, 4) k_passA(Geo g, StoreDev s, const f
             e[d] = l[d] + shc + 1;
             pv[d] = p2;
         }
+
         const int ei = e[0] + Bh * (e[1] + Bh * e[2]);
         // per-lane shared-memory atomics (measured faster here than warp aggregation)
         atomicAdd(&hist[ei], 1u);
@@ -894,7 +895,8 @@ struct PbParticle {
     float pv[3];
 };
 
-template <int NX, int NV>
+// PID: 4 for 4-byte particle IDs (or none), 0 for the narrow widths of Geo::nid
+template <int NX, int NV, int PID>
 struct PassB {
     Geo g;
     const StoreDev& sn;
@@ -906,8 +908,11 @@ struct PassB {
     int key0, lim;
     float dc, e0, e1;
 
-    // lc: the particle's coarse cell in the brick
-    __device__ __forceinline__ PbParticle move(int lc, const float* svc, const int* cchi, const int* cnu) const {
+    // lc: the particle's coarse cell in the brick; its velocity offsets are
+    // read from the table (1-byte codes) or given in coff (2-byte codes, read
+    // a round ahead)
+    __device__ __forceinline__ PbParticle move(int lc, const float* svc, const int* cchi, const int* cnu,
+                                               const float* coff) const {
         const int Bh = g.Bh;
         const int nbits = 8 * NX, half = 1 << (nbits - 1), bmask = (1 << nbits) - 1;
         const float inv2q = ldexpf(1.0f, -(nbits + 1));
@@ -918,7 +923,7 @@ struct PassB {
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
             const int Q = 2 * (cchi[d] + half) + 1;
-            const float p2 = svc[(d << (3 * g.lB)) + lc] + dec[cnu[d] + lim];
+            const float p2 = svc[(d << (3 * g.lB)) + lc] + (NV == 2 ? coff[d] : dec[cnu[d] + lim]);
             float un;
             const int bin = drift_bin(Q, p2, dc, inv2q, two8n, &un);
             const int sh = max(-1, min(1, bin >> nbits));
@@ -944,7 +949,10 @@ struct PassB {
             nu_n.put(d, pos, NV == 1 ? nu_from_table(dd, thr, stab, key0, lim)
                                      : nu_from_thresholds(dd, thr, lim, nu_estimate(dd, e0, e1)));
         }
-        if (sn.id) store_pid(sn.id, pos, g.nid, cid);
+        if (sn.id) {
+            if (PID == 4) reinterpret_cast<unsigned*>(sn.id)[pos] = cid;
+            else store_pid(sn.id, pos, g.nid, cid);
+        }
     }
 };
 
@@ -973,7 +981,7 @@ __device__ __forceinline__ void passB_stage(const Geo& g, const StoreDev& so, co
     }
 }
 
-template <int NX, int NV, bool BAT>
+template <int NX, int NV, bool BAT, int PID>
 __global__ void __launch_bounds__(PB_WARPS * 32, 5) k_passB(Geo g, StoreDev so, StoreDev sn, CodecDev cur, CodecDev next,
                                                         float dc, const unsigned* __restrict__ ghost,
                                                         const float* __restrict__ vc_new, unsigned* flags,
@@ -1005,7 +1013,7 @@ __global__ void __launch_bounds__(PB_WARPS * 32, 5) k_passB(Geo g, StoreDev so, 
     float* sthr = sdec + (NV == 1 ? 2 * lim + 1 : 0);                       // NV == 1: [lim + 2]
     unsigned char* stab = reinterpret_cast<unsigned char*>(sthr + (NV == 1 ? lim + 2 : 0));   // NV == 1: [VT_N]
     unsigned* wbase = reinterpret_cast<unsigned*>(stab + (NV == 1 ? VT_N : 0));
-    PassB<NX, NV> pb{g, sn, CodeRows<NX>(sn.chi, g.Np), CodeRows<NV>(sn.nu, g.Np), cur.dec, next.thr, stab, 0, lim,
+    PassB<NX, NV, PID> pb{g, sn, CodeRows<NX>(sn.chi, g.Np), CodeRows<NV>(sn.nu, g.Np), cur.dec, next.thr, stab, 0, lim,
                      dc, next.est[0], next.est[1]};
     const CodeRows<NX> chi_o(so.chi, g.Np);
     const CodeRows<NV> nu_o(so.nu, g.Np);
@@ -1047,8 +1055,11 @@ __global__ void __launch_bounds__(PB_WARPS * 32, 5) k_passB(Geo g, StoreDev so, 
                         cchi[d] = chi_o.get(d, i);
                         cnu[d] = nu_o.get_nu(d, i, lim);
                     }
-                    if (sn.id) cid = load_pid(so.id, i, g.nid);
-                    q = pb.move(upper_cell(sm_off, nbc, i), svc, cchi, cnu);
+                    if (sn.id) cid = PID == 4 ? reinterpret_cast<const unsigned*>(so.id)[i] : load_pid(so.id, i, g.nid);
+                    float coff[3];
+#pragma unroll
+                    for (int d = 0; d < 3; ++d) coff[d] = NV == 2 ? pb.dec[cnu[d] + lim] : 0.0f;
+                    q = pb.move(upper_cell(sm_off, nbc, i), svc, cchi, cnu, coff);
                     peers = __match_any_sync(am, q.ei);
                     leader = __ffs(peers) - 1;
                     if (lane == leader) wcnt[warp * H3 + q.ei] = (unsigned)__popc(peers);
@@ -1093,6 +1104,7 @@ __global__ void __launch_bounds__(PB_WARPS * 32, 5) k_passB(Geo g, StoreDev so, 
     float* svn = svc + 3 * nbc;                                             // [3][H3]: v_c* of the halo region
     // the first round's codes and ids first, so their latency overlaps the staging
     int nchi[3] = {0, 0, 0}, nnu[3] = {0, 0, 0};
+    float noff[3] = {0.0f, 0.0f, 0.0f};        // 2-byte codes: the next round's decoded offsets
     unsigned nid = 0;
     if (p0 + lane < p1) {
 #pragma unroll
@@ -1100,7 +1112,11 @@ __global__ void __launch_bounds__(PB_WARPS * 32, 5) k_passB(Geo g, StoreDev so, 
             nchi[d] = chi_o.get(d, p0 + lane);
             nnu[d] = nu_o.get_nu(d, p0 + lane, lim);
         }
-        if (sn.id) nid = load_pid(so.id, p0 + lane, g.nid);
+        if (sn.id)
+            nid = PID == 4 ? reinterpret_cast<const unsigned*>(so.id)[p0 + lane] : load_pid(so.id, p0 + lane, g.nid);
+        if (NV == 2)
+#pragma unroll
+            for (int d = 0; d < 3; ++d) noff[d] = pb.dec[nnu[d] + lim];
     }
     passB_stage(g, so, ghost, vc_new, brick, lane, 32, sm_off, run, svc, svn);
     __syncwarp();
@@ -1110,6 +1126,7 @@ __global__ void __launch_bounds__(PB_WARPS * 32, 5) k_passB(Geo g, StoreDev so, 
         const unsigned am = __ballot_sync(0xffffffffu, act);
         // this round's codes; the next round's are requested now
         const int cchi[3] = {nchi[0], nchi[1], nchi[2]}, cnu[3] = {nnu[0], nnu[1], nnu[2]};
+        const float coff[3] = {noff[0], noff[1], noff[2]};
         const unsigned cid = nid;
         if (i + 32 < p1) {
 #pragma unroll
@@ -1117,10 +1134,11 @@ __global__ void __launch_bounds__(PB_WARPS * 32, 5) k_passB(Geo g, StoreDev so, 
                 nchi[d] = chi_o.get(d, i + 32);
                 nnu[d] = nu_o.get_nu(d, i + 32, lim);
             }
-            if (sn.id) nid = load_pid(so.id, i + 32, g.nid);
+            if (sn.id)
+                nid = PID == 4 ? reinterpret_cast<const unsigned*>(so.id)[i + 32] : load_pid(so.id, i + 32, g.nid);
         }
         if (act) {
-            const PbParticle q = pb.move(upper_cell(sm_off, nbc, i), svc, cchi, cnu);
+            const PbParticle q = pb.move(upper_cell(sm_off, nbc, i), svc, cchi, cnu, coff);
             const unsigned peers = __match_any_sync(am, q.ei);
             const int leader = __ffs(peers) - 1;
             unsigned start = 0;
@@ -1129,6 +1147,9 @@ __global__ void __launch_bounds__(PB_WARPS * 32, 5) k_passB(Geo g, StoreDev so, 
             if (lane == leader) run[q.ei] = start + (unsigned)__popc(peers);
             pb.put(q, svn, start + (unsigned)__popc(peers & ((1u << lane) - 1u)), cid, flags);
         }
+        if (NV == 2 && i + 32 < p1)                // the next round's offsets, its codes having arrived
+#pragma unroll
+            for (int d = 0; d < 3; ++d) noff[d] = pb.dec[nnu[d] + lim];
         __syncwarp();
     }
 }
@@ -1190,12 +1211,15 @@ struct Disp {
         // CTAs for crowded bricks first (at most Np / (PB_BIG + 1) of them exist)
         const int nbig_ctas = (int)std::min<int64_t>(2 * g.nsm, g.Np / (PB_BIG + 1));
         const int grid = nbig_ctas + (g.nbricks + PB_WARPS - 1) / PB_WARPS;
-        if (bt.members > 1 || bt.ms)
-            k_passB<NX, NV, true><<<dim3(grid, bt.members), PB_WARPS * 32, sm, st>>>(g, so, sn, cur, next, dc, ghost,
-                                                                                   vcn, flags, big, nbig_ctas, bt);
-        else
-            k_passB<NX, NV, false><<<grid, PB_WARPS * 32, sm, st>>>(g, so, sn, cur, next, dc, ghost, vcn, flags, big,
-                                                                    nbig_ctas, bt);
+        const bool narrow = g.nid == 1 || g.nid == 2;
+        if (bt.members > 1 || bt.ms) {
+            const dim3 gb(grid, bt.members);
+            if (narrow) k_passB<NX, NV, true, 0><<<gb, PB_WARPS * 32, sm, st>>>(g, so, sn, cur, next, dc, ghost, vcn, flags, big, nbig_ctas, bt);
+            else k_passB<NX, NV, true, 4><<<gb, PB_WARPS * 32, sm, st>>>(g, so, sn, cur, next, dc, ghost, vcn, flags, big, nbig_ctas, bt);
+        } else {
+            if (narrow) k_passB<NX, NV, false, 0><<<grid, PB_WARPS * 32, sm, st>>>(g, so, sn, cur, next, dc, ghost, vcn, flags, big, nbig_ctas, bt);
+            else k_passB<NX, NV, false, 4><<<grid, PB_WARPS * 32, sm, st>>>(g, so, sn, cur, next, dc, ghost, vcn, flags, big, nbig_ctas, bt);
+        }
     }
 };
 
@@ -1208,8 +1232,10 @@ void set_smem_attrs() {
     cudaFuncSetAttribute(k_passA<NX, NV, 16, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
     cudaFuncSetAttribute(k_passA<NX, NV, 0, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
     cudaFuncSetAttribute(k_passA<NX, NV, 16, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
-    cudaFuncSetAttribute(k_passB<NX, NV, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
-    cudaFuncSetAttribute(k_passB<NX, NV, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+    cudaFuncSetAttribute(k_passB<NX, NV, false, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+    cudaFuncSetAttribute(k_passB<NX, NV, true, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+    cudaFuncSetAttribute(k_passB<NX, NV, false, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+    cudaFuncSetAttribute(k_passB<NX, NV, true, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
     cudaFuncSetAttribute(k_deposit<NX, 0, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
     cudaFuncSetAttribute(k_deposit<NX, 16, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
     cudaFuncSetAttribute(k_deposit<NX, 0, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
