@@ -73,21 +73,35 @@ double integrate(Fn f, double a0, double a1, int panels = 16) {
     return s * 0.5 * h;
 }
 
+// Panels of the 64-point rule for int_{a0}^{a1} of a function analytic away
+// from a = 0: each panel no longer than the distance of the interval from 0,
+// so that the rule's error (below rho^-128 with rho >= 2 + sqrt 3 for
+// singularities at least a panel's length away) is far under FP64 rounding.
+// A time step (a1 - a0 <= a0) takes one panel.
+int panels_for(double a0, double a1) {
+    const double lo = std::min(a0, a1), len = std::fabs(a1 - a0);
+    if (!(lo > 0.0)) return 16;
+    return (int)std::min(16.0, std::max(1.0, std::ceil(len / lo)));
+}
+
 struct Cosmo {
     double om, ol;
+    // the last two growth values g(a) (a step's g(a_to) is the next step's g(a_from))
+    mutable double memo_a[2] = {-1.0, -1.0}, memo_g[2] = {0.0, 0.0};
+    mutable int memo_next = 0;
     bool eds() const { return om == 1.0 && ol == 0.0; }
     double E(double a) const { return std::sqrt(om / (a * a * a) + (1.0 - om - ol) / (a * a) + ol); }
     // int da / (a^2 E): kick factor
     double kick(double a0, double a1) const {
         if (a1 == a0) return 0.0;
         if (eds()) return 2.0 * (std::sqrt(a1) - std::sqrt(a0));
-        return integrate([&](double a) { return 1.0 / (a * a * E(a)); }, a0, a1);
+        return integrate([&](double a) { return 1.0 / (a * a * E(a)); }, a0, a1, panels_for(a0, a1));
     }
     // int da / (a^3 E): drift factor
     double drift(double a0, double a1) const {
         if (a1 == a0) return 0.0;
         if (eds()) return 2.0 * (1.0 / std::sqrt(a0) - 1.0 / std::sqrt(a1));
-        return integrate([&](double a) { return 1.0 / (a * a * a * E(a)); }, a0, a1);
+        return integrate([&](double a) { return 1.0 / (a * a * a * E(a)); }, a0, a1, panels_for(a0, a1));
     }
     // Heath integral int_0^a dx / (x E(x))^3, with x = t^2 to smooth the origin
     double heath(double a) const {
@@ -97,17 +111,57 @@ struct Cosmo {
             return 2.0 * t / (xe * xe * xe);
         }, 0.0, std::sqrt(a));
     }
-    double D(double a) const { return 2.5 * om * E(a) * heath(a); }   // unnormalised
-    double f(double a) const {
-        double e = E(a), ok = 1.0 - om - ol;
-        return (-1.5 * om / (a * a * a) - ok / (a * a)) / (e * e) + 1.0 / (a * a * e * e * e * heath(a));
-    }
-    // momentum growth g = a^2 E f D (the normalisation of D cancels in ratios)
+    // momentum growth g = a^2 E f D with D = (5/2) Om E heath (unnormalised:
+    // the normalisation cancels in ratios) and f = d ln D / d ln a
     double g(double a) const {
         if (eds()) return a * std::sqrt(a);
-        return a * a * E(a) * f(a) * D(a);
+        for (int i = 0; i < 2; ++i)
+            if (memo_a[i] == a) return memo_g[i];
+        const double h = heath(a), e = E(a), ok = 1.0 - om - ol;
+        const double D = 2.5 * om * e * h;
+        const double f = (-1.5 * om / (a * a * a) - ok / (a * a)) / (e * e) + 1.0 / (a * a * e * e * e * h);
+        const double v = a * a * e * f * D;
+        memo_a[memo_next] = a;
+        memo_g[memo_next] = v;
+        memo_next ^= 1;
+        return v;
     }
 };
+
+// The largest a in (a0, hi] with h(a) <= limit, for h increasing with
+// h(a0) <= limit < h(hi) and derivative dh: Newton's method on h = limit
+// from the tangent at a0 (below the root when h is concave, as the drift
+// integral is), kept inside the bracket (bisection where a step leaves it),
+// then the root estimate stepped down by a few ulps until it meets the limit.
+template <class H, class DH>
+double largest_within(H h, DH dh, double a0, double hi, double limit) {
+    double lo = a0, up = hi, x = hi;
+    const double d0 = dh(a0);
+    if (d0 > 0.0) {
+        const double t = a0 + (limit - h(a0)) / d0;
+        if (t > a0 && t < hi) x = t;
+    }
+    for (int it = 0; it < 100; ++it) {
+        const double hx = h(x);
+        if (hx <= limit) lo = std::max(lo, x);
+        else up = std::min(up, x);
+        const double d = dh(x);
+        const double step = d > 0.0 ? (hx - limit) / d : 0.0;
+        if (d > 0.0 && std::fabs(step) <= 1e-15 * x) break;       // x is the root to rounding
+        if (up - lo <= 1e-15 * up) {
+            x = lo;
+            break;
+        }
+        double nx = d > 0.0 ? x - step : 0.5 * (lo + up);
+        if (!(nx > lo && nx < up)) nx = 0.5 * (lo + up);
+        x = nx;
+    }
+    for (int k = 0; k < 64 && x > lo; ++k) {
+        if (h(x) <= limit) return x;
+        x = std::max(lo, x - std::ldexp(x, -50) * (k + 1));
+    }
+    return lo;
+}
 
 bool is_device_ptr(const void* p) {
     if (!p) return false;
@@ -834,14 +888,10 @@ cube_status cube_max_speed(cube_ctx* c, double* p_max) {
 static double epoch_limit(const cube_ctx* c, double p, double a_max, double cells) {
     const double limit = cells * c->g.R;                 // fine cells
     const double a0 = c->a;
-    if (p * c->cosmo.drift(a0, a_max) <= limit) return a_max;
-    double lo = a0, hi = a_max;
-    for (int it = 0; it < 100 && hi - lo > 1e-15 * hi; ++it) {
-        const double mid = 0.5 * (lo + hi);
-        if (p * c->cosmo.drift(a0, mid) <= limit) lo = mid;
-        else hi = mid;
-    }
-    return lo;
+    const Cosmo& cm = c->cosmo;
+    if (p * cm.drift(a0, a_max) <= limit) return a_max;
+    return largest_within([&](double a) { return p * cm.drift(a0, a); },
+                          [&](double a) { return p / (a * a * a * cm.E(a)); }, a0, a_max, limit);
 }
 
 cube_status cube_max_force(cube_ctx* c, double* f_max) {
@@ -885,13 +935,14 @@ static cube_status limited_epoch(const Cosmo& cosmo, int R, double a0, double a_
     if (drift(hi) <= limit) {
         *a_to = hi;
     } else {
-        double lo = a0;
-        for (int it = 0; it < 100 && hi - lo > 1e-15 * hi; ++it) {
-            const double mid = 0.5 * (lo + hi);
-            if (drift(mid) <= limit) lo = mid;
-            else hi = mid;
-        }
-        *a_to = lo;
+        // d/da_to of the drift: the kick's growth times the drift factor, plus
+        // the kicked momentum times the drift integrand
+        auto slope = [&](double at) {
+            const double am = 0.5 * (a0 + at);
+            return 0.5 * f / (am * am * cosmo.E(am)) * cosmo.drift(a0, at) +
+                   (p + f * cosmo.kick(a_p, am)) / (at * at * at * cosmo.E(at));
+        };
+        *a_to = largest_within(drift, slope, a0, hi, limit);
         why = 1;
     }
     if (binding) *binding = why;
@@ -1270,8 +1321,9 @@ struct cube_batch {
     cudaStream_t st = nullptr;
     CUtensorMap map{};                  // 4-D map (x, y, z, member) of the members' ghosted Phi
     bool tma = false;
-    MemberStep* ms_dev = nullptr;       // [members]
+    MemberStep* ms_dev = nullptr;       // [members]: the stepped members' table, one entry per grid slot
     MemberStep* ms_host = nullptr;      // pinned [members]
+    std::vector<int> slots;             // the member of each slot of the last step
     unsigned* vmax_host = nullptr;      // pinned [members]: largest |p| per member (float bits)
     cudaEvent_t ms_copied = nullptr;    // the last table upload has been read
     cudaEvent_t vmax_ready = nullptr;   // the maxima read-back has arrived
@@ -1356,11 +1408,21 @@ cube_status cube_batch_member(cube_batch* b, int32_t i, cube_ctx** out) {
 // apart), enqueued, with an event marking its arrival
 static cube_status batch_vmax_enqueue(cube_batch* b) {
     const int K = (int)b->m.size();
+    bool same = true;
     for (int i = 0; i < K; ++i) {
-        cube_ctx* c = b->m[i];
-        if (!c->encoded) return fail(CUBE_E_STATE, "a member has no store: call cube_encode first");
-        launch_max_speed(c->g, c->store(c->cur), c->codec[c->cur].dec, c->vmax, b->st);
-        c->launches += 1;
+        if (!b->m[i]->encoded) return fail(CUBE_E_STATE, "a member has no store: call cube_encode first");
+        same = same && b->m[i]->cur == b->m[0]->cur;
+    }
+    if (same) {                                  // one launch over every member's store
+        cube_ctx* c = b->m[0];
+        launch_max_speed(c->g, c->store(c->cur), c->codec[c->cur].dec, c->vmax, b->st,
+                         Batch{K, b->stride, nullptr, nullptr});
+        b->launches += 2;
+    } else {
+        for (cube_ctx* c : b->m) {
+            launch_max_speed(c->g, c->store(c->cur), c->codec[c->cur].dec, c->vmax, b->st);
+            c->launches += 1;
+        }
     }
     CK(cudaMemcpy2DAsync(b->vmax_host, sizeof(unsigned), b->m[0]->vmax, b->stride, sizeof(unsigned), K,
                          cudaMemcpyDeviceToHost, b->st));
@@ -1432,23 +1494,26 @@ cube_status cube_batch_step(cube_batch* b, const double* a_from, const double* a
     }
     if (!nact) return CUBE_OK;
     CK(cudaEventSynchronize(b->ms_copied));                         // the previous table has been read
+    // one grid slot per stepped member: members that sit the step out get no CTAs
+    b->slots.clear();
     for (int i = 0; i < K; ++i) {
-        cube_ctx* c = b->m[i];
-        MemberStep& ms = b->ms_host[i];
-        ms = MemberStep{0.0f, 0.0f, 1.0, 0, 0};
         if (!(a_to[i] > a_from[i])) continue;
+        cube_ctx* c = b->m[i];
+        MemberStep& ms = b->ms_host[b->slots.size()];
         const double a_mid = 0.5 * (a_from[i] + a_to[i]);
         ms.kick = (float)c->cosmo.kick(c->a_p, a_mid);
         ms.dc = (float)(c->cosmo.drift(a_from[i], a_to[i]) / c->g.R);
         ms.ratio = c->cosmo.g(a_to[i]) / c->cosmo.g(a_from[i]);
         ms.active = 1;
+        ms.member = i;
+        b->slots.push_back(i);
     }
-    CK(cudaMemcpyAsync(b->ms_dev, b->ms_host, sizeof(MemberStep) * K, cudaMemcpyHostToDevice, b->st));
+    CK(cudaMemcpyAsync(b->ms_dev, b->ms_host, sizeof(MemberStep) * nact, cudaMemcpyHostToDevice, b->st));
     CK(cudaEventRecord(b->ms_copied, b->st));
     cube_ctx* c0 = b->m[0];
     const Geo& g = c0->g;
     const int k = cur, kn = 1 - cur;
-    const Batch bt{K, b->stride, b->ms_dev};
+    const Batch bt{nact, b->stride, b->ms_dev, b->slots.data()};
     launch_batch_clear(g, c0->vsum, c0->maxmig, b->st, bt);
     launch_deposit(g, c0->store(k), c0->mesh, particle_mass(g) * std::ldexp(1.0, -3 * g.sbits), b->st, bt);
     fft_x_r2c(c0->fft, c0->mesh, g.S, b->st, bt);
@@ -1470,10 +1535,7 @@ cube_status cube_batch_step(cube_batch* b, const double* a_from, const double* a
     CK(cudaGetLastError());
     for (int i = 0; i < K; ++i) {
         cube_ctx* c = b->m[i];
-        if (!(a_to[i] > a_from[i])) {
-            if (g.N > 256) c->phig_valid = false;   // large meshes' sweeps run member by member, over it too
-            continue;
-        }
+        if (!(a_to[i] > a_from[i])) continue;
         c->cur = kn;
         c->a_p = 0.5 * (a_from[i] + a_to[i]);
         c->a = a_to[i];

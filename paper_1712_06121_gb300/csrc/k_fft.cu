@@ -509,10 +509,9 @@ __device__ __forceinline__ void xpass_store(const float2* buf, const float2* tw,
 template <int N, bool BAT>
 __global__ void __launch_bounds__(XFFT_T) k_fft_x_r2c(float* mesh, int S, const float2* __restrict__ tw, Batch bt) {
     extern __shared__ float2 fsm[];
-    if constexpr (BAT) {                                     // member blockIdx.y of a batch
-        const int m = blockIdx.y;
-        if (bt.ms && !bt.ms[m].active) return;
-        mesh = moved(mesh, m * bt.stride);
+    if constexpr (BAT) {                                     // slot blockIdx.y of a batch
+        if (bt.ms && !bt.ms[blockIdx.y].active) return;
+        mesh = moved(mesh, slot_member(bt, blockIdx.y) * bt.stride);
     }
     constexpr int h = N / 2;
     float2* stw = fsm;               // [N]
@@ -549,9 +548,9 @@ template <int N, bool BAT>
 __global__ void __launch_bounds__(XFFT_T) k_fft_x_c2r(const float* mesh, int S, const float2* __restrict__ tw,
                                                      float* __restrict__ phig, Batch bt) {
     extern __shared__ float2 fsm[];
-    if constexpr (BAT) {                                     // member blockIdx.y of a batch
-        const int m = blockIdx.y;
-        if (bt.ms && !bt.ms[m].active) return;
+    if constexpr (BAT) {                                     // slot blockIdx.y of a batch
+        if (bt.ms && !bt.ms[blockIdx.y].active) return;
+        const int m = slot_member(bt, blockIdx.y);
         mesh = moved(mesh, m * bt.stride);
         phig = moved(phig, m * bt.stride);
     }
@@ -581,10 +580,9 @@ template <int N, bool INV, bool BAT>
 __global__ void __launch_bounds__(FFT_T, N <= 512 ? 2 : 1) k_fft_y(float* mesh, int S, const float2* __restrict__ tw,
                                                                     Batch bt) {
     extern __shared__ float2 fsm[];
-    if constexpr (BAT) {                                     // member blockIdx.z of a batch
-        const int m = blockIdx.z;
-        if (bt.ms && !bt.ms[m].active) return;
-        mesh = moved(mesh, m * bt.stride);
+    if constexpr (BAT) {                                     // slot blockIdx.z of a batch
+        if (bt.ms && !bt.ms[blockIdx.z].active) return;
+        mesh = moved(mesh, slot_member(bt, blockIdx.z) * bt.stride);
     }
     constexpr int h = N / 2;
     float2* stw = fsm;
@@ -640,10 +638,9 @@ __global__ void __launch_bounds__(FFT_T, N <= 512 ? 2 : 1) k_fft_z(float* mesh, 
                                                  const float* __restrict__ k2, const float* __restrict__ wdec, float g0,
                                                  Batch bt) {
     extern __shared__ float2 fsm[];
-    if constexpr (BAT) {                                     // member blockIdx.z of a batch
-        const int m = blockIdx.z;
-        if (bt.ms && !bt.ms[m].active) return;
-        mesh = moved(mesh, m * bt.stride);
+    if constexpr (BAT) {                                     // slot blockIdx.z of a batch
+        if (bt.ms && !bt.ms[blockIdx.z].active) return;
+        mesh = moved(mesh, slot_member(bt, blockIdx.z) * bt.stride);
     }
     constexpr int ncol = N / 2 + 1;
     float2* stw = fsm;
@@ -791,11 +788,10 @@ struct Sweeps {
     }
     // a batch (several members or a per-member table) takes the instances with a member dimension
     static bool batched(const Batch& bt) { return bt.members > 1 || bt.ms != nullptr; }
-    // member by member: every member, stepped or not (a member that sits the
-    // step out only has its scratch mesh and potential rewritten)
+    // slot by slot from the host: the members the launch lists
     template <class Fn>
     static void per_member(const Batch& bt, Fn fn) {
-        for (int m = 0; m < bt.members; ++m) fn((size_t)m * bt.stride);
+        for (int i = 0; i < bt.members; ++i) fn((size_t)slot_member(bt, i) * bt.stride);
     }
     static void x_r2c(const FftPlan& p, float* mesh, int S, cudaStream_t st, const Batch& bt) {
         attrs();

@@ -56,8 +56,8 @@ __device__ __forceinline__ void load4(const unsigned* __restrict__ in, int64_t b
 __global__ void k_scan_reduce(const unsigned* __restrict__ in, int64_t n, unsigned* __restrict__ bsum, bool vec,
                               Batch bt) {
     __shared__ unsigned sw[32];
-    const int m = blockIdx.y;
-    if (bt.ms && !bt.ms[m].active) return;
+    if (bt.ms && !bt.ms[blockIdx.y].active) return;
+    const int m = slot_member(bt, blockIdx.y);
     in = moved(in, m * bt.stride);
     bsum = moved(bsum, m * bt.stride);
     unsigned v[SCAN_ITEMS];
@@ -71,8 +71,8 @@ __global__ void k_scan_reduce(const unsigned* __restrict__ in, int64_t n, unsign
 // exclusive scan of the block sums in place (single block, any count)
 __global__ void k_scan_bsums(unsigned* bsum, int nb, unsigned* total_out, Batch bt) {
     __shared__ unsigned sw[32];
-    const int m = blockIdx.x;
-    if (bt.ms && !bt.ms[m].active) return;
+    if (bt.ms && !bt.ms[blockIdx.x].active) return;
+    const int m = slot_member(bt, blockIdx.x);
     bsum = moved(bsum, m * bt.stride);
     total_out = moved(total_out, m * bt.stride);
     unsigned carry = 0;
@@ -90,8 +90,8 @@ __global__ void k_scan_bsums(unsigned* bsum, int nb, unsigned* total_out, Batch 
 __global__ void k_scan_down(const unsigned* in, int64_t n, const unsigned* __restrict__ bsum, unsigned* out,
                             bool vec, Batch bt) {
     __shared__ unsigned sw[32];
-    const int m = blockIdx.y;
-    if (bt.ms && !bt.ms[m].active) return;
+    if (bt.ms && !bt.ms[blockIdx.y].active) return;
+    const int m = slot_member(bt, blockIdx.y);
     in = moved(in, m * bt.stride);
     bsum = moved(bsum, m * bt.stride);
     out = moved(out, m * bt.stride);
@@ -115,8 +115,8 @@ __global__ void k_scan_down(const unsigned* in, int64_t n, const unsigned* __res
 }
 
 __global__ void k_write_total(unsigned* out, int64_t n, const unsigned* total, Batch bt) {
-    const int m = blockIdx.x;
-    if (bt.ms && !bt.ms[m].active) return;
+    if (bt.ms && !bt.ms[blockIdx.x].active) return;
+    const int m = slot_member(bt, blockIdx.x);
     moved(out, m * bt.stride)[n] = *moved(total, m * bt.stride);
 }
 

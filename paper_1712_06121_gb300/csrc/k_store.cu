@@ -147,11 +147,12 @@ __global__ void k_encode_sigma(Geo g, const float* __restrict__ vel, const unsig
 __global__ void k_sigma_finalize(const float* __restrict__ part, int nparts, double count, double ratio,
                                  double fixed, double* sigma_out, Batch bt) {
     __shared__ double sh[32];
-    const int m = blockIdx.x;                                // member of a batch
+    const int slot = blockIdx.x;                             // slot of a batch
     if (bt.ms) {
-        if (!bt.ms[m].active) return;
-        ratio = bt.ms[m].ratio;
+        if (!bt.ms[slot].active) return;
+        ratio = bt.ms[slot].ratio;
     }
+    const int m = slot_member(bt, slot);
     part = moved(part, m * bt.stride);
     sigma_out = moved(sigma_out, m * bt.stride);
     // strided FP32 sums per thread (coalesced loads, fixed order), then a fixed tree in FP64
@@ -211,9 +212,9 @@ __device__ void codec_tables_body(int lim, const double* __restrict__ tanv, cons
 __global__ void k_codec_tables(int lim, const double* __restrict__ tanv, const double* __restrict__ tanh_,
                                const double* __restrict__ sigma, float* __restrict__ dec, float* __restrict__ thr,
                                float* __restrict__ est, unsigned char* __restrict__ vtab, Batch bt) {
-    const int m = blockIdx.y;                                // member of a batch
-    if (bt.ms && !bt.ms[m].active) return;
-    const size_t o = m * bt.stride;
+    const int slot = blockIdx.y;                             // slot of a batch
+    if (bt.ms && !bt.ms[slot].active) return;
+    const size_t o = slot_member(bt, slot) * bt.stride;
     codec_tables_body(lim, moved(tanv, o), moved(tanh_, o), *moved(sigma, o), moved(dec, o), moved(thr, o),
                       moved(est, o), moved(vtab, o));
 }
@@ -287,8 +288,14 @@ __global__ void __launch_bounds__(T_BRICK) k_decode(Geo g, StoreDev s, const flo
 // preserving as unsigned)
 template <int NV>
 __global__ void __launch_bounds__(T_BRICK) k_max_speed(Geo g, StoreDev s, const float* __restrict__ dec,
-                                                       unsigned* __restrict__ vmax_bits) {
+                                                       unsigned* __restrict__ vmax_bits, Batch bt) {
     extern __shared__ unsigned sm_off[];
+    {                                                        // member of slot blockIdx.y of a batch
+        const size_t o = slot_member(bt, blockIdx.y) * bt.stride;
+        s = moved(s, o);
+        dec = moved(dec, o);
+        vmax_bits = moved(vmax_bits, o);
+    }
     const int nbc = g.B * g.B * g.B;
     const int L0 = blockIdx.x * nbc;
     for (int c = threadIdx.x; c <= nbc; c += blockDim.x) sm_off[c] = s.offsets[L0 + c];
@@ -348,8 +355,9 @@ __global__ void __launch_bounds__(T_BRICK) k_deposit(Geo g, StoreDev s, float* _
     __shared__ unsigned wsum[T_BRICK / 32];
     int bx, by, bz, m;
     grid_brick<BAT>(g, &bx, &by, &bz, &m);
-    if constexpr (BAT) {                                     // member m of a batch
+    if constexpr (BAT) {                                     // slot m of a batch
         if (bt.ms && !bt.ms[m].active) return;
+        m = slot_member(bt, m);
         s = moved(s, m * bt.stride);
         mesh = moved(mesh, m * bt.stride);
     }
@@ -570,12 +578,13 @@ __global__ void __launch_bounds__(T_BRICK, 4) k_passA(Geo g, StoreDev s, const f
     const int lim = g.nulim;
     int bx, by, bz, m;
     const int brick = grid_brick<BAT>(g, &bx, &by, &bz, &m);
-    if constexpr (BAT) {                                     // member m of a batch
+    if constexpr (BAT) {                                     // slot m of a batch
         if (bt.ms) {
             if (!bt.ms[m].active) return;
             kick = bt.ms[m].kick;
             dc = bt.ms[m].dc;
         }
+        m = slot_member(bt, m);
         const size_t o = m * bt.stride;
         s = moved(s, o);
         phig = moved(phig, o);
@@ -848,9 +857,9 @@ template <bool BAT>
 __global__ void k_cells(Geo g, StepScratch w, unsigned* __restrict__ off_new, float* __restrict__ vc_new, Batch bt) {
     const int L = blockIdx.x * blockDim.x + threadIdx.x;
     if (L >= g.Ncc) return;
-    if constexpr (BAT) {                                     // member blockIdx.y of a batch
-        const int m = blockIdx.y;
-        if (bt.ms && !bt.ms[m].active) return;
+    if constexpr (BAT) {                                     // slot blockIdx.y of a batch
+        if (bt.ms && !bt.ms[blockIdx.y].active) return;
+        const int m = slot_member(bt, blockIdx.y);
         w = moved(w, m * bt.stride);
         off_new = moved(off_new, m * bt.stride);
         vc_new = moved(vc_new, m * bt.stride);
@@ -990,13 +999,13 @@ __global__ void __launch_bounds__(PB_WARPS * 32, 5) k_passB(Geo g, StoreDev so, 
     const int nbc = g.B * g.B * g.B, H3 = g.Bh * g.Bh * g.Bh;
     const int lim = g.nulim;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if constexpr (BAT) {                                     // member blockIdx.y of a batch
-        const int m = blockIdx.y;
+    if constexpr (BAT) {                                     // slot blockIdx.y of a batch
+        const int slot = blockIdx.y;
         if (bt.ms) {
-            if (!bt.ms[m].active) return;
-            dc = bt.ms[m].dc;
+            if (!bt.ms[slot].active) return;
+            dc = bt.ms[slot].dc;
         }
-        const size_t o = m * bt.stride;
+        const size_t o = slot_member(bt, slot) * bt.stride;
         so = moved(so, o);
         sn = moved(sn, o);
         cur = moved(cur, o);
@@ -1243,11 +1252,16 @@ void set_smem_attrs() {
     done = true;
 }
 
+// one word of every listed member of a batch set to zero
+__global__ void k_zero_slot_words(unsigned* p, Batch bt) {
+    for (int i = threadIdx.x; i < bt.members; i += blockDim.x) moved(p, slot_member(bt, i) * bt.stride)[0] = 0u;
+}
+
 // the step's cleared scratch of every stepped member of a batch: the
 // fixed-point momentum sums [3][Ncc] and the migration / crowded-brick words
 __global__ void k_batch_clear(int64_t n64, long long* __restrict__ vsum, int* __restrict__ mig, Batch bt) {
-    const int m = blockIdx.y;
-    if (bt.ms && !bt.ms[m].active) return;
+    if (bt.ms && !bt.ms[blockIdx.y].active) return;
+    const int m = slot_member(bt, blockIdx.y);
     vsum = moved(vsum, m * bt.stride);
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n64; t += (int64_t)gridDim.x * blockDim.x)
         vsum[t] = 0;
@@ -1305,11 +1319,14 @@ void launch_encode_scatter(const Geo& g, const float* pos, const float* vel, con
     else k_encode_scatter<2, 2><<<nb, 256, 0, st>>>(g, pos, vel, id_in, key_sorted, perm, vc, c.thr, c.est, s);
 }
 
-void launch_max_speed(const Geo& g, const StoreDev& s, const float* dec, unsigned* vmax_bits, cudaStream_t st) {
+void launch_max_speed(const Geo& g, const StoreDev& s, const float* dec, unsigned* vmax_bits, cudaStream_t st,
+                      const Batch& bt) {
     size_t sm = (size_t)(g.B * g.B * g.B + 1) * sizeof(unsigned);
-    cudaMemsetAsync(vmax_bits, 0, sizeof(unsigned), st);
-    if (g.nnu == 1) k_max_speed<1><<<g.nbricks, T_BRICK, sm, st>>>(g, s, dec, vmax_bits);
-    else k_max_speed<2><<<g.nbricks, T_BRICK, sm, st>>>(g, s, dec, vmax_bits);
+    if (bt.members == 1 && !bt.ms) cudaMemsetAsync(vmax_bits, 0, sizeof(unsigned), st);
+    else k_zero_slot_words<<<1, 256, 0, st>>>(vmax_bits, bt);
+    const dim3 grid(g.nbricks, bt.members);
+    if (g.nnu == 1) k_max_speed<1><<<grid, T_BRICK, sm, st>>>(g, s, dec, vmax_bits, bt);
+    else k_max_speed<2><<<grid, T_BRICK, sm, st>>>(g, s, dec, vmax_bits, bt);
 }
 
 void launch_decode(const Geo& g, const StoreDev& s, const float* dec, float* pos, float* vel, unsigned* id,

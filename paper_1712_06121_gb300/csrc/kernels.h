@@ -54,14 +54,27 @@ __device__ __forceinline__ int stable_round_rank(int digit, bool active, unsigne
 struct MemberStep {
     float kick, dc;     // the step's kick factor and drift per coarse cell
     double ratio;       // momentum growth ratio of the codec-scale update
-    int active;         // 0: the member is not stepped (its kernels return at once)
-    int pad;
+    int active;         // 0: the slot steps nothing (its kernels return at once)
+    int member;         // the member this grid slot steps
 };
+// A launch's grid has one slot per listed member: with a per-member table,
+// slot i steps member ms[i].member (a batch step lists only the members it
+// moves, so members that sit it out cost no CTAs); without one, slot i is
+// member i.  host_members mirrors ms[i].member for launches issued member by
+// member from the host (null: slot i is member i).
 struct Batch {
-    int members;
+    int members;                 // slots of the launch
     size_t stride;               // bytes between consecutive members' buffers
     const MemberStep* ms;        // [members] (device) or null
+    const int* host_members;     // [members] (host) or null
 };
+__host__ __device__ __forceinline__ int slot_member(const Batch& bt, int slot) {
+#ifdef __CUDA_ARCH__
+    return bt.ms ? bt.ms[slot].member : slot;
+#else
+    return bt.host_members ? bt.host_members[slot] : slot;
+#endif
+}
 template <class T>
 __host__ __device__ __forceinline__ T* moved(T* p, size_t off) {
     return p ? reinterpret_cast<T*>(reinterpret_cast<char*>(const_cast<typename std::remove_const<T>::type*>(p)) + off)
@@ -74,7 +87,7 @@ void set_last_error(const std::string& msg);     // message for cube_last_error(
 // ------------------------------------------------------------ k_scan.cu
 int scan_tmp_words(int64_t n);
 void exclusive_scan(const unsigned* in, unsigned* out, int64_t n, unsigned* tmp, cudaStream_t st,
-                    const Batch& bt = Batch{1, 0, nullptr});
+                    const Batch& bt = Batch{1, 0, nullptr, nullptr});
 // out2[0] = 64-bit sum, out2[1] = maximum of n counts
 void count_totals(const unsigned* counts, int64_t n, unsigned long long* out2, cudaStream_t st);
 int64_t radix_tmp_words(int64_t n);
@@ -130,7 +143,7 @@ __host__ __device__ __forceinline__ StepScratch moved(const StepScratch& w, size
                        moved(w.flags, off), moved(w.maxmig, off), moved(w.big, off)};
 }
 // a batch of one: a single context's launch
-constexpr Batch kSingle{1, 0, nullptr};
+constexpr Batch kSingle{1, 0, nullptr, nullptr};
 
 void launch_encode_keys(const Geo& g, const float* pos, const float* vel, unsigned* key, unsigned* val,
                         unsigned* counts, long long* vsum, unsigned* flags, cudaStream_t st);
@@ -139,28 +152,28 @@ int encode_sigma_blocks(const Geo& g);
 void launch_encode_sigma(const Geo& g, const float* vel, const unsigned* key_sorted_or_raw, const float* vc,
                          float* part, cudaStream_t st);
 void launch_sigma_finalize(const float* part, int nparts, double count, double ratio, double fixed,
-                           double* sigma_out, cudaStream_t st, const Batch& bt = Batch{1, 0, nullptr});
+                           double* sigma_out, cudaStream_t st, const Batch& bt = Batch{1, 0, nullptr, nullptr});
 void launch_codec_tables(int nulim, const double* tanv, const double* tanh, const CodecDev& c, cudaStream_t st,
-                         const Batch& bt = Batch{1, 0, nullptr});
+                         const Batch& bt = Batch{1, 0, nullptr, nullptr});
 void launch_encode_scatter(const Geo& g, const float* pos, const float* vel, const unsigned* id_in,
                            const unsigned* key_sorted, const unsigned* perm, const float* vc, const CodecDev& c,
                            StoreDev s, cudaStream_t st);
 void launch_decode(const Geo& g, const StoreDev& s, const float* dec, float* pos, float* vel, unsigned* id,
                    cudaStream_t st);
 void launch_deposit(const Geo& g, const StoreDev& s, float* mesh, double scale, cudaStream_t st,
-                    const Batch& bt = Batch{1, 0, nullptr});
+                    const Batch& bt = Batch{1, 0, nullptr, nullptr});
 // phig: ghosted Phi; tmap: TMA map of phig with the brick's tile as its box, or NULL (cp.async loads)
 // (tmap: a 4-D map over (x, y, z, member) of the members' ghosted Phi)
 void launch_passA(const Geo& g, const StoreDev& s, const float* phig, const CUtensorMap* tmap, const CodecDev& cur,
                   float kick, float dc, const StepScratch& w, const DriftDebug& dbg, cudaStream_t st,
-                  const Batch& bt = Batch{1, 0, nullptr});
+                  const Batch& bt = Batch{1, 0, nullptr, nullptr});
 // a batch step's cleared scratch (momentum sums, migration words) of its stepped members
 void launch_batch_clear(const Geo& g, long long* vsum, int* maxmig, cudaStream_t st, const Batch& bt);
 void launch_cells(const Geo& g, const StepScratch& w, unsigned* off_new, float* vc_new, cudaStream_t st,
-                  const Batch& bt = Batch{1, 0, nullptr});
+                  const Batch& bt = Batch{1, 0, nullptr, nullptr});
 void launch_passB(const Geo& g, const StoreDev& s_old, const StoreDev& s_new, const CodecDev& cur,
                   const CodecDev& next, float dc, const StepScratch& w, cudaStream_t st,
-                  const Batch& bt = Batch{1, 0, nullptr});
+                  const Batch& bt = Batch{1, 0, nullptr, nullptr});
 // sums over the current store: out[0..2] momentum of the decoded particles in
 // 2^-24 fixed point, out[3] the particle count (sum of the cell counts)
 void launch_store_sums(const Geo& g, const StoreDev& s, const float* dec, long long* out4, cudaStream_t st);
@@ -174,7 +187,9 @@ void launch_raw_kick_drift(const Geo& g, float* P, float* V, const float* phi, f
 void launch_raw_momentum(const Geo& g, const float* V, long long* out3, cudaStream_t st);
 void launch_iota(unsigned* out, int64_t n, cudaStream_t st);
 void launch_raw_max_speed(const Geo& g, const float* V, unsigned* vmax_bits, cudaStream_t st);
-void launch_max_speed(const Geo& g, const StoreDev& s, const float* dec, unsigned* vmax_bits, cudaStream_t st);
+// largest |p| of the store (float bits), of every listed member of a batch
+void launch_max_speed(const Geo& g, const StoreDev& s, const float* dec, unsigned* vmax_bits, cudaStream_t st,
+                      const Batch& bt = Batch{1, 0, nullptr, nullptr});
 
 // ------------------------------------------------------------ k_fft.cu
 struct FftPlan {
@@ -187,13 +202,13 @@ struct FftPlan {
 
 bool fft_size_supported(int N);                                                    // compiled mesh sizes
 void fft_x_r2c(const FftPlan& p, float* mesh, int S, cudaStream_t st,
-               const Batch& bt = Batch{1, 0, nullptr});                                      // rows: r2c
+               const Batch& bt = Batch{1, 0, nullptr, nullptr});                                      // rows: r2c
 void fft_y(const FftPlan& p, float* mesh, int S, bool inverse, cudaStream_t st,
-           const Batch& bt = Batch{1, 0, nullptr});                                          // y columns
+           const Batch& bt = Batch{1, 0, nullptr, nullptr});                                          // y columns
 void fft_z(const FftPlan& p, float* mesh, int S, float g0, bool green, cudaStream_t st,
-           const Batch& bt = Batch{1, 0, nullptr});                                          // z (+ Green, inverse)
+           const Batch& bt = Batch{1, 0, nullptr, nullptr});                                          // z (+ Green, inverse)
 void fft_x_c2r(const FftPlan& p, float* mesh, int S, float* phig, cudaStream_t st,
-               const Batch& bt = Batch{1, 0, nullptr});                                      // rows: c2r into ghosted Phi
+               const Batch& bt = Batch{1, 0, nullptr, nullptr});                                      // rows: c2r into ghosted Phi
 int pk_blocks(int N);
 void launch_pk_bin(const FftPlan& p, const float* mesh, int S, int nbins, double pfac, double kfund,
                    double* part, cudaStream_t st);
