@@ -411,6 +411,35 @@ __device__ __forceinline__ unsigned same_value_lanes(unsigned active, int v) {
 // 64-bit add into shared memory from 32-bit atomics: the low word's
 // wrap-arounds are carried into the high word, so the final value is the
 // exact sum mod 2^64 whatever the order.  lohi = {low word, high word}.
+// The block's largest v into *dst with one atomic (every thread of the block
+// calls it; blockDim.x a multiple of 32).
+__device__ __forceinline__ void block_max_to(unsigned v, unsigned* dst) {
+    __shared__ unsigned wmax[32];
+    v = __reduce_max_sync(0xffffffffu, v);
+    if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        unsigned m = threadIdx.x < (blockDim.x >> 5) ? wmax[threadIdx.x] : 0u;
+        m = __reduce_max_sync(0xffffffffu, m);
+        if (threadIdx.x == 0 && m) atomicMax(dst, m);
+    }
+}
+
+// The block's sum of v into *dst with one atomic (integer: exact in any order)
+__device__ __forceinline__ void block_sum_to(long long v, long long* dst) {
+    __shared__ long long wsum[32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        long long t = 0;
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += wsum[i];
+        if (t) atomicAdd(reinterpret_cast<unsigned long long*>(dst), (unsigned long long)t);
+    }
+    __syncthreads();
+}
+
 __device__ __forceinline__ void smem_add_u64(unsigned* lohi, unsigned long long u) {
     const unsigned lo = (unsigned)u, hi = (unsigned)(u >> 32);
     const unsigned old = atomicAdd(&lohi[0], lo);
@@ -419,13 +448,17 @@ __device__ __forceinline__ void smem_add_u64(unsigned* lohi, unsigned long long 
 }
 
 // Drift inside the old coarse cell, identical in both re-sort passes:
-// u_new = Q / 2^(8n+1) + p * dc  (one fused rounding).  Returns the bin
-// floor(u_new * 2^(8n)) relative to the old cell's origin.
-__device__ __forceinline__ int drift_bin(int Q, float p, float dc, float inv2q, float two8n, float* u_out) {
-    float u = (float)Q * inv2q;
-    float un = __fmaf_rn(p, dc, u);
-    *u_out = un;
-    return (int)floorf(un * two8n);
+// u_new = Q / 2^(8n+1) + p * dc (one fused rounding), formed in units of the
+// position code's bins as x = Q / 2 + p * dcs = u_new 2^(8n), dcs = dc 2^(8n):
+// scaling by a power of two commutes with the rounding, since no term is
+// subnormal (a nonzero sum of Q / 2^(8n+1) and the 48-bit product p dc is at
+// least 2^-64).  Q / 2 comes exactly from the bits of 2^22 + Q / 2 (Q < 2^23).
+// Returns the bin floor(x) relative to the old cell's origin; *x_out = x.
+__device__ __forceinline__ int drift_bin(int Q, float p, float dcs, float* x_out) {
+    const float u0s = __int_as_float(0x4A800000 | Q) - 4194304.0f;
+    const float x = __fmaf_rn(p, dcs, u0s);
+    *x_out = x;
+    return __float2int_rd(x);
 }
 
 }  // namespace cube

@@ -142,12 +142,7 @@ __global__ void __launch_bounds__(RAW_T) k_raw_kick_drift(Geo g, float* __restri
 __global__ void __launch_bounds__(RAW_T) k_raw_momentum(int64_t np, const float* __restrict__ V, long long* out3) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
 #pragma unroll
-    for (int d = 0; d < 3; ++d) {
-        long long s = i < np ? vel_fix(V[d * np + i]) : 0;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-        if ((threadIdx.x & 31) == 0) atomicAdd(reinterpret_cast<unsigned long long*>(&out3[d]), (unsigned long long)s);
-    }
+    for (int d = 0; d < 3; ++d) block_sum_to(i < np ? vel_fix(V[d * np + i]) : 0, &out3[d]);
 }
 
 // largest |p| over particles and axes, as the bits of a non-negative float
@@ -156,8 +151,7 @@ __global__ void __launch_bounds__(RAW_T) k_raw_max_speed(int64_t np, const float
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     float m = 0.0f;
     if (i < np) m = fmaxf(fmaxf(fabsf(V[i]), fabsf(V[np + i])), fabsf(V[2 * np + i]));
-    const unsigned b = __reduce_max_sync(0xffffffffu, __float_as_uint(m));
-    if ((threadIdx.x & 31) == 0) atomicMax(vmax_bits, b);
+    block_max_to(__float_as_uint(m), vmax_bits);
 }
 
 __global__ void k_iota(unsigned* out, int64_t n) {

@@ -310,8 +310,7 @@ __global__ void __launch_bounds__(T_BRICK) k_max_speed(Geo g, StoreDev s, const 
             m = fmaxf(m, fabsf(s.vc[(int64_t)d * g.Ncc + L0 + lc] + dec[nu + g.nulim]));
         }
     }
-    const unsigned b = __reduce_max_sync(0xffffffffu, __float_as_uint(m));
-    if ((threadIdx.x & 31) == 0) atomicMax(vmax_bits, b);
+    block_max_to(__float_as_uint(m), vmax_bits);
 }
 
 // ------------------------------------------------------------------ CIC deposit
@@ -704,9 +703,12 @@ __global__ void __launch_bounds__(T_BRICK, 4) k_passA(Geo g, StoreDev s, const f
     const float e0 = cur.est[0], e1 = cur.est[1];
     const int nbits = 8 * NX, half = 1 << (nbits - 1);
     const int sb = g.sbits, wmask = (1 << sb) - 1;
-    const float winv = ldexpf(1.0f, -sb);
-    const float inv2q = ldexpf(1.0f, -(nbits + 1));
-    const float two8n = ldexpf(1.0f, nbits);
+    // the in-cell CIC weight (Q mod 2^sb) 2^-sb exactly from the bits of
+    // 2^(23 - sb) + (Q mod 2^sb) 2^-sb
+    const int wexp = (127 + 23 - sb) << 23;
+    const float wbase = ldexpf(1.0f, 23 - sb);
+    const float dcs = ldexpf(dc, nbits);           // drift in bins of the position code
+    const float kick12 = kick * (-1.0f / 12.0f);   // the FD4 sums' 1/12 and the sign of -grad Phi
     float sacc = 0.0f;
     int mig = 0;
     bool migbad = false;
@@ -730,7 +732,7 @@ __global__ void __launch_bounds__(T_BRICK, 4) k_passA(Geo g, StoreDev s, const f
         for (int d = 0; d < 3; ++d) {
             Q[d] = 2 * (cchi[d] + half) + 1;
             n[d] = (d == 0 ? 4 : 2) + (l[d] << g.r) + (Q[d] >> sb);
-            w1[d] = u16_to_float((unsigned)(Q[d] & wmask)) * winv;       // exact (< 2^16)
+            w1[d] = __int_as_float(wexp | (Q[d] & wmask)) - wbase;
             w0[d] = 1.0f - w1[d];
         }
         // CIC gather of the FD4 gradient (56 nodes, read as 28 pairs of
@@ -769,9 +771,8 @@ __global__ void __launch_bounds__(T_BRICK, 4) k_passA(Geo g, StoreDev s, const f
             }
             gx2 = pfma(pmul(make_float2(w0[1], w1[1]), pk2(b ? w1[2] : w0[2])), fd4_cic_pair(r, w0[0], w1[0]), gx2);
         }
-        const float fsc = -1.0f / 12.0f;
-        const float force[3] = {(gx2.x + gx2.y) * fsc, __fmaf_rn(ca, gy2.x, cb * gy2.y) * fsc,
-                                __fmaf_rn(ca, gz2.x, cb * gz2.y) * fsc};
+        // the gathered sums of 12 dPhi/dx_d; F = -sum / 12 is folded into the kick factor
+        const float gsum[3] = {gx2.x + gx2.y, __fmaf_rn(ca, gy2.x, cb * gy2.y), __fmaf_rn(ca, gz2.x, cb * gz2.y)};
         // kick (update_vp): the code is decided on v - v_c + F K = offset + F K,
         // re-encoded against the same v_c; then the drift of the in-cell
         // offset Q / 2^(8n+1) by the decoded momentum, rounded once
@@ -780,15 +781,14 @@ __global__ void __launch_bounds__(T_BRICK, 4) k_passA(Geo g, StoreDev s, const f
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
             const float vcd = svc[(d << (3 * lB)) + lc];
-            const float dd = __fmaf_rn(force[d], kick, dec[cnu[d] + lim]);
+            const float dd = __fmaf_rn(gsum[d], kick12, dec[cnu[d] + lim]);
             const int nu1 = NV == 1 ? nu_from_table(dd, thr, stab, key0, lim)
                                     : nu_from_thresholds(dd, thr, lim, nu_estimate(dd, e0, e1));
             nu_r.put(d, i, nu1);
             const float off1 = dec[nu1 + lim];
             const float p2 = vcd + off1;
             sacc = __fmaf_rn(off1, off1, sacc);
-            un[d] = __fmaf_rn(p2, dc, u16_to_float((unsigned)Q[d]) * inv2q);
-            const int sh1 = (int)floorf(un[d] * two8n) >> nbits;
+            const int sh1 = drift_bin(Q[d], p2, dcs, &un[d]) >> nbits;
             const int shc = max(-1, min(1, sh1));
             migbad |= sh1 != shc;
             mig |= shc & 1;                        // 1 if the particle changes cell along d
@@ -807,9 +807,9 @@ __global__ void __launch_bounds__(T_BRICK, 4) k_passA(Geo g, StoreDev s, const f
 #pragma unroll
             for (int d = 0; d < 3; ++d) {
                 dbg.cell_old[d * g.Np + i] = cg[d];
-                dbg.u_new[d * g.Np + i] = un[d];
+                dbg.u_new[d * g.Np + i] = ldexpf(un[d], -nbits);
                 dbg.p[d * g.Np + i] = pv[d];
-                dbg.force[d * g.Np + i] = force[d];
+                dbg.force[d * g.Np + i] = gsum[d] * (-1.0f / 12.0f);
             }
         }
     }
@@ -915,7 +915,7 @@ struct PassB {
     const float* thr;
     const unsigned char* stab;
     int key0, lim;
-    float dc, e0, e1;
+    float dcs, e0, e1;     // dcs: the drift factor in bins of the position code (dc 2^(8n))
 
     // lc: the particle's coarse cell in the brick; its velocity offsets are
     // read from the table (1-byte codes) or given in coff (2-byte codes, read
@@ -924,8 +924,6 @@ struct PassB {
                                                const float* coff) const {
         const int Bh = g.Bh;
         const int nbits = 8 * NX, half = 1 << (nbits - 1), bmask = (1 << nbits) - 1;
-        const float inv2q = ldexpf(1.0f, -(nbits + 1));
-        const float two8n = ldexpf(1.0f, nbits);
         const int l[3] = {lc & (g.B - 1), (lc >> g.lB) & (g.B - 1), lc >> (2 * g.lB)};
         PbParticle r;
         int e[3];
@@ -933,8 +931,8 @@ struct PassB {
         for (int d = 0; d < 3; ++d) {
             const int Q = 2 * (cchi[d] + half) + 1;
             const float p2 = svc[(d << (3 * g.lB)) + lc] + (NV == 2 ? coff[d] : dec[cnu[d] + lim]);
-            float un;
-            const int bin = drift_bin(Q, p2, dc, inv2q, two8n, &un);
+            float x;
+            const int bin = drift_bin(Q, p2, dcs, &x);
             const int sh = max(-1, min(1, bin >> nbits));
             e[d] = l[d] + sh + 1;
             r.chi[d] = (bin & bmask) - half;
@@ -1023,7 +1021,7 @@ __global__ void __launch_bounds__(PB_WARPS * 32, 5) k_passB(Geo g, StoreDev so, 
     unsigned char* stab = reinterpret_cast<unsigned char*>(sthr + (NV == 1 ? lim + 2 : 0));   // NV == 1: [VT_N]
     unsigned* wbase = reinterpret_cast<unsigned*>(stab + (NV == 1 ? VT_N : 0));
     PassB<NX, NV, PID> pb{g, sn, CodeRows<NX>(sn.chi, g.Np), CodeRows<NV>(sn.nu, g.Np), cur.dec, next.thr, stab, 0, lim,
-                     dc, next.est[0], next.est[1]};
+                     ldexpf(dc, 8 * NX), next.est[0], next.est[1]};
     const CodeRows<NX> chi_o(so.chi, g.Np);
     const CodeRows<NV> nu_o(so.nu, g.Np);
     if (NV == 1) {
@@ -1189,13 +1187,21 @@ __global__ void __launch_bounds__(T_BRICK) k_store_sums(Geo g, StoreDev s, const
             m[d] += vel_fix(s.vc[(int64_t)d * g.Ncc + L0 + lc] + dec[nu + g.nulim]);
         }
     }
+    // warp sums, then the block's in shared memory, then one atomic per sum and block
+    __shared__ long long part[4][T_BRICK / 32];
     long long v[4] = {m[0], m[1], m[2], cnt};
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
-        if ((threadIdx.x & 31) == 0 && v[k])
-            atomicAdd(reinterpret_cast<unsigned long long*>(&out4[k]), (unsigned long long)v[k]);
+        if (lane == 0) part[k][wid] = v[k];
+    }
+    __syncthreads();
+    if (threadIdx.x < 4) {
+        long long t = 0;
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += part[threadIdx.x][i];
+        if (t) atomicAdd(reinterpret_cast<unsigned long long*>(&out4[threadIdx.x]), (unsigned long long)t);
     }
 }
 
