@@ -555,12 +555,16 @@ __global__ void __launch_bounds__(T_BRICK) k_deposit(Geo g, StoreDev s, float* _
 // (bricks of more than PB_BIG particles are listed for pass B's whole-CTA path)
 constexpr int PB_BIG = 1024;
 
+// threads of a pass A CTA and the CTAs it keeps resident per SM
+constexpr int PA_T = 256;
+constexpr int PA_MINB = 4;
+
 // One CTA per brick.  Shared memory: Phi tile of (F + 5)^3 fine nodes
 // ([o - 2, o + F + 3) per axis, periodic), brick offsets, the histogram of
 // destination cells over the brick and its one-cell halo (Bh^3 cells) with
 // fixed-point momentum sums, and (1-byte velocities) the codec tables.
 template <int NX, int NV, int FC, bool BAT>
-__global__ void __launch_bounds__(T_BRICK, 4) k_passA(Geo g, StoreDev s, const float* __restrict__ phig,
+__global__ void __launch_bounds__(PA_T, PA_MINB) k_passA(Geo g, StoreDev s, const float* __restrict__ phig,
                                                       const __grid_constant__ CUtensorMap tmap, int use_tma,
                                                       CodecDev cur, float kick, float dc, StepScratch w,
                                                       DriftDebug dbg, Batch bt) {
@@ -651,7 +655,7 @@ __global__ void __launch_bounds__(T_BRICK, 4) k_passA(Geo g, StoreDev s, const f
     if (!use_tma) {
         // rows of TX = F + 8 nodes start on a 16-byte boundary: 4-node chunks;
         // thread t < RPI * CX owns chunk column cx of rows t / CX, + RPI, ...
-        const int CX = TX >> 2, nrow = T * T, RPI = T_BRICK / CX;
+        const int CX = TX >> 2, nrow = T * T, RPI = PA_T / CX;
         if (threadIdx.x < RPI * CX) {
             const int cx = threadIdx.x % CX;
             int row = threadIdx.x / CX;
@@ -837,7 +841,7 @@ __global__ void __launch_bounds__(T_BRICK, 4) k_passA(Geo g, StoreDev s, const f
                           (unsigned long long)vs[d * H3 + t]);
         }
     }
-    __shared__ float red[T_BRICK / 32];
+    __shared__ float red[PA_T / 32];
     const float tot = block_sum_float(sacc, red);
     if (threadIdx.x == 0) w.part[brick] = tot;
     // block max of the migration
@@ -1213,11 +1217,11 @@ struct Disp {
         const dim3 grid(g.nb, g.nb, g.nb * bt.members);
         const bool bat = bt.members > 1 || bt.ms;
         if (g.F == 16) {
-            if (bat) k_passA<NX, NV, 16, true><<<grid, T_BRICK, sm, st>>>(g, s, phig, tmap, use_tma, cur, kick, dc, w, dbg, bt);
-            else k_passA<NX, NV, 16, false><<<grid, T_BRICK, sm, st>>>(g, s, phig, tmap, use_tma, cur, kick, dc, w, dbg, bt);
+            if (bat) k_passA<NX, NV, 16, true><<<grid, PA_T, sm, st>>>(g, s, phig, tmap, use_tma, cur, kick, dc, w, dbg, bt);
+            else k_passA<NX, NV, 16, false><<<grid, PA_T, sm, st>>>(g, s, phig, tmap, use_tma, cur, kick, dc, w, dbg, bt);
         } else {
-            if (bat) k_passA<NX, NV, 0, true><<<grid, T_BRICK, sm, st>>>(g, s, phig, tmap, use_tma, cur, kick, dc, w, dbg, bt);
-            else k_passA<NX, NV, 0, false><<<grid, T_BRICK, sm, st>>>(g, s, phig, tmap, use_tma, cur, kick, dc, w, dbg, bt);
+            if (bat) k_passA<NX, NV, 0, true><<<grid, PA_T, sm, st>>>(g, s, phig, tmap, use_tma, cur, kick, dc, w, dbg, bt);
+            else k_passA<NX, NV, 0, false><<<grid, PA_T, sm, st>>>(g, s, phig, tmap, use_tma, cur, kick, dc, w, dbg, bt);
         }
     }
     static void passB(const Geo& g, const StoreDev& so, const StoreDev& sn, const CodecDev& cur,
