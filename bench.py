@@ -501,14 +501,21 @@ def run_ensemble(args):
     def run_batched():
         """Every batch steps as soon as its members' largest momenta are back
         on the host (read back asynchronously behind its previous step), so
-        the host never waits on one batch while the others have work."""
+        the host never waits on one batch while the others have work; the
+        mesh half of each batch's next step is enqueued behind that
+        read-back, so its GPU works while the host waits."""
         bsteps[0] = 0
         cur = {}
+
+        def solve_next(b, idx):
+            cube.cube_batch_solve(b, [1 if cur[i] < scheds[i][-1] else 0 for i in idx])
+
         for b, idx, members in batches:
             for c, i in zip(members, idx):
                 cube.cube_encode(c, *dev[i], ens[i].a_init, ics[i].sigma_1d)
                 cur[i] = ens[i].a_init
             cube.cube_batch_epochs_enqueue(b)
+            solve_next(b, idx)
         live = list(batches)
         while live:
             nxt, moved_on = [], False
@@ -528,6 +535,7 @@ def run_ensemble(args):
                 moved_on = True
                 for i, a in zip(idx, a_to):
                     cur[i] = float(a)
+                solve_next(b, idx)
             live = nxt
             if not moved_on:
                 time.sleep(2e-5)
@@ -583,6 +591,7 @@ def run_ensemble(args):
                            "asynchronous max-|p| read-back (no host wait per step), tuned bricks"},
         "batched": {"value": len(ens) / times[("batched", True)], "unit": "sims/s",
                     "batch_steps": bsteps[0], "launches_per_batch_step": 16,
+                    "mesh_half": "enqueued behind each step's max-|p| read-back (cube_batch_solve)",
                     "kernel_launches_all_passes": launches_batched,
                     "what": f"one cube_batch per particle count ({len(batches)} batches), each step of a batch one "
                             "launch per kernel for all its members, members' own velocity-limited epochs, "

@@ -327,6 +327,19 @@ cube_status cube_debug_drifted(cube_ctx* ctx, int32_t* cell_old, float* u_new, f
    Errors: CUBE_E_ARG (NULL), CUBE_E_STATE (not kept, or no step yet). */
 cube_status cube_debug_force(cube_ctx* ctx, float* force);
 
+/* Self-check of the compact form in which the step kernels read 2-byte
+   velocity codes' tables (Eq. v decode values tan(pi k / M) gamma and Eq. nu
+   thresholds, Section 2.2): each entry is rebuilt, as the kernels rebuild
+   it, from a fixed FP32 approximation and a 4-bit correction, and compared
+   with the full table of the current store's codec, for every k in
+   [-lim, lim] (decode) and [0, lim + 1] (thresholds).  out2[0] = entries that
+   differ (0: the kernels see the exact tables), out2[1] = entries kept as
+   "read the full table" (correction out of range).  `out2` is host memory.
+   Synchronises.
+   Errors: CUBE_E_ARG (NULL, or codes other than 2-byte velocities),
+   CUBE_E_STATE (no store). */
+cube_status cube_debug_velocity_tables(cube_ctx* ctx, int64_t* out2);
+
 /* ---------------------------------------------------------------- tracing */
 
 /* Kernel phases of one cube_pm_step, in launch order:
@@ -516,11 +529,27 @@ cube_status cube_batch_member(cube_batch* batch, int32_t i, cube_ctx** out);
    equal the member's epoch); members with a_to[i] <= a_from[i] sit the step
    out.  Members stepped together must have taken the same number of steps
    since they were encoded (a member that sat a step out continues alone with
-   cube_pm_step).  Host arrays [members].  Enqueues 15 kernel launches for
+   cube_pm_step).  Host arrays [members].  Enqueues 16 kernel launches for
    the whole batch (a context stepped alone launches the same kernels once
-   per step).  Errors: CUBE_E_ARG, CUBE_E_STATE; device errors are latched in
-   each member's flags (cube_stats_get). */
+   per step), 6 of them the mesh half, which is skipped for members whose
+   potential cube_batch_solve already enqueued.  Errors: CUBE_E_ARG,
+   CUBE_E_STATE; device errors are latched in each member's flags
+   (cube_stats_get). */
 cube_status cube_batch_step(cube_batch* batch, const double* a_from, const double* a_to);
+
+/* The mesh half of the next cube_batch_step, enqueued early: the CIC
+   density of each flagged member's current store and its potential (the FFT
+   Poisson solve of Section 2.3.3's update_vp), which do not depend on the
+   step's epochs.  A caller can enqueue it right after a step, while the
+   read-back that decides the next epochs (cube_batch_epochs_enqueue) is in
+   flight, so that the GPU has work while the host waits.  The next
+   cube_batch_step uses these potentials for the members it moves that were
+   solved here since their store last changed, and solves any others itself:
+   the results are the same either way.  stepping: host array [members],
+   non-zero = solve.  Flagged members must have taken the same number of
+   steps.  Enqueues 6 launches (none if every flagged member is solved).
+   Errors: CUBE_E_ARG, CUBE_E_STATE. */
+cube_status cube_batch_solve(cube_batch* batch, const int32_t* stepping);
 
 /* For every member i with a_max[i] above its epoch: the largest a_to[i] <=
    a_max[i] that keeps the member's fastest particle within `cells` coarse

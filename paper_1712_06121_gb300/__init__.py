@@ -144,6 +144,8 @@ _sigs = {
     "cube_batch_launches": ([_P, ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
     "cube_batch_epochs_enqueue": ([_P], ctypes.c_int),
     "cube_batch_epochs_poll": ([_P, _P, ctypes.c_double, _P, ctypes.POINTER(ctypes.c_int32)], ctypes.c_int),
+    "cube_debug_velocity_tables": ([_P, ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
+    "cube_batch_solve": ([_P, _P], ctypes.c_int),
 }
 for _name, (_args, _res) in _sigs.items():
     _f = getattr(_lib, _name)
@@ -291,6 +293,13 @@ def cube_debug_drifted(ctx, cell_old, u_new, p):
 
 def cube_debug_force(ctx, force):
     _check(_lib.cube_debug_force(ctx, _ptr(force)))
+
+
+def cube_debug_velocity_tables(ctx):
+    """(entries the kernels' compact 2-byte tables rebuild wrongly, entries they read whole)."""
+    out = (ctypes.c_int64 * 2)()
+    _check(_lib.cube_debug_velocity_tables(ctx, out))
+    return int(out[0]), int(out[1])
 
 
 def cube_profile(ctx, max_steps):
@@ -486,6 +495,13 @@ def cube_batch_step(batch, a_from, a_to):
     af = np.ascontiguousarray(a_from, dtype=np.float64)
     at = np.ascontiguousarray(a_to, dtype=np.float64)
     _check(_lib.cube_batch_step(batch, af.ctypes.data, at.ctypes.data))
+
+
+def cube_batch_solve(batch, stepping):
+    """Enqueue the mesh half of the next batch step for the flagged members."""
+    import numpy as np
+    fl = np.ascontiguousarray(stepping, dtype=np.int32)
+    _check(_lib.cube_batch_solve(batch, fl.ctypes.data))
 
 
 def cube_batch_next_epochs(batch, a_max, cells=0.5):

@@ -250,6 +250,7 @@ struct cube_ctx {
     bool encoded = false;
     double a = 0.0, a_p = 0.0;
     int64_t steps = 0;
+    uint64_t version = 0;           // changes whenever the store does (encode, step, checkpoint load)
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     bool timed = false;
     int64_t launches = 0;               // kernels launched by this context
@@ -286,9 +287,10 @@ size_t state_layout(cube_ctx* c, char* base) {
         }
         carve(base, off, c->codec[k].dec, (size_t)(2 * g.nulim + 1) * 4);
         carve(base, off, c->codec[k].thr, (size_t)(g.nulim + 2) * 4);
-        carve(base, off, c->codec[k].est, 3 * 4);
+        carve(base, off, c->codec[k].est, 8 * 4);
         carve(base, off, c->codec[k].vtab, VT_N);
         carve(base, off, c->codec[k].sigma, 8);
+        if (g.nnu == 2) carve(base, off, c->codec[k].vdel, (size_t)g.nulim + 2);
     }
     carve(base, off, c->tanv, (size_t)(g.nulim + 1) * 8);
     carve(base, off, c->tanh_, (size_t)(g.nulim + 2) * 8);
@@ -602,6 +604,7 @@ static cube_status raw_encode(cube_ctx* c, const float* pos, const float* vel, c
     c->a = a;
     c->a_p = a;
     c->steps = 0;
+    c->version += 1;
     c->dbg_valid = false;
     c->timed = false;
     return CUBE_OK;
@@ -661,6 +664,7 @@ static cube_status encode_impl(cube_ctx* c, const float* pos, const float* vel, 
     c->a = a;
     c->a_p = a;
     c->steps = 0;
+    c->version += 1;
     c->dbg_valid = false;
     c->timed = false;
     return CUBE_OK;
@@ -742,6 +746,7 @@ cube_status cube_pm_step(cube_ctx* c, double a_from, double a_to) {
         c->a = a_to;
         c->a_p = a_mid;
         c->steps += 1;
+        c->version += 1;
         c->timed = true;
         return CUBE_OK;
     }
@@ -782,6 +787,7 @@ cube_status cube_pm_step(cube_ctx* c, double a_from, double a_to) {
     c->a = a_to;
     c->a_p = a_mid;
     c->steps += 1;
+    c->version += 1;
     c->dbg_valid = c->keep;
     c->timed = true;
     return CUBE_OK;
@@ -1132,6 +1138,7 @@ cube_status cube_checkpoint_load(cube_ctx* c, const void* buf) {
     c->a = h.a;
     c->a_p = h.a_p;
     c->steps = 0;
+    c->version += 1;
     c->dbg_valid = false;
     c->timed = false;
     if (tot[0] != (unsigned long long)g.Np || tot[1] > (unsigned long long)g.Np)
@@ -1271,6 +1278,20 @@ cube_status cube_debug_force(cube_ctx* c, float* force) {
     return latched(c);
 }
 
+cube_status cube_debug_velocity_tables(cube_ctx* c, int64_t* out2) {
+    if (!c || !out2) return fail(CUBE_E_ARG, "NULL argument");
+    if (c->raw || c->g.nnu != 2) return fail(CUBE_E_ARG, "the compact tables exist for 2-byte velocity codes only");
+    if (!c->encoded) return fail(CUBE_E_STATE, "no store: call cube_encode first");
+    launch_check_vel_tables(c->g.nulim, c->codec[c->cur], c->mom, c->st);
+    c->launches += 2;
+    long long h[2] = {0, 0};
+    CK(cudaMemcpyAsync(h, c->mom, sizeof(h), cudaMemcpyDeviceToHost, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    out2[0] = h[0];
+    out2[1] = h[1];
+    return latched(c);
+}
+
 cube_status cube_profile(cube_ctx* c, int32_t max_steps) {
     if (!c) return fail(CUBE_E_ARG, "ctx is NULL");
     if (max_steps < 0 || max_steps > 100000) return fail(CUBE_E_ARG, "max_steps out of range");
@@ -1324,6 +1345,11 @@ struct cube_batch {
     MemberStep* ms_dev = nullptr;       // [members]: the stepped members' table, one entry per grid slot
     MemberStep* ms_host = nullptr;      // pinned [members]
     std::vector<int> slots;             // the member of each slot of the last step
+    MemberStep* solve_dev = nullptr;    // [members]: the member table of the last cube_batch_solve
+    MemberStep* solve_host = nullptr;   // pinned [members]
+    cudaEvent_t solve_copied = nullptr; // that table's upload has been read
+    std::vector<int> solve_slots;
+    std::vector<uint64_t> solved;       // per member: store version whose potential phig holds (0: none)
     unsigned* vmax_host = nullptr;      // pinned [members]: largest |p| per member (float bits)
     cudaEvent_t ms_copied = nullptr;    // the last table upload has been read
     cudaEvent_t vmax_ready = nullptr;   // the maxima read-back has arrived
@@ -1340,6 +1366,9 @@ cube_status cube_batch_destroy(cube_batch* b) {
     if (b->ms_host) cudaFreeHost(b->ms_host);
     if (b->vmax_host) cudaFreeHost(b->vmax_host);
     if (b->ms_copied) cudaEventDestroy(b->ms_copied);
+    if (b->solve_dev) cudaFree(b->solve_dev);
+    if (b->solve_host) cudaFreeHost(b->solve_host);
+    if (b->solve_copied) cudaEventDestroy(b->solve_copied);
     if (b->vmax_ready) cudaEventDestroy(b->vmax_ready);
     delete b;
     return CUBE_OK;
@@ -1381,6 +1410,10 @@ cube_status cube_batch_create(const cube_params* params, int32_t members, void* 
     if (e == cudaSuccess) e = cudaMallocHost((void**)&b->vmax_host, sizeof(unsigned) * members);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ms_copied, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->vmax_ready, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&b->solve_dev, sizeof(MemberStep) * members);
+    if (e == cudaSuccess) e = cudaMallocHost((void**)&b->solve_host, sizeof(MemberStep) * members);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->solve_copied, cudaEventDisableTiming);
+    b->solved.assign(members, 0);
     if (e != cudaSuccess) return bad(e, "device memory");
     for (int i = 0; i < members; ++i) {
         cube_ctx* c = nullptr;
@@ -1476,6 +1509,53 @@ cube_status cube_batch_epochs_poll(cube_batch* b, const double* a_max, double ce
     return batch_epochs(b, a_max, cells, a_to);
 }
 
+// deposit and Poisson solve of the listed members' current stores into their
+// ghosted potentials (the mesh half of a step), one launch per kernel
+static cube_status batch_solve(cube_batch* b, const std::vector<int>& members) {
+    if (members.empty()) return CUBE_OK;
+    CK(cudaEventSynchronize(b->solve_copied));                      // the previous table has been read
+    b->solve_slots = members;
+    for (size_t j = 0; j < members.size(); ++j)
+        b->solve_host[j] = MemberStep{0.0f, 0.0f, 1.0, 1, members[j]};
+    const int n = (int)members.size();
+    CK(cudaMemcpyAsync(b->solve_dev, b->solve_host, sizeof(MemberStep) * n, cudaMemcpyHostToDevice, b->st));
+    CK(cudaEventRecord(b->solve_copied, b->st));
+    cube_ctx* c0 = b->m[0];
+    const Geo& g = c0->g;
+    const int k = b->m[members[0]]->cur;
+    const Batch bt{n, b->stride, b->solve_dev, b->solve_slots.data()};
+    launch_deposit(g, c0->store(k), c0->mesh, particle_mass(g) * std::ldexp(1.0, -3 * g.sbits), b->st, bt);
+    fft_x_r2c(c0->fft, c0->mesh, g.S, b->st, bt);
+    fft_y(c0->fft, c0->mesh, g.S, false, b->st, bt);
+    const float g0 = (float)(-1.5 * c0->P.omega_m / std::pow((double)g.N, 3));
+    fft_z(c0->fft, c0->mesh, g.S, g0, true, b->st, bt);
+    fft_y(c0->fft, c0->mesh, g.S, true, b->st, bt);
+    fft_x_c2r(c0->fft, c0->mesh, g.S, c0->phig, b->st, bt);
+    b->launches += 6;
+    CK(cudaGetLastError());
+    for (int i : members) {
+        b->solved[i] = b->m[i]->version;
+        b->m[i]->phig_valid = true;
+    }
+    return CUBE_OK;
+}
+
+cube_status cube_batch_solve(cube_batch* b, const int32_t* stepping) {
+    if (!b || !stepping) return fail(CUBE_E_ARG, "NULL argument");
+    std::vector<int> list;
+    int cur = -1;
+    for (int i = 0; i < (int)b->m.size(); ++i) {
+        if (!stepping[i]) continue;
+        cube_ctx* c = b->m[i];
+        if (!c->encoded) return fail(CUBE_E_STATE, "a member has no store: call cube_encode first");
+        if (cur >= 0 && c->cur != cur)
+            return fail(CUBE_E_STATE, "members solved together must have taken the same number of steps");
+        cur = c->cur;
+        if (b->solved[i] != c->version) list.push_back(i);
+    }
+    return batch_solve(b, list);
+}
+
 cube_status cube_batch_step(cube_batch* b, const double* a_from, const double* a_to) {
     if (!b || !a_from || !a_to) return fail(CUBE_E_ARG, "NULL argument");
     const int K = (int)b->m.size();
@@ -1513,15 +1593,15 @@ cube_status cube_batch_step(cube_batch* b, const double* a_from, const double* a
     cube_ctx* c0 = b->m[0];
     const Geo& g = c0->g;
     const int k = cur, kn = 1 - cur;
+    // the potential of every stepped member's current store: solved ahead
+    // (cube_batch_solve) or now
+    std::vector<int> need;
+    for (int i : b->slots)
+        if (b->solved[i] != b->m[i]->version) need.push_back(i);
+    cube_status ss = batch_solve(b, need);
+    if (ss != CUBE_OK) return ss;
     const Batch bt{nact, b->stride, b->ms_dev, b->slots.data()};
     launch_batch_clear(g, c0->vsum, c0->maxmig, b->st, bt);
-    launch_deposit(g, c0->store(k), c0->mesh, particle_mass(g) * std::ldexp(1.0, -3 * g.sbits), b->st, bt);
-    fft_x_r2c(c0->fft, c0->mesh, g.S, b->st, bt);
-    fft_y(c0->fft, c0->mesh, g.S, false, b->st, bt);
-    const float g0 = (float)(-1.5 * c0->P.omega_m / std::pow((double)g.N, 3));
-    fft_z(c0->fft, c0->mesh, g.S, g0, true, b->st, bt);
-    fft_y(c0->fft, c0->mesh, g.S, true, b->st, bt);
-    fft_x_c2r(c0->fft, c0->mesh, g.S, c0->phig, b->st, bt);
     StepScratch w{c0->counts[kn], c0->vsum, c0->ghost, c0->part, c0->flags, c0->maxmig, c0->maxmig + 1};
     const DriftDebug nodbg{nullptr, nullptr, nullptr, nullptr};
     launch_passA(g, c0->store(k), c0->phig, b->tma ? &b->map : nullptr, c0->codec[k], 0.0f, 0.0f, w, nodbg, b->st,
@@ -1531,7 +1611,7 @@ cube_status cube_batch_step(cube_batch* b, const double* a_from, const double* a
     exclusive_scan(c0->ghost, c0->ghost, (int64_t)g.nbricks * (g.Bh * g.Bh * g.Bh), c0->scan_tmp, b->st, bt);
     launch_cells(g, w, c0->offsets[kn], c0->vc[kn], b->st, bt);
     launch_passB(g, c0->store(k), c0->store(kn), c0->codec[k], c0->codec[kn], 0.0f, w, b->st, bt);
-    b->launches += 1 + 1 + 5 + 1 + 2 + 4 + 1 + 1;
+    b->launches += 1 + 1 + 2 + 4 + 1 + 1;
     CK(cudaGetLastError());
     for (int i = 0; i < K; ++i) {
         cube_ctx* c = b->m[i];
@@ -1540,6 +1620,7 @@ cube_status cube_batch_step(cube_batch* b, const double* a_from, const double* a
         c->a_p = 0.5 * (a_from[i] + a_to[i]);
         c->a = a_to[i];
         c->steps += 1;
+        c->version += 1;
         c->phig_valid = true;
         c->dbg_valid = false;
         c->timed = false;

@@ -237,6 +237,101 @@ __device__ __forceinline__ int nu_from_table(float d, const float* __restrict__ 
     return d < 0.0f ? -k : k;
 }
 
+// ---- 2-byte velocity tables as an approximation plus a 4-bit correction
+// The decode values dec[k] = tan(pi k / M) gamma and the thresholds thr[k]
+// (tan(pi (k - 1/2) / M) / s rounded up) of 2-byte codes are 2^16-entry
+// tables whose entries a kernel reads at random: in global memory every
+// lookup is an L2 round trip.  Both are tan(m pi / (2M)) gamma at m = 2k and
+// m = 2k - 1, so each entry is stored as the difference, in ulps, between
+// its exact FP32 value and tan_half_steps(m), a fixed FP32 evaluation that
+// every kernel repeats bit for bit: 4 bits per entry (one byte holds both
+// tables' corrections for one k), 32 KB that stay in L1.  A difference
+// outside [-7, 7] is stored as -8 and that entry is read from the full table.
+// The result is the table's value in every case; the approximation's
+// accuracy only decides how rarely the full table is read.
+struct VelApprox {
+    float c;      // pi / (2M), M = 2 lim + 1
+    float gam;    // sqrt(2 sigma^2 / pi) = 1 / s
+    int M;
+};
+
+// tan(m pi / (2M)) gamma for 0 < m < M in FP32 to a few ulps: the angle, or
+// above pi/4 its complement (M - m) pi / (2M) (tan = 1 / tan of the
+// complement), lies in (0, pi/4], where the Taylor series of tan to x^23
+// (Abramowitz & Stegun 4.3.67, coefficients 2^2n (2^2n - 1) |B_2n| / (2n)!)
+// is within 5e-8 relative.  Explicitly rounded operations only, so every
+// kernel gets the same bits.
+__device__ __forceinline__ float tan_half_steps(int m, const VelApprox& va) {
+    const bool cot = 2 * m > va.M;
+    const int mm = cot ? va.M - m : m;                         // < 2^16
+    const float x = __fmul_rn(__fsub_rn(__int_as_float(0x4B000000 | mm), 8388608.0f), va.c);
+    const float x2 = __fmul_rn(x, x);
+    float p = 3.9278322e-05f;
+    p = __fmaf_rn(p, x2, 9.691538e-05f);
+    p = __fmaf_rn(p, x2, 0.00023912912f);
+    p = __fmaf_rn(p, x2, 0.0005900274f);
+    p = __fmaf_rn(p, x2, 0.0014558344f);
+    p = __fmaf_rn(p, x2, 0.003592128f);
+    p = __fmaf_rn(p, x2, 0.008863236f);
+    p = __fmaf_rn(p, x2, 0.021869488f);
+    p = __fmaf_rn(p, x2, 0.053968254f);
+    p = __fmaf_rn(p, x2, 0.13333334f);
+    p = __fmaf_rn(p, x2, 0.33333334f);
+    p = __fmaf_rn(p, x2, 1.0f);
+    const float t = __fmul_rn(x, p);
+    return cot ? __fdividef(va.gam, t) : __fmul_rn(t, va.gam);
+}
+
+// the signed 4-bit correction in bits lo..lo+3 of b
+__device__ __forceinline__ int vdelta(unsigned b, int lo) { return (int)(b << (28 - lo)) >> 28; }
+
+// the correction byte of k: decode difference in bits 0-3, threshold difference in bits 4-7
+__device__ __forceinline__ unsigned char vdelta_pack(int dd, int dt) {
+    const int a = (dd < -7 || dd > 7) ? -8 : dd, b = (dt < -7 || dt > 7) ? -8 : dt;
+    return (unsigned char)((a & 15) | ((b & 15) << 4));
+}
+
+// exact 2-byte tables through the corrections; dec_g / thr_g the full tables
+// (dec_g indexed by nu + lim), vdel [lim + 2] the correction bytes
+struct VelTables {
+    const float* __restrict__ dec_g;
+    const float* __restrict__ thr_g;
+    const unsigned char* __restrict__ vdel;
+    VelApprox va;
+    int lim;
+    // dec[nu + lim] for |nu| <= lim
+    __device__ __forceinline__ float dec(int nu) const {
+        const int k = abs(nu);
+        if (k == 0) return 0.0f;
+        const int dd = vdelta(__ldg(&vdel[k]), 0);
+        const float v = dd == -8 ? dec_g[k + lim]
+                                 : __int_as_float(__float_as_int(tan_half_steps(2 * k, va)) + dd);
+        return nu < 0 ? -v : v;
+    }
+    // thr[k] for 0 <= k <= lim + 1 (thr[0] = 0, thr[lim + 1] = +inf)
+    __device__ __forceinline__ float thr(int k) const {
+        if (k <= 0) return 0.0f;
+        if (k > lim) return __int_as_float(0x7f800000);
+        const int dt = vdelta(__ldg(&vdel[k]), 4);
+        return dt == -8 ? thr_g[k] : __int_as_float(__float_as_int(tan_half_steps(2 * k - 1, va)) + dt);
+    }
+};
+
+// nu_from_thresholds with the thresholds of a VelTables
+__device__ __forceinline__ int nu_from_tables(float d, const VelTables& vt, int est) {
+    const float a = fabsf(d);
+    int k = min(max(est, 0), vt.lim);
+    const float lo = vt.thr(k), hi = vt.thr(k + 1);
+    if (a >= hi) {
+        ++k;
+        while (k < vt.lim && a >= vt.thr(k + 1)) ++k;
+    } else if (a < lo) {
+        --k;
+        while (k > 0 && a < vt.thr(k)) --k;
+    }
+    return d < 0.0f ? -k : k;
+}
+
 // Starting guess for nu_from_thresholds: (M/pi) atan(|d| s) with the
 // arctangent from the polynomial of Abramowitz & Stegun 4.4.47 (Hastings),
 // |error| <= 1e-5 rad on [0, 1], and atan(x) = pi/2 - atan(1/x) above 1.

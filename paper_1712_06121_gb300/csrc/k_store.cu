@@ -170,24 +170,35 @@ __global__ void k_sigma_finalize(const float* __restrict__ part, int nparts, dou
 // single block) the bucket table for the codec scale sg
 __device__ void codec_tables_body(int lim, const double* __restrict__ tanv, const double* __restrict__ tanh_,
                                   double sg, float* __restrict__ dec, float* __restrict__ thr,
-                                  float* __restrict__ est, unsigned char* __restrict__ vtab) {
+                                  float* __restrict__ est, unsigned char* __restrict__ vtab,
+                                  unsigned char* __restrict__ vdel) {
     const double s = sqrt(PI_D / (2.0 * sg * sg));
     const double gam = sqrt(2.0 * sg * sg / PI_D);
+    const double m = (double)(2 * lim + 1);
+    const VelApprox va{(float)(PI_D / (2.0 * m)), (float)gam, 2 * lim + 1};
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k <= lim + 1; k += gridDim.x * blockDim.x) {
+        int ddec = 0, dthr = 0;                          // corrections of the 2-byte tables (vdel)
         if (k == 0) {
             dec[lim] = 0.0f;
             thr[0] = 0.0f;
-            const double m = (double)(2 * lim + 1);
             est[0] = (float)s;
             est[1] = (float)(m / PI_D);
+            est[3] = va.c;
+            est[4] = va.gam;
         } else if (k <= lim) {
             float dv = (float)(tanv[k] * gam);
             dec[lim + k] = dv;
             dec[lim - k] = -dv;
-            thr[k] = __double2float_ru(tanh_[k] / s);
+            const float tv = __double2float_ru(tanh_[k] / s);
+            thr[k] = tv;
+            if (vdel) {
+                ddec = __float_as_int(dv) - __float_as_int(tan_half_steps(2 * k, va));
+                dthr = __float_as_int(tv) - __float_as_int(tan_half_steps(2 * k - 1, va));
+            }
         } else {
             thr[lim + 1] = __int_as_float(0x7f800000);   // +inf
         }
+        if (vdel) vdel[k] = vdelta_pack(ddec, dthr);
     }
     if (vtab) {   // 1-byte codes (lim < 256), one block: the bucket table of nu_from_table
         __shared__ float sthr[256];
@@ -211,12 +222,13 @@ __device__ void codec_tables_body(int lim, const double* __restrict__ tanv, cons
 
 __global__ void k_codec_tables(int lim, const double* __restrict__ tanv, const double* __restrict__ tanh_,
                                const double* __restrict__ sigma, float* __restrict__ dec, float* __restrict__ thr,
-                               float* __restrict__ est, unsigned char* __restrict__ vtab, Batch bt) {
+                               float* __restrict__ est, unsigned char* __restrict__ vtab,
+                               unsigned char* __restrict__ vdel, Batch bt) {
     const int slot = blockIdx.y;                             // slot of a batch
     if (bt.ms && !bt.ms[slot].active) return;
     const size_t o = slot_member(bt, slot) * bt.stride;
     codec_tables_body(lim, moved(tanv, o), moved(tanh_, o), *moved(sigma, o), moved(dec, o), moved(thr, o),
-                      moved(est, o), moved(vtab, o));
+                      moved(est, o), moved(vtab, o), moved(vdel, o));
 }
 
 template <int NX, int NV>
@@ -705,6 +717,9 @@ __global__ void __launch_bounds__(PA_T, PA_MINB) k_passA(Geo g, StoreDev s, cons
         __syncthreads();
     }
     const float e0 = cur.est[0], e1 = cur.est[1];
+    // 2-byte codes: the decode and threshold tables through their L1-resident corrections
+    const VelTables vt{cur.dec, cur.thr, cur.vdel, VelApprox{NV == 2 ? cur.est[3] : 0.0f, NV == 2 ? cur.est[4] : 0.0f,
+                                                             2 * lim + 1}, lim};
     const int nbits = 8 * NX, half = 1 << (nbits - 1);
     const int sb = g.sbits, wmask = (1 << sb) - 1;
     // the in-cell CIC weight (Q mod 2^sb) 2^-sb exactly from the bits of
@@ -785,11 +800,11 @@ __global__ void __launch_bounds__(PA_T, PA_MINB) k_passA(Geo g, StoreDev s, cons
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
             const float vcd = svc[(d << (3 * lB)) + lc];
-            const float dd = __fmaf_rn(gsum[d], kick12, dec[cnu[d] + lim]);
+            const float dd = __fmaf_rn(gsum[d], kick12, NV == 1 ? dec[cnu[d] + lim] : vt.dec(cnu[d]));
             const int nu1 = NV == 1 ? nu_from_table(dd, thr, stab, key0, lim)
-                                    : nu_from_thresholds(dd, thr, lim, nu_estimate(dd, e0, e1));
+                                    : nu_from_tables(dd, vt, nu_estimate(dd, e0, e1));
             nu_r.put(d, i, nu1);
-            const float off1 = dec[nu1 + lim];
+            const float off1 = NV == 1 ? dec[nu1 + lim] : vt.dec(nu1);
             const float p2 = vcd + off1;
             sacc = __fmaf_rn(off1, off1, sacc);
             const int sh1 = drift_bin(Q[d], p2, dcs, &un[d]) >> nbits;
@@ -1024,6 +1039,8 @@ __global__ void __launch_bounds__(PB_WARPS * 32, 5) k_passB(Geo g, StoreDev so, 
     float* sthr = sdec + (NV == 1 ? 2 * lim + 1 : 0);                       // NV == 1: [lim + 2]
     unsigned char* stab = reinterpret_cast<unsigned char*>(sthr + (NV == 1 ? lim + 2 : 0));   // NV == 1: [VT_N]
     unsigned* wbase = reinterpret_cast<unsigned*>(stab + (NV == 1 ? VT_N : 0));
+    // (2-byte codes read the full tables here: the compact form of pass A
+    // costs pass B more in instructions than its loads cost in latency)
     PassB<NX, NV, PID> pb{g, sn, CodeRows<NX>(sn.chi, g.Np), CodeRows<NV>(sn.nu, g.Np), cur.dec, next.thr, stab, 0, lim,
                      ldexpf(dc, 8 * NX), next.est[0], next.est[1]};
     const CodeRows<NX> chi_o(so.chi, g.Np);
@@ -1267,6 +1284,25 @@ __global__ void k_zero_slot_words(unsigned* p, Batch bt) {
     for (int i = threadIdx.x; i < bt.members; i += blockDim.x) moved(p, slot_member(bt, i) * bt.stride)[0] = 0u;
 }
 
+// every entry of the 2-byte tables as VelTables rebuilds it, against the tables
+__global__ void k_check_vel_tables(int lim, CodecDev c, long long* out2) {
+    const VelTables vt{c.dec, c.thr, c.vdel, VelApprox{c.est[3], c.est[4], 2 * lim + 1}, lim};
+    long long bad = 0, whole = 0;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k <= lim + 1; k += gridDim.x * blockDim.x) {
+        if (k <= lim) {
+            bad += __float_as_int(vt.dec(k)) != __float_as_int(c.dec[lim + k]);
+            bad += __float_as_int(vt.dec(-k)) != __float_as_int(c.dec[lim - k]);
+        }
+        bad += __float_as_int(vt.thr(k)) != __float_as_int(c.thr[k]);
+        if (k >= 1 && k <= lim) {
+            const unsigned b = c.vdel[k];
+            whole += (vdelta(b, 0) == -8) + (vdelta(b, 4) == -8);
+        }
+    }
+    block_sum_to(bad, &out2[0]);
+    block_sum_to(whole, &out2[1]);
+}
+
 // the step's cleared scratch of every stepped member of a batch: the
 // fixed-point momentum sums [3][Ncc] and the migration / crowded-brick words
 __global__ void k_batch_clear(int64_t n64, long long* __restrict__ vsum, int* __restrict__ mig, Batch bt) {
@@ -1316,7 +1352,8 @@ void launch_codec_tables(int nulim, const double* tanv, const double* tanh_, con
     // 1-byte codes (nulim 127) fit one block, which also builds the bucket table
     const bool one = nulim + 2 <= 256;
     k_codec_tables<<<dim3(nblk(nulim + 2, 256), bt.members), 256, 0, st>>>(nulim, tanv, tanh_, c.sigma, c.dec, c.thr,
-                                                                          c.est, one ? c.vtab : nullptr, bt);
+                                                                          c.est, one ? c.vtab : nullptr,
+                                                                          one ? nullptr : c.vdel, bt);
 }
 
 void launch_encode_scatter(const Geo& g, const float* pos, const float* vel, const unsigned* id_in,
@@ -1422,6 +1459,11 @@ void launch_passB(const Geo& g, const StoreDev& so, const StoreDev& sn, const Co
     else if (g.nchi == 1) { set_smem_attrs<1, 2>(); Disp<1, 2>::passB(g, so, sn, cur, next, dc, w.ghost, vcn, w.flags, w.big, sm, st, bt); }
     else if (g.nnu == 1) { set_smem_attrs<2, 1>(); Disp<2, 1>::passB(g, so, sn, cur, next, dc, w.ghost, vcn, w.flags, w.big, sm, st, bt); }
     else { set_smem_attrs<2, 2>(); Disp<2, 2>::passB(g, so, sn, cur, next, dc, w.ghost, vcn, w.flags, w.big, sm, st, bt); }
+}
+
+void launch_check_vel_tables(int lim, const CodecDev& c, long long* out2, cudaStream_t st) {
+    cudaMemsetAsync(out2, 0, 2 * sizeof(long long), st);
+    k_check_vel_tables<<<nblk(lim + 2, 256), 256, 0, st>>>(lim, c, out2);
 }
 
 void launch_store_sums(const Geo& g, const StoreDev& s, const float* dec, long long* out4, cudaStream_t st) {

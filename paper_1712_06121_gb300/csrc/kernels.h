@@ -106,9 +106,11 @@ struct StoreDev {
 struct CodecDev {
     float* dec;         // [2 lim + 1]: dec[nu + lim] = tan(pi nu / M) * sqrt(2 sigma^2 / pi)
     float* thr;         // [lim + 2]: encode thresholds (see nu_from_thresholds)
-    float* est;         // [3]: s and M/pi for the starting guess; [2] the first bucket key of vtab (int bits)
+    float* est;         // [8]: s and M/pi for the starting guess; [2] the first bucket key of vtab (int bits);
+                        // [3], [4]: pi / (2M) and 1 / s of the 2-byte tables' approximation (VelApprox)
     unsigned char* vtab;   // [VT_N] (1-byte codes): code at the start of each bucket of |d| (see nu_from_table)
     double* sigma;      // device scalar
+    unsigned char* vdel;   // [lim + 2] (2-byte codes): corrections of dec and thr to tan_half_steps (VelTables)
 };
 
 struct DriftDebug {
@@ -136,7 +138,8 @@ __host__ __device__ __forceinline__ StoreDev moved(const StoreDev& s, size_t off
                     moved(s.nu, off), moved(s.id, off)};
 }
 __host__ __device__ __forceinline__ CodecDev moved(const CodecDev& c, size_t off) {
-    return CodecDev{moved(c.dec, off), moved(c.thr, off), moved(c.est, off), moved(c.vtab, off), moved(c.sigma, off)};
+    return CodecDev{moved(c.dec, off), moved(c.thr, off), moved(c.est, off), moved(c.vtab, off), moved(c.sigma, off),
+                    moved(c.vdel, off)};
 }
 __host__ __device__ __forceinline__ StepScratch moved(const StepScratch& w, size_t off) {
     return StepScratch{moved(w.counts_new, off), moved(w.vsum_new, off), moved(w.ghost, off), moved(w.part, off),
@@ -177,6 +180,8 @@ void launch_passB(const Geo& g, const StoreDev& s_old, const StoreDev& s_new, co
 // sums over the current store: out[0..2] momentum of the decoded particles in
 // 2^-24 fixed point, out[3] the particle count (sum of the cell counts)
 void launch_store_sums(const Geo& g, const StoreDev& s, const float* dec, long long* out4, cudaStream_t st);
+// 2-byte codes: out2[0] entries of dec / thr that VelTables rebuilds differently, out2[1] entries it reads whole
+void launch_check_vel_tables(int lim, const CodecDev& c, long long* out2, cudaStream_t st);
 
 // uncompressed FP32 particles (k_raw.cu)
 void launch_raw_encode(const Geo& g, const float* pos, const float* vel, const unsigned* id_in, float* P, float* V,

@@ -11,6 +11,8 @@ per kernel (cube_batch_*).
 * cube_batch_next_epochs equals cube_next_epoch member by member, and its
   non-blocking form (enqueue, then poll) gives the same epochs.
 * One batch step launches 16 kernels whatever the member count.
+* The mesh half solved ahead (cube_batch_solve), for every member or for
+  some, gives the same stores, and each potential is solved once.
 """
 import dataclasses
 
@@ -56,8 +58,9 @@ def _params(cube, w):
 STORE_KEYS = ("counts", "offsets", "vc", "chi", "nu", "ids")
 
 
-@pytest.mark.parametrize("nps,xb,vb", [(32, 1, 1), (24, 2, 2), (16, 1, 2)])
-def test_batch_members_equal_their_runs_alone(cube, nps, xb, vb):
+@pytest.mark.parametrize("nps,xb,vb,ahead", [(32, 1, 1, "none"), (24, 2, 2, "none"), (16, 1, 2, "none"),
+                                            (32, 1, 1, "all"), (24, 2, 2, "some")])
+def test_batch_members_equal_their_runs_alone(cube, nps, xb, vb, ahead):
     mem = _members(nps, xb, vb)
     k = len(mem)
     nsteps = 5
@@ -72,9 +75,14 @@ def test_batch_members_equal_their_runs_alone(cube, nps, xb, vb):
         got = []
         l0 = cube.cube_batch_launches(b)
         for s in range(nsteps):
+            if ahead != "none":
+                flags = [1] * k if ahead == "all" else [i % 2 for i in range(k)]
+                cube.cube_batch_solve(b, flags)
+                cube.cube_batch_solve(b, flags)                  # already solved: no launches
             cube.cube_batch_step(b, [sc[s] for sc in scheds], [sc[s + 1] for sc in scheds])
             got.append([read_store(cube, c) for c in ctxs])
-        assert cube.cube_batch_launches(b) - l0 == 16 * nsteps
+        # 10 launches of the particle half per step, 6 of the mesh half per solve
+        assert cube.cube_batch_launches(b) - l0 == (16 if ahead != "some" else 22) * nsteps
         for c in ctxs:
             st = cube.cube_stats_get(c)                      # raises on a latched device error
             assert st.steps == nsteps and st.max_migration <= 1

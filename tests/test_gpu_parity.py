@@ -378,6 +378,38 @@ def test_force_matches_oracle(cube, name, nps, nf, brick, deconv):
     assert err <= 1e-4, err
 
 
+@pytest.mark.parametrize("xb", [1, 2])
+@pytest.mark.parametrize("sigma", [0.05, 0.7, 3.0, 40.0])
+def test_two_byte_velocity_tables_are_exact(cube, xb, sigma):
+    """2-byte velocity codes (Section 2.2, Eqs. v and nu): the step kernels
+    read the decode values and thresholds as a fixed FP32 approximation of
+    tan plus a 4-bit correction; every entry they rebuild equals the full
+    table's, for codec scales over three decades, after the encode and after
+    each step (each step builds the next codec)."""
+    w, ic = _ics(16, 32)
+    n = 16 ** 3
+    prm, ctx = _ctx(cube, 32, n, xb, 2, w)
+    try:
+        cube.cube_encode(ctx, ic.pos, ic.vel, ic.ids, w.a_init, sigma)
+        bad, whole = cube.cube_debug_velocity_tables(ctx)
+        assert bad == 0 and whole == 0, (bad, whole)
+        sched = synth.uniform_schedule(w.a_init, 0.05, 2)
+        for i in range(2):
+            cube.cube_pm_step(ctx, sched[i], sched[i + 1])
+            bad, whole = cube.cube_debug_velocity_tables(ctx)
+            assert bad == 0 and whole == 0, (i, bad, whole)
+    finally:
+        cube.cube_destroy(ctx)
+    prm, ctx = _ctx(cube, 32, n, xb, 1, w)
+    try:
+        cube.cube_encode(ctx, ic.pos, ic.vel, ic.ids, w.a_init, sigma)
+        with pytest.raises(cube.CubeError) as e:
+            cube.cube_debug_velocity_tables(ctx)
+        assert e.value.status == cube.CUBE_E_ARG
+    finally:
+        cube.cube_destroy(ctx)
+
+
 def _decoded_momentum_bound(st):
     """(FP64 sum of the oracle-decoded momenta, bound on the GPU's sum): the
     GPU sums FP32 decodes (v_c + table offset, each within one FP32 rounding
