@@ -244,6 +244,95 @@ def _crowded_ics(nps, nf, w, a0, a1, seed=1712101):
     return np.mod(pos, nf).astype(np.float32), vel.astype(np.float32), ic.ids
 
 
+@pytest.mark.parametrize("xb,vb", [(1, 1), (2, 2)])
+def test_uniformly_moving_lattice_translates_exactly(cube, xb, vb):
+    """Degenerate case: particles on the lattice q = 2i + 1/2 fine cells all
+    moving with one velocity.  Their CIC density is exactly uniform, so the
+    potential and the force are exactly zero on the GPU (FP32) as in the
+    oracle (FP64); every velocity code is 0 with v_c = v, and the whole
+    store after each step equals the oracle's full step (Figs. update_xp and
+    update_vp) bit for bit, the lattice translated across cells and the
+    periodic edge."""
+    nps, nf = 16, 32
+    n = nps ** 3
+    w = synth.WORKLOADS["pm64"]
+    g1 = (2.0 * np.arange(nps) + 0.5).astype(np.float32)
+    z, y, x = np.meshgrid(g1, g1, g1, indexing="ij")
+    pos = np.stack([x.ravel(), y.ravel(), z.ravel()]).astype(np.float32)
+    om, ol, _ = w.omega()
+    a0 = w.a_init
+    sched = [a0, a0 * 1.3, a0 * 1.7, a0 * 2.2]
+    # a bulk flow of about 0.6 fine cells per step in x, less in y and z
+    sp = 0.6 / cosmo.drift_factor(sched[0], sched[1], om, ol)
+    vel = np.broadcast_to(np.array([[sp], [-0.45 * sp], [0.2 * sp]], np.float32), (3, n)).copy()
+    ids = np.arange(n, dtype=np.uint32)
+    prm, ctx = _ctx(cube, nf, n, xb, vb, w)
+    try:
+        cube.cube_encode(ctx, pos, vel, ids, a0, 1.0)
+        cube.cube_keep_drifted(ctx, True)
+        g = read_store(cube, ctx)
+        ref = pm.Store(oracle_params(pm, prm, g["brick"]), g["counts"], g["vc"], g["chi"], g["nu"], g["ids"],
+                       g["sigma"], g["a"], g["a_p"])
+        assert np.all(g["nu"] == 0)
+        for i in range(3):
+            cube.cube_pm_step(ctx, sched[i], sched[i + 1])
+            f = np.empty((3, n), np.float32)
+            cube.cube_debug_force(ctx, f)
+            assert np.all(f == 0.0)
+            ref = pm.step(ref, sched[i], sched[i + 1])
+            g = read_store(cube, ctx)
+            assert_store_equal(g, ref, f"lattice step {i}")
+            assert g["sigma"] == ref.sigma
+        st = cube.cube_stats_get(ctx)
+        assert st.max_migration <= 1
+    finally:
+        cube.cube_destroy(ctx)
+
+
+def test_a_single_particle(cube):
+    """The smallest store: one particle.  Encode against the oracle; its
+    self-force vanishes in the oracle (the same CIC kernel deposits and
+    interpolates and the FD4 difference is antisymmetric, so a particle
+    exerts no net force on itself), and the GPU's is within 1e-4 of the
+    largest FD4 gradient of the potential (FP32 rounding of a potential
+    whose one source holds the whole box's mass); the re-sorted store of
+    each step equals the oracle's re-encode of the GPU's drifted particle."""
+    nf, n = 32, 1
+    w = synth.WORKLOADS["pm64"]
+    pos = np.array([[13.3], [0.7], [31.9]], np.float32)
+    vel = np.array([[0.8], [-0.3], [0.05]], np.float32)
+    ids = np.array([7], np.uint32)
+    prm, ctx = _ctx(cube, nf, n, 1, 2, w)
+    try:
+        cube.cube_encode(ctx, pos, vel, ids, w.a_init, 0.5)
+        P = oracle_params(pm, prm, read_store(cube, ctx)["brick"])
+        want = pm.encode(P, pos, vel, ids, w.a_init, 0.5)
+        assert_store_equal(read_store(cube, ctx), want, "single particle encode")
+        cube.cube_keep_drifted(ctx, True)
+        sched = synth.uniform_schedule(w.a_init, 0.05, 2)
+        for i in range(2):
+            before = read_store(cube, ctx)
+            old = pm.Store(P, before["counts"], before["vc"], before["chi"], before["nu"], before["ids"],
+                           before["sigma"], before["a"], before["a_p"])
+            cube.cube_pm_step(ctx, sched[i], sched[i + 1])
+            f = np.empty((3, n), np.float32)
+            cube.cube_debug_force(ctx, f)
+            x, _, _ = pm.decode(old)
+            rho = mesh.cic_deposit(x, nf, P.mass)
+            fref = mesh.force_at(x, rho, prm.omega_m, prm.deconv_power)
+            phi = mesh.potential(rho, prm.omega_m, prm.deconv_power)
+            gscale = max(np.max(np.abs(gr)) for gr in mesh.fd4_gradient(phi))
+            assert gscale > 0
+            assert np.max(np.abs(fref)) <= 1e-9 * gscale
+            assert np.max(np.abs(f - fref)) <= 1e-4 * gscale
+            cell, u, p, sig = _drifted(cube, ctx, n)
+            g = read_store(cube, ctx)
+            ref = pm.encode_drifted(P, cell, u, p, before["ids"], sig, g["a"], g["a_p"])
+            assert_store_equal(g, ref, f"single particle step {i}")
+    finally:
+        cube.cube_destroy(ctx)
+
+
 @pytest.mark.parametrize("xb,vb,brick", [(1, 1, 4), (2, 2, 4), (1, 2, 2)])
 def test_crowded_bricks_resort_is_bit_exact(cube, xb, vb, brick):
     """Bricks with more particles than one warp's share (re-sorted by a whole
