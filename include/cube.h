@@ -532,7 +532,9 @@ cube_status cube_batch_member(cube_batch* batch, int32_t i, cube_ctx** out);
    cube_pm_step).  Host arrays [members].  Enqueues 16 kernel launches for
    the whole batch (a context stepped alone launches the same kernels once
    per step), 6 of them the mesh half, which is skipped for members whose
-   potential cube_batch_solve already enqueued.  Errors: CUBE_E_ARG,
+   potential cube_batch_solve already enqueued.  For meshes up to 256^3 each
+   half is captured as a CUDA graph on the second step with the same store
+   parity and number of moving members, and replayed on later ones.  Errors: CUBE_E_ARG,
    CUBE_E_STATE; device errors are latched in each member's flags
    (cube_stats_get). */
 cube_status cube_batch_step(cube_batch* batch, const double* a_from, const double* a_to);

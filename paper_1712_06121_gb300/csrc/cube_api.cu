@@ -3,6 +3,8 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <functional>
+#include <map>
 #include <string>
 #include <vector>
 
@@ -1350,6 +1352,13 @@ struct cube_batch {
     cudaEvent_t solve_copied = nullptr; // that table's upload has been read
     std::vector<int> solve_slots;
     std::vector<uint64_t> solved;       // per member: store version whose potential phig holds (0: none)
+    // CUDA graphs of the two halves of a batch step, by (half, store parity, slots)
+    struct Graph {
+        int uses = 0;
+        cudaGraphExec_t exec = nullptr;
+    };
+    std::map<int, Graph> graphs;
+    bool graphs_on = false;             // meshes up to 256 (whose sweeps have batched instances)
     unsigned* vmax_host = nullptr;      // pinned [members]: largest |p| per member (float bits)
     cudaEvent_t ms_copied = nullptr;    // the last table upload has been read
     cudaEvent_t vmax_ready = nullptr;   // the maxima read-back has arrived
@@ -1369,6 +1378,8 @@ cube_status cube_batch_destroy(cube_batch* b) {
     if (b->solve_dev) cudaFree(b->solve_dev);
     if (b->solve_host) cudaFreeHost(b->solve_host);
     if (b->solve_copied) cudaEventDestroy(b->solve_copied);
+    for (auto& kv : b->graphs)
+        if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
     if (b->vmax_ready) cudaEventDestroy(b->vmax_ready);
     delete b;
     return CUBE_OK;
@@ -1414,6 +1425,7 @@ cube_status cube_batch_create(const cube_params* params, int32_t members, void* 
     if (e == cudaSuccess) e = cudaMallocHost((void**)&b->solve_host, sizeof(MemberStep) * members);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->solve_copied, cudaEventDisableTiming);
     b->solved.assign(members, 0);
+    b->graphs_on = params[0].n_fine <= 256;
     if (e != cudaSuccess) return bad(e, "device memory");
     for (int i = 0; i < members; ++i) {
         cube_ctx* c = nullptr;
@@ -1509,6 +1521,46 @@ cube_status cube_batch_epochs_poll(cube_batch* b, const double* a_max, double ce
     return batch_epochs(b, a_max, cells, a_to);
 }
 
+// One half of a batch step from a CUDA graph.  The launch sequence of a half
+// depends only on the key (which half, the store parity, the number of
+// slots): per-member values reach the kernels through the device table.  The
+// first use of a key launches directly (which also sets the kernels'
+// attributes), the second captures the sequence and instantiates it, later
+// ones replay it.  Any capture error turns graphs off for the batch and
+// launches directly.
+static cube_status batch_graph(cube_batch* b, int key, const std::function<void()>& enqueue) {
+    if (!b->graphs_on) {
+        enqueue();
+        return CUBE_OK;
+    }
+    cube_batch::Graph& e = b->graphs[key];
+    if (e.exec) {
+        CK(cudaGraphLaunch(e.exec, b->st));
+        return CUBE_OK;
+    }
+    if (e.uses++ == 0) {
+        enqueue();
+        return CUBE_OK;
+    }
+    cudaGraph_t gr = nullptr;
+    cudaError_t err = cudaStreamBeginCapture(b->st, cudaStreamCaptureModeThreadLocal);
+    if (err == cudaSuccess) {
+        enqueue();
+        err = cudaStreamEndCapture(b->st, &gr);
+        if (err == cudaSuccess) err = cudaGraphInstantiate(&e.exec, gr, 0);
+        if (gr) cudaGraphDestroy(gr);
+    }
+    if (err != cudaSuccess) {
+        cudaGetLastError();
+        e.exec = nullptr;
+        b->graphs_on = false;
+        enqueue();
+        return CUBE_OK;
+    }
+    CK(cudaGraphLaunch(e.exec, b->st));
+    return CUBE_OK;
+}
+
 // deposit and Poisson solve of the listed members' current stores into their
 // ghosted potentials (the mesh half of a step), one launch per kernel
 static cube_status batch_solve(cube_batch* b, const std::vector<int>& members) {
@@ -1524,13 +1576,16 @@ static cube_status batch_solve(cube_batch* b, const std::vector<int>& members) {
     const Geo& g = c0->g;
     const int k = b->m[members[0]]->cur;
     const Batch bt{n, b->stride, b->solve_dev, b->solve_slots.data()};
-    launch_deposit(g, c0->store(k), c0->mesh, particle_mass(g) * std::ldexp(1.0, -3 * g.sbits), b->st, bt);
-    fft_x_r2c(c0->fft, c0->mesh, g.S, b->st, bt);
-    fft_y(c0->fft, c0->mesh, g.S, false, b->st, bt);
     const float g0 = (float)(-1.5 * c0->P.omega_m / std::pow((double)g.N, 3));
-    fft_z(c0->fft, c0->mesh, g.S, g0, true, b->st, bt);
-    fft_y(c0->fft, c0->mesh, g.S, true, b->st, bt);
-    fft_x_c2r(c0->fft, c0->mesh, g.S, c0->phig, b->st, bt);
+    cube_status gs = batch_graph(b, (0 * 2 + k) * 8192 + n, [&] {
+        launch_deposit(g, c0->store(k), c0->mesh, particle_mass(g) * std::ldexp(1.0, -3 * g.sbits), b->st, bt);
+        fft_x_r2c(c0->fft, c0->mesh, g.S, b->st, bt);
+        fft_y(c0->fft, c0->mesh, g.S, false, b->st, bt);
+        fft_z(c0->fft, c0->mesh, g.S, g0, true, b->st, bt);
+        fft_y(c0->fft, c0->mesh, g.S, true, b->st, bt);
+        fft_x_c2r(c0->fft, c0->mesh, g.S, c0->phig, b->st, bt);
+    });
+    if (gs != CUBE_OK) return gs;
     b->launches += 6;
     CK(cudaGetLastError());
     for (int i : members) {
@@ -1601,16 +1656,19 @@ cube_status cube_batch_step(cube_batch* b, const double* a_from, const double* a
     cube_status ss = batch_solve(b, need);
     if (ss != CUBE_OK) return ss;
     const Batch bt{nact, b->stride, b->ms_dev, b->slots.data()};
-    launch_batch_clear(g, c0->vsum, c0->maxmig, b->st, bt);
-    StepScratch w{c0->counts[kn], c0->vsum, c0->ghost, c0->part, c0->flags, c0->maxmig, c0->maxmig + 1};
+    const StepScratch w{c0->counts[kn], c0->vsum, c0->ghost, c0->part, c0->flags, c0->maxmig, c0->maxmig + 1};
     const DriftDebug nodbg{nullptr, nullptr, nullptr, nullptr};
-    launch_passA(g, c0->store(k), c0->phig, b->tma ? &b->map : nullptr, c0->codec[k], 0.0f, 0.0f, w, nodbg, b->st,
-                 bt);
-    launch_sigma_finalize(c0->part, g.nbricks, 3.0 * (double)g.Np, 1.0, 0.0, c0->codec[kn].sigma, b->st, bt);
-    launch_codec_tables(g.nulim, c0->tanv, c0->tanh_, c0->codec[kn], b->st, bt);
-    exclusive_scan(c0->ghost, c0->ghost, (int64_t)g.nbricks * (g.Bh * g.Bh * g.Bh), c0->scan_tmp, b->st, bt);
-    launch_cells(g, w, c0->offsets[kn], c0->vc[kn], b->st, bt);
-    launch_passB(g, c0->store(k), c0->store(kn), c0->codec[k], c0->codec[kn], 0.0f, w, b->st, bt);
+    cube_status gs = batch_graph(b, (1 * 2 + k) * 8192 + nact, [&] {
+        launch_batch_clear(g, c0->vsum, c0->maxmig, b->st, bt);
+        launch_passA(g, c0->store(k), c0->phig, b->tma ? &b->map : nullptr, c0->codec[k], 0.0f, 0.0f, w, nodbg,
+                     b->st, bt);
+        launch_sigma_finalize(c0->part, g.nbricks, 3.0 * (double)g.Np, 1.0, 0.0, c0->codec[kn].sigma, b->st, bt);
+        launch_codec_tables(g.nulim, c0->tanv, c0->tanh_, c0->codec[kn], b->st, bt);
+        exclusive_scan(c0->ghost, c0->ghost, (int64_t)g.nbricks * (g.Bh * g.Bh * g.Bh), c0->scan_tmp, b->st, bt);
+        launch_cells(g, w, c0->offsets[kn], c0->vc[kn], b->st, bt);
+        launch_passB(g, c0->store(k), c0->store(kn), c0->codec[k], c0->codec[kn], 0.0f, w, b->st, bt);
+    });
+    if (gs != CUBE_OK) return gs;
     b->launches += 1 + 1 + 2 + 4 + 1 + 1;
     CK(cudaGetLastError());
     for (int i = 0; i < K; ++i) {
