@@ -41,6 +41,37 @@ __device__ __forceinline__ int grid_brick(const Geo& g, int* bx, int* by, int* b
     return *bx + g.nb * (*by + g.nb * *bz);
 }
 
+// One axis of the flattened (cell, brick) slot of a halo cell (flat_slot),
+// for the brick at coordinate `me` on that axis and halo coordinate e in
+// [0, Bh): the cell's home brick coordinate (bits 0-7), its coordinate in
+// that brick (8-11), this brick's rank among the cell's candidate bricks
+// (12-15), the number of candidates (16-19) and of candidate slots before
+// the cell (20-23).  Bricks of 1, 2 or 4 cells and at most 256 bricks per
+// side keep every field in range.
+__device__ __forceinline__ unsigned halo_axis_desc(const Geo& g, int me, int e) {
+    const int c = wrap1(me * g.B - 1 + e, g.Nc);
+    const int lx = c & (g.B - 1), hbc = c >> g.lB;
+    const int lo = lx == 0 ? wrap1(hbc - 1, g.nb) : -1;
+    const int hi = lx == g.B - 1 ? wrap1(hbc + 1, g.nb) : -1;
+    const int r = (hbc < me) + (lo >= 0 && lo < me) + (hi >= 0 && hi < me);
+    return (unsigned)hbc | ((unsigned)lx << 8) | ((unsigned)r << 12) | ((unsigned)ncand(lx, g.B) << 16) |
+           ((unsigned)ncand_before(lx) << 20);
+}
+
+// the flattened slot (flat_slot) and the storage rank (cell_rank) of the
+// halo cell whose three axes have descriptions ax, ay, az
+__device__ __forceinline__ void halo_slot(const Geo& g, unsigned ax, unsigned ay, unsigned az, int64_t* slot,
+                                          int* rank_L) {
+    const int S1 = g.Bh, S2 = S1 * S1;
+    const int hb = (int)(ax & 255u) + g.nb * ((int)(ay & 255u) + g.nb * (int)(az & 255u));
+    const int nc0 = (ax >> 16) & 15, nc1 = (ay >> 16) & 15, nc2 = (az >> 16) & 15;
+    const int pre = (int)((az >> 20) & 15) * S2 + nc2 * ((int)((ay >> 20) & 15) * S1 + nc1 * (int)((ax >> 20) & 15));
+    const int rank = ((int)((az >> 12) & 15) * nc1 + (int)((ay >> 12) & 15)) * nc0 + (int)((ax >> 12) & 15);
+    *slot = (int64_t)hb * (S2 * S1) + pre + rank;
+    *rank_L = (hb << (3 * g.lB)) + (int)((ax >> 8) & 15) + ((int)((ay >> 8) & 15) << g.lB) +
+              ((int)((az >> 8) & 15) << (2 * g.lB));
+}
+
 __device__ __forceinline__ void brick_coords(const Geo& g, int brick, int* bx, int* by, int* bz) {
     *bx = brick % g.nb;
     *by = (brick / g.nb) % g.nb;
@@ -652,17 +683,10 @@ __global__ void __launch_bounds__(PA_T, PA_MINB) k_passA(Geo g, StoreDev s, cons
     // brick's rank among the cell's candidate bricks (12-15), the number of
     // candidates (16-19) and of candidate slots before the cell (20-23); the
     // flattened slot of a halo cell combines the three axes (flat_slot)
-    __shared__ unsigned axis_desc[3 * 8];
+    __shared__ unsigned axis_desc[3 * 6];
     if (threadIdx.x < 3 * Bh) {
         const int d = threadIdx.x / Bh, ee = threadIdx.x - d * Bh;
-        const int me = d == 0 ? bx : d == 1 ? by : bz;
-        const int c = wrap1(me * g.B - 1 + ee, g.Nc);
-        const int lx = c & (g.B - 1), hbc = c >> g.lB;
-        const int lo = lx == 0 ? wrap1(hbc - 1, g.nb) : -1;
-        const int hi = lx == g.B - 1 ? wrap1(hbc + 1, g.nb) : -1;
-        const int r = (hbc < me) + (lo >= 0 && lo < me) + (hi >= 0 && hi < me);
-        axis_desc[threadIdx.x] = (unsigned)hbc | ((unsigned)lx << 8) | ((unsigned)r << 12) |
-                                 ((unsigned)ncand(lx, g.B) << 16) | ((unsigned)ncand_before(lx) << 20);
+        axis_desc[threadIdx.x] = halo_axis_desc(g, d == 0 ? bx : d == 1 ? by : bz, ee);
     }
     if (!use_tma) {
         // rows of TX = F + 8 nodes start on a 16-byte boundary: 4-node chunks;
@@ -836,20 +860,15 @@ __global__ void __launch_bounds__(PA_T, PA_MINB) k_passA(Geo g, StoreDev s, cons
     __syncthreads();
     // each halo cell's slot in the flattened (cell, brick) order and its cell
     // rank, from the per-axis descriptions staged before the particle loop
-    const int S1 = Bh, S2 = Bh * Bh;
     for (int t = threadIdx.x; t < H3; t += blockDim.x) {
         const unsigned h = hist[t];
         int ec[3];
         split3(t, Bh, mBh, ec);
-        const unsigned ax = axis_desc[ec[0]], ay = axis_desc[Bh + ec[1]], az = axis_desc[2 * Bh + ec[2]];
-        const int hb = (int)(ax & 255u) + g.nb * ((int)(ay & 255u) + g.nb * (int)(az & 255u));
-        const int nc0 = (ax >> 16) & 15, nc1 = (ay >> 16) & 15, nc2 = (az >> 16) & 15;
-        const int pre = (int)((az >> 20) & 15) * S2 + nc2 * ((int)((ay >> 20) & 15) * S1 + nc1 * (int)((ax >> 20) & 15));
-        const int rank = ((int)((az >> 12) & 15) * nc1 + (int)((ay >> 12) & 15)) * nc0 + (int)((ax >> 12) & 15);
-        w.ghost[(int64_t)hb * H3 + pre + rank] = h;          // every slot has exactly one writer
+        int64_t slot;
+        int L;
+        halo_slot(g, axis_desc[ec[0]], axis_desc[Bh + ec[1]], axis_desc[2 * Bh + ec[2]], &slot, &L);
+        w.ghost[slot] = h;                                   // every slot has exactly one writer
         if (h) {
-            const int L = (hb << (3 * lB)) + (int)((ax >> 8) & 15) + ((int)((ay >> 8) & 15) << lB) +
-                          ((int)((az >> 8) & 15) << (2 * lB));
 #pragma unroll
             for (int d = 0; d < 3; ++d)
                 atomicAdd(reinterpret_cast<unsigned long long*>(&w.vsum_new[(int64_t)d * g.Ncc + L]),
@@ -996,14 +1015,29 @@ __device__ __forceinline__ void passB_stage(const Geo& g, const StoreDev& so, co
     const int bc[3] = {bx, by, bz};
     for (int c = t0; c <= nbc; c += nthr) sm_off[c] = so.offsets[L0 + c];
     for (int t = t0; t < 3 * nbc; t += nthr) svc[t] = so.vc[(int64_t)(t >> (3 * g.lB)) * g.Ncc + L0 + (t & (nbc - 1))];
-    for (int t = t0; t < H3; t += nthr) {
+    // the 3 Bh (<= 18) per-axis descriptions of the halo coordinates, one per
+    // lane of every warp, read by the others through shuffles
+    const int lane = threadIdx.x & 31;
+    unsigned dsc = 0u;
+    if (lane < 3 * Bh) {
+        const int d = lane / Bh;
+        dsc = halo_axis_desc(g, bc[d], lane - d * Bh);
+    }
+    for (int base = t0 - lane; base < H3; base += nthr) {     // warp-uniform bounds
+        const int t = base + lane;
         int e[3];
-        split3(t, Bh, mBh, e);
-        run[t] = ghost[flat_slot(g, bc, e)];
-        const int L = cell_rank(g, wrap1(bx * g.B - 1 + e[0], g.Nc), wrap1(by * g.B - 1 + e[1], g.Nc),
-                                wrap1(bz * g.B - 1 + e[2], g.Nc));
+        split3(min(t, H3 - 1), Bh, mBh, e);
+        const unsigned ax = __shfl_sync(0xffffffffu, dsc, e[0]);
+        const unsigned ay = __shfl_sync(0xffffffffu, dsc, Bh + e[1]);
+        const unsigned az = __shfl_sync(0xffffffffu, dsc, 2 * Bh + e[2]);
+        if (t < H3) {
+            int64_t slot;
+            int L;
+            halo_slot(g, ax, ay, az, &slot, &L);
+            run[t] = ghost[slot];
 #pragma unroll
-        for (int d = 0; d < 3; ++d) svn[d * H3 + t] = vc_new[(int64_t)d * g.Ncc + L];
+            for (int d = 0; d < 3; ++d) svn[d * H3 + t] = vc_new[(int64_t)d * g.Ncc + L];
+        }
     }
 }
 
@@ -1148,6 +1182,8 @@ __global__ void __launch_bounds__(PB_WARPS * 32, 5) k_passB(Geo g, StoreDev so, 
     }
     passB_stage(g, so, ghost, vc_new, brick, lane, 32, sm_off, run, svc, svn);
     __syncwarp();
+    // each lane's cell, advanced with its particle index (cells are contiguous and in order)
+    int lcell = upper_cell(sm_off, nbc, min(p0 + lane, p1 - 1));
     for (unsigned base = p0; base < p1; base += 32) {
         const unsigned i = base + lane;
         const bool act = i < p1;
@@ -1166,7 +1202,8 @@ __global__ void __launch_bounds__(PB_WARPS * 32, 5) k_passB(Geo g, StoreDev so, 
                 nid = PID == 4 ? reinterpret_cast<const unsigned*>(so.id)[i + 32] : load_pid(so.id, i + 32, g.nid);
         }
         if (act) {
-            const PbParticle q = pb.move(upper_cell(sm_off, nbc, i), svc, cchi, cnu, coff);
+            while (lcell + 1 < nbc && sm_off[lcell + 1] <= i) ++lcell;
+            const PbParticle q = pb.move(lcell, svc, cchi, cnu, coff);
             const unsigned peers = __match_any_sync(am, q.ei);
             const int leader = __ffs(peers) - 1;
             unsigned start = 0;
