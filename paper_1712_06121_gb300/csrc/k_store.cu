@@ -30,6 +30,35 @@ __device__ __forceinline__ int upper_cell(const unsigned* off, int ncell, unsign
     return lo;
 }
 
+// Cells of a warp's 32 consecutive particles base + lane, from c0, the cell
+// of particle base (off[c0] <= base < off[c0 + 1]; a brick's cells are
+// contiguous and in order).  Lane j holds b_j = off[c0 + 1 + j] - base, which
+// does not decrease with j, and the cell of particle base + l is
+// c0 + #{j : b_j <= l}: a binary search over the lanes through shuffles.
+// More than 32 cell starts within the round (empty cells) are finished by a
+// walk.  *c_next is the cell of particle base + 32.  All 32 lanes call it,
+// converged; every shuffle and vote below runs on all of them.
+__device__ __forceinline__ int warp_cells(const unsigned* off, int ncell, unsigned base, int c0, int* c_next) {
+    const unsigned lane = threadIdx.x & 31;
+    const int cj = c0 + 1 + (int)lane;
+    const unsigned b = cj < ncell ? off[cj] - base : 0xffffffffu;
+    int k = 0;
+#pragma unroll
+    for (int st = 16; st >= 1; st >>= 1)
+        k += __shfl_sync(0xffffffffu, b, k + st - 1) <= lane ? st : 0;
+    const unsigned b31 = __shfl_sync(0xffffffffu, b, 31);    // by every lane, before any branch
+    if (k == 31 && b31 <= lane) k = 32;
+    int c = c0 + k;
+    if (k == 32)
+        while (c + 1 < ncell && off[c + 1] <= base + lane) ++c;
+    const unsigned m = __ballot_sync(0xffffffffu, b <= 32u);
+    int cn = c0 + __popc(m);
+    if (m == 0xffffffffu)
+        while (cn + 1 < ncell && off[cn + 1] <= base + 32) ++cn;
+    *c_next = cn;
+    return c;
+}
+
 // brick of a CTA launched on the (nb, nb, nb x members) grid: its
 // coordinates and storage rank; *m the member of a batch
 template <bool BAT>
@@ -1182,8 +1211,7 @@ __global__ void __launch_bounds__(PB_WARPS * 32, 5) k_passB(Geo g, StoreDev so, 
     }
     passB_stage(g, so, ghost, vc_new, brick, lane, 32, sm_off, run, svc, svn);
     __syncwarp();
-    // each lane's cell, advanced with its particle index (cells are contiguous and in order)
-    int lcell = upper_cell(sm_off, nbc, min(p0 + lane, p1 - 1));
+    int c0 = upper_cell(sm_off, nbc, p0);      // the cell of each round's first particle
     for (unsigned base = p0; base < p1; base += 32) {
         const unsigned i = base + lane;
         const bool act = i < p1;
@@ -1201,8 +1229,10 @@ __global__ void __launch_bounds__(PB_WARPS * 32, 5) k_passB(Geo g, StoreDev so, 
             if (sn.id)
                 nid = PID == 4 ? reinterpret_cast<const unsigned*>(so.id)[i + 32] : load_pid(so.id, i + 32, g.nid);
         }
+        int cnext;
+        const int lcell = warp_cells(sm_off, nbc, base, c0, &cnext);
+        c0 = cnext;
         if (act) {
-            while (lcell + 1 < nbc && sm_off[lcell + 1] <= i) ++lcell;
             const PbParticle q = pb.move(lcell, svc, cchi, cnu, coff);
             const unsigned peers = __match_any_sync(am, q.ei);
             const int leader = __ffs(peers) - 1;
