@@ -121,20 +121,6 @@ __device__ double block_sum_double(double v, double* sh) {
     return s;
 }
 
-__device__ float block_sum_float(float v, float* sh) {
-    // fixed-shape tree: deterministic for a given block size
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    if (lane == 0) sh[w] = v;
-    __syncthreads();
-    float s = 0.0f;
-    if (threadIdx.x == 0)
-        for (int i = 0; i < nw; ++i) s += sh[i];
-    __syncthreads();
-    return s;
-}
-
 __device__ __forceinline__ double snap_sigma_dev(double x) {
     // nearest 2^(m/16) in log2 (ties up), floor 2^-30
     x = fmax(x, 9.313225746154785e-10);
@@ -741,8 +727,9 @@ __global__ void __launch_bounds__(PA_T, PA_MINB) k_passA(Geo g, StoreDev s, cons
     // the brick's particle range, and the first round's codes, requested
     // while the tile is in flight
     const unsigned q1 = min(s.offsets[L0 + nbc], (unsigned)g.Np);
-    unsigned i = min(s.offsets[L0], q1) + threadIdx.x;
-    if (threadIdx.x == 0 && q1 - (i - threadIdx.x) > (unsigned)PB_BIG) w.big[1 + atomicAdd(w.big, 1)] = brick;
+    const unsigned q0 = min(s.offsets[L0], q1);
+    unsigned i = q0 + threadIdx.x;
+    if (threadIdx.x == 0 && q1 - q0 > (unsigned)PB_BIG) w.big[1 + atomicAdd(w.big, 1)] = brick;
     const CodeRows<NX> chi_r(s.chi, g.Np);
     const CodeRows<NV> nu_r(s.nu, g.Np);
     int nchi[3] = {0, 0, 0}, nnu[3] = {0, 0, 0};
@@ -753,21 +740,19 @@ __global__ void __launch_bounds__(PA_T, PA_MINB) k_passA(Geo g, StoreDev s, cons
             nnu[d] = nu_r.get_nu(d, i, lim);
         }
     }
+    // the cell of every particle of the brick, when they fit the table,
+    // written while the tile is in flight (each thread reads its cells' bounds)
+    const bool table = q1 - q0 <= (unsigned)DEP_QCAP;                  // block-uniform
+    if (table)
+        for (int c = threadIdx.x; c < nbc; c += blockDim.x)
+            for (unsigned q = max(s.offsets[L0 + c], q0), qe = min(s.offsets[L0 + c + 1], q1); q < qe; ++q)
+                qcell[q - q0] = (unsigned char)c;
     cp_async_wait_all();
     const bool tile_ok = !use_tma || mbar_wait_bounded(&tile_bar, 0);
     if (__syncthreads_or(!tile_ok)) {       // the tile copy never completed: report, drain, leave
         if (threadIdx.x == 0) atomicOr(w.flags, ERR_TIMEOUT);
         mbar_wait_bounded(&tile_bar, 0);
         return;
-    }
-    // the cell of every particle of the brick, when they fit the table
-    const unsigned q0 = i - threadIdx.x;
-    const bool table = q1 - q0 <= (unsigned)DEP_QCAP;                  // block-uniform
-    if (table) {
-        for (int c = threadIdx.x; c < nbc; c += blockDim.x)
-            for (unsigned q = max(sm_off[c], q0), qe = min(sm_off[c + 1], q1); q < qe; ++q)
-                qcell[q - q0] = (unsigned char)c;
-        __syncthreads();
     }
     const float e0 = cur.est[0], e1 = cur.est[1];
     // 2-byte codes: the decode and threshold tables through their L1-resident corrections
@@ -886,7 +871,33 @@ __global__ void __launch_bounds__(PA_T, PA_MINB) k_passA(Geo g, StoreDev s, cons
         }
     }
     if (migbad) atomicOr(w.flags, ERR_MIGRATION);
+    // the block's sum of squared offsets (a fixed tree: each warp's shuffle
+    // tree, then the warps in order) and whether any particle changed cell,
+    // finished by thread 0 after the barrier that also opens the write-out
+    __shared__ float red[PA_T / 32];
+    __shared__ unsigned redmig[PA_T / 32];
+    {
+        float v = sacc;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        const unsigned wm = __reduce_or_sync(0xffffffffu, (unsigned)mig);
+        if ((threadIdx.x & 31) == 0) {
+            red[threadIdx.x >> 5] = v;
+            redmig[threadIdx.x >> 5] = wm;
+        }
+    }
     __syncthreads();
+    if (threadIdx.x == 0) {
+        float tot = 0.0f;
+        unsigned mm = 0u;
+#pragma unroll
+        for (int k = 0; k < PA_T / 32; ++k) {
+            tot += red[k];
+            mm |= redmig[k];
+        }
+        w.part[brick] = tot;
+        if (mm) atomicMax(w.maxmig, (int)mm);
+    }
     // each halo cell's slot in the flattened (cell, brick) order and its cell
     // rank, from the per-axis descriptions staged before the particle loop
     for (int t = threadIdx.x; t < H3; t += blockDim.x) {
@@ -904,16 +915,6 @@ __global__ void __launch_bounds__(PA_T, PA_MINB) k_passA(Geo g, StoreDev s, cons
                           (unsigned long long)vs[d * H3 + t]);
         }
     }
-    __shared__ float red[PA_T / 32];
-    const float tot = block_sum_float(sacc, red);
-    if (threadIdx.x == 0) w.part[brick] = tot;
-    // block max of the migration
-    __shared__ int mmax;
-    if (threadIdx.x == 0) mmax = 0;
-    __syncthreads();
-    if (mig) atomicMax(&mmax, mig);
-    __syncthreads();
-    if (threadIdx.x == 0 && mmax) atomicMax(w.maxmig, mmax);
 }
 
 // ------------------------------------------------------------------ new cells
