@@ -447,7 +447,14 @@ __global__ void __launch_bounds__(T_BRICK) k_deposit(Geo g, StoreDev s, float* _
         if (lane == 31) wsum[wp] = v;
         __syncthreads();
         for (int k = 0; k < wp; ++k) v += wsum[k];
-        if (t < E3) cpref[t + 1] = v;
+        if (t < E3) {
+            cpref[t + 1] = v;
+            // this cell's slots of the per-particle cell table (used when
+            // the brick's total fits it), before the barrier that publishes
+            // the scan
+            if (E3 <= 256)
+                for (unsigned q = v - cnt, qe = min(v, (unsigned)DEP_QCAP); q < qe; ++q) qcell[q] = (unsigned char)t;
+        }
         if (t == 0) cpref[0] = 0;
     }
     __syncthreads();
@@ -459,16 +466,12 @@ __global__ void __launch_bounds__(T_BRICK) k_deposit(Geo g, StoreDev s, float* _
     const bool small = 3 * sb < 32 && total < (1u << (32 - 3 * sb));
     const int ws = small ? 0 : 1;                                   // log2 words per node
     const bool table = total <= (unsigned)DEP_QCAP && E3 <= 256;    // block-uniform
-    if (table)
-        for (int t = threadIdx.x; t < E3; t += blockDim.x)
-            for (unsigned q = cpref[t], q1 = min(cpref[t + 1], total); q < q1; ++q) qcell[q] = (unsigned char)t;
     const int ox = c0[0] * g.R, oy = c0[1] * g.R, oz = c0[2] * g.R;
     if (NX == 1 && small && table) {
         // the common case: padded 32-bit tile, node (x, y, z) of the brick at
         // (x + 4) + DX ((y + 1) + DY (z + 1)); a particle's 8 corners at fixed
         // offsets from its base node, no range checks
         const int DX = F + 8, DY = F + 2, DXY = DX * DY;
-        __syncthreads();                                                    // cell table complete
         const int8_t* cx = reinterpret_cast<const int8_t*>(s.chi);
         const int8_t* cy = cx + g.Np;
         const int8_t* cz = cy + g.Np;
@@ -536,7 +539,6 @@ __global__ void __launch_bounds__(T_BRICK) k_deposit(Geo g, StoreDev s, float* _
         }
         return;
     }
-    __syncthreads();
     for (unsigned q = threadIdx.x; q < total; q += blockDim.x) {
         const int t = table ? (int)qcell[q] : upper_cell(cpref, E3, q);
         const unsigned i = cstart[t] + (q - cpref[t]);
