@@ -334,6 +334,44 @@ def test_a_single_particle(cube):
 
 
 @pytest.mark.parametrize("xb,vb,brick", [(1, 1, 4), (2, 2, 4), (1, 2, 2)])
+def test_sparse_bricks_resort_is_bit_exact(cube, xb, vb, brick):
+    """Bricks with about one particle per coarse cell and a third of the
+    cells empty (4096 particles at uniform random positions, 16^3 coarse
+    cells): with bricks of side 4 a round of 32 consecutive particles spans
+    up to 49 cell starts, more than the re-sort's per-warp binary search
+    covers, so it finishes those lanes' cells by a walk; bricks of side 2
+    hold 17 or fewer particles, so every warp's only round is partial.  The
+    re-sorted store equals the oracle's re-encode of the drifted particles
+    (codes, counts, order, v_c) for 3 steps."""
+    w = synth.WORKLOADS["pm64"]
+    nf, n = 64, 4096
+    rng = np.random.default_rng(1712202)
+    pos = rng.uniform(0.0, nf, (3, n)).astype(np.float32)
+    vel = (0.3 * rng.standard_normal((3, n))).astype(np.float32)
+    ids = np.arange(n, dtype=np.uint32)
+    sched = synth.uniform_schedule(0.5, 0.515, 3)
+    prm, ctx = _ctx(cube, nf, n, xb, vb, w, brick=brick)
+    try:
+        cube.cube_encode(ctx, pos, vel, ids, sched[0], 0.3)
+        cube.cube_keep_drifted(ctx, True)
+        for i in range(3):
+            before = read_store(cube, ctx)
+            assert np.count_nonzero(before["counts"] == 0) > before["counts"].size // 4
+            cube.cube_pm_step(ctx, sched[i], sched[i + 1])
+            cell, u, p, sig = _drifted(cube, ctx, n)
+            g = read_store(cube, ctx)
+            P = oracle_params(pm, prm, g["brick"])
+            old = pm.Store(P, before["counts"], before["vc"], before["chi"], before["nu"], before["ids"],
+                           before["sigma"], before["a"], before["a_p"])
+            assert np.array_equal(np.stack(old.cells()), cell)
+            ref = pm.encode_drifted(P, cell, u, p, before["ids"], sig, g["a"], g["a_p"])
+            assert_store_equal(g, ref, f"sparse step {i} x{xb}v{vb} brick {brick}")
+        assert cube.cube_stats_get(ctx).max_migration <= 1
+    finally:
+        cube.cube_destroy(ctx)
+
+
+@pytest.mark.parametrize("xb,vb,brick", [(1, 1, 4), (2, 2, 4), (1, 2, 2)])
 def test_crowded_bricks_resort_is_bit_exact(cube, xb, vb, brick):
     """Bricks with more particles than one warp's share (re-sorted by a whole
     CTA) give the same store as the oracle's re-encode of the drifted
