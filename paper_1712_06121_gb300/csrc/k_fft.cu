@@ -521,8 +521,13 @@ __global__ void __launch_bounds__(XFFT_T) k_fft_x_r2c(float* mesh, int S, const 
     constexpr int R1 = x_first_radix<h>();
     xpass_load<h, R1, false, false>(buf, mesh, row0, S, tw);
     tile_fft<h, R1, 2, false, true, XFFT_T>(buf, stw);
-    for (int t = threadIdx.x; t < (h / 2 + 1) * NC; t += XFFT_T) {
-        const int k = t % (h / 2 + 1), c = t / (h / 2 + 1);
+    // X[k] and X[h - k] from Z[k] and Z[h - k], k = 0 .. h / 2: the warps
+    // take k < h / 2 of one row at a time, so that (h / 2 a multiple of 16)
+    // each half-warp's Z[k] are one 16-element block of the swizzled tile,
+    // free of bank conflicts; the self-paired k = h / 2 of the 16 rows last
+    for (int t = threadIdx.x; t < (h / 2) * NC + NC; t += XFFT_T) {
+        const bool mid = t >= (h / 2) * NC;
+        const int k = mid ? h / 2 : t % (h / 2), c = mid ? t - (h / 2) * NC : t / (h / 2);
         float2* dst = reinterpret_cast<float2*>(mesh + (row0 + c) * S);
         const float2 zk = buf[sidx<true>(k % h, c)];
         const float2 zm = buf[sidx<true>((h - k) % h, c)];
